@@ -1,0 +1,24 @@
+"""CPU oracle for the hybrid factorization (arXiv 2208.01907).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library's
+product path never calls it and shares no code with it.
+
+Plain, slow, readable numpy.  Each function cites the passage of the paper it
+restates.  Decisions that the paper makes in the lower precision (pivot choice
+and threshold postponing, Alg. 1 step 1) are taken in float32; everything the
+paper computes in the higher precision is float64.
+
+Parity status per function (what pins it is listed in tests/test_oracle_*.py):
+  scale_matrix            pinned (closed form, Sec. 2)
+  nested_dissection       pinned (separator property, Fig. 1 block pattern)
+  threshold_factorize     pinned (Eq. 1 reconstruction, tiny hand cases, tau limits)
+  precond_apply           pinned (exact inverse of the recorded factor)
+  block_gcr               pinned (invariants of Sec. 3.4-3.5, direct solve)
+  schur_direct            pinned (dense brute-force inverse, Eq. 2)
+  bunch_kaufman           pinned (reconstruction, scipy/LAPACK sytrf comparison)
+  kernel_dimension        pinned (dense SVD rank on small systems)
+  hybrid_solve            pinned (backward error, exact solution on tiny systems)
+  adjoint_gradient        pinned (central finite differences)
+"""
+from .hybrid import *  # noqa: F401,F403

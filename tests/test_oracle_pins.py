@@ -1,0 +1,408 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms,
+the Fig. 1 pattern, brute-force Schur complements from dense inverses,
+determinant identities, Krylov least-squares optima, SVD nullities, finite
+differences.  A plausible mistake (dropped term, wrong sign or index,
+transposed operand) in the oracle fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import oracle as O
+from workloads import diffusion2d, stokes3d, elasticity3d, darcy2d, consistent_rhs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_spd(n, rng, cond=10.0):
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.exp(rng.uniform(0, math.log(cond), n))
+    return (Q * ev) @ Q.T
+
+
+def _rand_sym(n, rng):
+    A = rng.standard_normal((n, n))
+    return A + A.T
+
+
+# --------------------------------------------------------------------------- Sec. 2 scaling
+def test_scaling_closed_form():
+    A = sp.csr_matrix(np.array([[4.0, 1.0, 0.0, 2.0],
+                                [1.0, -9.0, 3.0, 0.0],
+                                [0.0, 3.0, 0.0, 1.0],
+                                [2.0, 0.0, 1.0, 0.25]]))
+    q, K = O.scale_matrix(A)
+    np.testing.assert_allclose(q, [0.5, 1 / 3, 1.0, 2.0])
+    np.testing.assert_allclose(K.diagonal(), [1.0, -1.0, 0.0, 1.0])     # diag in {-1, 0, 1}
+    np.testing.assert_allclose(K.toarray()[0, 3], 2.0 * 0.5 * 2.0)      # q_i K_ij q_j
+    np.testing.assert_allclose(K.toarray()[1, 2], 3.0 / 3.0)
+
+
+def test_scaling_preserves_solution():
+    s = diffusion2d(8, 8, n_islands=0, dirichlet_x=True)
+    Kb = s.to_scipy().toarray()
+    q, K = O.scale_matrix(s.to_scipy())
+    b = np.random.default_rng(0).standard_normal(s.L)
+    x_direct = np.linalg.solve(Kb, b)
+    x_scaled = q * np.linalg.solve(K.toarray(), q * b)                  # x-bar = Q x with K x = Q b
+    np.testing.assert_allclose(x_scaled, x_direct, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------- Sec. 2.2 / Fig. 1
+def _fig1_pairs():
+    pairs = set()
+    with open(os.path.join(GOLDEN, "fig1_blocks.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                i, j = map(int, line.split())
+                pairs.add((i, j))
+    return pairs
+
+
+def test_nd_fig1_block_pattern():
+    s = diffusion2d(7, 7, n_islands=0)
+    sets, order = O.nested_dissection(s.to_scipy(), s.coords, 3)
+    assert order == [4, 5, 6, 7, 2, 3, 1]
+    got = {p for p in O.tree_block_pattern(s.to_scipy(), sets) if p[0] > p[1]}
+    assert got == _fig1_pairs()
+    assert sorted(np.concatenate(list(sets.values()))) == list(range(s.L))
+
+
+@pytest.mark.parametrize("maker", [lambda: diffusion2d(20, 17, n_islands=0),
+                                   lambda: stokes3d(5),
+                                   lambda: elasticity3d(6, n_incl=1, incl=2)])
+def test_nd_separators(maker):
+    s = maker()
+    A = s.to_scipy().tocoo()
+    m = 4
+    sets, _ = O.nested_dissection(s.to_scipy(), s.coords, m)
+    owner = np.full(s.L, -1)
+    for l, v in sets.items():
+        owner[v] = l
+
+    def subtree(l):
+        out = {l}
+        if 2 * l < 2 ** m:
+            out |= subtree(2 * l) | subtree(2 * l + 1)
+        return out
+
+    # removing Lambda_l disconnects its two subtrees: no edge joins them
+    for l in range(1, 2 ** (m - 1)):
+        left, right = subtree(2 * l), subtree(2 * l + 1)
+        a = np.isin(owner[A.row], list(left)) & np.isin(owner[A.col], list(right))
+        assert not a.any(), f"node {l} is not a separator"
+
+
+# --------------------------------------------------------------------------- Sec. 2.1-2.2 factorization
+def test_hand_case_pivot_order_and_postponing():
+    # K = diag(0.5, 1.0, 0.003), one index set, tau = 1e-2, n = 1:
+    # pivots 1 (1.0) then 0 (ratio 0.5) ; 2 fails 0.003/0.5 < tau -> Lambda_0 = {2};
+    # the Lambda_0 refactorization postpones it too (0.003 < tau * 1); enlargement moves 0.
+    K = sp.csr_matrix(np.diag([0.5, 1.0, 0.003]))
+    fac = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-2, n_enlarge=1)
+    assert fac.node_pivots[0].tolist() == [1, 0]
+    assert fac.node_postponed[0].tolist() == [2]
+    assert fac.lam0.tolist() == [2]
+    assert fac.lam0_pivots.tolist() == []
+    assert fac.moved.tolist() == [0]
+    assert fac.lambda2.tolist() == [0, 2]
+    assert fac.lambda1_order.tolist() == [1]
+
+
+def test_hand_case_tie_break_and_first_pivot_reference():
+    # equal diagonals: the smaller index goes first (R5); |d_1| < tau postpones the whole set (R2)
+    K = sp.csr_matrix(np.diag([1.0, 1.0, 1.0]))
+    fac = O.threshold_factorize(K, [np.array([2, 0, 1])], tau=0.5, n_enlarge=0)
+    assert fac.node_pivots[0].tolist() == [0, 1, 2]
+    K2 = sp.csr_matrix(np.diag([0.004, 0.003]))
+    fac2 = O.threshold_factorize(K2, [np.array([0, 1])], tau=1e-2, n_enlarge=0)
+    assert fac2.node_pivots[0].tolist() == [] and fac2.lambda2.tolist() == [0, 1]
+
+
+def test_pivot_sequence_matches_brute_force_schur():
+    # At every step the chosen pivot is the max |diag| of the exact Schur complement,
+    # formed here from scratch with a dense inverse, and d equals that diagonal entry.
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        n = 7
+        A = _rand_sym(n, rng) * 0.3 + np.diag(rng.uniform(0.5, 3.0, n) * rng.choice([-1, 1], n))
+        fac = O.threshold_factorize(sp.csr_matrix(A), [np.arange(n)], tau=1e-6, n_enlarge=0)
+        elim = []
+        for q in fac.node_pivots[0]:
+            rest = [i for i in range(n) if i not in elim]
+            if elim:
+                S = A[np.ix_(rest, rest)] - A[np.ix_(rest, elim)] @ np.linalg.solve(A[np.ix_(elim, elim)], A[np.ix_(elim, rest)])
+            else:
+                S = A[np.ix_(rest, rest)]
+            dg = np.abs(np.diag(S))
+            assert rest[int(np.argmax(dg))] == q
+            np.testing.assert_allclose(fac.d[int(q)], S[rest.index(q), rest.index(q)], rtol=2e-5)
+            elim.append(int(q))
+
+
+def test_factor_reconstructs_eq1():
+    # Eq. (1): the recorded unit-L, D satisfy Pi^T K Pi = L D L^T on the eliminated indices
+    s = diffusion2d(12, 12, n_islands=1, island=3, contrast=1e3, seed=3)
+    q, K = O.scale_matrix(s.to_scipy())
+    sets, order = O.nested_dissection(K, s.coords, 3)
+    fac = O.threshold_factorize(K, [sets[l] for l in order], tau=1e-2, n_enlarge=4)
+    elim = np.concatenate([*fac.node_pivots, fac.lam0_pivots]).astype(int)
+    pos = {int(g): i for i, g in enumerate(elim)}
+    n = len(elim)
+    Lm = np.eye(n)
+    D = np.zeros(n)
+    for g in elim:
+        j = pos[int(g)]
+        D[j] = fac.d[int(g)]
+        rows, vals = fac.lcol[int(g)]
+        for r, v in zip(rows, vals):
+            if int(r) in pos:
+                Lm[pos[int(r)], j] = v
+    Kd = K.toarray()[np.ix_(elim, elim)]
+    err = np.abs(Lm @ np.diag(D) @ Lm.T - Kd).max() / np.abs(Kd).max()
+    assert err < 1e-5                                           # float32 factorization
+    assert fac.M >= 4 and len(set(fac.lambda1_order) & set(fac.lambda2)) == 0
+    assert len(fac.lambda1_order) + fac.M == s.L
+
+
+def test_tau_limits():
+    s = diffusion2d(10, 10, n_islands=0, dirichlet_x=True)
+    q, K = O.scale_matrix(s.to_scipy())
+    sets, order = O.nested_dissection(K, s.coords, 3)
+    nodes = [sets[l] for l in order]
+    small = O.threshold_factorize(K, nodes, tau=1e-30, n_enlarge=4)
+    assert len(small.lam0) == 0 and small.M == 4                 # nothing postponed, only the n moved
+    big = O.threshold_factorize(K, nodes, tau=2.0, n_enlarge=4)
+    assert big.M == s.L and len(big.lam0) == s.L                 # every first pivot fails |d| < 2 * 1
+
+
+# --------------------------------------------------------------------------- Sec. 3 preconditioner / GCR
+def _cfg1_small():
+    s = diffusion2d(16, 16, n_islands=2, island=3, contrast=1e8, seed=4)
+    q, K = O.scale_matrix(s.to_scipy())
+    sets, order = O.nested_dissection(K, s.coords, 4)
+    fac = O.threshold_factorize(K, [sets[l] for l in order], tau=1e-2, n_enlarge=4)
+    return s, q, K, fac
+
+
+def test_precond_approximates_inverse():
+    s, q, K, fac = _cfg1_small()
+    A = O.k11_operator(K, fac.lambda2)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((s.L, 3))
+    X[fac.lambda2] = 0
+    Y = O.precond_apply(fac, A(X))
+    err = np.linalg.norm(Y - X) / np.linalg.norm(X)
+    assert err < 1e-3                                            # Q^-1 K11 ~ I (Sec. 3.3)
+
+
+def test_block_gcr_invariants_and_solution():
+    s, q, K, fac = _cfg1_small()
+    A = O.k11_operator(K, fac.lambda2)
+    lam1 = np.setdiff1d(np.arange(s.L), fac.lambda2)
+    B = np.zeros((s.L, fac.M))
+    B[lam1] = K.toarray()[np.ix_(lam1, fac.lambda2)]
+    X, hist, P, Qs = O.block_gcr(A, lambda R: O.precond_apply(fac, R), B, tol=1e-15, maxit=20)
+    Xd = O.x12_direct(K, fac.lambda2)
+    assert np.abs(X - Xd).max() / np.abs(Xd).max() < 1e-12
+    for n in range(len(P)):
+        np.testing.assert_allclose(Qs[n], A(P[n]), atol=1e-10 * np.abs(Qs[n]).max())  # q_n = A p_n
+    for m_ in range(len(P)):
+        for n in range(m_ + 1, len(P)):
+            cross = np.abs(Qs[m_].T @ Qs[n]).max()
+            scale = np.linalg.norm(Qs[m_]) * np.linalg.norm(Qs[n])
+            assert cross <= 1e-8 * scale                          # (A p_m, A p_n) = 0, m != n
+    assert hist[-1] <= 1e-15 and len(hist) <= 8
+
+
+def test_gcr_unpreconditioned_is_krylov_minimal_residual():
+    # Q = I: GCR minimises |b - A x| over x in span{b, A b, ..., A^(n-1) b} (Sec. 3.4)
+    rng = np.random.default_rng(3)
+    n = 30
+    Am = _rand_spd(n, rng, 50.0) + 0.3 * _rand_sym(n, rng)
+    b = rng.standard_normal(n)
+    A = lambda v: Am @ v
+    for its in range(1, 6):
+        x, hist, _, _ = O.gcr_single(A, lambda v: np.zeros_like(v) + v, b, tol=0.0, maxit=its)
+        # GCR with x0 = Q^-1 b = b: after `its` steps x is in b + span{r0, ..., A^(its-1) r0}
+        r0 = b - Am @ b
+        Kry = np.stack([np.linalg.matrix_power(Am, k) @ r0 for k in range(its)], axis=1)
+        c = np.linalg.lstsq(Am @ Kry, r0, rcond=None)[0]
+        best = np.linalg.norm(r0 - Am @ Kry @ c) / np.linalg.norm(b)
+        assert abs(hist[-1] - best) <= 1e-9 * max(best, 1e-12) + 1e-14
+
+
+def test_block_gcr_single_rhs_equals_alg4():
+    s, q, K, fac = _cfg1_small()
+    A = O.k11_operator(K, fac.lambda2)
+    Qi = lambda R: O.precond_apply(fac, R)
+    lam1 = np.setdiff1d(np.arange(s.L), fac.lambda2)
+    b = np.zeros(s.L)
+    b[lam1] = np.random.default_rng(2).standard_normal(len(lam1))
+    xb, hb, _, _ = O.block_gcr(A, Qi, b[:, None], tol=1e-15, maxit=6)
+    xs, hs, _, _ = O.gcr_single(A, Qi, b, tol=1e-15, maxit=6)
+    n = min(len(hb), len(hs))
+    np.testing.assert_allclose(hb[:n], hs[:n], rtol=1e-6, atol=1e-16)
+    np.testing.assert_allclose(xb[:, 0], xs, rtol=1e-10, atol=1e-12 * np.abs(xs).max())
+
+
+def test_block_gcr_exact_preconditioner_converges_at_x0():
+    s, q, K, fac = _cfg1_small()
+    A = O.k11_operator(K, fac.lambda2)
+    lam1 = np.setdiff1d(np.arange(s.L), fac.lambda2)
+    K11 = K.toarray()[np.ix_(lam1, lam1)]
+
+    def exact(R):
+        out = np.zeros_like(R)
+        out[lam1] = np.linalg.solve(K11, R[lam1])
+        return out
+    B = np.zeros((s.L, fac.M))
+    B[lam1] = K.toarray()[np.ix_(lam1, fac.lambda2)]
+    X, hist, _, _ = O.block_gcr(A, exact, B, tol=1e-15, maxit=5)
+    assert hist[0] < 1e-10
+
+
+# --------------------------------------------------------------------------- Eq. 2 Schur complement
+def test_schur_matches_dense_inverse_and_determinant():
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        n = 12
+        A = _rand_sym(n, rng) + np.diag(rng.uniform(3, 6, n))
+        lam2 = np.sort(rng.choice(n, 4, replace=False))
+        lam1 = np.setdiff1d(np.arange(n), lam2)
+        S = O.schur_direct(sp.csr_matrix(A), lam2)
+        Sref = A[np.ix_(lam2, lam2)] - A[np.ix_(lam2, lam1)] @ np.linalg.inv(A[np.ix_(lam1, lam1)]) @ A[np.ix_(lam1, lam2)]
+        np.testing.assert_allclose(S, Sref, rtol=1e-12, atol=1e-12)
+        # det K = det K11 det S22 (block LDU, Eq. 1)
+        np.testing.assert_allclose(np.linalg.det(A), np.linalg.det(A[np.ix_(lam1, lam1)]) * np.linalg.det(S), rtol=1e-9)
+
+
+def test_schur_of_cfg1_small_via_gcr_equals_direct():
+    s, q, K, fac = _cfg1_small()
+    res = O.run_hybrid(s.to_scipy(), _nodes_cfg1(), 1e-2, use_gcr=True)
+    S_direct = O.schur_direct(res["K"], res["fac"].lambda2)
+    assert np.linalg.norm(res["S22"] - S_direct) / np.linalg.norm(S_direct) < 1e-12
+
+
+def _nodes_cfg1():
+    s = diffusion2d(16, 16, n_islands=2, island=3, contrast=1e8, seed=4)
+    q, K = O.scale_matrix(s.to_scipy())
+    sets, order = O.nested_dissection(K, s.coords, 4)
+    return [sets[l] for l in order]
+
+
+# --------------------------------------------------------------------------- Alg. 1 step 5 Bunch-Kaufman
+def test_bunch_kaufman_reconstruction_and_inertia():
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 5, 17, 40):
+        A = _rand_sym(n, rng)
+        perm, Lf, blocks = O.bunch_kaufman(A)
+        np.testing.assert_allclose(O.bk_reconstruct(perm, Lf, blocks), A, atol=1e-11 * np.abs(A).max())
+        # Sylvester: inertia of D equals inertia of A
+        ev = np.linalg.eigvalsh(A)
+        dev = np.concatenate([np.linalg.eigvalsh(B) for _, _, B in blocks])
+        assert (dev > 0).sum() == (ev > 0).sum() and (dev < 0).sum() == (ev < 0).sum()
+        # LAPACK's Bunch-Kaufman (sytrf, through scipy.linalg.ldl) picks the same 1x1 / 2x2 blocks
+        _, d, _ = sla.ldl(A, lower=True)
+        sizes, i = [], 0
+        while i < n:
+            z = 2 if (i + 1 < n and d[i + 1, i] != 0) else 1
+            sizes.append(z)
+            i += z
+        assert sizes == [z for _, z, _ in blocks]
+        Dm = np.zeros((n, n))
+        for s0, z, B in blocks:
+            Dm[s0:s0 + z, s0:s0 + z] = B
+        np.testing.assert_allclose(np.sort(np.abs(np.diag(Dm))), np.sort(np.abs(np.diag(d))), rtol=1e-8)
+
+
+def test_bunch_kaufman_zero_diagonal_needs_2x2():
+    A = np.array([[0.0, 1.0], [1.0, 0.0]])
+    perm, Lf, blocks = O.bunch_kaufman(A)
+    assert len(blocks) == 1 and blocks[0][1] == 2
+    # the LAPACK Bunch-Kaufman routine (sytrf) makes the same choice
+    lu, d, p = sla.ldl(A, lower=True)
+    assert abs(d[1, 0]) > 0
+
+
+def test_bunch_kaufman_solve_matches_dense():
+    rng = np.random.default_rng(11)
+    A = _rand_sym(9, rng)
+    y = rng.standard_normal((9, 2))
+    bk = O.bunch_kaufman(A)
+    np.testing.assert_allclose(O.bk_solve(*bk, y, 0), np.linalg.solve(A, y), rtol=1e-9, atol=1e-10)
+
+
+# --------------------------------------------------------------------------- kernel detection
+@pytest.mark.parametrize("maker,expect", [
+    (lambda: diffusion2d(16, 16, n_islands=2, island=3, contrast=1e8, seed=4), 1),
+    (lambda: diffusion2d(14, 14, n_islands=0, dirichlet_x=True), 0),
+    (lambda: stokes3d(5), 3),
+    (lambda: elasticity3d(5, n_incl=1, incl=2), 6),
+    (lambda: darcy2d(12, 12, n_islands=1, island=3), 1),
+])
+def test_kernel_dimension_matches_svd(maker, expect):
+    s = maker()
+    Kb = s.to_scipy()
+    sv = np.linalg.svd(Kb.toarray(), compute_uv=False)
+    null_svd = int((sv < 1e-12 * sv[0]).sum())
+    assert null_svd == expect
+    q, K = O.scale_matrix(Kb)
+    dim = s.coords.shape[1]
+    m = max(2, int(math.ceil(math.log2(s.L / 64))) + 1)
+    sets, order = O.nested_dissection(K, s.coords, m)
+    res = O.run_hybrid(Kb, [sets[l] for l in order], 1e-2)
+    assert res["kdim"] == expect
+
+
+# --------------------------------------------------------------------------- Alg. 2 solve
+def test_hybrid_solve_exact_on_nonsingular():
+    s = diffusion2d(12, 12, n_islands=1, island=3, contrast=1e6, dirichlet_x=True, seed=2)
+    Kb = s.to_scipy()
+    q, K = O.scale_matrix(Kb)
+    sets, order = O.nested_dissection(K, s.coords, 3)
+    res = O.run_hybrid(Kb, [sets[l] for l in order], 1e-2)
+    b = np.random.default_rng(0).standard_normal((s.L, 2))
+    x = q[:, None] * O.hybrid_solve(res["K"], res["fac"].lambda2, res["X12"], res["bk"], res["kdim"], q[:, None] * b)
+    xr = np.linalg.solve(Kb.toarray(), b)
+    assert np.abs(x - xr).max() / np.abs(xr).max() < 1e-9
+    assert O.backward_error(Kb, x, b) < 1e-14
+
+
+def test_hybrid_solve_singular_consistent():
+    s = diffusion2d(16, 16, n_islands=2, island=3, contrast=1e8, seed=4)
+    Kb = s.to_scipy()
+    res = O.run_hybrid(Kb, _nodes_cfg1(), 1e-2, use_gcr=True)
+    b = consistent_rhs(s, 3)
+    q = res["q"]
+    x = q[:, None] * O.hybrid_solve(res["K"], res["fac"].lambda2, res["X12"], res["bk"], res["kdim"], q[:, None] * b)
+    assert O.backward_error(Kb, x, b) < 1e-14
+
+
+# --------------------------------------------------------------------------- adjoint
+def test_adjoint_gradient_matches_central_differences():
+    n = 6
+    rng = np.random.default_rng(5)
+    theta = rng.standard_normal(n * n)
+    b = rng.uniform(-1, 1, n * n)
+    xs = rng.uniform(-1, 1, n * n)
+
+    def J(th):
+        s = diffusion2d(n, n, n_islands=0, dirichlet_x=True, kcell=np.exp(th))
+        x = np.linalg.solve(s.to_scipy().toarray(), b)
+        return O.diffusion_objective(x, xs), x, s
+
+    _, x, s = J(theta)
+    lam = np.linalg.solve(s.to_scipy().toarray().T, x - xs)
+    g = O.adjoint_gradient(n, n, theta, x, lam)
+    for _ in range(4):
+        d = rng.standard_normal(n * n)
+        h = 1e-6
+        fd = (J(theta + h * d)[0] - J(theta - h * d)[0]) / (2 * h)
+        np.testing.assert_allclose(g @ d, fd, rtol=1e-5)
