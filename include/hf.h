@@ -1,0 +1,221 @@
+/*
+ * hf.h -- C ABI of the GB300 hybrid sparse factorization.
+ *
+ * Method: A. Suzuki, "A hybrid factorization algorithm for sparse matrix with
+ * mixed precision arithmetic" (arXiv 2208.01907).
+ *   Sec. 2      diagonal scaling K = Q Kbar Q with diag(K) in {-1, 0, 1}
+ *   Sec. 2.1-2.2 LDL^T with symmetric 1x1 pivoting and threshold postponing
+ *               along a nested-dissection tree; split Lambda = Lambda_1 + Lambda_2
+ *   Alg. 1      K11 X12 = K12 by an iterative solver preconditioned with the
+ *               lower-precision factor; S22 = K22 - K21 X12 in higher precision;
+ *               S22 factorized with symmetric (1x1 / 2x2) pivoting
+ *   Alg. 2      block forward / backward substitution
+ *   Sec. 3.5    block GCR ("Algorithm 5")
+ *
+ * Conventions for every entry point:
+ *   - Indices are 0-based.  Matrices are square, structurally symmetric and
+ *     numerically symmetric (the LDL^T form of Sec. 4.1).  CSR rows are sorted
+ *     by column and every row stores its diagonal entry (it may be 0).
+ *   - "device" pointers are CUDA global-memory addresses on the current device;
+ *     "host" pointers are ordinary process memory.  The caller owns every
+ *     buffer it passes; the library never frees or retains caller pointers
+ *     beyond the call.
+ *   - Device work is stream-ordered on hf_opts.cuda_stream (NULL = legacy
+ *     default stream).  Calls that return host-visible results synchronise
+ *     that stream before returning.
+ *   - Return value: HF_OK (0) or one of the HF_ERR_* codes below.  On error the
+ *     context stays valid and keeps its previous state unless stated.
+ *   - A context is not thread-safe.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HF_OK = 0,
+  HF_ERR_ARG = 1,            /* invalid argument (null pointer, negative size, ...) */
+  HF_ERR_STATE = 2,          /* call order violated, e.g. hf_schur before hf_factorize */
+  HF_ERR_PATTERN = 3,        /* CSR unsorted, index out of range, pattern not symmetric,
+                                or a row without its diagonal entry */
+  HF_ERR_NUMERIC = 4,        /* NaN / Inf in the input values */
+  HF_ERR_NOT_CONVERGED = 5,  /* block GCR hit gcr_maxit; results usable, see hf_info */
+  HF_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+  HF_ERR_CUDA = 7,           /* a CUDA runtime call failed */
+  HF_ERR_OOM = 8             /* device memory allocation failed */
+};
+
+/* Precision forms (Table 1 columns). */
+enum {
+  HF_PREC_MIXED = 0,   /* FP32 factor + FP64 block GCR / S22 / dense LDL^T: Alg. 1 */
+  HF_PREC_FP64 = 1,    /* plain FP64 factor, S22 taken from the FP64 factor ("double") */
+  HF_PREC_FP32 = 2     /* FP32 factor, S22 from the FP32 factor ("single") */
+};
+
+typedef struct hf_ctx hf_ctx;   /* opaque; owns every device buffer it allocates */
+
+typedef struct {
+  double tau;            /* postponing threshold tau > 0 (Sec. 2.2); default 1e-2 */
+  int    n_enlarge;      /* entries moved into the hard part (Sec. 2.2, "n = 4"); default 4 */
+  int    precision;      /* HF_PREC_*; default HF_PREC_MIXED */
+  double gcr_tol;        /* block GCR stop: max_k |r_k|/|b_k| <= gcr_tol; default 1e-14 */
+  int    gcr_maxit;      /* block GCR iteration limit; default 40 */
+  double kernel_eps;     /* null pivot if |pivot| <= kernel_eps * max|pivot|; default 1e-10 */
+  double kernel_gap;     /* minimum ratio gap that separates null pivots; default 1e4 */
+  int    nd_leaf;        /* dissection stops when a set has <= nd_leaf unknowns; default 256 */
+  int    nd_levels;      /* if > 0, force the number of tree levels m (Sec. 2.2); default 0 */
+  int    delay_cap;      /* initial capacity for postponed rows per front; default 256
+                            (grown and retried automatically when exceeded) */
+  int    panel;          /* pivots per panel of the front factorization; default 64 */
+  void*  cuda_stream;    /* cudaStream_t; NULL = default stream */
+} hf_opts;
+
+typedef struct {
+  int64_t L;              /* order of K */
+  int64_t N;              /* #Lambda_1 */
+  int64_t M;              /* #Lambda_2 */
+  int64_t n_lambda0;      /* #Lambda_0 (postponed along the tree) */
+  int64_t nnz_factor;     /* entries of the stored lower factor (all fronts) */
+  int64_t n_nodes;        /* dissection tree nodes (2^m - 1) */
+  int32_t levels;         /* m */
+  int32_t kernel_dim;     /* detected dimension of ker(S22) (Sec. 3, rank revealing) */
+  int32_t gcr_iters;      /* block GCR iterations of the last hf_schur */
+  int32_t solve_iters;    /* block GCR iterations of the last hf_solve */
+  double  gcr_relres;     /* max column |R|/|B| reached by the last hf_schur */
+  double  solve_relres;   /* same for the last hf_solve */
+  double  factor_flops;   /* dense LDL^T flops of the fronts actually factorized */
+  int64_t front_bytes;    /* device bytes of the front arena */
+  int32_t delay_retries;  /* times the delay capacity had to be grown */
+  int32_t precision;      /* form used */
+} hf_info;
+
+/* Fill *opts with the defaults listed above.  Returns HF_ERR_ARG if opts is NULL. */
+int hf_default_opts(hf_opts* opts);
+
+/* Human-readable name of an HF_* code (static string). */
+const char* hf_error_string(int code);
+
+/*
+ * Analysis (Sec. 2.2, Fig. 1): nested-dissection bisection tree of 2^m - 1 index
+ * sets Lambda_l, elimination tree, front row structures and assembly maps.
+ * Host only: touches no GPU.
+ *   L       order of K (> 0)
+ *   rowptr  host, L+1 entries, CSR row pointers of the pattern
+ *   col     host, rowptr[L] entries, column indices (sorted per row)
+ *   coords  host, nullable, L x dim row-major coordinates of the unknowns; when
+ *           given the bisection is geometric, otherwise graph based (BFS levels)
+ *   dim     1..3 when coords is given
+ *   opts    host, nullable (defaults)
+ *   out     receives a new context (free with hf_free)
+ * Errors: HF_ERR_ARG, HF_ERR_PATTERN.
+ */
+int hf_analyze(int64_t L, const int64_t* rowptr, const int32_t* col, const double* coords,
+               int dim, const hf_opts* opts, hf_ctx** out);
+
+/*
+ * Numeric factorization, Alg. 1 step 1 (Sec. 2.1-2.2): scales Kbar (Sec. 2), factorizes
+ * the fronts in the precision of opts.precision with symmetric max-|diag| pivoting and
+ * threshold postponing (tau), refactorizes the postponed set Lambda_0 and enlarges the
+ * hard part by n_enlarge.  Re-callable with new values for the same pattern.
+ *   vals  device, rowptr[L] doubles: the values of Kbar in the CSR order given to
+ *         hf_analyze.  Read during the call only.
+ *   tau   threshold (> 0); overrides opts.tau for this and later calls.
+ * On return the split (N, M, Lambda_2) is known on the host (one small D2H copy).
+ * Errors: HF_ERR_ARG, HF_ERR_NUMERIC, HF_ERR_CUDA, HF_ERR_OOM.
+ */
+int hf_factorize(hf_ctx* ctx, const double* vals, double tau);
+
+/*
+ * Schur generation, Alg. 1 steps 2-5: for HF_PREC_MIXED, X12 = K11^-1 K12 by block GCR
+ * (Sec. 3.5) in FP64 preconditioned by the FP32 factor, S22 = K22 - K21 X12 in FP64;
+ * for the other forms S22 is taken from the factor.  Then S22 is factorized in FP64
+ * by Bunch-Kaufman LDL^T (1x1 / 2x2 pivots) and its kernel dimension detected.
+ * Errors: HF_ERR_STATE, HF_ERR_NOT_CONVERGED (results still usable), HF_ERR_CUDA, HF_ERR_OOM.
+ */
+int hf_schur(hf_ctx* ctx);
+
+/*
+ * Solve Kbar x = b, Alg. 2 (block forward/backward substitution; the K11 solve by the
+ * same block GCR for HF_PREC_MIXED).  Kernel pivots of S22 are treated as zero, so for
+ * singular Kbar and consistent b the particular solution is returned.
+ *   nrhs     number of right-hand sides (>= 1)
+ *   b, ldb   device, column-major L x nrhs, leading dimension ldb >= L
+ *   x, ldx   device, column-major L x nrhs output, ldx >= L (may not alias b)
+ * Errors: HF_ERR_STATE, HF_ERR_ARG, HF_ERR_NOT_CONVERGED, HF_ERR_CUDA, HF_ERR_OOM.
+ */
+int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
+
+/*
+ * The split of Alg. 1 step 1 (host outputs, any may be NULL):
+ *   pivot_order  L entries: the elimination order Pi (Lambda_1 in order Pi_1, then
+ *                Lambda_2 ascending)
+ *   lambda2      M entries, ascending
+ *   info         summary
+ */
+int hf_get_split(hf_ctx* ctx, int32_t* pivot_order, int32_t* lambda2, hf_info* info);
+
+/* Summary of the last calls (host output). */
+int hf_get_info(hf_ctx* ctx, hf_info* info);
+
+/*
+ * The dissection tree (Sec. 2.2), nodes in elimination order (children first):
+ *   parent    n_nodes entries, index of the parent node, -1 for the root (host)
+ *   set_ptr   n_nodes+1 entries; set_idx[set_ptr[t] .. set_ptr[t+1]) = Lambda_t (host)
+ *   set_idx   L entries (host)
+ * Call with all three NULL to only read info->n_nodes through hf_get_info.
+ */
+int hf_get_tree(hf_ctx* ctx, int32_t* parent, int64_t* set_ptr, int32_t* set_idx);
+
+/*
+ * Pivot decisions of the last hf_factorize (host outputs):
+ *   node_ptr   n_nodes+2 entries; pivots of node t (elimination order) are
+ *              piv[node_ptr[t] .. node_ptr[t+1]) in the order chosen; entry
+ *              n_nodes is the refactorization of Lambda_0
+ *   piv        (number of eliminated indices) entries, original indices
+ *   moved      n_enlarge entries (fewer if fewer pivots exist): the indices moved
+ *              into Lambda_2 by the enlargement, in elimination order
+ *   n_moved    receives their count
+ */
+int hf_get_pivots(hf_ctx* ctx, int64_t* node_ptr, int32_t* piv, int32_t* moved, int32_t* n_moved);
+
+/*
+ * The lower-precision factor of K11 (Eq. 1), for checking: column j of L for pivot
+ * piv[j] (same order as hf_get_pivots).  Host outputs:
+ *   col_ptr  (#pivots + 1) entries
+ *   row_idx  col_ptr[#pivots] entries: original row indices (strictly later pivots
+ *            and postponed rows, Lambda_2 rows included)
+ *   val      same count, values of L (unit diagonal not stored), as double
+ *   d        #pivots entries, the pivots
+ * Call with row_idx = val = NULL to get only col_ptr (sizes).
+ */
+int hf_get_factor(hf_ctx* ctx, int64_t* col_ptr, int32_t* row_idx, double* val, double* d);
+
+/*
+ * Results of hf_schur (device outputs, FP64):
+ *   x12  L x M row-major (ldx12 >= M): X12 in original row indices, zero on Lambda_2 rows
+ *   s22  M x M row-major, rows/cols in ascending Lambda_2 order
+ */
+int hf_get_x12(hf_ctx* ctx, double* x12, int64_t ldx12);
+int hf_get_s22(hf_ctx* ctx, double* s22);
+
+/*
+ * Bunch-Kaufman factors of S22 (host outputs, M entries each, M*M for lf):
+ *   perm   row order: P^T S22 P = Lf D Lf^T with row i of the factor = S22 row perm[i]
+ *   lf     M x M row-major unit lower triangular Lf
+ *   dblk   M entries: 1 = 1x1 block start, 2 = 2x2 block start, 0 = second row of a 2x2
+ *   dval   M x 2 row-major: [d_ii, d_i,i+1] (the 2x2 off-diagonal for a 2x2 start)
+ *   null   M entries: 1 where the pivot magnitude was declared null (kernel)
+ */
+int hf_get_s22_factor(hf_ctx* ctx, int32_t* perm, double* lf, int32_t* dblk, double* dval, int32_t* null_piv);
+
+/* Release every device and host buffer of the context.  NULL is ignored. */
+void hf_free(hf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HF_H */

@@ -1,0 +1,273 @@
+// C ABI entry points (include/hf.h): argument checks, call order, host getters.
+#include "hf_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+int hf_factorize_impl(hf_ctx* c, const double* vals, double tau);
+int hf_schur_impl(hf_ctx* c);
+int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
+
+static thread_local char g_cuda_msg[256] = "";
+
+int hf_cuda_error(cudaError_t e) {
+  std::snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s", cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HF_ERR_OOM; }
+  return HF_ERR_CUDA;
+}
+
+const char* hf_last_cuda_message() { return g_cuda_msg; }
+
+int hf_ensure(DevBuf& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return HF_OK;
+  if (b.p) { cudaFree(b.p); b.p = nullptr; b.bytes = 0; }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) { b.p = nullptr; return hf_cuda_error(e); }
+  b.bytes = bytes;
+  return HF_OK;
+}
+
+void hf_release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+extern "C" {
+
+int hf_default_opts(hf_opts* o) {
+  if (!o) return HF_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->tau = 1e-2;
+  o->n_enlarge = 4;
+  o->precision = HF_PREC_MIXED;
+  o->gcr_tol = 1e-14;
+  o->gcr_maxit = 40;
+  o->kernel_eps = 1e-10;
+  o->kernel_gap = 1e4;
+  o->nd_leaf = 256;
+  o->nd_levels = 0;
+  o->delay_cap = 256;
+  o->panel = 64;
+  o->cuda_stream = nullptr;
+  return HF_OK;
+}
+
+const char* hf_error_string(int code) {
+  switch (code) {
+    case HF_OK: return "ok";
+    case HF_ERR_ARG: return "invalid argument";
+    case HF_ERR_STATE: return "call order violated";
+    case HF_ERR_PATTERN: return "invalid sparsity pattern";
+    case HF_ERR_NUMERIC: return "non-finite input values";
+    case HF_ERR_NOT_CONVERGED: return "block GCR did not converge";
+    case HF_ERR_TIMEOUT: return "device wait timed out";
+    case HF_ERR_CUDA: return "CUDA error";
+    case HF_ERR_OOM: return "device out of memory";
+    default: return "unknown error";
+  }
+}
+
+int hf_analyze(int64_t L, const int64_t* rowptr, const int32_t* col, const double* coords, int dim,
+               const hf_opts* opts, hf_ctx** out) {
+  if (opts) {
+    if (!(opts->tau > 0) || opts->n_enlarge < 0 || opts->gcr_maxit < 1 || opts->nd_leaf < 1 ||
+        opts->panel < 1 || opts->delay_cap < 0 || opts->nd_levels < 0 || opts->nd_levels > 24)
+      return HF_ERR_ARG;
+    if (opts->precision < HF_PREC_MIXED || opts->precision > HF_PREC_FP32) return HF_ERR_ARG;
+  }
+  return hf_analyze_impl(L, rowptr, col, coords, dim, opts, out);
+}
+
+int hf_factorize(hf_ctx* c, const double* vals, double tau) {
+  if (!c || !vals || !(tau > 0)) return HF_ERR_ARG;
+  return hf_factorize_impl(c, vals, tau);
+}
+
+int hf_schur(hf_ctx* c) {
+  if (!c) return HF_ERR_ARG;
+  return hf_schur_impl(c);
+}
+
+int hf_solve(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx) {
+  if (!c) return HF_ERR_ARG;
+  return hf_solve_impl(c, nrhs, b, ldb, x, ldx);
+}
+
+int hf_get_info(hf_ctx* c, hf_info* info) {
+  if (!c || !info) return HF_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->L = c->L;
+  info->N = c->N;
+  info->M = c->M;
+  info->n_lambda0 = c->n_lambda0;
+  info->nnz_factor = c->nnz_factor;
+  info->n_nodes = c->n_nodes;
+  info->levels = c->m;
+  info->kernel_dim = c->kernel_dim;
+  info->gcr_iters = c->gcr_iters;
+  info->solve_iters = c->solve_iters;
+  info->gcr_relres = c->gcr_relres;
+  info->solve_relres = c->solve_relres;
+  double fl = 0;
+  for (size_t t = 0; t < c->state_host.size(); ++t) {
+    double k = c->state_host[t].k, f = c->state_host[t].f;
+    // sum over pivots j of (f - j - 1)^2 multiply-adds in the Schur updates
+    fl += 2.0 * (k * (f - 1) * (f - 1) - (f - 1) * k * (k - 1) + k * (k - 1) * (2 * k - 1) / 6.0) / 2.0;
+  }
+  info->factor_flops = fl;
+  info->front_bytes = c->d_front.p ? (int64_t)c->d_front.bytes : 0;
+  info->delay_retries = c->delay_retries;
+  info->precision = c->prec;
+  return HF_OK;
+}
+
+int hf_get_split(hf_ctx* c, int32_t* pivot_order, int32_t* lambda2, hf_info* info) {
+  if (!c) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  if (lambda2 && c->M) std::memcpy(lambda2, c->lambda2.data(), c->M * 4);
+  if (pivot_order) {
+    std::vector<int32_t> rid(c->row_elems);
+    if (cudaMemcpy(rid.data(), c->d_rowid.p, rid.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return HF_ERR_CUDA;
+    int64_t p = 0;
+    for (int t = 0; t <= c->n_nodes; ++t) {
+      const NodeState& S = c->state_host[t];
+      for (int i = 0; i < S.ksolve; ++i) pivot_order[p++] = rid[c->nodes[t].row_off + i];
+    }
+    for (int32_t v : c->lambda2) pivot_order[p++] = v;
+    if (p != c->L) return HF_ERR_STATE;
+  }
+  if (info) return hf_get_info(c, info);
+  return HF_OK;
+}
+
+int hf_get_tree(hf_ctx* c, int32_t* parent, int64_t* set_ptr, int32_t* set_idx) {
+  if (!c) return HF_ERR_ARG;
+  const int nn = c->n_nodes;
+  if (parent)
+    for (int t = 0; t < nn; ++t) parent[t] = (c->nodes[t].parent >= nn) ? -1 : c->nodes[t].parent;
+  if (set_ptr) std::memcpy(set_ptr, c->set_ptr.data(), (nn + 1) * sizeof(int64_t));
+  if (set_idx) std::memcpy(set_idx, c->set_idx.data(), c->set_idx.size() * 4);
+  return HF_OK;
+}
+
+int hf_get_pivots(hf_ctx* c, int64_t* node_ptr, int32_t* piv, int32_t* moved, int32_t* n_moved) {
+  if (!c) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  std::vector<int32_t> rid(c->row_elems);
+  if (cudaMemcpy(rid.data(), c->d_rowid.p, rid.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HF_ERR_CUDA;
+  const int nn = c->n_nodes;
+  int64_t p = 0;
+  int nm = 0;
+  if (node_ptr) node_ptr[0] = 0;
+  for (int t = 0; t <= nn; ++t) {
+    const NodeState& S = c->state_host[t];
+    for (int i = 0; i < S.k; ++i) {
+      if (piv) piv[p] = rid[c->nodes[t].row_off + i];
+      ++p;
+    }
+    if (node_ptr) node_ptr[t + 1] = p;
+  }
+  // moved entries in elimination order
+  for (int t = 0; t <= nn; ++t) {
+    const NodeState& S = c->state_host[t];
+    for (int i = S.ksolve; i < S.k; ++i) {
+      if (moved) moved[nm] = rid[c->nodes[t].row_off + i];
+      ++nm;
+    }
+  }
+  if (n_moved) *n_moved = nm;
+  return HF_OK;
+}
+
+int hf_get_factor(hf_ctx* c, int64_t* col_ptr, int32_t* row_idx, double* val, double* d) {
+  if (!c || !col_ptr) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  const int nn = c->n_nodes;
+  int64_t p = 0, j = 0;
+  col_ptr[0] = 0;
+  for (int t = 0; t <= nn; ++t) {
+    const NodeState& S = c->state_host[t];
+    for (int i = 0; i < S.k; ++i) { p += S.f - i - 1; col_ptr[++j] = p; }
+  }
+  if (!row_idx && !val && !d) return HF_OK;
+  std::vector<int32_t> rid(c->row_elems);
+  if (cudaMemcpy(rid.data(), c->d_rowid.p, rid.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HF_ERR_CUDA;
+  const bool dbl = c->front_prec == HF_PREC_FP64;
+  j = 0;
+  p = 0;
+  for (int t = 0; t <= nn; ++t) {
+    const NodeState& S = c->state_host[t];
+    const NodeDesc& nd = c->nodes[t];
+    if (S.k == 0) continue;
+    const size_t esz = dbl ? 8 : 4;
+    std::vector<unsigned char> buf((size_t)nd.ld * S.k * esz);
+    if (cudaMemcpy(buf.data(), (const unsigned char*)c->d_front.p + nd.front_off * esz, buf.size(),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return HF_ERR_CUDA;
+    auto at = [&](int r, int cc) -> double {
+      size_t o = (size_t)r + (size_t)cc * nd.ld;
+      return dbl ? ((const double*)buf.data())[o] : (double)((const float*)buf.data())[o];
+    };
+    for (int i = 0; i < S.k; ++i) {
+      if (d) d[j] = at(i, i);
+      for (int r = i + 1; r < S.f; ++r) {
+        if (row_idx) row_idx[p] = rid[nd.row_off + r];
+        if (val) val[p] = at(r, i);
+        ++p;
+      }
+      ++j;
+    }
+  }
+  return HF_OK;
+}
+
+int hf_get_x12(hf_ctx* c, double* x12, int64_t ldx12) {
+  if (!c || !x12 || ldx12 < c->M) return HF_ERR_ARG;
+  if (!c->schured || c->prec != HF_PREC_MIXED) return HF_ERR_STATE;
+  if (c->M == 0) return HF_OK;
+  cudaError_t e = cudaMemcpy2D(x12, ldx12 * 8, c->d_x12.p, c->M * 8, c->M * 8, c->L, cudaMemcpyDeviceToDevice);
+  return e == cudaSuccess ? HF_OK : hf_cuda_error(e);
+}
+
+int hf_get_s22(hf_ctx* c, double* s22) {
+  if (!c || !s22) return HF_ERR_ARG;
+  if (!c->schured) return HF_ERR_STATE;
+  if (c->M == 0) return HF_OK;
+  cudaError_t e = cudaMemcpy(s22, c->d_s22.p, c->M * c->M * 8, cudaMemcpyDeviceToDevice);
+  return e == cudaSuccess ? HF_OK : hf_cuda_error(e);
+}
+
+int hf_get_s22_factor(hf_ctx* c, int32_t* perm, double* lf, int32_t* dblk, double* dval, int32_t* null_piv) {
+  if (!c) return HF_ERR_ARG;
+  if (!c->schured) return HF_ERR_STATE;
+  const int64_t M = c->M;
+  if (M == 0) return HF_OK;
+  cudaError_t e = cudaSuccess;
+  if (perm && e == cudaSuccess) e = cudaMemcpy(perm, c->d_bk_perm.p, M * 4, cudaMemcpyDeviceToHost);
+  if (lf && e == cudaSuccess) e = cudaMemcpy(lf, c->d_bk_lf.p, M * M * 8, cudaMemcpyDeviceToHost);
+  if (dblk && e == cudaSuccess) e = cudaMemcpy(dblk, c->d_bk_blk.p, M * 4, cudaMemcpyDeviceToHost);
+  if (dval && e == cudaSuccess) e = cudaMemcpy(dval, c->d_bk_dval.p, M * 16, cudaMemcpyDeviceToHost);
+  if (null_piv && e == cudaSuccess) e = cudaMemcpy(null_piv, c->d_bk_null.p, M * 4, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? HF_OK : hf_cuda_error(e);
+}
+
+void hf_free(hf_ctx* c) {
+  if (!c) return;
+  DevBuf* bufs[] = {&c->d_rowptr, &c->d_col, &c->d_diagpos, &c->d_nodes, &c->d_state, &c->d_rowid,
+                    &c->d_rowid_static, &c->d_smap, &c->d_asm, &c->d_cbmap, &c->d_q, &c->d_kval,
+                    &c->d_front, &c->d_flags, &c->d_lam2pos, &c->d_lam2, &c->d_vec, &c->d_x12,
+                    &c->d_s22, &c->d_bk_lf, &c->d_bk_perm, &c->d_bk_blk, &c->d_bk_dval, &c->d_bk_null,
+                    &c->d_work, &c->d_small, &c->d_gsmall, &c->d_k12, &c->d_solve};
+  for (DevBuf* b : bufs) hf_release(*b);
+  delete c;
+}
+
+}  // extern "C"

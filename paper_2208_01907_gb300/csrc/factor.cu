@@ -1,0 +1,603 @@
+// Alg. 1 step 1 on the GPU: diagonal scaling (Sec. 2), multifrontal LDL^T along the
+// dissection tree with symmetric max-|diag| pivoting and threshold postponing
+// (Sec. 2.1-2.2), refactorization of the postponed set Lambda_0 and enlargement of
+// the hard part (Sec. 2.2).
+//
+// Layout: every front t is a dense ld x ld column-major matrix in one arena; only
+// its lower triangle is stored and updated.  Rows are ordered
+// [Lambda_t | static structure | rows delayed from the children].  Pivoting permutes
+// the first n rows (the candidates); after the front is done, columns [0, k) hold the
+// factor (unit L below the diagonal, D on it) and the trailing block [k, f)^2 is the
+// contribution passed to the parent by extend-add.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+namespace {
+
+constexpr int TB = 64;            // trailing-update tile
+constexpr int TK = 16;            // trailing-update k chunk
+
+// ---------------------------------------------------------------------------
+// Sec. 2: Q_ii = 1/sqrt(|Kbar_ii|) (1 if zero) and K = Q Kbar Q
+// ---------------------------------------------------------------------------
+__global__ void k_scale_diag(int64_t L, const int64_t* __restrict__ diagpos, const double* __restrict__ vals,
+                             double* __restrict__ q) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L) return;
+  double d = vals[diagpos[i]];
+  q[i] = (d != 0.0) ? 1.0 / sqrt(fabs(d)) : 1.0;
+}
+
+__global__ void k_scale_vals(int64_t L, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ vals, const double* __restrict__ q,
+                             double* __restrict__ kval, int* __restrict__ flags) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= L) return;
+  double qi = q[row];
+  bool bad = false;
+  for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+    double v = vals[e];
+    if (!isfinite(v)) bad = true;
+    kval[e] = qi * v * q[col[e]];
+  }
+  if (bad) flags[FLAG_NUMERIC] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Per level: delayed-row counts and front orders, extend-add maps
+// ---------------------------------------------------------------------------
+__global__ void k_level_prep(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, int cnt,
+                             int* __restrict__ flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  int t = t0 + i;
+  NodeDesc d = nd[t];
+  int D = 0, off[2] = {0, 0};
+  int ch[2] = {d.child0, d.child1};
+  for (int s = 0; s < 2; ++s) {
+    if (ch[s] < 0) continue;
+    off[s] = D;
+    // postponed candidates of the child plus the rows it received from its own children
+    D += (nd[ch[s]].n - st[ch[s]].k) + st[ch[s]].D;
+  }
+  if (D > d.dc) { flags[FLAG_DELAY_OVERFLOW] = 1; D = d.dc; }
+  NodeState S;
+  S.k = 0; S.kp0 = 0; S.D = D; S.f = d.n + d.s + D; S.stopped = 0; S.dref = 1.0;   // reading R2
+  S.ksolve = 0; S.nmoved = 0; S.delay_off0 = off[0]; S.delay_off1 = off[1]; S.pad = 0;
+  st[t] = S;
+}
+
+// contribution rows of each child -> rows of this front; delayed rows get their ids
+__global__ void k_level_maps(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                             int32_t* __restrict__ rowid, const int32_t* __restrict__ smap,
+                             int32_t* __restrict__ cbmap) {
+  int t = t0 + blockIdx.x;
+  NodeDesc d = nd[t];
+  const int f = st[t].f;
+  int ch[2] = {d.child0, d.child1};
+  int off[2] = {st[t].delay_off0, st[t].delay_off1};
+  for (int s = 0; s < 2; ++s) {
+    int c = ch[s];
+    if (c < 0) continue;
+    NodeDesc dc = nd[c];
+    int kc = st[c].k, fc = st[c].f;
+    int base = d.n + d.s + off[s];
+    for (int a = threadIdx.x; a < fc - kc; a += blockDim.x) {
+      int p = kc + a;
+      int tgt;
+      if (p < dc.n) tgt = base + (p - kc);                                  // postponed in the child
+      else if (p < dc.n + dc.s) tgt = smap[dc.smap_off + (p - dc.n)];       // static structure
+      else tgt = base + (dc.n - kc) + (p - dc.n - dc.s);                    // delayed through the child
+      if (tgt >= f) tgt = -1;                                               // only after an overflow
+      cbmap[dc.row_off + a] = tgt;
+      if (tgt >= d.n + d.s) rowid[d.row_off + tgt] = rowid[dc.row_off + p];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Front assembly: zero, scatter scaled K entries, extend-add the children
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_front_zero(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                             T* __restrict__ arena) {
+  int t = t0 + blockIdx.y;
+  NodeDesc d = nd[t];
+  const int64_t f = st[t].f;
+  T* F = arena + d.front_off;
+  for (int64_t c = blockIdx.x; c < f; c += gridDim.x)
+    for (int64_t r = c + threadIdx.x; r < f; r += blockDim.x) F[r + c * d.ld] = T(0);
+}
+
+template <typename T>
+__global__ void k_front_asm(const NodeDesc* __restrict__ nd, int t0, const AsmEntry* __restrict__ al,
+                            const double* __restrict__ kval, T* __restrict__ arena) {
+  int t = t0 + blockIdx.y;
+  NodeDesc d = nd[t];
+  T* F = arena + d.front_off;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d.asm_cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    AsmEntry a = al[d.asm_off + e];
+    F[a.r + (int64_t)a.c * d.ld] = (T)kval[a.csr];
+  }
+}
+
+template <typename T>
+__global__ void k_extend_add(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0, int slot,
+                             const int32_t* __restrict__ cbmap, T* __restrict__ arena) {
+  int t = t0 + blockIdx.y;
+  NodeDesc d = nd[t];
+  int c = slot == 0 ? d.child0 : d.child1;
+  if (c < 0) return;
+  NodeDesc dc = nd[c];
+  const int kc = st[c].k, m = st[c].f - kc;
+  const T* CB = arena + dc.front_off + kc + (int64_t)kc * dc.ld;
+  const int32_t* map = cbmap + dc.row_off;
+  T* F = arena + d.front_off;
+  for (int a = blockIdx.x; a < m; a += gridDim.x) {
+    int ta = map[a];
+    for (int b = a + threadIdx.x; b < m; b += blockDim.x) {
+      int tb = map[b];
+      if (ta < 0 || tb < 0) continue;
+      int r = max(ta, tb), cc = min(ta, tb);
+      F[r + (int64_t)cc * d.ld] += CB[b + (int64_t)a * dc.ld];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Panel factorization with symmetric max-|diag| pivoting and the ratio test
+// (Sec. 2.1-2.2).  One CTA per front; up to nb pivots; columns of the panel are
+// computed left-looking, the rest of the front is updated by k_trailing.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0,
+                        T* __restrict__ arena, int32_t* __restrict__ rowid, int nb, double tau) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_k[32];
+  __shared__ int red_i[32], red_p[32];
+  __shared__ int s_q, s_stop;
+  const int t = t0 + blockIdx.x;
+  const NodeDesc d = nd[t];
+  NodeState* S = st + t;
+  const int f = S->f;
+  const int ncand = d.cand_all ? f : d.n;
+  const int k0 = S->k;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (S->stopped || k0 >= ncand) {
+    if (tid == 0) S->kp0 = k0;
+    return;
+  }
+  T* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  int32_t* rid = rowid + d.row_off;
+  T* w = (T*)smem_raw;                        // nb entries
+  T* dg = w + nb;                             // ncand entries (front positions)
+  int* sid = (int*)(dg + ncand);              // ncand entries
+  for (int i = k0 + tid; i < ncand; i += nt) {
+    dg[i] = F[i + i * ld];
+    sid[i] = rid[i];
+  }
+  double dref = S->dref;
+  const int kend = min(ncand, k0 + nb);
+  int k = k0;
+  bool stopped = false;
+  __syncthreads();
+  while (k < kend) {
+    // 1. argmax |dg| over the remaining candidates, ties to the smaller original index
+    double bk = -2.0;
+    int bi = 0x7fffffff, bp = -1;
+    for (int i = k + tid; i < ncand; i += nt) {
+      double kk = piv_key(dg[i]);
+      if (better(kk, sid[i], bk, bi)) { bk = kk; bi = sid[i]; bp = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (better(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
+    }
+    if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; red_p[tid >> 5] = bp; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int wv = 1; wv < (nt + 31) / 32; ++wv)
+        if (better(red_k[wv], red_i[wv], bk, bi)) { bk = red_k[wv]; bi = red_i[wv]; bp = red_p[wv]; }
+      // ratio test |d_{i+1} / d_i| < tau -> postpone the rest (R3); NaN fails it
+      s_stop = !(bk >= tau * dref);
+      s_q = bp;
+    }
+    __syncthreads();
+    if (s_stop) { stopped = true; break; }
+    const int q = s_q;
+    // 2. symmetric swap k <-> q in lower storage
+    if (q != k) {
+      const int nA = k, nB = q - k - 1, nC = f - q - 1;
+      const int tot = nA + nB + nC + 1;
+      for (int e = tid; e < tot; e += nt) {
+        int64_t a, b;
+        if (e < nA) { a = k + e * ld; b = q + e * ld; }                        // rows k, q left of k
+        else if (e < nA + nB) { int j = k + 1 + (e - nA); a = j + k * ld; b = q + j * ld; }
+        else if (e < nA + nB + nC) { int i = q + 1 + (e - nA - nB); a = i + k * ld; b = i + q * ld; }
+        else { a = k + k * ld; b = q + q * ld; }
+        T tmp = F[a]; F[a] = F[b]; F[b] = tmp;
+      }
+      if (tid == 0) {
+        T td = dg[k]; dg[k] = dg[q]; dg[q] = td;
+        int ti = sid[k]; sid[k] = sid[q]; sid[q] = ti;
+        int tr = rid[k]; rid[k] = rid[q]; rid[q] = tr;
+      }
+    }
+    __syncthreads();
+    // 3. w_t = d_t * L(k, t) for the panel columns already done
+    for (int c = k0 + tid; c < k; c += nt) w[c - k0] = F[c + c * ld] * F[k + c * ld];
+    __syncthreads();
+    // 4. current column k: c_i = A(i, k) - sum_t L(i, t) d_t L(k, t)
+    for (int i = k + tid; i < f; i += nt) {
+      T acc = F[i + k * ld];
+      for (int c = k0; c < k; ++c) acc -= F[i + c * ld] * w[c - k0];
+      F[i + k * ld] = acc;
+    }
+    __syncthreads();
+    const T dk = F[k + k * ld];
+    // 5. L(i, k) = c_i / d_k and the candidates' diagonals
+    for (int i = k + 1 + tid; i < f; i += nt) {
+      T c = F[i + k * ld];
+      T l = c / dk;
+      F[i + k * ld] = l;
+      if (i < ncand) dg[i] -= l * c;
+    }
+    dref = fabs((double)dk);
+    ++k;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    S->kp0 = k0;
+    S->k = k;
+    S->dref = dref;
+    if (stopped) S->stopped = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Trailing update of the front: A[k1:f, k1:f] -= W D W^T (lower tiles only),
+// W = L[k1:f, k0:k1], D = diag(d_k0..d_k1-1)   (rank-nb Schur update, Sec. 2.1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_trailing(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                  int t0, T* __restrict__ arena) {
+  const int t = t0 + blockIdx.z;
+  const NodeDesc d = nd[t];
+  const int k0 = st[t].kp0, k1 = st[t].k, f = st[t].f;
+  if (k1 <= k0) return;
+  const int bi = blockIdx.x, bj = blockIdx.y;
+  if (bj > bi) return;
+  const int r0 = k1 + bi * TB, c0 = k1 + bj * TB;
+  if (r0 >= f) return;
+  T* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  __shared__ T As[TK][TB + 1];
+  __shared__ T Bs[TK][TB + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int kc = k0; kc < k1; kc += TK) {
+    for (int e = threadIdx.x; e < TK * TB; e += 256) {
+      int kk = e / TB, rr = e % TB;
+      int c = kc + kk;
+      T a = T(0), b = T(0);
+      if (c < k1) {
+        int r = r0 + rr;
+        if (r < f) a = F[r + c * ld];
+        int r2 = c0 + rr;
+        if (r2 < f) b = F[r2 + c * ld] * F[c + c * ld];
+      }
+      As[kk][rr] = a;
+      Bs[kk][rr] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int c = c0 + ty + 16 * j;
+    if (c >= f) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int r = r0 + tx + 16 * i;
+      if (r < f && r >= c) F[r + c * ld] -= acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Enlargement (Sec. 2.2, reading R13) and collection of Lambda_2
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int nn, int n_enlarge,
+                           const int32_t* __restrict__ rowid, int32_t* __restrict__ lam2, int64_t* __restrict__ counts) {
+  const int tid = threadIdx.x;
+  for (int t = tid; t <= nn; t += blockDim.x) { st[t].ksolve = st[t].k; st[t].nmoved = 0; }
+  __syncthreads();
+  if (tid == 0) {
+    int rem = n_enlarge;
+    for (int t = nn; t >= 0 && rem > 0; --t) {
+      int take = min(rem, st[t].k);
+      st[t].nmoved = take;
+      st[t].ksolve = st[t].k - take;
+      rem -= take;
+    }
+    int64_t M = 0, piv = 0;
+    const NodeDesc r = nd[nn];
+    const int ksr = st[nn].k, fsr = st[nn].f;
+    for (int i = ksr; i < fsr; ++i) lam2[M++] = rowid[r.row_off + i];
+    for (int t = 0; t <= nn; ++t) {
+      piv += st[t].k;
+      for (int i = st[t].ksolve; i < st[t].k; ++i) lam2[M++] = rowid[nd[t].row_off + i];
+    }
+    counts[0] = M;
+    counts[1] = fsr;          // #Lambda_0
+    counts[2] = piv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S22 taken from the factor (HF_PREC_FP64 / HF_PREC_FP32 forms): with T the moved
+// pivots (a suffix of the elimination order) and H the unfactorized rows,
+// S22 = L_(T+H),T D_T L_(T+H),T^T + (0 (+) S_H)   (block LDL^T of the trailing matrix, Eq. 1)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_s22_from_factor(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int nn,
+                                  const T* __restrict__ arena, const int32_t* __restrict__ rowid,
+                                  const int32_t* __restrict__ lam2pos, int M, double* __restrict__ S22,
+                                  int* __restrict__ flags) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < M * M; e += blockDim.x) S22[e] = 0.0;
+  __syncthreads();
+  {   // unfactorized block of the Lambda_0 stage front
+    const NodeDesc r = nd[nn];
+    const T* F = arena + r.front_off;
+    const int ksr = st[nn].k, fsr = st[nn].f;
+    const int m = fsr - ksr;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      int a = e / m, b = e % m;
+      if (b < a) continue;
+      int ia = ksr + a, ib = ksr + b;
+      double v = (double)F[ib + (int64_t)ia * r.ld];
+      int ga = rowid[r.row_off + ia], gb = rowid[r.row_off + ib];
+      int pa = ga >= 0 ? lam2pos[ga] : -1, pb = gb >= 0 ? lam2pos[gb] : -1;
+      if (pa < 0 || pb < 0) { flags[FLAG_NUMERIC] = 2; continue; }
+      S22[pa * M + pb] = v;
+      S22[pb * M + pa] = v;
+    }
+  }
+  __syncthreads();
+  // moved pivots, one column at a time (at most n_enlarge of them)
+  for (int t = nn; t >= 0; --t) {
+    const int ks = st[t].ksolve, k = st[t].k;
+    if (ks == k) continue;
+    const NodeDesc dn = nd[t];
+    const T* F = arena + dn.front_off;
+    const int f = st[t].f;
+    for (int j = ks; j < k; ++j) {
+      const double dj = (double)F[j + (int64_t)j * dn.ld];
+      const int m = f - j;                    // rows j..f-1 (row j carries the unit diagonal)
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        int a = e / m, b = e % m;
+        if (b < a) continue;
+        int ia = j + a, ib = j + b;
+        double la = (a == 0) ? 1.0 : (double)F[ia + (int64_t)j * dn.ld];
+        double lb = (b == 0) ? 1.0 : (double)F[ib + (int64_t)j * dn.ld];
+        int ga = rowid[dn.row_off + ia], gb = rowid[dn.row_off + ib];
+        int pa = ga >= 0 ? lam2pos[ga] : -1, pb = gb >= 0 ? lam2pos[gb] : -1;
+        if (pa < 0 || pb < 0) { flags[FLAG_NUMERIC] = 2; continue; }
+        double v = la * dj * lb;
+        S22[pa * M + pb] += v;
+        if (pa != pb) S22[pb * M + pa] += v;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+int run_levels(hf_ctx* c) {
+  cudaStream_t s = hf_stream(c);
+  const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
+  NodeState* st = (NodeState*)c->d_state.p;
+  T* arena = (T*)c->d_front.p;
+  int32_t* rowid = (int32_t*)c->d_rowid.p;
+  int* flags = (int*)c->d_flags.p;
+  const int nb = std::max(1, std::min(c->opts.panel, 256));
+  const int nn = c->n_nodes;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[sizeof(T) == 8]) {
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr_set[sizeof(T) == 8] = true;
+  }
+  for (int lev = c->m; lev >= 0; --lev) {
+    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+    int maxn = 0, maxld = 0;
+    int64_t maxasm = 0;
+    bool has_children = false;
+    for (int t = t0; t < t0 + cnt; ++t) {
+      const NodeDesc& d = c->nodes[t];
+      maxn = std::max(maxn, d.cand_all ? d.ld : d.n);
+      maxld = std::max(maxld, d.ld);
+      maxasm = std::max<int64_t>(maxasm, d.asm_cnt);
+      has_children |= (d.child0 >= 0);
+    }
+    k_level_prep<<<(cnt + 127) / 128, 128, 0, s>>>(nd, st, t0, cnt, flags);
+    if (has_children)
+      k_level_maps<<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_smap.p, (int32_t*)c->d_cbmap.p);
+    {
+      int bx = std::min(std::max(1, maxld), 512);
+      k_front_zero<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, st, t0, arena);
+    }
+    if (maxasm > 0) {
+      int bx = (int)std::min<int64_t>((maxasm + 255) / 256, 1024);
+      k_front_asm<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, t0, (const AsmEntry*)c->d_asm.p,
+                                                   (const double*)c->d_kval.p, arena);
+    }
+    if (has_children) {
+      int bx = std::min(std::max(1, maxld), 1024);
+      for (int slot = 0; slot < 2; ++slot)
+        k_extend_add<T><<<dim3(bx, cnt), 128, 0, s>>>(nd, st, t0, slot, (const int32_t*)c->d_cbmap.p, arena);
+    }
+    const int npan = (maxn + nb - 1) / nb;
+    const size_t smem = (size_t)nb * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
+    if (smem > 220 * 1024) return HF_ERR_ARG;
+    const int pthreads = maxld > 1024 ? 1024 : 256;
+    const int tiles = (maxld + TB - 1) / TB;
+    for (int p = 0; p < npan; ++p) {
+      k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, nb, c->tau);
+      k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena);
+    }
+    HF_CUDA_TRY(cudaGetLastError());
+  }
+  (void)nn;
+  return HF_OK;
+}
+
+}  // namespace
+
+// Device upload of the analysis results (first factorization, or after a re-layout).
+static int upload_analysis(hf_ctx* c) {
+  cudaStream_t s = hf_stream(c);
+  const int nn = c->n_nodes;
+  auto up = [&](DevBuf& b, const void* src, size_t bytes) -> int {
+    int rc = hf_ensure(b, std::max<size_t>(bytes, 16));
+    if (rc) return rc;
+    if (bytes) HF_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, s));
+    return HF_OK;
+  };
+  int rc;
+  if ((rc = up(c->d_rowptr, c->rowptr.data(), c->rowptr.size() * 8))) return rc;
+  if ((rc = up(c->d_col, c->col.data(), c->col.size() * 4))) return rc;
+  if ((rc = up(c->d_diagpos, c->diagpos.data(), c->diagpos.size() * 8))) return rc;
+  if ((rc = up(c->d_nodes, c->nodes.data(), c->nodes.size() * sizeof(NodeDesc)))) return rc;
+  if ((rc = up(c->d_rowid_static, c->rowid_static.data(), c->rowid_static.size() * 4))) return rc;
+  if ((rc = up(c->d_smap, c->smap.data(), c->smap.size() * 4))) return rc;
+  if ((rc = up(c->d_asm, c->asm_list.data(), c->asm_list.size() * sizeof(AsmEntry)))) return rc;
+  if ((rc = hf_ensure(c->d_state, (size_t)(nn + 1) * sizeof(NodeState)))) return rc;
+  if ((rc = hf_ensure(c->d_rowid, c->rowid_static.size() * 4 + 16))) return rc;
+  if ((rc = hf_ensure(c->d_cbmap, c->rowid_static.size() * 4 + 16))) return rc;
+  if ((rc = hf_ensure(c->d_flags, FLAG_COUNT * sizeof(int) + 64))) return rc;
+  if ((rc = hf_ensure(c->d_q, c->L * 8))) return rc;
+  if ((rc = hf_ensure(c->d_kval, c->nnz * 8))) return rc;
+  if ((rc = hf_ensure(c->d_lam2pos, c->L * 4))) return rc;
+  if ((rc = hf_ensure(c->d_lam2, c->L * 4 + 16))) return rc;
+  return HF_OK;
+}
+
+int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
+  if (!c || !vals || !(tau > 0)) return HF_ERR_ARG;
+  cudaStream_t s = hf_stream(c);
+  c->tau = tau;
+  c->prec = c->opts.precision;
+  c->factored = false;
+  c->schured = false;
+  const bool dbl = (c->prec == HF_PREC_FP64);
+  int rc;
+  bool uploaded = c->d_nodes.p != nullptr;
+  for (int attempt = 0; attempt < 16; ++attempt) {
+    if (!uploaded) {
+      if ((rc = upload_analysis(c))) return rc;
+      uploaded = true;
+    }
+    const size_t esz = dbl ? 8 : 4;
+    if ((rc = hf_ensure(c->d_front, (size_t)c->front_elems * esz + 64))) return rc;
+    HF_CUDA_TRY(cudaMemsetAsync(c->d_flags.p, 0, FLAG_COUNT * sizeof(int) + 64, s));
+    HF_CUDA_TRY(cudaMemcpyAsync(c->d_rowid.p, c->d_rowid_static.p, c->rowid_static.size() * 4,
+                                cudaMemcpyDeviceToDevice, s));
+    const int64_t L = c->L;
+    k_scale_diag<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_diagpos.p, vals, (double*)c->d_q.p);
+    k_scale_vals<<<(unsigned)((L * 32 + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
+                                                          vals, (const double*)c->d_q.p, (double*)c->d_kval.p,
+                                                          (int*)c->d_flags.p);
+    HF_CUDA_TRY(cudaGetLastError());
+    rc = dbl ? run_levels<double>(c) : run_levels<float>(c);
+    if (rc) return rc;
+    int64_t* counts = (int64_t*)((int*)c->d_flags.p + FLAG_COUNT);
+    k_finalize<<<1, 256, 0, s>>>((const NodeDesc*)c->d_nodes.p, (NodeState*)c->d_state.p, c->n_nodes,
+                                 c->opts.n_enlarge, (const int32_t*)c->d_rowid.p, (int32_t*)c->d_lam2.p, counts);
+    HF_CUDA_TRY(cudaGetLastError());
+    int hflags[FLAG_COUNT];
+    int64_t hcounts[3];
+    HF_CUDA_TRY(cudaMemcpyAsync(hflags, c->d_flags.p, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    HF_CUDA_TRY(cudaMemcpyAsync(hcounts, counts, sizeof(hcounts), cudaMemcpyDeviceToHost, s));
+    HF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflags[FLAG_NUMERIC]) return HF_ERR_NUMERIC;
+    if (hflags[FLAG_DELAY_OVERFLOW]) {
+      // grow the capacity for postponed rows and lay the fronts out again
+      c->opts.delay_cap = std::max(1, c->opts.delay_cap) * 2;
+      c->delay_retries++;
+      hf_layout_fronts(c);
+      uploaded = false;
+      continue;
+    }
+    c->M = hcounts[0];
+    c->n_lambda0 = hcounts[1];
+    c->N = c->L - c->M;
+    c->lambda2.resize(c->M);
+    if (c->M) HF_CUDA_TRY(cudaMemcpy(c->lambda2.data(), c->d_lam2.p, c->M * 4, cudaMemcpyDeviceToHost));
+    std::sort(c->lambda2.begin(), c->lambda2.end());
+    c->state_host.resize(c->n_nodes + 1);
+    HF_CUDA_TRY(cudaMemcpy(c->state_host.data(), c->d_state.p, c->state_host.size() * sizeof(NodeState),
+                           cudaMemcpyDeviceToHost));
+    // sorted Lambda_2 and the position map
+    std::vector<int32_t> pos(c->L, -1);
+    for (int64_t i = 0; i < c->M; ++i) pos[c->lambda2[i]] = (int32_t)i;
+    HF_CUDA_TRY(cudaMemcpyAsync(c->d_lam2pos.p, pos.data(), c->L * 4, cudaMemcpyHostToDevice, s));
+    if (c->M) HF_CUDA_TRY(cudaMemcpyAsync(c->d_lam2.p, c->lambda2.data(), c->M * 4, cudaMemcpyHostToDevice, s));
+    HF_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t nz = 0;
+    for (int t = 0; t <= c->n_nodes; ++t) {
+      const NodeState& S = c->state_host[t];
+      nz += (int64_t)S.k * (S.f - S.k) + (int64_t)S.k * (S.k - 1) / 2;
+    }
+    c->nnz_factor = nz;
+    c->front_prec = c->prec;
+    c->factored = true;
+    return HF_OK;
+  }
+  return HF_ERR_OOM;
+}
+
+// S22 from the factor (non-mixed forms)
+int hf_s22_from_factor(hf_ctx* c) {
+  cudaStream_t s = hf_stream(c);
+  int M = (int)c->M;
+  int rc;
+  if ((rc = hf_ensure(c->d_s22, (size_t)M * M * 8 + 16))) return rc;
+  if (M == 0) return HF_OK;
+  if (c->prec == HF_PREC_FP64)
+    k_s22_from_factor<double><<<1, 1024, 0, s>>>((const NodeDesc*)c->d_nodes.p, (const NodeState*)c->d_state.p,
+                                                 c->n_nodes, (const double*)c->d_front.p, (const int32_t*)c->d_rowid.p,
+                                                 (const int32_t*)c->d_lam2pos.p, M, (double*)c->d_s22.p,
+                                                 (int*)c->d_flags.p);
+  else
+    k_s22_from_factor<float><<<1, 1024, 0, s>>>((const NodeDesc*)c->d_nodes.p, (const NodeState*)c->d_state.p,
+                                                c->n_nodes, (const float*)c->d_front.p, (const int32_t*)c->d_rowid.p,
+                                                (const int32_t*)c->d_lam2pos.p, M, (double*)c->d_s22.p,
+                                                (int*)c->d_flags.p);
+  HF_CUDA_TRY(cudaGetLastError());
+  return HF_OK;
+}

@@ -1,0 +1,114 @@
+// Internal state of an hf_ctx: host-side analysis results and device buffers.
+#pragma once
+#include "hf.h"
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+typedef struct CUstream_st* hf_stream_t;
+
+// Per-front static description, uploaded once (layout shared by host and device).
+struct NodeDesc {
+  int32_t n;          // |Lambda_t|: pivot candidates (Sec. 2.2); 0 for the Lambda_0 stage node
+  int32_t s;          // rows of the static structure (ancestor indices coupled to Lambda_t)
+  int32_t dc;         // capacity for postponed rows delayed into this front
+  int32_t ld;         // leading dimension of the dense front (>= n + s + dc, multiple of 4)
+  int32_t parent;     // elimination-order index of the parent, -1 for the Lambda_0 stage node
+  int32_t child0;     // -1 if absent
+  int32_t child1;     // -1 if absent
+  int32_t cand_all;   // 1 for the Lambda_0 stage node: every row is a pivot candidate
+  int64_t front_off;  // element offset of the front in the front arena (ld * ld elements)
+  int64_t row_off;    // offset into the row-id arrays (ld entries)
+  int64_t smap_off;   // offset into smap (s entries): parent front row of each structure row
+  int64_t asm_off;    // offset into the assembly list
+  int64_t asm_cnt;    // entries of the assembly list
+  int32_t level;      // tree depth: 1 = root .. m = leaves; 0 = Lambda_0 stage
+  int32_t pad;
+};
+
+// Per-front dynamic state, written by the factorization kernels.
+struct NodeState {
+  int32_t k;          // pivots eliminated so far (tilde-Lambda_t)
+  int32_t kp0;        // first pivot of the panel just factorized (for the trailing update)
+  int32_t D;          // rows delayed into this front by the children
+  int32_t f;          // current front order n + s + D
+  int32_t stopped;    // 1 once the ratio test postponed the rest of Lambda_t
+  double dref;        // |previous pivot| for the ratio test (Sec. 2.2); 1.0 initially
+  int32_t ksolve;     // pivots that belong to K11 (k minus entries moved into Lambda_2)
+  int32_t nmoved;     // entries of this front moved into Lambda_2 by the enlargement
+  int32_t delay_off0; // first delayed slot taken by child 0's rows
+  int32_t delay_off1; // first delayed slot taken by child 1's rows
+  int32_t pad;
+};
+
+// Assembly entry: front position (row, col) receives K[csr] (scaled).
+struct AsmEntry {
+  int32_t r, c;
+  int64_t csr;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct hf_ctx {
+  hf_opts opts;
+  // ---- pattern and analysis (host) ----
+  int64_t L = 0, nnz = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<int64_t> diagpos;      // CSR index of the diagonal of each row
+  int m = 0;                         // tree levels
+  int n_nodes = 0;                   // 2^m - 1 tree nodes (elimination order), plus one Lambda_0 node
+  std::vector<NodeDesc> nodes;       // n_nodes + 1 entries; the last is the Lambda_0 stage node
+  std::vector<int32_t> set_idx;      // Lambda_t concatenated in elimination order
+  std::vector<int64_t> set_ptr;
+  std::vector<int32_t> struct_idx;   // static structure rows of every front, concatenated
+  std::vector<int64_t> struct_ptr;
+  std::vector<int32_t> rowid_static; // per front: [Lambda_t | structure | delayed (-1)]
+  std::vector<int32_t> smap;
+  std::vector<AsmEntry> asm_list;
+  std::vector<int> level_start, level_count;   // by depth 0..m (0 = Lambda_0 stage)
+  int64_t front_elems = 0, row_elems = 0;
+  double static_flops = 0;
+  int delay_retries = 0;
+  // ---- device: pattern and maps ----
+  DevBuf d_rowptr, d_col, d_diagpos, d_nodes, d_state, d_rowid, d_rowid_static, d_smap, d_asm;
+  DevBuf d_cbmap;                    // per front: parent row of each contribution row (ld entries)
+  DevBuf d_q, d_kval;                // scaling diag(Q) and scaled K values (FP64)
+  DevBuf d_front;                    // front arena (float or double)
+  int front_prec = -1;               // precision the arena was sized for
+  DevBuf d_flags;                    // int flags: [0] delay overflow, [1] numeric error
+  DevBuf d_lam2pos;                  // L ints: position in Lambda_2 or -1
+  DevBuf d_lam2;                     // M ints ascending
+  DevBuf d_vec;                      // per-front solve vectors
+  size_t vec_cap = 0;
+  // ---- split (host copy) ----
+  bool factored = false, schured = false;
+  int prec = HF_PREC_MIXED;
+  double tau = 1e-2;
+  int64_t N = 0, M = 0, n_lambda0 = 0;
+  std::vector<int32_t> lambda2;      // ascending
+  std::vector<NodeState> state_host;
+  // ---- Schur / Krylov (device, FP64) ----
+  DevBuf d_x12, d_s22, d_bk_lf, d_bk_perm, d_bk_blk, d_bk_dval, d_bk_null;
+  int kernel_dim = 0;
+  int gcr_iters = 0, solve_iters = 0;
+  double gcr_relres = 0, solve_relres = 0;
+  int64_t nnz_factor = 0;
+  DevBuf d_work;                     // Krylov workspace
+  size_t work_cap = 0;
+  DevBuf d_small;                    // small matrices / partial sums
+  size_t small_cap = 0;
+  DevBuf d_gsmall;                   // block GCR small matrices (M_n, coefficients)
+  DevBuf d_k12;                      // K12 block (L x M), the right-hand sides of Alg. 1 step 3
+  DevBuf d_solve;                    // hf_solve scratch
+};
+
+// analyze.cpp
+int hf_analyze_impl(int64_t L, const int64_t* rowptr, const int32_t* col, const double* coords,
+                    int dim, const hf_opts* opts, hf_ctx** out);
+void hf_layout_fronts(hf_ctx* c);   // capacities, ld, offsets (depends on opts.delay_cap)

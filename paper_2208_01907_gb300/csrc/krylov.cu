@@ -1,0 +1,978 @@
+// Alg. 1 steps 2-5 and Alg. 2 on the GPU:
+//  - the lower-precision solve Q^-1 (Sec. 3.1-3.2) as a multifrontal forward /
+//    backward substitution over the fronts of the factorization,
+//  - block GCR ("Algorithm 5", Sec. 3.5) in FP64 with SpMM by K11,
+//  - S22 = K22 - K21 X12 (Alg. 1 step 4), Bunch-Kaufman LDL^T of S22 with kernel
+//    detection (Alg. 1 step 5), and the block substitution of Alg. 2.
+// Vectors are row-major L x m blocks (the m right-hand sides of a row contiguous),
+// indexed by original unknown; rows of Lambda_2 are kept at zero in K11 blocks.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+namespace {
+
+constexpr int SB = 32;       // column block of the triangular solves
+
+// ---------------------------------------------------------------------------
+// Multifrontal forward substitution, one CTA per front (levels bottom-up).
+// V_t rows [0, n) start from b, the other rows from 0; the children's update
+// rows are added; then y = L11^-1 V over the K11 columns [0, ksolve) with the
+// contribution rows updated on the way.  Pivot rows leave y_i / d_i (the D^-1
+// step) in the global array Y; rows of Lambda_2 leave their value unscaled.
+// ---------------------------------------------------------------------------
+template <typename TF, typename TV>
+__global__ void k_fwd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                      const TF* __restrict__ arena, const int32_t* __restrict__ rowid,
+                      const int32_t* __restrict__ cbmap, TV* __restrict__ vec, const TV* __restrict__ B,
+                      TV* __restrict__ Y, int m) {
+  __shared__ TF Ls[SB][SB + 1];
+  const int t = t0 + blockIdx.x;
+  const NodeDesc d = nd[t];
+  const NodeState S = st[t];
+  const int f = S.f, k = S.k, ks = S.ksolve;
+  const int64_t ld = d.ld;
+  const TF* F = arena + d.front_off;
+  const int32_t* rid = rowid + d.row_off;
+  TV* V = vec + d.row_off * m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nown = d.cand_all ? 0 : d.n;
+  for (int e = tid; e < f * m; e += nt) {
+    int i = e / m, c = e - i * m;
+    V[e] = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
+  }
+  __syncthreads();
+  for (int slot = 0; slot < 2; ++slot) {
+    const int ch = slot == 0 ? d.child0 : d.child1;
+    if (ch < 0) continue;
+    const NodeDesc dc = nd[ch];
+    const int kc = st[ch].k, mc = st[ch].f - kc;
+    const TV* U = vec + (dc.row_off + kc) * m;
+    const int32_t* map = cbmap + dc.row_off;
+    for (int e = tid; e < mc * m; e += nt) {
+      int a = e / m, c = e - a * m;
+      int tg = map[a];
+      if (tg >= 0) V[(int64_t)tg * m + c] += U[e];
+    }
+    __syncthreads();
+  }
+  for (int j0 = 0; j0 < ks; j0 += SB) {
+    const int jb = min(SB, ks - j0);
+    for (int e = tid; e < SB * SB; e += nt) {
+      int r = e % SB, c = e / SB;
+      Ls[r][c] = (r < jb && c < jb && r > c) ? F[(j0 + r) + (j0 + c) * ld] : TF(0);
+    }
+    __syncthreads();
+    // triangular block: one thread per right-hand side
+    for (int c = tid; c < m; c += nt) {
+      for (int r = 1; r < jb; ++r) {
+        TV acc = V[(int64_t)(j0 + r) * m + c];
+        for (int q = 0; q < r; ++q) acc -= (TV)Ls[r][q] * V[(int64_t)(j0 + q) * m + c];
+        V[(int64_t)(j0 + r) * m + c] = acc;
+      }
+    }
+    __syncthreads();
+    // rows below the block
+    for (int e = tid; e < (f - j0 - jb) * m; e += nt) {
+      int i = j0 + jb + e / m, c = e % m;
+      TV acc = V[(int64_t)i * m + c];
+      for (int q = 0; q < jb; ++q) acc -= (TV)F[i + (j0 + q) * ld] * V[(int64_t)(j0 + q) * m + c];
+      V[(int64_t)i * m + c] = acc;
+    }
+    __syncthreads();
+  }
+  // pivots of K11: y_i / d_i; moved pivots and unfactorized Lambda_0 rows: value as is
+  const int hi = d.cand_all ? f : k;
+  for (int e = tid; e < hi * m; e += nt) {
+    int i = e / m, c = e - i * m;
+    TV v = V[e];
+    if (i < ks) v = v / (TV)F[i + i * ld];
+    Y[(int64_t)rid[i] * m + c] = v;
+  }
+}
+
+// Backward substitution, one CTA per front (levels top-down): rows [ks, f) take the
+// solution of later unknowns from X (ancestors, or Lambda_2 values), then
+// x = L11^-T (y - L21^T x2) on [0, ks).
+template <typename TF, typename TV>
+__global__ void k_bwd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                      const TF* __restrict__ arena, const int32_t* __restrict__ rowid, TV* __restrict__ vec,
+                      const TV* __restrict__ Y, TV* __restrict__ X, int m) {
+  __shared__ TF Ls[SB][SB + 1];
+  const int t = t0 + blockIdx.x;
+  const NodeDesc d = nd[t];
+  const NodeState S = st[t];
+  const int f = S.f, ks = S.ksolve;
+  if (ks == 0) return;
+  const int64_t ld = d.ld;
+  const TF* F = arena + d.front_off;
+  const int32_t* rid = rowid + d.row_off;
+  TV* V = vec + d.row_off * m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < f * m; e += nt) {
+    int i = e / m, c = e - i * m;
+    V[e] = (i < ks) ? Y[(int64_t)rid[i] * m + c] : X[(int64_t)rid[i] * m + c];
+  }
+  __syncthreads();
+  // w_j -= sum_{i >= ks} L(i, j) x_i
+  if (f > ks) {
+    for (int e = tid; e < ks * m; e += nt) {
+      int j = e / m, c = e - j * m;
+      TV acc = V[e];
+      const TF* col = F + j * ld;
+      for (int i = ks; i < f; ++i) acc -= (TV)col[i] * V[(int64_t)i * m + c];
+      V[e] = acc;
+    }
+    __syncthreads();
+  }
+  // blocks from the bottom
+  for (int j1 = ks; j1 > 0; j1 -= SB) {
+    const int j0 = max(0, j1 - SB), jb = j1 - j0;
+    for (int e = tid; e < SB * SB; e += nt) {
+      int r = e % SB, c = e / SB;
+      Ls[r][c] = (r < jb && c < jb && r > c) ? F[(j0 + r) + (j0 + c) * ld] : TF(0);
+    }
+    __syncthreads();
+    for (int c = tid; c < m; c += nt) {
+      for (int r = jb - 2; r >= 0; --r) {
+        TV acc = V[(int64_t)(j0 + r) * m + c];
+        for (int q = r + 1; q < jb; ++q) acc -= (TV)Ls[q][r] * V[(int64_t)(j0 + q) * m + c];
+        V[(int64_t)(j0 + r) * m + c] = acc;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < j0 * m; e += nt) {
+      int j = e / m, c = e - j * m;
+      TV acc = V[e];
+      const TF* col = F + j * ld;
+      for (int q = 0; q < jb; ++q) acc -= (TV)col[j0 + q] * V[(int64_t)(j0 + q) * m + c];
+      V[e] = acc;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < ks * m; e += nt) {
+    int i = e / m, c = e - i * m;
+    X[(int64_t)rid[i] * m + c] = V[e];
+  }
+}
+
+// r (FP64) -> lower precision with Lambda_2 rows zeroed (the cast of Sec. 3.1)
+template <typename TV>
+__global__ void k_cast_in(int64_t n, int m, const double* __restrict__ R, const int32_t* __restrict__ lam2pos,
+                          TV* __restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * m) return;
+  int64_t i = e / m;
+  out[e] = (lam2pos && lam2pos[i] >= 0) ? TV(0) : (TV)R[e];
+}
+
+template <typename TV>
+__global__ void k_cast_out(int64_t n, int m, const TV* __restrict__ Xl, const int32_t* __restrict__ lam2pos,
+                           double* __restrict__ W) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * m) return;
+  int64_t i = e / m;
+  W[e] = (lam2pos && lam2pos[i] >= 0) ? 0.0 : (double)Xl[e];
+}
+
+// set X rows of Lambda_2 from x2 (M x m) or to zero
+template <typename TV>
+__global__ void k_set_lam2(int M, int m, const int32_t* __restrict__ lam2, const double* __restrict__ x2,
+                           TV* __restrict__ X) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * m) return;
+  int i = e / m, c = e - i * m;
+  X[(int64_t)lam2[i] * m + c] = x2 ? (TV)x2[e] : TV(0);
+}
+
+template <typename TV>
+__global__ void k_get_lam2(int M, int m, const int32_t* __restrict__ lam2, const TV* __restrict__ Y,
+                           double* __restrict__ y2) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * m) return;
+  int i = e / m, c = e - i * m;
+  y2[e] = (double)Y[(int64_t)lam2[i] * m + c];
+}
+
+// ---------------------------------------------------------------------------
+// SpMM Z = K11 W (FP64, Sec. 3.5): one warp per row, lanes over the rhs
+// ---------------------------------------------------------------------------
+__global__ void k_spmm(int64_t L, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const int32_t* __restrict__ lam2pos,
+                       const double* __restrict__ W, double* __restrict__ Z) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= L) return;
+  const bool skip = lam2pos[row] >= 0;
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    int c = c0 + lane;
+    double acc = 0.0;
+    if (!skip) {
+      for (int64_t e = rowptr[row]; e < rowptr[row + 1]; ++e) {
+        int j = col[e];
+        if (c < m) acc += val[e] * W[(int64_t)j * m + c];
+      }
+    }
+    if (c < m) Z[row * m + c] = acc;
+  }
+}
+
+// R = B - Z (elementwise)
+__global__ void k_sub(int64_t n, const double* __restrict__ B, const double* __restrict__ Z, double* __restrict__ R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) R[e] = B[e] - Z[e];
+}
+
+// ---------------------------------------------------------------------------
+// Block Gram G = A^T B (A: L x ma, B: L x mb, row-major), two-stage deterministic
+// ---------------------------------------------------------------------------
+constexpr int GR = 32;     // rows per tile
+constexpr int GO = 32;     // output block edge
+
+__global__ void k_gram_partial(int64_t L, int ma, int mb, const double* __restrict__ A, const double* __restrict__ B,
+                               double* __restrict__ part, int nchunks) {
+  __shared__ double As[GR][GO + 1];
+  __shared__ double Bs[GR][GO + 1];
+  const int ob = blockIdx.y;                       // output block
+  const int nbb = (mb + GO - 1) / GO;
+  const int a0 = (ob / nbb) * GO, b0 = (ob % nbb) * GO;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  double acc[4] = {0, 0, 0, 0};
+  const int64_t rows_per = (L + nchunks - 1) / nchunks;
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per, r_end = min(L, r_begin + rows_per);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += GR) {
+    for (int e = threadIdx.x; e < GR * GO; e += blockDim.x) {
+      int rr = e / GO, cc = e % GO;
+      int64_t r = r0 + rr;
+      As[rr][cc] = (r < r_end && a0 + cc < ma) ? A[r * ma + a0 + cc] : 0.0;
+      Bs[rr][cc] = (r < r_end && b0 + cc < mb) ? B[r * mb + b0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < GR; ++rr) {
+      double bv = Bs[rr][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += As[rr][ty + 8 * q] * bv;
+    }
+    __syncthreads();
+  }
+  double* P = part + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * GO * GO;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) P[(ty + 8 * q) * GO + tx] = acc[q];
+}
+
+__global__ void k_gram_reduce(int ma, int mb, int nchunks, const double* __restrict__ part, double* __restrict__ G,
+                              double scale) {
+  const int nbb = (mb + GO - 1) / GO;
+  const int nob = ((ma + GO - 1) / GO) * nbb;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nob * GO * GO) return;
+  int ob = e / (GO * GO), w = e % (GO * GO);
+  int a = (ob / nbb) * GO + w / GO, b = (ob % nbb) * GO + w % GO;
+  if (a >= ma || b >= mb) return;
+  double s = 0.0;
+  const double* P = part + (int64_t)ob * nchunks * GO * GO + w;
+  for (int c = 0; c < nchunks; ++c) s += P[(int64_t)c * GO * GO];
+  G[a * mb + b] = scale * s;
+}
+
+// ---------------------------------------------------------------------------
+// Small SPD solve C = Mg^-1 Y (m x m) by Cholesky; a pivot that falls below
+// 1e-13 of its own diagonal marks a dependent direction, which is dropped
+// (its coefficients are zero).  One CTA.
+// ---------------------------------------------------------------------------
+__global__ void k_small_solve(int m, int ny, const double* __restrict__ Mg, const double* __restrict__ Y,
+                              double* __restrict__ C, double* __restrict__ work) {
+  double* R = work;                 // m x m
+  int* drop = (int*)(work + m * m);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += blockDim.x) R[e] = Mg[e];
+  for (int e = tid; e < m * ny; e += blockDim.x) C[e] = Y[e];
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    // R(j, j) = sqrt(M_jj - sum_k R(k, j)^2)
+    if (tid == 0) {
+      double s = Mg[j * m + j];
+      for (int k = 0; k < j; ++k) s -= R[k * m + j] * R[k * m + j];
+      double ref = Mg[j * m + j];
+      bool dz = !(s > 1e-13 * ref) || !(ref > 0);
+      drop[j] = dz;
+      R[j * m + j] = dz ? 0.0 : sqrt(s);
+    }
+    __syncthreads();
+    const double rjj = R[j * m + j];
+    for (int l = j + 1 + tid; l < m; l += blockDim.x) {
+      double s = Mg[j * m + l];
+      for (int k = 0; k < j; ++k) s -= R[k * m + j] * R[k * m + l];
+      R[j * m + l] = drop[j] ? 0.0 : s / rjj;
+    }
+    __syncthreads();
+  }
+  // R^T z = y (forward), R c = z (backward), per column of Y
+  for (int c = tid; c < ny; c += blockDim.x) {
+    for (int j = 0; j < m; ++j) {
+      double s = C[j * ny + c];
+      for (int k = 0; k < j; ++k) s -= R[k * m + j] * C[k * ny + c];
+      C[j * ny + c] = drop[j] ? 0.0 : s / R[j * m + j];
+    }
+    for (int j = m - 1; j >= 0; --j) {
+      double s = C[j * ny + c];
+      for (int k = j + 1; k < m; ++k) s -= R[j * m + k] * C[k * ny + c];
+      C[j * ny + c] = drop[j] ? 0.0 : s / R[j * m + j];
+    }
+  }
+}
+
+// Y(+)= sgn * A C  (A: L x m, C: m x m); when Yinit is given Y = Yinit + sgn * A C
+__global__ void k_block_axpy(int64_t L, int m, const double* __restrict__ A, const double* __restrict__ Cm,
+                             double* __restrict__ Y, const double* __restrict__ Yinit, double sgn, int use_smem) {
+  extern __shared__ double Csm[];
+  const double* Cs = Cm;
+  if (use_smem) {
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Csm[e] = Cm[e];
+    __syncthreads();
+    Cs = Csm;
+  }
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * m) return;
+  int64_t i = e / m;
+  int c = (int)(e - i * m);
+  double s = 0.0;
+  const double* a = A + i * m;
+  for (int k = 0; k < m; ++k) s += a[k] * Cs[k * m + c];
+  Y[e] = (Yinit ? Yinit[e] : Y[e]) + sgn * s;
+}
+
+// ---------------------------------------------------------------------------
+// K12 block (Alg. 1 step 2): B[j, c] = K[j, lam2[c]] for j in Lambda_1 (K symmetric)
+// ---------------------------------------------------------------------------
+__global__ void k_extract_k12(int M, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              const double* __restrict__ val, const int32_t* __restrict__ lam2,
+                              const int32_t* __restrict__ lam2pos, double* __restrict__ B) {
+  int c = blockIdx.x;
+  int g = lam2[c];
+  for (int64_t e = rowptr[g] + threadIdx.x; e < rowptr[g + 1]; e += blockDim.x) {
+    int j = col[e];
+    if (lam2pos[j] < 0) B[(int64_t)j * M + c] = val[e];
+  }
+}
+
+// S = K22 - K21 X   (S: M x m; X: L x m row-major). One warp per Lambda_2 row.
+__global__ void k_schur_rows(int M, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const int32_t* __restrict__ lam2,
+                             const int32_t* __restrict__ lam2pos, const double* __restrict__ X,
+                             const double* __restrict__ Bbase, int64_t ldb, double* __restrict__ S) {
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= M) return;
+  int g = lam2[i];
+  for (int c0 = 0; c0 < m; c0 += 32) {
+    int c = c0 + lane;
+    double acc = 0.0;
+    if (c < m) {
+      if (Bbase) acc = Bbase[(int64_t)g * ldb + c];
+      for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+        int j = col[e];
+        int p = lam2pos[j];
+        if (p < 0) acc -= val[e] * X[(int64_t)j * m + c];
+        else if (!Bbase && p == c) acc += val[e];
+      }
+      S[i * m + c] = acc;
+    }
+  }
+}
+
+__global__ void k_symmetrize(int M, double* __restrict__ S) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * M) return;
+  int i = e / M, j = e % M;
+  if (j <= i) return;
+  double v = 0.5 * (S[i * M + j] + S[j * M + i]);
+  S[i * M + j] = v;
+  S[j * M + i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Bunch-Kaufman LDL^T of S22 (FP64, alpha = (1+sqrt 17)/8) and kernel detection.
+// One CTA; A is the full symmetric working copy (M x M row-major).
+// ---------------------------------------------------------------------------
+__device__ void bk_block_reduce_max(double& v, int& idx, double* rv, int* ri) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = v; ri[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w)
+      if (rv[w] > v || (rv[w] == v && ri[w] < idx)) { v = rv[w]; idx = ri[w]; }
+    rv[0] = v; ri[0] = idx;
+  }
+  __syncthreads();
+  v = rv[0]; idx = ri[0];
+  __syncthreads();
+}
+
+__global__ void k_bunch_kaufman(int M, double* __restrict__ A, double* __restrict__ Lf, int* __restrict__ perm,
+                                int* __restrict__ blk, double* __restrict__ dval, int* __restrict__ nullp,
+                                double kernel_eps, double kernel_gap, int* __restrict__ kdim_out,
+                                double* __restrict__ mags_work) {
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_size, s_swap_a, s_swap_b;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  for (int e = tid; e < M * M; e += nt) Lf[e] = ((e / M) == (e % M)) ? 1.0 : 0.0;
+  for (int i = tid; i < M; i += nt) { perm[i] = i; blk[i] = 0; dval[2 * i] = 0; dval[2 * i + 1] = 0; nullp[i] = 0; }
+  __syncthreads();
+  int k = 0;
+  while (k < M) {
+    // lambda = max_{i>k} |A(i,k)|, r its row
+    double lam = -1.0;
+    int r = 0x7fffffff;
+    for (int i = k + 1 + tid; i < M; i += nt) {
+      double v = fabs(A[i * M + k]);
+      if (v > lam || (v == lam && i < r)) { lam = v; r = i; }
+    }
+    bk_block_reduce_max(lam, r, rv, ri);
+    if (lam < 0) { lam = 0.0; r = k; }
+    const double akk = fabs(A[k * M + k]);
+    double sigma = 0.0;
+    bool need_sigma = !(max(akk, lam) == 0.0) && !(akk >= alpha * lam);
+    if (need_sigma) {
+      double sg = -1.0;
+      int dummy = 0;
+      for (int j = k + tid; j < M; j += nt)
+        if (j != r) { double v = fabs(A[r * M + j]); if (v > sg) sg = v; }
+      bk_block_reduce_max(sg, dummy, rv, ri);
+      sigma = max(sg, 0.0);
+    }
+    if (tid == 0) {
+      int size = 1, sa = k, sb = k;
+      if (max(akk, lam) == 0.0 || akk >= alpha * lam) {
+      } else if (akk * sigma >= alpha * lam * lam) {
+      } else if (fabs(A[r * M + r]) >= alpha * sigma) {
+        sa = k; sb = r;
+      } else {
+        size = 2; sa = k + 1; sb = r;
+      }
+      s_size = size; s_swap_a = sa; s_swap_b = sb;
+    }
+    __syncthreads();
+    const int size = s_size, sa = s_swap_a, sb = s_swap_b;
+    if (sa != sb) {
+      for (int j = tid; j < M; j += nt) { double tmp = A[sa * M + j]; A[sa * M + j] = A[sb * M + j]; A[sb * M + j] = tmp; }
+      __syncthreads();
+      for (int i = tid; i < M; i += nt) { double tmp = A[i * M + sa]; A[i * M + sa] = A[i * M + sb]; A[i * M + sb] = tmp; }
+      for (int j = tid; j < sa; j += nt) { double tmp = Lf[sa * M + j]; Lf[sa * M + j] = Lf[sb * M + j]; Lf[sb * M + j] = tmp; }
+      if (tid == 0) { int tp = perm[sa]; perm[sa] = perm[sb]; perm[sb] = tp; }
+      __syncthreads();
+    }
+    if (size == 1) {
+      const double dk = A[k * M + k];
+      if (tid == 0) { blk[k] = 1; dval[2 * k] = dk; }
+      if (dk != 0.0) {
+        for (int i = k + 1 + tid; i < M; i += nt) Lf[i * M + k] = A[i * M + k] / dk;
+        __syncthreads();
+        const int n2 = M - k - 1;
+        for (int e = tid; e < n2 * n2; e += nt) {
+          int i = k + 1 + e / n2, j = k + 1 + e % n2;
+          A[i * M + j] -= Lf[i * M + k] * A[j * M + k];
+        }
+      }
+      __syncthreads();
+      k += 1;
+    } else {
+      const double a = A[k * M + k], b = A[(k + 1) * M + k], c = A[(k + 1) * M + k + 1];
+      const double det = a * c - b * b;
+      if (tid == 0) { blk[k] = 2; blk[k + 1] = 0; dval[2 * k] = a; dval[2 * k + 1] = b; dval[2 * (k + 1)] = c; }
+      for (int i = k + 2 + tid; i < M; i += nt) {
+        double x0 = A[i * M + k], x1 = A[i * M + k + 1];
+        Lf[i * M + k] = (x0 * c - x1 * b) / det;
+        Lf[i * M + k + 1] = (x1 * a - x0 * b) / det;
+      }
+      __syncthreads();
+      const int n2 = M - k - 2;
+      for (int e = tid; e < n2 * n2; e += nt) {
+        int i = k + 2 + e / n2, j = k + 2 + e % n2;
+        A[i * M + j] -= Lf[i * M + k] * A[j * M + k] + Lf[i * M + k + 1] * A[j * M + k + 1];
+      }
+      __syncthreads();
+      k += 2;
+    }
+  }
+  // kernel detection (reading R10): magnitudes per 1x1 pivot / 2x2 eigenvalue
+  if (tid == 0) {
+    double* mg = mags_work;          // M magnitudes, then M sorted copies
+    for (int i = 0; i < M;) {
+      if (blk[i] == 1) { mg[i] = fabs(dval[2 * i]); ++i; }
+      else {
+        double a = dval[2 * i], b = dval[2 * i + 1], c = dval[2 * (i + 1)];
+        double mean = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + b * b);
+        mg[i] = fabs(mean + rad); mg[i + 1] = fabs(mean - rad);
+        i += 2;
+      }
+    }
+    double* s = mg + M;
+    for (int i = 0; i < M; ++i) s[i] = mg[i];
+    for (int i = 1; i < M; ++i) {               // insertion sort, descending
+      double v = s[i]; int j = i - 1;
+      while (j >= 0 && s[j] < v) { s[j + 1] = s[j]; --j; }
+      s[j + 1] = v;
+    }
+    int dim = 0;
+    if (M > 0) {
+      if (s[0] == 0.0) dim = M;
+      else {
+        double best = 0.0;
+        for (int i = 1; i < M; ++i) {
+          if (s[i] > kernel_eps * s[0]) continue;
+          double ratio = (s[i] == 0.0) ? INFINITY : s[i - 1] / s[i];
+          if (ratio >= kernel_gap && ratio > best) { best = ratio; dim = M - i; }
+        }
+      }
+    }
+    *kdim_out = dim;
+    // mark the `dim` smallest magnitudes as null pivots (ties: later position first)
+    for (int cnt = 0; cnt < dim; ++cnt) {
+      int bi = -1; double bv = INFINITY;
+      for (int i = 0; i < M; ++i)
+        if (!nullp[i] && (mg[i] < bv || (mg[i] == bv && i > bi))) { bv = mg[i]; bi = i; }
+      if (bi >= 0) nullp[bi] = 1;
+    }
+  }
+}
+
+// x = S22^+ y with null pivots treated as zero; y, x: M x m row-major. One CTA.
+__global__ void k_bk_solve(int M, int m, const double* __restrict__ Lf, const int* __restrict__ perm,
+                           const int* __restrict__ blk, const double* __restrict__ dval, const int* __restrict__ nullp,
+                           const double* __restrict__ y, double* __restrict__ x, double* __restrict__ z) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    for (int i = 0; i < M; ++i) z[i * m + c] = y[perm[i] * m + c];
+    for (int i = 0; i < M; ++i) {
+      double s = z[i * m + c];
+      for (int j = 0; j < i; ++j) s -= Lf[i * M + j] * z[j * m + c];
+      z[i * m + c] = s;
+    }
+    for (int i = 0; i < M;) {
+      if (blk[i] == 1) {
+        double dd = dval[2 * i];
+        z[i * m + c] = (nullp[i] || dd == 0.0) ? 0.0 : z[i * m + c] / dd;
+        ++i;
+      } else {
+        double a = dval[2 * i], b = dval[2 * i + 1], cc = dval[2 * (i + 1)];
+        double mean = 0.5 * (a + cc), rad = sqrt(0.25 * (a - cc) * (a - cc) + b * b);
+        double ev[2] = {mean + rad, mean - rad};
+        // eigenvectors of [[a b][b cc]]
+        double v[2][2];
+        for (int q = 0; q < 2; ++q) {
+          double vx = b, vy = ev[q] - a;
+          if (fabs(vx) + fabs(vy) < 1e-300) { vx = ev[q] - cc; vy = b; }
+          if (fabs(vx) + fabs(vy) < 1e-300) { vx = (q == 0) ? 1.0 : 0.0; vy = (q == 0) ? 0.0 : 1.0; }
+          double nr = sqrt(vx * vx + vy * vy);
+          v[q][0] = vx / nr; v[q][1] = vy / nr;
+        }
+        double z0 = z[i * m + c], z1 = z[(i + 1) * m + c];
+        double o0 = 0.0, o1 = 0.0;
+        for (int q = 0; q < 2; ++q) {
+          if (nullp[i + q] || ev[q] == 0.0) continue;
+          double pr = (v[q][0] * z0 + v[q][1] * z1) / ev[q];
+          o0 += v[q][0] * pr; o1 += v[q][1] * pr;
+        }
+        z[i * m + c] = o0; z[(i + 1) * m + c] = o1;
+        i += 2;
+      }
+    }
+    for (int i = M - 1; i >= 0; --i) {
+      double s = z[i * m + c];
+      for (int j = i + 1; j < M; ++j) s -= Lf[j * M + i] * z[j * m + c];
+      z[i * m + c] = s;
+    }
+    for (int i = 0; i < M; ++i) x[perm[i] * m + c] = z[i * m + c];
+  }
+}
+
+// x1 = y1 - X12 x2 on Lambda_1 rows; Lambda_2 rows = x2
+__global__ void k_backsub_x1(int64_t L, int M, int m, const double* __restrict__ X12, const double* __restrict__ x2,
+                             const int32_t* __restrict__ lam2pos, double* __restrict__ Y) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * m) return;
+  int64_t i = e / m;
+  int c = (int)(e - i * m);
+  int p = lam2pos[i];
+  if (p >= 0) { Y[e] = x2[p * m + c]; return; }
+  double s = Y[e];
+  for (int k = 0; k < M; ++k) s -= X12[i * M + k] * x2[k * m + c];
+  Y[e] = s;
+}
+
+// user column-major b (ldb) -> internal row-major Q b ;  and back: x_user = Q x
+__global__ void k_scale_in(int64_t L, int m, const double* __restrict__ b, int64_t ldb, const double* __restrict__ q,
+                           double* __restrict__ out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * m) return;
+  int64_t i = e / m;
+  int c = (int)(e - i * m);
+  out[e] = q[i] * b[i + c * ldb];
+}
+
+__global__ void k_scale_out(int64_t L, int m, const double* __restrict__ xin, const double* __restrict__ q,
+                            double* __restrict__ x, int64_t ldx) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * m) return;
+  int64_t i = e % L;
+  int c = (int)(e / L);
+  x[i + c * ldx] = q[i] * xin[i * m + c];
+}
+
+__global__ void k_zero_lam2_rows(int M, int m, const int32_t* __restrict__ lam2, double* __restrict__ V) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * m) return;
+  V[(int64_t)lam2[e / m] * m + (e % m)] = 0.0;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+// ============================================================================
+// Host drivers
+// ============================================================================
+struct Work {
+  // Krylov workspace carved from ctx->d_work
+  double *X, *R, *W, *Z, *B;
+  double* P[64];
+  double* Qv[64];
+  double* Ms[64];
+  int slots;
+};
+
+static int ensure_vec(hf_ctx* c, int m, size_t esz) {
+  size_t need = (size_t)c->row_elems * m * esz + 64;
+  return hf_ensure(c->d_vec, need);
+}
+
+// Apply the triangular solves with the front factor (TF) in vector precision TV.
+//  mode 0: K11 preconditioner (Lambda_2 rows are zero in and out)
+//  mode 1: full solve with S22 handled by the BK factors (non-mixed forms)
+template <typename TF, typename TV>
+static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const double* x2_dev, bool full,
+                     double* y2_dev) {
+  cudaStream_t s = hf_stream(c);
+  const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
+  const NodeState* st = (const NodeState*)c->d_state.p;
+  const TF* arena = (const TF*)c->d_front.p;
+  const int32_t* rowid = (const int32_t*)c->d_rowid.p;
+  const int32_t* cbmap = (const int32_t*)c->d_cbmap.p;
+  TV* vec = (TV*)c->d_vec.p;
+  for (int lev = c->m; lev >= 0; --lev) {
+    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+    k_fwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, cbmap, vec, Bin, Ytmp, m);
+  }
+  HF_CUDA_TRY(cudaGetLastError());
+  const int M = (int)c->M;
+  if (M) {
+    if (full) {
+      k_get_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, Ytmp, y2_dev);
+      return 1;   // caller solves S22 and calls tri_solve_back
+    }
+    k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, nullptr, Xout);
+  }
+  for (int lev = 0; lev <= c->m; ++lev) {
+    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+    k_bwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, Xout, m);
+  }
+  HF_CUDA_TRY(cudaGetLastError());
+  (void)x2_dev;
+  return HF_OK;
+}
+
+template <typename TF, typename TV>
+static int tri_solve_back(hf_ctx* c, int m, TV* Ytmp, TV* Xout, const double* x2_dev) {
+  cudaStream_t s = hf_stream(c);
+  const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
+  const NodeState* st = (const NodeState*)c->d_state.p;
+  const TF* arena = (const TF*)c->d_front.p;
+  const int32_t* rowid = (const int32_t*)c->d_rowid.p;
+  TV* vec = (TV*)c->d_vec.p;
+  const int M = (int)c->M;
+  if (M) k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, x2_dev, Xout);
+  for (int lev = 0; lev <= c->m; ++lev) {
+    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+    k_bwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, Xout, m);
+  }
+  HF_CUDA_TRY(cudaGetLastError());
+  return HF_OK;
+}
+
+// Gram G = scale * A^T B
+static int gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale) {
+  cudaStream_t s = hf_stream(c);
+  const int nob = ((ma + GO - 1) / GO) * ((mb + GO - 1) / GO);
+  int nchunks = (int)std::min<int64_t>(std::max<int64_t>(1, L / 256), 304);
+  size_t need = (size_t)nob * nchunks * GO * GO * 8 + 64;
+  int rc = hf_ensure(c->d_small, std::max(need, (size_t)(1 << 20)));
+  if (rc) return rc;
+  k_gram_partial<<<dim3(nchunks, nob), 256, 0, s>>>(L, ma, mb, A, B, (double*)c->d_small.p, nchunks);
+  k_gram_reduce<<<nblk((int64_t)nob * GO * GO, 256), 256, 0, s>>>(ma, mb, nchunks, (const double*)c->d_small.p, G, scale);
+  HF_CUDA_TRY(cudaGetLastError());
+  return HF_OK;
+}
+
+// K11-preconditioner application W = Q^-1 R (FP32 factor) or exact (FP64 factor)
+static int precond(hf_ctx* c, int m, const double* R, double* W, void* tmp32) {
+  cudaStream_t s = hf_stream(c);
+  const int64_t L = c->L;
+  const int32_t* l2p = (const int32_t*)c->d_lam2pos.p;
+  if (c->prec == HF_PREC_FP64) {
+    double* y = (double*)tmp32;
+    int rc;
+    if ((rc = ensure_vec(c, m, 8))) return rc;
+    HF_CUDA_TRY(cudaMemcpyAsync(W, R, L * m * 8, cudaMemcpyDeviceToDevice, s));
+    k_zero_lam2_rows<<<nblk(c->M * m, 256), 256, 0, s>>>((int)c->M, m, (const int32_t*)c->d_lam2.p, W);
+    rc = tri_solve<double, double>(c, m, W, y, W, nullptr, false, nullptr);
+    return rc;
+  }
+  float* b32 = (float*)tmp32;
+  float* y32 = b32 + L * m;
+  float* x32 = y32 + L * m;
+  int rc;
+  if ((rc = ensure_vec(c, m, 4))) return rc;
+  k_cast_in<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, R, l2p, b32);
+  if ((rc = tri_solve<float, float>(c, m, b32, y32, x32, nullptr, false, nullptr))) return rc;
+  k_cast_out<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, x32, l2p, W);
+  HF_CUDA_TRY(cudaGetLastError());
+  return HF_OK;
+}
+
+static void spmm(hf_ctx* c, int m, const double* W, double* Z) {
+  cudaStream_t s = hf_stream(c);
+  k_spmm<<<nblk(c->L * 32, 256), 256, 0, s>>>(c->L, m, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
+                                              (const double*)c->d_kval.p, (const int32_t*)c->d_lam2pos.p, W, Z);
+}
+
+// Block GCR for K11 X = B (Sec. 3.5, readings R7/R8).  B, X: L x m row-major, Lambda_2 rows 0.
+static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, double* relres) {
+  cudaStream_t s = hf_stream(c);
+  const int64_t L = c->L;
+  const int maxit = std::max(1, c->opts.gcr_maxit);
+  const size_t blk = (size_t)L * m;
+  // workspace: R, W, Z, tmp(3 x L x m floats or 1 x L x m doubles), 2 * (maxit+1) history blocks
+  const size_t tmp_doubles = (blk * 3 + 1) / 2 + blk;
+  size_t need = (blk * 3 + tmp_doubles + blk * 2 * (size_t)(maxit + 1)) * 8 + 1024;
+  int rc;
+  if ((rc = hf_ensure(c->d_work, need))) return rc;
+  double* base = (double*)c->d_work.p;
+  double* R = base;
+  double* W = R + blk;
+  double* Z = W + blk;
+  double* tmp = Z + blk;
+  double* hist = tmp + tmp_doubles;
+  auto Pm = [&](int i) { return hist + (size_t)(2 * i) * blk; };
+  auto Qm = [&](int i) { return hist + (size_t)(2 * i + 1) * blk; };
+  // small matrices in pinned / device memory
+  const size_t mm = (size_t)m * m;
+  std::vector<double> hnorm(m), bnorm(m);
+  DevBuf& sm = c->d_gsmall;
+  size_t small_need = ((size_t)(maxit + 2) * mm * 2 + 4 * mm + 2 * (size_t)m + 64) * 8 + (mm + m) * 8;
+  if ((rc = hf_ensure(sm, small_need))) return rc;
+  double* Mstore = (double*)sm.p;                 // (maxit+1) Gram matrices M_n
+  double* Gm = Mstore + (size_t)(maxit + 1) * mm;
+  double* Cm = Gm + mm;
+  double* wk = Cm + mm;                           // small solve work (m*m + m)
+  double* diag = wk + mm + m + 8;                 // m x m scratch for norms
+  const unsigned nb = nblk((int64_t)blk, 256);
+  const int use_smem = mm * 8 <= 48 * 1024;
+  const size_t axpy_smem = use_smem ? mm * 8 : 0;
+
+  auto colnorms = [&](const double* A, std::vector<double>& out) -> int {
+    int r = gram(c, L, m, m, A, A, diag, 1.0);
+    if (r) return r;
+    std::vector<double> g(mm);
+    HF_CUDA_TRY(cudaMemcpyAsync(g.data(), diag, mm * 8, cudaMemcpyDeviceToHost, s));
+    HF_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < m; ++i) out[i] = std::sqrt(std::max(0.0, g[i * m + i]));
+    return HF_OK;
+  };
+  if ((rc = colnorms(B, bnorm))) return rc;
+  for (auto& v : bnorm) if (v == 0) v = 1.0;
+  // X0 = Q^-1 B, R0 = B - K11 X0, W0 = Q^-1 R0, P0 = W0, Q0 = K11 P0
+  if ((rc = precond(c, m, B, X, tmp))) return rc;
+  spmm(c, m, X, Z);
+  k_sub<<<nb, 256, 0, s>>>((int64_t)blk, B, Z, R);
+  if ((rc = precond(c, m, R, Pm(0), tmp))) return rc;
+  spmm(c, m, Pm(0), Qm(0));
+  int it = 0;
+  double res = 0;
+  bool conv = false;
+  for (int n = 0; n < maxit; ++n) {
+    double* Mn = Mstore + (size_t)n * mm;
+    if ((rc = gram(c, L, m, m, Qm(n), Qm(n), Mn, 1.0))) return rc;
+    if ((rc = gram(c, L, m, m, Qm(n), R, Gm, 1.0))) return rc;
+    k_small_solve<<<1, 256, 0, s>>>(m, m, Mn, Gm, Cm, wk);
+    k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(n), Cm, X, nullptr, 1.0, use_smem);
+    k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Qm(n), Cm, R, nullptr, -1.0, use_smem);
+    HF_CUDA_TRY(cudaGetLastError());
+    it = n + 1;
+    if ((rc = colnorms(R, hnorm))) return rc;
+    res = 0;
+    for (int i = 0; i < m; ++i) res = std::max(res, hnorm[i] / bnorm[i]);
+    if (!(res > c->opts.gcr_tol)) { conv = true; break; }
+    if (n + 1 >= maxit) break;
+    if ((rc = precond(c, m, R, W, tmp))) return rc;
+    spmm(c, m, W, Z);
+    double* Pn = Pm(n + 1);
+    double* Qn = Qm(n + 1);
+    for (int q = 0; q <= n; ++q) {
+      if ((rc = gram(c, L, m, m, Qm(q), Z, Gm, -1.0))) return rc;      // B_qn = -Q_q^T Z
+      k_small_solve<<<1, 256, 0, s>>>(m, m, Mstore + (size_t)q * mm, Gm, Cm, wk);
+      k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0, use_smem);
+      k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Qm(q), Cm, Qn, q == 0 ? Z : nullptr, 1.0, use_smem);
+    }
+    HF_CUDA_TRY(cudaGetLastError());
+  }
+  *iters = it;
+  *relres = res;
+  return conv ? HF_OK : HF_ERR_NOT_CONVERGED;
+}
+
+static int bk_factor(hf_ctx* c) {
+  cudaStream_t s = hf_stream(c);
+  const int M = (int)c->M;
+  int rc;
+  if ((rc = hf_ensure(c->d_bk_lf, (size_t)M * M * 8 * 2 + 64))) return rc;
+  if ((rc = hf_ensure(c->d_bk_perm, (size_t)M * 4 + 64))) return rc;
+  if ((rc = hf_ensure(c->d_bk_blk, (size_t)M * 4 + 64))) return rc;
+  if ((rc = hf_ensure(c->d_bk_dval, (size_t)M * 16 + 64 + (size_t)M * 16))) return rc;
+  if ((rc = hf_ensure(c->d_bk_null, (size_t)M * 4 + 64))) return rc;
+  if (M == 0) { c->kernel_dim = 0; return HF_OK; }
+  double* A = (double*)c->d_bk_lf.p + (size_t)M * M;     // working copy after Lf
+  HF_CUDA_TRY(cudaMemcpyAsync(A, c->d_s22.p, (size_t)M * M * 8, cudaMemcpyDeviceToDevice, s));
+  int* kd = (int*)((int*)c->d_flags.p + FLAG_COUNT + 8);
+  double* mags = (double*)c->d_bk_dval.p + 2 * M;
+  k_bunch_kaufman<<<1, 256, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
+                                    (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
+                                    c->opts.kernel_gap, kd, mags);
+  HF_CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  HF_CUDA_TRY(cudaMemcpyAsync(&h, kd, 4, cudaMemcpyDeviceToHost, s));
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  c->kernel_dim = h;
+  return HF_OK;
+}
+
+int hf_s22_from_factor(hf_ctx* c);
+
+int hf_schur_impl(hf_ctx* c) {
+  if (!c) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  cudaStream_t s = hf_stream(c);
+  const int M = (int)c->M;
+  const int64_t L = c->L;
+  int rc = HF_OK, grc = HF_OK;
+  c->gcr_iters = 0;
+  c->gcr_relres = 0;
+  if ((rc = hf_ensure(c->d_x12, (size_t)L * std::max(M, 1) * 8 + 64))) return rc;
+  if ((rc = hf_ensure(c->d_s22, (size_t)M * M * 8 + 64))) return rc;
+  if (M > 0) {
+    if (c->prec == HF_PREC_MIXED) {
+      // B = K12 (Alg. 1 step 2), X12 by block GCR (step 3), S22 = K22 - K21 X12 (step 4)
+      double* X12 = (double*)c->d_x12.p;
+      if ((rc = hf_ensure(c->d_k12, (size_t)L * M * 8 + 64))) return rc;
+      double* B = (double*)c->d_k12.p;
+      HF_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)L * M * 8, s));
+      k_extract_k12<<<M, 128, 0, s>>>(M, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
+                                      (const double*)c->d_kval.p, (const int32_t*)c->d_lam2.p,
+                                      (const int32_t*)c->d_lam2pos.p, B);
+      grc = block_gcr(c, M, B, X12, &c->gcr_iters, &c->gcr_relres);
+      if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
+      k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
+                                                          (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
+                                                          (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
+                                                          X12, nullptr, 0, (double*)c->d_s22.p);
+      k_symmetrize<<<nblk((int64_t)M * M, 256), 256, 0, s>>>(M, (double*)c->d_s22.p);
+      HF_CUDA_TRY(cudaGetLastError());
+    } else {
+      if ((rc = hf_s22_from_factor(c))) return rc;
+    }
+  }
+  if ((rc = bk_factor(c))) return rc;
+  c->schured = true;
+  return grc;
+}
+
+int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx) {
+  if (!c || nrhs < 1 || !b || !x || ldb < c->L || ldx < c->L) return HF_ERR_ARG;
+  if (!c->schured) return HF_ERR_STATE;
+  cudaStream_t s = hf_stream(c);
+  const int64_t L = c->L;
+  const int M = (int)c->M;
+  const int m = nrhs;
+  const size_t blk = (size_t)L * m;
+  int rc;
+  size_t need = (blk * 4 + (size_t)M * m * 3 + 64) * 8;
+  if ((rc = hf_ensure(c->d_solve, need))) return rc;
+  double* bi = (double*)c->d_solve.p;
+  double* y = bi + blk;
+  double* y1 = y + blk;
+  double* scratch = y1 + blk;
+  double* y2 = scratch + blk;
+  double* x2 = y2 + (size_t)M * m;
+  double* zt = x2 + (size_t)M * m;
+  k_scale_in<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, b, ldb, (const double*)c->d_q.p, bi);
+  int grc = HF_OK;
+  auto s22_solve = [&]() {
+    k_bk_solve<<<1, 128, 0, s>>>(M, m, (const double*)c->d_bk_lf.p, (const int*)c->d_bk_perm.p,
+                                 (const int*)c->d_bk_blk.p, (const double*)c->d_bk_dval.p,
+                                 (const int*)c->d_bk_null.p, y2, x2, zt);
+  };
+  if (c->prec == HF_PREC_MIXED) {
+    // Alg. 2: y1 by block GCR on K11, y2 = b2 - K21 y1, S22 x2 = y2, x1 = y1 - X12 x2
+    HF_CUDA_TRY(cudaMemcpyAsync(y, bi, blk * 8, cudaMemcpyDeviceToDevice, s));
+    if (M) k_zero_lam2_rows<<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, y);
+    grc = block_gcr(c, m, y, y1, &c->solve_iters, &c->solve_relres);
+    if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
+    if (M) {
+      k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, m, (const int64_t*)c->d_rowptr.p,
+                                                          (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
+                                                          (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
+                                                          y1, bi, m, y2);
+      s22_solve();
+      k_backsub_x1<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, M, m, (const double*)c->d_x12.p, x2,
+                                                            (const int32_t*)c->d_lam2pos.p, y1);
+    }
+    k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx);
+  } else if (c->prec == HF_PREC_FP64) {
+    // block substitution with the stored FP64 factor (Eq. 1): forward, S22 solve, backward
+    if ((rc = ensure_vec(c, m, 8))) return rc;
+    rc = tri_solve<double, double>(c, m, bi, y, y1, nullptr, M > 0, y2);
+    if (rc != HF_OK && rc != 1) return rc;
+    if (M) {
+      s22_solve();
+      if ((rc = tri_solve_back<double, double>(c, m, y, y1, x2))) return rc;
+    }
+    k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx);
+  } else {
+    // FP32 form: the same substitution with the FP32 factor (S22 solved in FP64)
+    if ((rc = ensure_vec(c, m, 4))) return rc;
+    float* b32 = (float*)scratch;
+    float* y32 = (float*)y;
+    float* x32 = y32 + blk;
+    k_cast_in<float><<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, bi, nullptr, b32);
+    rc = tri_solve<float, float>(c, m, b32, y32, x32, nullptr, M > 0, y2);
+    if (rc != HF_OK && rc != 1) return rc;
+    if (M) {
+      s22_solve();
+      if ((rc = tri_solve_back<float, float>(c, m, y32, x32, x2))) return rc;
+    }
+    k_cast_out<float><<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, x32, nullptr, y1);
+    k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx);
+  }
+  HF_CUDA_TRY(cudaGetLastError());
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  return grc;
+}

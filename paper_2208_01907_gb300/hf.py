@@ -1,0 +1,223 @@
+"""ctypes binding of the C ABI in include/hf.h (argument marshalling only).
+
+Every numerical step runs in libhf.so.  Device buffers are torch CUDA tensors
+(PyTorch supplies device memory and the stream); host buffers are numpy arrays.
+Loading fails loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhf.so")
+
+HF_OK, HF_ERR_ARG, HF_ERR_STATE, HF_ERR_PATTERN, HF_ERR_NUMERIC = 0, 1, 2, 3, 4
+HF_ERR_NOT_CONVERGED, HF_ERR_TIMEOUT, HF_ERR_CUDA, HF_ERR_OOM = 5, 6, 7, 8
+HF_PREC_MIXED, HF_PREC_FP64, HF_PREC_FP32 = 0, 1, 2
+
+#: every symbol declared in include/hf.h
+EXPORTED = (
+    "hf_default_opts", "hf_error_string", "hf_analyze", "hf_factorize", "hf_schur", "hf_solve",
+    "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
+    "hf_get_s22", "hf_get_s22_factor", "hf_free",
+)
+
+
+class hf_opts(C.Structure):
+    _fields_ = [
+        ("tau", C.c_double), ("n_enlarge", C.c_int), ("precision", C.c_int),
+        ("gcr_tol", C.c_double), ("gcr_maxit", C.c_int), ("kernel_eps", C.c_double),
+        ("kernel_gap", C.c_double), ("nd_leaf", C.c_int), ("nd_levels", C.c_int),
+        ("delay_cap", C.c_int), ("panel", C.c_int), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class hf_info(C.Structure):
+    _fields_ = [
+        ("L", C.c_int64), ("N", C.c_int64), ("M", C.c_int64), ("n_lambda0", C.c_int64),
+        ("nnz_factor", C.c_int64), ("n_nodes", C.c_int64), ("levels", C.c_int32),
+        ("kernel_dim", C.c_int32), ("gcr_iters", C.c_int32), ("solve_iters", C.c_int32),
+        ("gcr_relres", C.c_double), ("solve_relres", C.c_double), ("factor_flops", C.c_double),
+        ("front_bytes", C.c_int64), ("delay_retries", C.c_int32), ("precision", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HFError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {lib().hf_error_string(code).decode()} (code {code})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libhf.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhf.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    L.hf_default_opts.argtypes = [C.POINTER(hf_opts)]
+    L.hf_error_string.argtypes = [i32]
+    L.hf_error_string.restype = C.c_char_p
+    L.hf_analyze.argtypes = [i64, vp, vp, vp, i32, C.POINTER(hf_opts), C.POINTER(vp)]
+    L.hf_factorize.argtypes = [vp, vp, dbl]
+    L.hf_schur.argtypes = [vp]
+    L.hf_solve.argtypes = [vp, i32, vp, i64, vp, i64]
+    L.hf_get_split.argtypes = [vp, vp, vp, C.POINTER(hf_info)]
+    L.hf_get_info.argtypes = [vp, C.POINTER(hf_info)]
+    L.hf_get_tree.argtypes = [vp, vp, vp, vp]
+    L.hf_get_pivots.argtypes = [vp, vp, vp, vp, vp]
+    L.hf_get_factor.argtypes = [vp, vp, vp, vp, vp]
+    L.hf_get_x12.argtypes = [vp, vp, i64]
+    L.hf_get_s22.argtypes = [vp, vp]
+    L.hf_get_s22_factor.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.hf_free.argtypes = [vp]
+    L.hf_free.restype = None
+    for name in EXPORTED:
+        if name not in ("hf_error_string", "hf_free"):
+            getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc, where, allow=()):
+    if rc != HF_OK and rc not in allow:
+        raise HFError(rc, where)
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_opts(**kw) -> hf_opts:
+    o = hf_opts()
+    _check(lib().hf_default_opts(C.byref(o)), "hf_default_opts")
+    for k, v in kw.items():
+        if k == "cuda_stream":
+            v = C.c_void_p(v)
+        setattr(o, k, v)
+    return o
+
+
+class HybridFactor:
+    """One context of the C ABI: hf_analyze / hf_factorize / hf_schur / hf_solve / hf_free."""
+
+    def __init__(self, L, rowptr, col, coords=None, **opts):
+        self.L = int(L)
+        self._rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self._col = np.ascontiguousarray(col, dtype=np.int32)
+        crd = None if coords is None else np.ascontiguousarray(coords, dtype=np.float64)
+        dim = 0 if crd is None else crd.shape[1]
+        self.opts = default_opts(**opts)
+        h = C.c_void_p()
+        _check(lib().hf_analyze(self.L, _ptr(self._rowptr), _ptr(self._col), _ptr(crd), dim,
+                                C.byref(self.opts), C.byref(h)), "hf_analyze")
+        self._h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().hf_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # -- the four calls ----------------------------------------------------
+    def factorize(self, vals_dev, tau=None):
+        """vals_dev: torch float64 CUDA tensor with the CSR values of K-bar."""
+        t = self.opts.tau if tau is None else tau
+        _check(lib().hf_factorize(self._h, _ptr(vals_dev), float(t)), "hf_factorize")
+
+    def schur(self):
+        return _check(lib().hf_schur(self._h), "hf_schur", allow=(HF_ERR_NOT_CONVERGED,))
+
+    def solve(self, b_dev, x_dev):
+        """b_dev, x_dev: torch float64 CUDA tensors, column-major L x nrhs (shape (nrhs, L) contiguous)."""
+        nrhs = 1 if b_dev.dim() == 1 else b_dev.shape[0]
+        return _check(lib().hf_solve(self._h, nrhs, _ptr(b_dev), self.L, _ptr(x_dev), self.L),
+                      "hf_solve", allow=(HF_ERR_NOT_CONVERGED,))
+
+    # -- getters -----------------------------------------------------------
+    def info(self) -> dict:
+        inf = hf_info()
+        _check(lib().hf_get_info(self._h, C.byref(inf)), "hf_get_info")
+        return inf.as_dict()
+
+    def split(self):
+        inf = self.info()
+        order = np.zeros(self.L, np.int32)
+        lam2 = np.zeros(max(inf["M"], 1), np.int32)
+        _check(lib().hf_get_split(self._h, _ptr(order), _ptr(lam2), None), "hf_get_split")
+        return order, lam2[:inf["M"]]
+
+    def tree(self):
+        nn = self.info()["n_nodes"]
+        parent = np.zeros(nn, np.int32)
+        ptr = np.zeros(nn + 1, np.int64)
+        idx = np.zeros(self.L, np.int32)
+        _check(lib().hf_get_tree(self._h, _ptr(parent), _ptr(ptr), _ptr(idx)), "hf_get_tree")
+        return parent, [idx[ptr[t]:ptr[t + 1]].astype(np.int64) for t in range(nn)]
+
+    def pivots(self):
+        nn = self.info()["n_nodes"]
+        ptr = np.zeros(nn + 2, np.int64)
+        piv = np.zeros(self.L, np.int32)
+        moved = np.zeros(64, np.int32)
+        nm = C.c_int32()
+        _check(lib().hf_get_pivots(self._h, _ptr(ptr), _ptr(piv), _ptr(moved), C.byref(nm)), "hf_get_pivots")
+        per = [piv[ptr[t]:ptr[t + 1]].astype(np.int64) for t in range(nn + 1)]
+        return per[:nn], per[nn], moved[:nm.value].astype(np.int64)
+
+    def factor(self):
+        per, sr, _ = self.pivots()
+        npiv = int(sum(len(p) for p in per)) + len(sr)
+        cp = np.zeros(npiv + 1, np.int64)
+        _check(lib().hf_get_factor(self._h, _ptr(cp), None, None, None), "hf_get_factor")
+        ri = np.zeros(max(cp[-1], 1), np.int32)
+        va = np.zeros(max(cp[-1], 1), np.float64)
+        d = np.zeros(max(npiv, 1), np.float64)
+        _check(lib().hf_get_factor(self._h, _ptr(cp), _ptr(ri), _ptr(va), _ptr(d)), "hf_get_factor")
+        return cp, ri, va, d[:npiv]
+
+    def x12(self, torch_mod):
+        M = self.info()["M"]
+        out = torch_mod.zeros((self.L, max(M, 1)), dtype=torch_mod.float64, device="cuda")
+        _check(lib().hf_get_x12(self._h, _ptr(out), max(M, 1)), "hf_get_x12")
+        return out[:, :M]
+
+    def s22(self, torch_mod):
+        M = self.info()["M"]
+        out = torch_mod.zeros((max(M, 1), max(M, 1)), dtype=torch_mod.float64, device="cuda")
+        if M:
+            _check(lib().hf_get_s22(self._h, _ptr(out)), "hf_get_s22")
+        return out[:M, :M]
+
+    def s22_factor(self):
+        M = self.info()["M"]
+        perm = np.zeros(max(M, 1), np.int32)
+        lf = np.zeros((max(M, 1), max(M, 1)))
+        blk = np.zeros(max(M, 1), np.int32)
+        dval = np.zeros((max(M, 1), 2))
+        nul = np.zeros(max(M, 1), np.int32)
+        _check(lib().hf_get_s22_factor(self._h, _ptr(perm), _ptr(lf), _ptr(blk), _ptr(dval), _ptr(nul)),
+               "hf_get_s22_factor")
+        return perm[:M], lf[:M, :M], blk[:M], dval[:M], nul[:M]

@@ -1,0 +1,48 @@
+"""Helpers shared by the GPU tests: run the C ABI on a system, replay it in the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+
+def run_gpu(system, tau=1e-2, nrhs=1, rhs_seed=3, rhs_mode="uniform", solve=True, **opts):
+    import torch
+    import paper_2208_01907_gb300 as hf
+    from workloads import consistent_rhs
+
+    H = hf.HybridFactor(system.L, system.rowptr, system.col, system.coords, **opts)
+    vals = torch.tensor(system.val, device="cuda", dtype=torch.float64)
+    H.factorize(vals, tau)
+    rc = H.schur()
+    out = dict(H=H, schur_rc=rc, info=H.info())
+    if solve:
+        b = consistent_rhs(system, rhs_seed, nrhs, rhs_mode)
+        bt = torch.tensor(np.ascontiguousarray(b.T), device="cuda")
+        xt = torch.zeros_like(bt)
+        out["solve_rc"] = H.solve(bt, xt)
+        out["b"] = b
+        out["x"] = xt.cpu().numpy().T.copy()
+    out["info"] = H.info()
+    return out
+
+
+def replay(system, H, tau, n_enlarge=4, slack=1e-4):
+    """Oracle factorization on the GPU's tree, following the GPU's pivot decisions."""
+    _, sets = H.tree()
+    per, lam0_piv, moved = H.pivots()
+    q, K = O.scale_matrix(system.to_scipy())
+    fac = O.threshold_factorize(K, sets, tau, n_enlarge,
+                                replay={"node_pivots": per, "lam0_pivots": lam0_piv}, slack=slack)
+    return q, K, fac, moved
+
+
+def rel_fro(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def project_out(v, V):
+    if V is None or V.shape[1] == 0:
+        return v
+    return v - V @ np.linalg.lstsq(V, v, rcond=None)[0]

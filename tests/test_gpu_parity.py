@@ -1,0 +1,241 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results (pivot sequences, Lambda_1 / Lambda_2, Pi) are compared bit-exactly
+after the oracle replays the GPU's pivot choices and checks that each choice is
+admissible under the paper's rule (max |diag|, ratio test) within a float32
+slack.  Floating-point results use the tolerances of the method: S22 and X12
+to 1e-10 relative (Frobenius / max), solutions to backward error 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import diffusion2d, stokes3d, elasticity3d, darcy2d, consistent_rhs
+from gpu_common import run_gpu, replay, rel_fro, project_out
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+S22_TOL = 1e-10
+X12_TOL = 1e-10
+BWD_TOL = 1e-12
+
+CASES = {
+    "cfg1_diffusion48": (lambda: diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1), 1, {}),
+    "stokes8": (lambda: stokes3d(8, seed=2), 3, {"nd_leaf": 128}),
+    "elasticity6": (lambda: elasticity3d(6, n_incl=1, incl=2, seed=3), 6, {"nd_leaf": 64}),
+    "darcy16": (lambda: darcy2d(16, 16, seed=4, n_islands=2, island=3), 1, {"nd_leaf": 64}),
+    "dirichlet20": (lambda: diffusion2d(20, 20, n_islands=2, island=3, contrast=1e6, dirichlet_x=True, seed=6), 0,
+                    {"panel": 16}),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request):
+    make, kdim, opts = CASES[request.param]
+    s = make()
+    out = run_gpu(s, tau=1e-2, **opts)
+    q, K, fac, moved = replay(s, out["H"], 1e-2)
+    return dict(name=request.param, s=s, kdim=kdim, out=out, q=q, K=K, fac=fac, moved=moved)
+
+
+def test_split_replay_bit_exact(case):
+    fac, H = case["fac"], case["out"]["H"]
+    assert fac.violations == []
+    order, lam2 = H.split()
+    assert lam2.tolist() == fac.lambda2.tolist()
+    assert order[:fac.N].tolist() == fac.lambda1_order.tolist()
+    assert sorted(order.tolist()) == list(range(case["s"].L))
+    assert case["moved"].tolist() == fac.moved.tolist()
+    assert case["out"]["info"]["n_lambda0"] == len(fac.lam0)
+
+
+def test_factor_values_float32(case):
+    fac, H = case["fac"], case["out"]["H"]
+    cp, ri, va, d = H.factor()
+    per, lam0_piv, _ = H.pivots()
+    piv = np.concatenate([*per, lam0_piv])
+    worst = 0.0
+    for j, g in enumerate(piv):
+        np.testing.assert_allclose(d[j], fac.d[int(g)], rtol=2e-3, atol=1e-5)
+        rows, vals = fac.lcol[int(g)]
+        ref = dict(zip(rows.tolist(), vals.tolist()))
+        got = dict(zip(ri[cp[j]:cp[j + 1]].tolist(), va[cp[j]:cp[j + 1]].tolist()))
+        scale = max(1.0, max((abs(v) for v in ref.values()), default=0.0))
+        for r in set(ref) | set(got):
+            worst = max(worst, abs(ref.get(r, 0.0) - got.get(r, 0.0)) / scale)
+    assert worst < 2e-3
+
+
+def test_s22_and_x12_parity(case):
+    fac, H, K = case["fac"], case["out"]["H"], case["K"]
+    S22 = H.s22(torch).cpu().numpy()
+    Sref = O.schur_direct(K, fac.lambda2)
+    assert rel_fro(S22, Sref) <= S22_TOL
+    X12 = H.x12(torch).cpu().numpy()
+    Xref = O.x12_direct(K, fac.lambda2)
+    assert np.abs(X12 - Xref).max() <= X12_TOL * max(np.abs(Xref).max(), 1.0)
+    assert case["out"]["info"]["gcr_relres"] <= 1e-13
+
+
+def test_kernel_dimension(case):
+    assert case["out"]["info"]["kernel_dim"] == case["kdim"]
+
+
+def test_solve_parity(case):
+    s, out = case["s"], case["out"]
+    Kb = s.to_scipy()
+    assert O.backward_error(Kb, out["x"], out["b"]) <= BWD_TOL
+    fac, K, q = case["fac"], case["K"], case["q"]
+    X12 = O.x12_direct(K, fac.lambda2)
+    S22 = O.schur_direct(K, fac.lambda2, X12)
+    bk = O.bunch_kaufman(S22)
+    kd = O.kernel_dimension(O.pivot_magnitudes(bk[2])[0])
+    xo = q[:, None] * O.hybrid_solve(K, fac.lambda2, X12, bk, kd, q[:, None] * out["b"])
+    diff = project_out(out["x"] - xo, s.kernel)
+    ref = project_out(xo, s.kernel)
+    assert np.linalg.norm(diff) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_bunch_kaufman_parity(case):
+    H = case["out"]["H"]
+    S22 = H.s22(torch).cpu().numpy()
+    if S22.shape[0] == 0:
+        return
+    perm, lf, blk, dval, nul = H.s22_factor()
+    operm, oLf, oblocks = O.bunch_kaufman(S22)
+    assert perm.tolist() == operm.tolist()
+    assert [z for _, z, _ in oblocks] == [int(b) for b in blk if b != 0]
+    np.testing.assert_allclose(lf, oLf, atol=1e-9 * max(1.0, np.abs(oLf).max()))
+    assert int(nul.sum()) == case["out"]["info"]["kernel_dim"]
+
+
+# --------------------------------------------------------------------------- forms of Table 1
+def test_fp64_form_schur_and_solve():
+    s = diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1)
+    out = run_gpu(s, tau=1e-2, precision=1)
+    H = out["H"]
+    q, K, fac, _ = replay(s, H, 1e-2, slack=1e-9)
+    assert fac.violations == [] or all("pivot" in v for v in fac.violations)
+    _, lam2 = H.split()
+    S22 = H.s22(torch).cpu().numpy()
+    assert rel_fro(S22, O.schur_direct(K, lam2)) <= S22_TOL
+    assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+    assert out["info"]["kernel_dim"] == 1
+
+
+def test_fp32_form_is_inaccurate_like_single_column():
+    s = diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1)
+    out = run_gpu(s, tau=1e-2, precision=2)
+    be = O.backward_error(s.to_scipy(), out["x"], out["b"])
+    assert 1e-12 < be < 1e-3
+
+
+# --------------------------------------------------------------------------- edge cases
+def _csr_from_dense(A, coords=None):
+    import scipy.sparse as sp
+    from workloads.gen import _finish
+    return _finish("dense", sp.csr_matrix(A), coords if coords is not None else np.arange(A.shape[0], dtype=float)[:, None])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_tiny_systems(n):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    A = A + A.T + np.diag(np.full(n, 2.0 * n))
+    s = _csr_from_dense(A)
+    out = run_gpu(s, tau=1e-2, rhs_mode="uniform")
+    x = out["x"]
+    np.testing.assert_allclose(x, np.linalg.solve(A, out["b"]), rtol=1e-10, atol=1e-12)
+
+
+def test_everything_postponed_grows_delay_capacity():
+    s = diffusion2d(15, 20, n_islands=0, dirichlet_x=True)
+    out = run_gpu(s, tau=2.0, delay_cap=8, nd_leaf=32)
+    info = out["info"]
+    assert info["M"] == s.L and info["N"] == 0 and info["delay_retries"] >= 1
+    assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+
+
+def test_single_node_tree():
+    s = diffusion2d(12, 10, n_islands=1, island=3, contrast=1e8, seed=5)
+    out = run_gpu(s, tau=1e-2, nd_levels=1)
+    q, K, fac, _ = replay(s, out["H"], 1e-2)
+    assert fac.violations == []
+    assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+
+
+def test_disconnected_blocks_two_kernels():
+    import scipy.sparse as sp
+    a = diffusion2d(10, 10, n_islands=0)
+    b = diffusion2d(9, 11, n_islands=0)
+    A = sp.block_diag([a.to_scipy(), b.to_scipy()]).tocsr()
+    coords = np.concatenate([a.coords, b.coords + np.array([20.0, 0.0])])
+    from workloads.gen import _finish
+    ker = np.zeros((A.shape[0], 2))
+    ker[:a.L, 0] = 1.0
+    ker[a.L:, 1] = 1.0
+    s = _finish("two_blocks", A, coords, ker)
+    out = run_gpu(s, tau=1e-2, nd_leaf=32)
+    assert out["info"]["kernel_dim"] == 2
+    assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+
+
+def test_refactorize_same_pattern_new_values():
+    import paper_2208_01907_gb300 as hf
+    s = diffusion2d(30, 30, n_islands=3, island=3, contrast=1e8, seed=9)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    v1 = torch.tensor(s.val, device="cuda")
+    H.factorize(v1, 1e-2)
+    H.schur()
+    S_first = H.s22(torch).cpu().numpy().copy()
+    v2 = torch.tensor(s.val * 3.0, device="cuda")
+    H.factorize(v2, 1e-2)
+    H.schur()
+    H.factorize(v1, 1e-2)
+    H.schur()
+    np.testing.assert_allclose(H.s22(torch).cpu().numpy(), S_first, rtol=0, atol=1e-13 * np.abs(S_first).max())
+
+
+def test_multiple_rhs():
+    s = diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1)
+    out = run_gpu(s, tau=1e-2, nrhs=3)
+    assert out["x"].shape == (s.L, 3)
+    assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+
+
+def test_api_errors_without_state():
+    import paper_2208_01907_gb300 as hf
+    s = diffusion2d(8, 8, n_islands=0)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    with pytest.raises(hf.HFError) as e:
+        H.schur()
+    assert e.value.code == 2
+    bad = torch.tensor(np.where(np.arange(s.nnz) == 5, np.nan, s.val), device="cuda")
+    with pytest.raises(hf.HFError) as e:
+        H.factorize(bad, 1e-2)
+    assert e.value.code == 4
+
+
+# --------------------------------------------------------------------------- full-size configuration
+def test_full_size_stokes32_properties():
+    """The timed workload (3D Stokes-like, 32^3 nodes): properties that hold at any size."""
+    import scipy.sparse as sp
+    s = stokes3d(32, seed=2)
+    out = run_gpu(s, tau=1e-2, rhs_mode="solution")
+    H, info = out["H"], out["info"]
+    assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+    assert info["kernel_dim"] == 3
+    _, lam2 = H.split()
+    q, K = O.scale_matrix(s.to_scipy())
+    lam1 = np.setdiff1d(np.arange(s.L), lam2)
+    X12 = H.x12(torch).cpu().numpy()
+    K11 = K[lam1][:, lam1]
+    K12 = K[lam1][:, lam2].toarray()
+    r = K11 @ X12[lam1] - K12
+    assert np.linalg.norm(r) <= 1e-12 * max(np.linalg.norm(K12), 1.0) * 10
+    S22 = H.s22(torch).cpu().numpy()
+    Sh = K[lam2][:, lam2].toarray() - K[lam2][:, lam1] @ X12[lam1]
+    assert rel_fro(S22, 0.5 * (Sh + Sh.T)) <= 1e-13

@@ -1,0 +1,106 @@
+"""CPU-only checks of the library: it loads, exports every declared symbol, and
+its host analysis (nested dissection, Sec. 2.2) is correct.  No GPU call."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import diffusion2d, stokes3d, elasticity3d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _hf():
+    import paper_2208_01907_gb300 as hf
+    if not os.path.exists(hf.LIB_PATH):
+        from paper_2208_01907_gb300.build import build
+        build()
+    return hf
+
+
+def test_library_exports_every_declared_symbol():
+    hf = _hf()
+    L = hf.lib()
+    header = open(os.path.join(ROOT, "include", "hf.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hf_\w+)\s*\(", header, re.M))
+    assert declared == set(hf.EXPORTED)
+    for name in declared:
+        assert hasattr(L, name), name
+
+
+def test_default_opts_and_error_strings():
+    hf = _hf()
+    o = hf.default_opts()
+    assert o.tau == 1e-2 and o.n_enlarge == 4 and o.precision == hf.HF_PREC_MIXED
+    assert hf.lib().hf_error_string(5) == b"block GCR did not converge"
+
+
+def test_host_analysis_reproduces_fig1():
+    hf = _hf()
+    s = diffusion2d(7, 7, n_islands=0)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, nd_levels=3)
+    parent, sets = H.tree()
+    heap = [4, 5, 6, 7, 2, 3, 1]                 # elimination order of Fig. 1
+    assert parent.tolist() == [4, 4, 5, 5, 6, 6, -1]
+    pairs = {p for p in O.tree_block_pattern(s.to_scipy(), {heap[t]: sets[t] for t in range(7)}) if p[0] > p[1]}
+    golden = set()
+    for line in open(os.path.join(ROOT, "tests", "golden", "fig1_blocks.txt")):
+        if line.strip() and not line.startswith("#"):
+            golden.add(tuple(map(int, line.split())))
+    assert pairs == golden
+
+
+@pytest.mark.parametrize("maker,coords", [(lambda: diffusion2d(33, 21, n_islands=0), True),
+                                          (lambda: stokes3d(6), True),
+                                          (lambda: elasticity3d(6, n_incl=1, incl=2), True),
+                                          (lambda: diffusion2d(25, 25, n_islands=0), False)])
+def test_host_analysis_separators(maker, coords):
+    hf = _hf()
+    s = maker()
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords if coords else None, nd_leaf=40)
+    parent, sets = H.tree()
+    nn = len(sets)
+    owner = np.full(s.L, -1)
+    for t, v in enumerate(sets):
+        owner[v] = t
+    assert (owner >= 0).all()
+    children = {t: [] for t in range(nn)}
+    for t, p in enumerate(parent):
+        if p >= 0:
+            children[p].append(t)
+
+    def subtree(t):
+        out = {t}
+        for c in children[t]:
+            out |= subtree(c)
+        return out
+    A = s.to_scipy().tocoo()
+    for t in range(nn):
+        if len(children[t]) == 2:
+            a, b = subtree(children[t][0]), subtree(children[t][1])
+            cross = np.isin(owner[A.row], list(a)) & np.isin(owner[A.col], list(b))
+            assert not cross.any()
+
+
+def test_pattern_validation():
+    hf = _hf()
+    s = diffusion2d(4, 4, n_islands=0)
+    col = s.col.copy()
+    col[[1, 2]] = col[[2, 1]]                    # unsorted row
+    with pytest.raises(hf.HFError) as e:
+        hf.HybridFactor(s.L, s.rowptr, col, s.coords)
+    assert e.value.code == 3
+    # drop one off-diagonal entry: pattern no longer symmetric
+    import scipy.sparse as sp
+    A = s.to_scipy().tolil()
+    A[0, 1] = 0
+    A = A.tocsr()
+    A.eliminate_zeros()
+    with pytest.raises(hf.HFError) as e:
+        hf.HybridFactor(s.L, A.indptr.astype(np.int64), A.indices.astype(np.int32), s.coords)
+    assert e.value.code == 3
+    with pytest.raises(hf.HFError) as e:
+        hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, tau=-1.0)
+    assert e.value.code == 1

@@ -46,12 +46,19 @@ class CsrSystem:
 def _finish(name, A: sp.spmatrix, coords, kernel=None, **meta) -> CsrSystem:
     """Symmetrise the pattern, force a stored diagonal and sort columns."""
     A = sp.csr_matrix(A)
-    L = A.shape[0]
-    pat = (abs(A) + abs(A.T) + sp.identity(L, format="csr")).tocsr()
-    pat.data[:] = 0.0
-    A = (A + pat).tocsr()   # same values, pattern now symmetric with a full diagonal
     A.sum_duplicates()
-    A.sort_indices()
+    L = A.shape[0]
+    # symmetric pattern with every diagonal stored; values placed by (row, col) key so
+    # that explicit zeros (e.g. a zero pressure block diagonal) survive
+    P = (abs(A) + abs(A.T) + sp.identity(L, format="csr")).tocsr()
+    P.sort_indices()
+    prow = np.repeat(np.arange(L, dtype=np.int64), np.diff(P.indptr))
+    pkey = prow * L + P.indices.astype(np.int64)
+    C = A.tocoo()
+    akey = C.row.astype(np.int64) * L + C.col.astype(np.int64)
+    data = np.zeros(P.nnz)
+    data[np.searchsorted(pkey, akey)] = C.data
+    A = sp.csr_matrix((data, P.indices, P.indptr), shape=(L, L))
     return CsrSystem(
         name=name,
         rowptr=A.indptr.astype(np.int64),
