@@ -23,10 +23,20 @@ the design notes):
       and Q_{n+1} likewise (Sec. 3.5).
   R8  Block GCR starts as Alg. 4 (X0 = Q^-1 B) and stops when every column
       satisfies |r_k| / |b_k| <= tol.
+  R3b Null-pivot test: a candidate whose current diagonal is below tau times
+      the magnitude of the terms it was formed from (|K_ii| plus the
+      accumulated |l_ik|^2 |d_k| of earlier eliminations) has lost its
+      digits to cancellation; the lower precision cannot resolve it, so it is
+      postponed on its own (skipped) and the elimination of the set goes on.
+      Without it, float32 noise pivots of a singular K pass the ratio test
+      and the kernel never reaches S22 (Sec. 3 requires it there).
   R10 Kernel detection: pivot magnitudes of the S22 LDL^T sorted; the kernel
       is the tail after the largest ratio gap >= gap_min whose tail lies
       below kernel_eps * max.
-  R11 S22 is factorized by Bunch-Kaufman 1x1/2x2 pivoting, alpha = (1+sqrt 17)/8.
+  R11 S22 is factorized with symmetric complete (Bunch-Parlett) pivoting,
+      1x1 or 2x2 blocks, alpha = (1+sqrt 17)/8: the largest entries of the
+      whole remaining block go first, so null pivots come last (rank
+      revealing, as the kernel detection needs).
   R13 The enlargement moves the last n = 4 entries of the elimination order
       into hat-Lambda_0.  These are the last entries of tilde-Lambda_0 when it
       holds at least n of them; when tilde-Lambda_0 is shorter (every
@@ -46,9 +56,9 @@ import scipy.sparse.linalg as spla
 __all__ = [
     "scale_matrix", "nested_dissection", "tree_block_pattern", "threshold_factorize",
     "FactorResult", "precond_apply", "k11_operator", "block_gcr", "gcr_single",
-    "schur_direct", "x12_direct", "bunch_kaufman", "bk_reconstruct", "pivot_magnitudes",
+    "schur_direct", "x12_direct", "bunch_kaufman", "bunch_parlett", "bk_reconstruct", "pivot_magnitudes",
     "kernel_dimension", "bk_solve", "hybrid_solve", "relative_residual", "backward_error",
-    "run_hybrid", "adjoint_gradient", "diffusion_objective",
+    "run_hybrid", "s22_noise", "adjoint_gradient", "diffusion_objective",
 ]
 
 
@@ -157,8 +167,12 @@ class FactorResult:
         return len(self.lambda2)
 
 
-def _eliminate(S, remaining, q, fac):
-    """One rank-1 Schur update with weight 1/d on the remaining indices (Sec. 2.1)."""
+def _eliminate(S, G, remaining, q, fac):
+    """One rank-1 Schur update with weight 1/d on the remaining indices (Sec. 2.1).
+
+    G accumulates, per index, |K_ii| plus the magnitudes |l_i|^2 |d| of the
+    updates its diagonal received (used by the null-pivot test R3b).
+    """
     d = S[q, q]
     remaining[q] = False
     row = S[q]
@@ -166,38 +180,56 @@ def _eliminate(S, remaining, q, fac):
     col = row[rows].copy()
     if rows.size:
         S[np.ix_(rows, rows)] -= np.outer(col, col) / d
-    fac.d[int(q)] = np.float32(d)
-    fac.lcol[int(q)] = (rows, (col / d).astype(np.float32))
+        G[rows] += np.abs(col * (col / d))
+    fac.d[int(q)] = d
+    fac.lcol[int(q)] = (rows, col / d)
     return d
 
 
-def _factor_set(S, remaining, cand, tau, fac, replay_seq=None, slack=1e-4, max_piv=None, tag=""):
+def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_test=True, tag=""):
     """Symmetric max-|diag| pivoting with threshold postponing on one index set (Sec. 2.1-2.2).
 
-    Returns (chosen, postponed).  In replay mode the chosen sequence is taken
-    from ``replay_seq`` and each step is checked to be an admissible choice of
-    this rule up to a relative float32 slack; violations are recorded.
+    Each step takes the candidate of largest |diag| (R5 ties).  If it fails the
+    ratio test (R2/R3) the rest of the set is postponed (stop); if it passes but
+    fails the null-pivot test (R3b) only that candidate is postponed (skip).
+    Returns (chosen, postponed, skipped).
+
+    Replay mode: ``replay = (accepted sequence, set of skipped indices)`` chosen
+    by another implementation.  The oracle follows it: it skips the listed
+    candidates when they come up as the maximum and accepts the listed pivots
+    in order, recording any step that this rule would not admit (within a
+    relative slack for the other implementation's rounding).
     """
     cand = list(np.asarray(cand, dtype=np.int64))
-    chosen = []
+    chosen, skipped = [], []
     d_ref = 1.0                                   # R2: first pivot compared with the unit diagonal
+    seq, skip_set = (None, set()) if replay is None else (list(replay[0]), set(int(x) for x in replay[1]))
     step = 0
     while cand:
-        if max_piv is not None and len(chosen) >= max_piv:
-            break
         dg = np.abs(np.array([S[c, c] for c in cand], dtype=np.float64))
+        dg[np.isnan(dg)] = -1.0
         best = max(range(len(cand)), key=lambda t: (dg[t], -cand[t]))   # R5 tie -> smallest index
-        if replay_seq is None:
+        if seq is None:
             t = best
-            if not (dg[t] >= tau * d_ref):          # R3 ratio test (also stops on NaN)
+            if not (dg[t] >= tau * d_ref):                           # R3 ratio test (NaN stops)
                 break
+            if null_test and not (dg[t] >= tau * float(G[cand[t]])):  # R3b null pivot: skip it
+                skipped.append(cand.pop(t))
+                continue
         else:
-            if step >= len(replay_seq):
-                if dg[best] >= tau * d_ref * (1 + slack):
+            bq = cand[best]
+            if bq in skip_set and step <= len(seq):
+                # the other implementation skipped this candidate when it was the maximum
+                if null_test and dg[best] > tau * float(G[bq]) * (1 + slack):
+                    fac.violations.append(f"{tag}: skipped {bq} passes the null test")
+                skipped.append(cand.pop(best))
+                continue
+            if step >= len(seq):
+                if dg[best] >= tau * d_ref * (1 + slack) and not (null_test and dg[best] < tau * float(G[bq])):
                     fac.violations.append(f"{tag}: replay stopped at step {step} but oracle ratio "
                                           f"{dg[best] / d_ref:.6g} >= tau")
                 break
-            q = int(replay_seq[step])
+            q = int(seq[step])
             if q not in cand:
                 fac.violations.append(f"{tag}: replay pivot {q} is not a candidate")
                 break
@@ -206,39 +238,53 @@ def _factor_set(S, remaining, cand, tau, fac, replay_seq=None, slack=1e-4, max_p
                 fac.violations.append(f"{tag}: step {step} pivot {q} |d|={dg[t]:.8g} < max {dg[best]:.8g}")
             if dg[t] < tau * d_ref * (1 - slack):
                 fac.violations.append(f"{tag}: step {step} pivot {q} fails the ratio test")
+            if null_test and dg[t] < tau * float(G[q]) * (1 - slack):
+                fac.violations.append(f"{tag}: step {step} pivot {q} fails the null test")
         q = cand.pop(t)
-        d = _eliminate(S, remaining, q, fac)
+        d = _eliminate(S, G, remaining, q, fac)
         d_ref = abs(float(d))
         chosen.append(q)
         step += 1
-    if replay_seq is not None and step < len(replay_seq):
-        fac.violations.append(f"{tag}: oracle could not follow replay past step {step}")
-    return np.array(chosen, dtype=np.int64), np.array(cand, dtype=np.int64)
+    if seq is not None:
+        if step < len(seq):
+            fac.violations.append(f"{tag}: oracle could not follow replay past step {step}")
+        missing = skip_set - set(skipped)
+        if missing:
+            fac.violations.append(f"{tag}: replay skipped {sorted(missing)[:5]} never came up as maximum")
+    postponed = np.array(sorted(set(cand) | set(skipped)), dtype=np.int64)
+    return np.array(chosen, dtype=np.int64), postponed, np.array(skipped, dtype=np.int64)
 
 
 def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: int = 4,
-                        replay: dict | None = None, slack: float = 1e-4) -> FactorResult:
-    """Alg. 1 step 1 in float32: factor along the tree, postpone, refactor Lambda_0, enlarge.
+                        replay: dict | None = None, slack: float = 1e-4, dtype=np.float32,
+                        null_test: bool = True) -> FactorResult:
+    """Alg. 1 step 1: factor along the tree, postpone, refactor Lambda_0, enlarge.
 
     ``nodes``: index arrays Lambda_l in elimination order (children before parents).
-    ``replay``: optional {"node_pivots": [...], "lam0_pivots": [...]} chosen by
-    another implementation; the oracle follows it and records any choice that
-    this rule would not admit.
+    ``dtype``: the lower precision of the factorization (float32 for the mixed
+    form; float64 reproduces the plain double form of Table 1).
+    ``replay``: optional {"node_pivots": [...], "node_skipped": [...],
+    "lam0_pivots": [...], "lam0_skipped": [...]} chosen by another implementation;
+    the oracle follows it and records any choice that this rule would not admit.
     """
     L = K.shape[0]
-    S = K.toarray().astype(np.float32)          # current Schur complement, lower precision
+    S = K.toarray().astype(dtype)                  # current Schur complement
+    G = np.abs(np.diag(S)).copy()                  # R3b magnitude of the terms in each diagonal
     remaining = np.ones(L, dtype=bool)
     fac = FactorResult([], [], None, None, None, None, None)
+    fac.node_skipped = []
     for t, lam in enumerate(nodes):
-        seq = None if replay is None else replay["node_pivots"][t]
-        ch, pp = _factor_set(S, remaining, lam, tau, fac, seq, slack, tag=f"node{t}")
+        rp = None if replay is None else (replay["node_pivots"][t], replay["node_skipped"][t])
+        ch, pp, sk = _factor_set(S, G, remaining, lam, tau, fac, rp, slack, null_test, tag=f"node{t}")
         fac.node_pivots.append(ch)
         fac.node_postponed.append(pp)
+        fac.node_skipped.append(sk)
     lam0 = np.concatenate(fac.node_postponed) if fac.node_postponed else np.zeros(0, np.int64)
     fac.lam0 = np.sort(lam0)
-    seq = None if replay is None else replay["lam0_pivots"]
-    ch0, hat0 = _factor_set(S, remaining, fac.lam0, tau, fac, seq, slack, tag="lambda0")
+    rp = None if replay is None else (replay["lam0_pivots"], replay["lam0_skipped"])
+    ch0, hat0, sk0 = _factor_set(S, G, remaining, fac.lam0, tau, fac, rp, slack, null_test, tag="lambda0")
     fac.lam0_pivots = ch0
+    fac.lam0_skipped = sk0
     # R13: move the last n entries of the elimination order into hat-Lambda_0.  They are
     # the last entries of tilde-Lambda_0 whenever it holds n or more of them.
     order = np.concatenate([*fac.node_pivots, ch0]).astype(np.int64)
@@ -262,7 +308,8 @@ def precond_apply(fac: FactorResult, R: np.ndarray) -> np.ndarray:
     L = R.shape[0]
     in1 = np.ones(L, dtype=bool)
     in1[fac.lambda2] = False
-    y = np.array(R, dtype=np.float32, copy=True).reshape(L, -1)
+    dt = np.asarray(next(iter(fac.d.values()))).dtype if fac.d else np.float32
+    y = np.array(R, dtype=dt, copy=True).reshape(L, -1)
     y[~in1] = 0
     order = fac.lambda1_order
     for p in order:                                   # forward, unit lower triangular
@@ -395,12 +442,69 @@ def schur_direct(K: sp.csr_matrix, lambda2, X12=None):
 # ---------------------------------------------------------------------------
 # Alg. 1 step 5: higher-precision symmetric factorization of S22 with 2x2 pivots
 # ---------------------------------------------------------------------------
-def bunch_kaufman(A):
-    """Textbook Bunch-Kaufman LDL^T, alpha = (1+sqrt 17)/8 (R11).
+def bunch_parlett(A):
+    """Symmetric LDL^T with complete (Bunch-Parlett) pivoting, alpha = (1+sqrt 17)/8 (R11).
 
-    Returns (perm, Lf, blocks): P^T A P = Lf D Lf^T with perm the row order,
-    Lf unit lower triangular and blocks a list of (start, size, D_block).
+    At each step, over the remaining block: mu0 = max |a_ii|, mu1 = max_{i>j} |a_ij|
+    (ties: smallest index; off-diagonal ties: smallest column, then row).  If
+    mu0 >= alpha mu1 the largest diagonal is a 1x1 pivot, otherwise the largest
+    off-diagonal pair (i, j) forms a 2x2 pivot.
+    Returns (perm, Lf, blocks): P^T A P = Lf D Lf^T, row i of the factor = row perm[i] of A.
     """
+    A = np.array(A, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    alpha = (1.0 + math.sqrt(17.0)) / 8.0
+    perm = np.arange(n)
+    Lf = np.eye(n)
+    blocks = []
+
+    def swap(i, j):
+        if i == j:
+            return
+        A[[i, j], :] = A[[j, i], :]
+        A[:, [i, j]] = A[:, [j, i]]
+        Lf[[i, j], :i] = Lf[[j, i], :i]
+        perm[[i, j]] = perm[[j, i]]
+
+    k = 0
+    while k < n:
+        dgs = np.abs(np.diag(A)[k:])
+        i0 = int(np.argmax(dgs))
+        mu0 = dgs[i0]
+        mu1, bi, bj = 0.0, -1, -1
+        for j in range(k, n):                     # column-major scan of the strict lower triangle
+            if j + 1 < n:
+                colv = np.abs(A[j + 1:, j])
+                r = int(np.argmax(colv))
+                if colv[r] > mu1:
+                    mu1, bi, bj = colv[r], j + 1 + r, j
+        if mu0 == 0.0 and mu1 == 0.0:
+            blocks.append((k, 1, np.array([[0.0]])))
+            k += 1
+            continue
+        if mu0 >= alpha * mu1:
+            swap(k, k + i0)
+            d = A[k, k]
+            l = A[k + 1:, k] / d
+            A[k + 1:, k + 1:] -= np.outer(l, A[k + 1:, k])
+            Lf[k + 1:, k] = l
+            blocks.append((k, 1, np.array([[d]])))
+            k += 1
+        else:
+            swap(k, bj)
+            swap(k + 1, bi)
+            D = A[k:k + 2, k:k + 2].copy()
+            C = A[k + 2:, k:k + 2]
+            l = np.linalg.solve(D, C.T).T
+            A[k + 2:, k + 2:] -= l @ C.T
+            Lf[k + 2:, k:k + 2] = l
+            blocks.append((k, 2, D))
+            k += 2
+    return perm, Lf, blocks
+
+
+def bunch_kaufman(A):
+    """Textbook Bunch-Kaufman LDL^T (partial pivoting), kept to pin the block formulas."""
     A = np.array(A, dtype=np.float64, copy=True)
     n = A.shape[0]
     alpha = (1.0 + math.sqrt(17.0)) / 8.0
@@ -427,7 +531,7 @@ def bunch_kaufman(A):
             r, lam = k, 0.0
         size = 1
         if max(akk, lam) == 0.0:
-            pass                                        # zero column: 1x1 zero pivot
+            pass
         elif akk >= alpha * lam:
             pass
         else:
@@ -460,7 +564,7 @@ def bunch_kaufman(A):
 
 
 def bk_reconstruct(perm, Lf, blocks):
-    """A = P Lf D Lf^T P^T from the Bunch-Kaufman factors."""
+    """A = P Lf D Lf^T P^T from the factors of bunch_parlett / bunch_kaufman."""
     n = len(perm)
     D = np.zeros((n, n))
     for s, z, B in blocks:
@@ -484,17 +588,29 @@ def pivot_magnitudes(blocks):
     return np.array(mags), owners
 
 
-def kernel_dimension(mags, kernel_eps=1e-10, gap_min=1e4):
-    """R10: the tail after the largest ratio gap >= gap_min whose tail is <= kernel_eps * max."""
+def kernel_dimension(mags, kernel_eps=1e-10, gap_min=1e4, ref=0.0, noise=0.0):
+    """R10: the tail after the largest ratio gap >= gap_min whose tail is <= the null threshold.
+
+    threshold = max(kernel_eps * scale, noise) with scale = max(max pivot magnitude, ref);
+    ref is max |diag(K22)| of the scaled K (1 unless every hard index has a zero
+    diagonal): S22 is a difference of O(1) terms, so its null pivots are small
+    relative to the unit diagonal even when S22 itself is small.  ``noise`` is an
+    estimate of the error of S22 (100 |K21 Q^-1 (K12 - K11 X12)|_max for an
+    iterative X12): pivots at or below it cannot be told from zero.
+    """
     if len(mags) == 0:
         return 0
     s = np.sort(np.asarray(mags))[::-1]
-    if s[0] == 0:
+    scale = max(s[0], ref)
+    if scale == 0:
         return len(s)
+    thr = max(kernel_eps * scale, noise)
     best, dim = 0.0, 0
-    for i in range(1, len(s)):
-        if s[i] > kernel_eps * s[0]:
+    for i in range(0 if s[0] <= thr else 1, len(s)):
+        if s[i] > thr:
             continue
+        if i == 0:                                 # every pivot is null relative to the unit scale
+            return len(s)
         ratio = math.inf if s[i] == 0 else s[i - 1] / s[i]
         if ratio >= gap_min and ratio > best:
             best, dim = ratio, len(s) - i
@@ -502,6 +618,7 @@ def kernel_dimension(mags, kernel_eps=1e-10, gap_min=1e4):
 
 
 def bk_solve(perm, Lf, blocks, y, kdim):
+    # (works for the factors of bunch_parlett and bunch_kaufman alike)
     """x = S^+ y with the kdim smallest pivot magnitudes treated as zero (kernel pivots)."""
     n = len(perm)
     mags, owners = pivot_magnitudes(blocks)
@@ -556,10 +673,10 @@ def backward_error(Kbar: sp.csr_matrix, x, b):
 
 
 def run_hybrid(Kbar: sp.csr_matrix, nodes, tau, n_enlarge=4, replay=None, kernel_eps=1e-10,
-               gap_min=1e4, use_gcr=False, gcr_tol=1e-14, gcr_maxit=50):
-    """Alg. 1 end to end: scale, threshold factorization, X12, S22, Bunch-Kaufman, kernel dim."""
+               gap_min=1e4, use_gcr=False, gcr_tol=1e-14, gcr_maxit=50, dtype=np.float32):
+    """Alg. 1 end to end: scale, threshold factorization, X12, S22, Bunch-Parlett, kernel dim."""
     q, K = scale_matrix(Kbar)
-    fac = threshold_factorize(K, nodes, tau, n_enlarge, replay)
+    fac = threshold_factorize(K, nodes, tau, n_enlarge, replay, dtype=dtype)
     if use_gcr and fac.M:
         lam1, _, K12, _, _ = _blocks(K, fac.lambda2)
         B = np.zeros((K.shape[0], fac.M))
@@ -569,9 +686,25 @@ def run_hybrid(Kbar: sp.csr_matrix, nodes, tau, n_enlarge=4, replay=None, kernel
     else:
         X12, hist = x12_direct(K, fac.lambda2), None
     S22 = schur_direct(K, fac.lambda2, X12)
-    bk = bunch_kaufman(S22) if fac.M else (np.zeros(0, int), np.zeros((0, 0)), [])
-    kdim = kernel_dimension(pivot_magnitudes(bk[2])[0], kernel_eps, gap_min) if fac.M else 0
-    return dict(q=q, K=K, fac=fac, X12=X12, S22=S22, bk=bk, kdim=kdim, gcr_hist=hist)
+    noise = s22_noise(K, fac, X12) if (use_gcr and fac.M) else 0.0
+    bk = bunch_parlett(S22) if fac.M else (np.zeros(0, int), np.zeros((0, 0)), [])
+    ref = float(np.abs(K.diagonal()[fac.lambda2]).max()) if fac.M else 0.0
+    kdim = kernel_dimension(pivot_magnitudes(bk[2])[0], kernel_eps, gap_min, ref, noise) if fac.M else 0
+    return dict(q=q, K=K, fac=fac, X12=X12, S22=S22, bk=bk, kdim=kdim, gcr_hist=hist, noise=noise)
+
+
+def s22_noise(K: sp.csr_matrix, fac: FactorResult, X12, factor=100.0):
+    """Error estimate of S22 = K22 - K21 X12 for an iterative X12 (used by R10).
+
+    The error of X12 is K11^-1 R with R = K12 - K11 X12; the preconditioner
+    stands in for K11^-1, so E = K21 Q^-1 R and the estimate is factor * max|E|.
+    """
+    lam1, _, K12, K21, _ = _blocks(K, fac.lambda2)
+    B = np.zeros((K.shape[0], fac.M))
+    B[lam1] = K12.toarray()
+    R = B - k11_operator(K, fac.lambda2)(X12)
+    W = precond_apply(fac, R)
+    return factor * float(np.abs(K21 @ W[lam1]).max())
 
 
 # ---------------------------------------------------------------------------

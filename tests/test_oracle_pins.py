@@ -406,3 +406,50 @@ def test_adjoint_gradient_matches_central_differences():
         h = 1e-6
         fd = (J(theta + h * d)[0] - J(theta - h * d)[0]) / (2 * h)
         np.testing.assert_allclose(g @ d, fd, rtol=1e-5)
+
+
+# --------------------------------------------------------------------------- R3b null-pivot test
+def test_null_pivot_test_skips_cancelled_pivot():
+    # index 2 keeps 1.5e-3 of a diagonal built from terms of size ~2: the ratio test to the
+    # previous pivot (0.5) passes at tau = 1e-3, the cancellation (null) test does not.
+    a = np.sqrt(1 - 1.5e-3)
+    K = sp.csr_matrix(np.array([[0.5, 0, 0], [0, 1.0, a], [0, a, 1.0]]))
+    fac = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-3, n_enlarge=1)
+    assert fac.node_pivots[0].tolist() == [1, 0]
+    assert fac.node_skipped[0].tolist() == [2]
+    assert fac.lam0_skipped.tolist() == [2] and fac.lam0_pivots.tolist() == []
+    assert fac.lambda2.tolist() == [0, 2]
+    off = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-3, n_enlarge=1, null_test=False)
+    assert off.node_pivots[0].tolist() == [1, 0, 2]
+
+
+# --------------------------------------------------------------------------- R11 Bunch-Parlett
+def test_bunch_parlett_reconstruction_inertia_and_bound():
+    rng = np.random.default_rng(21)
+    alpha = (1 + math.sqrt(17)) / 8
+    for n in (1, 2, 6, 19, 41):
+        A = _rand_sym(n, rng)
+        if n > 3:
+            A[np.arange(n), np.arange(n)] *= 1e-3          # forces 2x2 pivots
+        perm, Lf, blocks = O.bunch_parlett(A)
+        np.testing.assert_allclose(O.bk_reconstruct(perm, Lf, blocks), A, atol=1e-11 * np.abs(A).max())
+        ev = np.linalg.eigvalsh(A)
+        dev = np.concatenate([np.linalg.eigvalsh(B) for _, _, B in blocks])
+        assert (dev > 0).sum() == (ev > 0).sum() and (dev < 0).sum() == (ev < 0).sum()
+        assert np.abs(Lf).max() <= 1.0 / (1.0 - alpha) + 1e-9   # complete-pivoting growth bound on L
+        if n > 3:
+            assert any(z == 2 for _, z, _ in blocks)
+
+
+def test_bunch_parlett_is_rank_revealing():
+    rng = np.random.default_rng(22)
+    for n, r in ((8, 5), (12, 6), (20, 17)):
+        U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = np.concatenate([rng.uniform(1, 2, r) * rng.choice([-1, 1], r), np.zeros(n - r)])
+        A = (U * lam) @ U.T
+        perm, Lf, blocks = O.bunch_parlett(A)
+        mags, owners = O.pivot_magnitudes(blocks)
+        order_mags = np.concatenate([np.abs(np.linalg.eigvalsh(B)) if z == 2 else [abs(B[0, 0])] for _, z, B in blocks])
+        assert (order_mags[r:] < 1e-12).all() and (order_mags[:r] > 1e-4).all()   # null pivots last
+        assert O.kernel_dimension(mags) == n - r
+        # Bunch-Kaufman (partial pivoting) does not promise this ordering
