@@ -64,7 +64,9 @@ typedef struct {
   int    precision;      /* HF_PREC_*; default HF_PREC_MIXED */
   double gcr_tol;        /* block GCR stop: max_k |r_k|/|b_k| <= gcr_tol; default 1e-14 */
   int    gcr_maxit;      /* block GCR iteration limit; default 40 */
-  double kernel_eps;     /* null pivot if |pivot| <= kernel_eps * max|pivot|; default 1e-10 */
+  double kernel_eps;     /* null pivot of S22 if |pivot| <= max(kernel_eps * scale, noise), scale =
+                            max(max|pivot|, max|diag K22|), noise = 100 x the estimated error of
+                            S22; default 1e-10 */
   double kernel_gap;     /* minimum ratio gap that separates null pivots; default 1e4 */
   int    nd_leaf;        /* dissection stops when a set has <= nd_leaf unknowns; default 256 */
   int    nd_levels;      /* if > 0, force the number of tree levels m (Sec. 2.2); default 0 */
@@ -133,7 +135,8 @@ int hf_factorize(hf_ctx* ctx, const double* vals, double tau);
  * Schur generation, Alg. 1 steps 2-5: for HF_PREC_MIXED, X12 = K11^-1 K12 by block GCR
  * (Sec. 3.5) in FP64 preconditioned by the FP32 factor, S22 = K22 - K21 X12 in FP64;
  * for the other forms S22 is taken from the factor.  Then S22 is factorized in FP64
- * by Bunch-Kaufman LDL^T (1x1 / 2x2 pivots) and its kernel dimension detected.
+ * by LDL^T with complete symmetric pivoting (Bunch-Parlett, 1x1 / 2x2 blocks), which puts
+ * the null pivots last, and its kernel dimension is detected.
  * Errors: HF_ERR_STATE, HF_ERR_NOT_CONVERGED (results still usable), HF_ERR_CUDA, HF_ERR_OOM.
  */
 int hf_schur(hf_ctx* ctx);
@@ -148,6 +151,17 @@ int hf_schur(hf_ctx* ctx);
  * Errors: HF_ERR_STATE, HF_ERR_ARG, HF_ERR_NOT_CONVERGED, HF_ERR_CUDA, HF_ERR_OOM.
  */
 int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
+
+/*
+ * The lower-precision solve of Sec. 3.1-3.2, W = Q^-1 R with Q the factor of K11 (Eq. 1),
+ * on m vectors of the scaled unknowns (K = Q_s Kbar Q_s): R is cast to the factor's
+ * precision, solved by forward / diagonal / backward substitution, and cast back.
+ *   m     number of vectors (>= 1)
+ *   R, W  device, row-major L x m (the m entries of an unknown contiguous); rows of
+ *         Lambda_2 are ignored in R and set to zero in W.  W may not alias R.
+ * Errors: HF_ERR_STATE (before hf_factorize), HF_ERR_ARG, HF_ERR_CUDA, HF_ERR_OOM.
+ */
+int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
 
 /*
  * The split of Alg. 1 step 1 (host outputs, any may be NULL):
@@ -183,6 +197,17 @@ int hf_get_tree(hf_ctx* ctx, int32_t* parent, int64_t* set_ptr, int32_t* set_idx
 int hf_get_pivots(hf_ctx* ctx, int64_t* node_ptr, int32_t* piv, int32_t* moved, int32_t* n_moved);
 
 /*
+ * Candidate order of every front after the factorization, to replay its decisions:
+ *   node_ptr  n_nodes+2 entries; cand[node_ptr[t] .. node_ptr[t+1]) are the pivot candidates
+ *             of node t (Lambda_t; entry n_nodes is the Lambda_0 stage) in final front order
+ *   cand      original indices (host)
+ *   counts    2*(n_nodes+1) entries (k_t, nact_t): cand[0, k) were eliminated in that order,
+ *             cand[k, nact) were postponed by the ratio test, cand[nact, end) were postponed one
+ *             at a time by the null-pivot test (the first one skipped is last)
+ */
+int hf_get_pivot_events(hf_ctx* ctx, int64_t* node_ptr, int32_t* cand, int32_t* counts);
+
+/*
  * The lower-precision factor of K11 (Eq. 1), for checking: column j of L for pivot
  * piv[j] (same order as hf_get_pivots).  Host outputs:
  *   col_ptr  (#pivots + 1) entries
@@ -203,7 +228,7 @@ int hf_get_x12(hf_ctx* ctx, double* x12, int64_t ldx12);
 int hf_get_s22(hf_ctx* ctx, double* s22);
 
 /*
- * Bunch-Kaufman factors of S22 (host outputs, M entries each, M*M for lf):
+ * LDL^T factors of S22 (complete symmetric pivoting; host outputs, M entries each, M*M for lf):
  *   perm   row order: P^T S22 P = Lf D Lf^T with row i of the factor = S22 row perm[i]
  *   lf     M x M row-major unit lower triangular Lf
  *   dblk   M entries: 1 = 1x1 block start, 2 = 2x2 block start, 0 = second row of a 2x2

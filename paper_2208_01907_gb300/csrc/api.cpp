@@ -11,6 +11,7 @@
 int hf_factorize_impl(hf_ctx* c, const double* vals, double tau);
 int hf_schur_impl(hf_ctx* c);
 int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
+int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W);
 
 static thread_local char g_cuda_msg[256] = "";
 
@@ -96,6 +97,11 @@ int hf_schur(hf_ctx* c) {
 int hf_solve(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx) {
   if (!c) return HF_ERR_ARG;
   return hf_solve_impl(c, nrhs, b, ldb, x, ldx);
+}
+
+int hf_precond(hf_ctx* c, int m, const double* R, double* W) {
+  if (!c) return HF_ERR_ARG;
+  return hf_precond_impl(c, m, R, W);
 }
 
 int hf_get_info(hf_ctx* c, hf_info* info) {
@@ -186,6 +192,31 @@ int hf_get_pivots(hf_ctx* c, int64_t* node_ptr, int32_t* piv, int32_t* moved, in
   return HF_OK;
 }
 
+int hf_get_pivot_events(hf_ctx* c, int64_t* node_ptr, int32_t* cand, int32_t* counts) {
+  if (!c || !node_ptr) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  const int nn = c->n_nodes;
+  std::vector<int32_t> rid;
+  if (cand) {
+    rid.resize(c->row_elems);
+    if (cudaMemcpy(rid.data(), c->d_rowid.p, rid.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return HF_ERR_CUDA;
+  }
+  node_ptr[0] = 0;
+  int64_t p = 0;
+  for (int t = 0; t <= nn; ++t) {
+    const NodeState& S = c->state_host[t];
+    const int ncand = c->nodes[t].cand_all ? S.f : c->nodes[t].n;
+    for (int i = 0; i < ncand; ++i) {
+      if (cand) cand[p] = rid[c->nodes[t].row_off + i];
+      ++p;
+    }
+    node_ptr[t + 1] = p;
+    if (counts) { counts[2 * t] = S.k; counts[2 * t + 1] = S.nact; }
+  }
+  return HF_OK;
+}
+
 int hf_get_factor(hf_ctx* c, int64_t* col_ptr, int32_t* row_idx, double* val, double* d) {
   if (!c || !col_ptr) return HF_ERR_ARG;
   if (!c->factored) return HF_ERR_STATE;
@@ -265,7 +296,8 @@ void hf_free(hf_ctx* c) {
                     &c->d_rowid_static, &c->d_smap, &c->d_asm, &c->d_cbmap, &c->d_q, &c->d_kval,
                     &c->d_front, &c->d_flags, &c->d_lam2pos, &c->d_lam2, &c->d_vec, &c->d_x12,
                     &c->d_s22, &c->d_bk_lf, &c->d_bk_perm, &c->d_bk_blk, &c->d_bk_dval, &c->d_bk_null,
-                    &c->d_work, &c->d_small, &c->d_gsmall, &c->d_k12, &c->d_solve};
+                    &c->d_work, &c->d_small, &c->d_gsmall, &c->d_k12, &c->d_solve, &c->d_gmag,
+                    &c->d_pos0, &c->d_vec2};
   for (DevBuf* b : bufs) hf_release(*b);
   delete c;
 }

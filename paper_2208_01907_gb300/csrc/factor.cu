@@ -67,7 +67,8 @@ __global__ void k_level_prep(const NodeDesc* __restrict__ nd, NodeState* __restr
   if (D > d.dc) { flags[FLAG_DELAY_OVERFLOW] = 1; D = d.dc; }
   NodeState S;
   S.k = 0; S.kp0 = 0; S.D = D; S.f = d.n + d.s + D; S.stopped = 0; S.dref = 1.0;   // reading R2
-  S.ksolve = 0; S.nmoved = 0; S.delay_off0 = off[0]; S.delay_off1 = off[1]; S.pad = 0;
+  S.ksolve = 0; S.nmoved = 0; S.delay_off0 = off[0]; S.delay_off1 = off[1];
+  S.nact = d.cand_all ? S.f : d.n;
   st[t] = S;
 }
 
@@ -148,6 +149,52 @@ __global__ void k_extend_add(const NodeDesc* __restrict__ nd, const NodeState* _
   }
 }
 
+// Term magnitudes G of the front rows (reading R3b): |K_ii| for the rows of Lambda_t,
+// plus what the children accumulated for their contribution rows.
+template <typename T>
+__global__ void k_g_assemble(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                             const int32_t* __restrict__ rowid, const int32_t* __restrict__ cbmap,
+                             const int64_t* __restrict__ diagpos, const double* __restrict__ kval,
+                             T* __restrict__ G, int32_t* __restrict__ pos0) {
+  const int t = t0 + blockIdx.x;
+  const NodeDesc d = nd[t];
+  const int f = st[t].f;
+  const int nown = d.cand_all ? 0 : d.n;
+  T* Gt = G + d.row_off;
+  for (int i = threadIdx.x; i < f; i += blockDim.x) {
+    Gt[i] = (i < nown) ? (T)fabs(kval[diagpos[rowid[d.row_off + i]]]) : T(0);
+    pos0[d.row_off + i] = i;                  // pivoting permutes this with the rows
+  }
+  __syncthreads();
+  for (int slot = 0; slot < 2; ++slot) {
+    const int c = slot == 0 ? d.child0 : d.child1;
+    if (c < 0) continue;
+    const NodeDesc dc = nd[c];
+    const int kc = st[c].k, m = st[c].f - kc;
+    const T* Gc = G + dc.row_off + kc;
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+      int tg = cbmap[dc.row_off + a];
+      if (tg >= 0) Gt[tg] += Gc[a];
+    }
+    __syncthreads();
+  }
+}
+
+// symmetric swap of rows/columns a < b of a lower-stored front (order f)
+template <typename T>
+__device__ __forceinline__ void sym_swap(T* F, int64_t ld, int f, int a, int b, int tid, int nt) {
+  const int nA = a, nB = b - a - 1, nC = f - b - 1;
+  const int tot = nA + nB + nC + 1;
+  for (int e = tid; e < tot; e += nt) {
+    int64_t x, y;
+    if (e < nA) { x = a + e * ld; y = b + e * ld; }                            // rows a, b left of a
+    else if (e < nA + nB) { int j = a + 1 + (e - nA); x = j + a * ld; y = b + j * ld; }
+    else if (e < nA + nB + nC) { int i = b + 1 + (e - nA - nB); x = i + a * ld; y = i + b * ld; }
+    else { x = a + a * ld; y = b + b * ld; }
+    T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Panel factorization with symmetric max-|diag| pivoting and the ratio test
 // (Sec. 2.1-2.2).  One CTA per front; up to nb pivots; columns of the panel are
@@ -155,42 +202,45 @@ __global__ void k_extend_add(const NodeDesc* __restrict__ nd, const NodeState* _
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0,
-                        T* __restrict__ arena, int32_t* __restrict__ rowid, int nb, double tau) {
+                        T* __restrict__ arena, int32_t* __restrict__ rowid, T* __restrict__ Gall,
+                        int32_t* __restrict__ pos0all, int nb, double tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_k[32];
   __shared__ int red_i[32], red_p[32];
-  __shared__ int s_q, s_stop;
+  __shared__ int s_q, s_act;
   const int t = t0 + blockIdx.x;
   const NodeDesc d = nd[t];
   NodeState* S = st + t;
   const int f = S->f;
   const int ncand = d.cand_all ? f : d.n;
   const int k0 = S->k;
+  int nact = S->nact;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (S->stopped || k0 >= ncand) {
+  if (S->stopped || k0 >= nact) {
     if (tid == 0) S->kp0 = k0;
     return;
   }
   T* F = arena + d.front_off;
+  T* G = Gall + d.row_off;
   const int64_t ld = d.ld;
   int32_t* rid = rowid + d.row_off;
+  int32_t* pos0 = pos0all + d.row_off;
   T* w = (T*)smem_raw;                        // nb entries
   T* dg = w + nb;                             // ncand entries (front positions)
   int* sid = (int*)(dg + ncand);              // ncand entries
-  for (int i = k0 + tid; i < ncand; i += nt) {
+  for (int i = k0 + tid; i < nact; i += nt) {
     dg[i] = F[i + i * ld];
     sid[i] = rid[i];
   }
   double dref = S->dref;
-  const int kend = min(ncand, k0 + nb);
   int k = k0;
   bool stopped = false;
   __syncthreads();
-  while (k < kend) {
-    // 1. argmax |dg| over the remaining candidates, ties to the smaller original index
+  while (k < k0 + nb && k < nact) {
+    // 1. argmax |dg| over the active candidates, ties to the smaller original index (R5)
     double bk = -2.0;
     int bi = 0x7fffffff, bp = -1;
-    for (int i = k + tid; i < ncand; i += nt) {
+    for (int i = k + tid; i < nact; i += nt) {
       double kk = piv_key(dg[i]);
       if (better(kk, sid[i], bk, bi)) { bk = kk; bi = sid[i]; bp = i; }
     }
@@ -206,29 +256,43 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
     if (tid == 0) {
       for (int wv = 1; wv < (nt + 31) / 32; ++wv)
         if (better(red_k[wv], red_i[wv], bk, bi)) { bk = red_k[wv]; bi = red_i[wv]; bp = red_p[wv]; }
-      // ratio test |d_{i+1} / d_i| < tau -> postpone the rest (R3); NaN fails it
-      s_stop = !(bk >= tau * dref);
+      // ratio test |d_{i+1} / d_i| < tau stops the set (R2/R3; NaN fails it);
+      // the null-pivot test |d| < tau * G postpones this candidate alone (R3b)
+      int act = 0;
+      if (!(bk >= tau * dref)) act = 1;
+      else if (!(bk >= tau * (double)G[bp])) act = 2;
+      s_act = act;
       s_q = bp;
     }
     __syncthreads();
-    if (s_stop) { stopped = true; break; }
-    const int q = s_q;
+    const int act = s_act, q = s_q;
+    if (act == 1) { stopped = true; break; }
+    if (act == 2) {
+      // move the null candidate to the end of the active range
+      const int last = nact - 1;
+      if (q != last) {
+        sym_swap(F, ld, f, q, last, tid, nt);
+        if (tid == 0) {
+          T td = dg[q]; dg[q] = dg[last]; dg[last] = td;
+          int ti = sid[q]; sid[q] = sid[last]; sid[last] = ti;
+          int tr = rid[q]; rid[q] = rid[last]; rid[last] = tr;
+          int tp = pos0[q]; pos0[q] = pos0[last]; pos0[last] = tp;
+          T tg = G[q]; G[q] = G[last]; G[last] = tg;
+        }
+      }
+      --nact;
+      __syncthreads();
+      continue;
+    }
     // 2. symmetric swap k <-> q in lower storage
     if (q != k) {
-      const int nA = k, nB = q - k - 1, nC = f - q - 1;
-      const int tot = nA + nB + nC + 1;
-      for (int e = tid; e < tot; e += nt) {
-        int64_t a, b;
-        if (e < nA) { a = k + e * ld; b = q + e * ld; }                        // rows k, q left of k
-        else if (e < nA + nB) { int j = k + 1 + (e - nA); a = j + k * ld; b = q + j * ld; }
-        else if (e < nA + nB + nC) { int i = q + 1 + (e - nA - nB); a = i + k * ld; b = i + q * ld; }
-        else { a = k + k * ld; b = q + q * ld; }
-        T tmp = F[a]; F[a] = F[b]; F[b] = tmp;
-      }
+      sym_swap(F, ld, f, k, q, tid, nt);
       if (tid == 0) {
         T td = dg[k]; dg[k] = dg[q]; dg[q] = td;
         int ti = sid[k]; sid[k] = sid[q]; sid[q] = ti;
         int tr = rid[k]; rid[k] = rid[q]; rid[q] = tr;
+        int tp = pos0[k]; pos0[k] = pos0[q]; pos0[q] = tp;
+        T tg = G[k]; G[k] = G[q]; G[q] = tg;
       }
     }
     __syncthreads();
@@ -243,12 +307,13 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
     }
     __syncthreads();
     const T dk = F[k + k * ld];
-    // 5. L(i, k) = c_i / d_k and the candidates' diagonals
+    // 5. L(i, k) = c_i / d_k, the candidates' diagonals and the term magnitudes
     for (int i = k + 1 + tid; i < f; i += nt) {
       T c = F[i + k * ld];
       T l = c / dk;
       F[i + k * ld] = l;
-      if (i < ncand) dg[i] -= l * c;
+      if (i < nact) dg[i] -= l * c;
+      G[i] += fabs(l * c);
     }
     dref = fabs((double)dk);
     ++k;
@@ -258,6 +323,7 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
     S->kp0 = k0;
     S->k = k;
     S->dref = dref;
+    S->nact = nact;
     if (stopped) S->stopped = 1;
   }
 }
@@ -423,6 +489,7 @@ int run_levels(hf_ctx* c) {
   const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
   NodeState* st = (NodeState*)c->d_state.p;
   T* arena = (T*)c->d_front.p;
+  T* gmag = (T*)c->d_gmag.p;
   int32_t* rowid = (int32_t*)c->d_rowid.p;
   int* flags = (int*)c->d_flags.p;
   const int nb = std::max(1, std::min(c->opts.panel, 256));
@@ -461,13 +528,16 @@ int run_levels(hf_ctx* c) {
       for (int slot = 0; slot < 2; ++slot)
         k_extend_add<T><<<dim3(bx, cnt), 128, 0, s>>>(nd, st, t0, slot, (const int32_t*)c->d_cbmap.p, arena);
     }
+    k_g_assemble<T><<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_cbmap.p,
+                                        (const int64_t*)c->d_diagpos.p, (const double*)c->d_kval.p, gmag,
+                                        (int32_t*)c->d_pos0.p);
     const int npan = (maxn + nb - 1) / nb;
     const size_t smem = (size_t)nb * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
     if (smem > 220 * 1024) return HF_ERR_ARG;
     const int pthreads = maxld > 1024 ? 1024 : 256;
     const int tiles = (maxld + TB - 1) / TB;
     for (int p = 0; p < npan; ++p) {
-      k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, nb, c->tau);
+      k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag, (int32_t*)c->d_pos0.p, nb, c->tau);
       k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena);
     }
     HF_CUDA_TRY(cudaGetLastError());
@@ -524,6 +594,8 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     }
     const size_t esz = dbl ? 8 : 4;
     if ((rc = hf_ensure(c->d_front, (size_t)c->front_elems * esz + 64))) return rc;
+    if ((rc = hf_ensure(c->d_gmag, (size_t)c->row_elems * esz + 64))) return rc;
+    if ((rc = hf_ensure(c->d_pos0, (size_t)c->row_elems * 4 + 64))) return rc;
     HF_CUDA_TRY(cudaMemsetAsync(c->d_flags.p, 0, FLAG_COUNT * sizeof(int) + 64, s));
     HF_CUDA_TRY(cudaMemcpyAsync(c->d_rowid.p, c->d_rowid_static.p, c->rowid_static.size() * 4,
                                 cudaMemcpyDeviceToDevice, s));

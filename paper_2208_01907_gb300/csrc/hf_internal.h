@@ -40,7 +40,7 @@ struct NodeState {
   int32_t nmoved;     // entries of this front moved into Lambda_2 by the enlargement
   int32_t delay_off0; // first delayed slot taken by child 0's rows
   int32_t delay_off1; // first delayed slot taken by child 1's rows
-  int32_t pad;
+  int32_t nact;       // candidates [k, nact) still active; [nact, n) were skipped as null pivots
 };
 
 // Assembly entry: front position (row, col) receives K[csr] (scaled).
@@ -80,6 +80,9 @@ struct hf_ctx {
   DevBuf d_cbmap;                    // per front: parent row of each contribution row (ld entries)
   DevBuf d_q, d_kval;                // scaling diag(Q) and scaled K values (FP64)
   DevBuf d_front;                    // front arena (float or double)
+  DevBuf d_gmag;                     // per front row: |K_ii| + accumulated |l|^2 |d| (null-pivot test)
+  DevBuf d_pos0;                     // per front row: its position before pivoting
+  DevBuf d_vec2;                     // per-front solve scratch (rows before pivoting)
   int front_prec = -1;               // precision the arena was sized for
   DevBuf d_flags;                    // int flags: [0] delay overflow, [1] numeric error
   DevBuf d_lam2pos;                  // L ints: position in Lambda_2 or -1
@@ -96,6 +99,7 @@ struct hf_ctx {
   // ---- Schur / Krylov (device, FP64) ----
   DevBuf d_x12, d_s22, d_bk_lf, d_bk_perm, d_bk_blk, d_bk_dval, d_bk_null;
   int kernel_dim = 0;
+  double s22_noise = 0;              // error estimate of S22 used by the kernel rule
   int gcr_iters = 0, solve_iters = 0;
   double gcr_relres = 0, solve_relres = 0;
   int64_t nnz_factor = 0;

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 namespace {
@@ -27,7 +28,8 @@ constexpr int SB = 32;       // column block of the triangular solves
 template <typename TF, typename TV>
 __global__ void k_fwd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
                       const TF* __restrict__ arena, const int32_t* __restrict__ rowid,
-                      const int32_t* __restrict__ cbmap, TV* __restrict__ vec, const TV* __restrict__ B,
+                      const int32_t* __restrict__ pos0all, const int32_t* __restrict__ cbmap,
+                      TV* __restrict__ vec, TV* __restrict__ vec2, const TV* __restrict__ B,
                       TV* __restrict__ Y, int m) {
   __shared__ TF Ls[SB][SB + 1];
   const int t = t0 + blockIdx.x;
@@ -37,14 +39,15 @@ __global__ void k_fwd(const NodeDesc* __restrict__ nd, const NodeState* __restri
   const int64_t ld = d.ld;
   const TF* F = arena + d.front_off;
   const int32_t* rid = rowid + d.row_off;
+  const int32_t* pos0 = pos0all + d.row_off;
   TV* V = vec + d.row_off * m;
+  TV* Vpre = vec2 + d.row_off * m;               // rows in the order before pivoting
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nown = d.cand_all ? 0 : d.n;
-  for (int e = tid; e < f * m; e += nt) {
-    int i = e / m, c = e - i * m;
-    V[e] = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
-  }
+  const int nperm = d.cand_all ? f : d.n;        // rows [0, nperm) were permuted by pivoting
+  for (int e = tid; e < f * m; e += nt) Vpre[e] = TV(0);
   __syncthreads();
+  // children's update rows land where the extend-add put them: before this front's pivoting
   for (int slot = 0; slot < 2; ++slot) {
     const int ch = slot == 0 ? d.child0 : d.child1;
     if (ch < 0) continue;
@@ -55,10 +58,19 @@ __global__ void k_fwd(const NodeDesc* __restrict__ nd, const NodeState* __restri
     for (int e = tid; e < mc * m; e += nt) {
       int a = e / m, c = e - a * m;
       int tg = map[a];
-      if (tg >= 0) V[(int64_t)tg * m + c] += U[e];
+      if (tg >= 0) Vpre[(int64_t)tg * m + c] += U[e];
     }
     __syncthreads();
   }
+  // into pivoted order, plus b on the rows of Lambda_t
+  for (int e = tid; e < f * m; e += nt) {
+    int i = e / m, c = e - i * m;
+    int src = (i < nperm) ? pos0[i] : i;
+    TV v = Vpre[(int64_t)src * m + c];
+    if (i < nown) v += B[(int64_t)rid[i] * m + c];
+    V[e] = v;
+  }
+  __syncthreads();
   for (int j0 = 0; j0 < ks; j0 += SB) {
     const int jb = min(SB, ks - j0);
     for (int e = tid; e < SB * SB; e += nt) {
@@ -220,6 +232,13 @@ __global__ void k_spmm(int64_t L, int m, const int64_t* __restrict__ rowptr, con
   }
 }
 
+// zero the columns of a row-major L x m block whose mask entry is set (deflation)
+__global__ void k_zero_cols(int64_t L, int m, const int* __restrict__ mask, double* __restrict__ R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L * m) return;
+  if (mask[e % m]) R[e] = 0.0;
+}
+
 // R = B - Z (elementwise)
 __global__ void k_sub(int64_t n, const double* __restrict__ B, const double* __restrict__ Z, double* __restrict__ R) {
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -361,10 +380,11 @@ __global__ void k_extract_k12(int M, const int64_t* __restrict__ rowptr, const i
 }
 
 // S = K22 - K21 X   (S: M x m; X: L x m row-major). One warp per Lambda_2 row.
+// mode 0: S = K22 - K21 X;  mode 1: S = Bbase(Lambda_2 rows) - K21 X;  mode 2: S = -K21 X
 __global__ void k_schur_rows(int M, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                              const double* __restrict__ val, const int32_t* __restrict__ lam2,
                              const int32_t* __restrict__ lam2pos, const double* __restrict__ X,
-                             const double* __restrict__ Bbase, int64_t ldb, double* __restrict__ S) {
+                             const double* __restrict__ Bbase, int64_t ldb, double* __restrict__ S, int mode) {
   int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= M) return;
@@ -373,12 +393,12 @@ __global__ void k_schur_rows(int M, int m, const int64_t* __restrict__ rowptr, c
     int c = c0 + lane;
     double acc = 0.0;
     if (c < m) {
-      if (Bbase) acc = Bbase[(int64_t)g * ldb + c];
+      if (mode == 1) acc = Bbase[(int64_t)g * ldb + c];
       for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
         int j = col[e];
         int p = lam2pos[j];
         if (p < 0) acc -= val[e] * X[(int64_t)j * m + c];
-        else if (!Bbase && p == c) acc += val[e];
+        else if (mode == 0 && p == c) acc += val[e];
       }
       S[i * m + c] = acc;
     }
@@ -396,34 +416,46 @@ __global__ void k_symmetrize(int M, double* __restrict__ S) {
 }
 
 // ---------------------------------------------------------------------------
-// Bunch-Kaufman LDL^T of S22 (FP64, alpha = (1+sqrt 17)/8) and kernel detection.
+// LDL^T of S22 (FP64) with complete symmetric (Bunch-Parlett) pivoting, 1x1 / 2x2
+// blocks, alpha = (1+sqrt 17)/8 (reading R11), then kernel detection (R10).
 // One CTA; A is the full symmetric working copy (M x M row-major).
 // ---------------------------------------------------------------------------
-__device__ void bk_block_reduce_max(double& v, int& idx, double* rv, int* ri) {
+__device__ void block_argmax(double& v, long long& key, double* rv, long long* rk) {
+  // maximum of v; ties go to the smaller key
   for (int o = 16; o > 0; o >>= 1) {
     double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+    if (ov > v || (ov == v && ok < key)) { v = ov; key = ok; }
   }
-  if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = v; ri[threadIdx.x >> 5] = idx; }
+  if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = v; rk[threadIdx.x >> 5] = key; }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w)
-      if (rv[w] > v || (rv[w] == v && ri[w] < idx)) { v = rv[w]; idx = ri[w]; }
-    rv[0] = v; ri[0] = idx;
+      if (rv[w] > v || (rv[w] == v && rk[w] < key)) { v = rv[w]; key = rk[w]; }
+    rv[0] = v; rk[0] = key;
   }
   __syncthreads();
-  v = rv[0]; idx = ri[0];
+  v = rv[0]; key = rk[0];
   __syncthreads();
 }
 
-__global__ void k_bunch_kaufman(int M, double* __restrict__ A, double* __restrict__ Lf, int* __restrict__ perm,
+__device__ void bp_swap(double* A, double* Lf, int* perm, int M, int a, int b) {
+  if (a == b) return;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) { double t = A[a * M + j]; A[a * M + j] = A[b * M + j]; A[b * M + j] = t; }
+  __syncthreads();
+  for (int i = threadIdx.x; i < M; i += blockDim.x) { double t = A[i * M + a]; A[i * M + a] = A[i * M + b]; A[i * M + b] = t; }
+  for (int j = threadIdx.x; j < a; j += blockDim.x) { double t = Lf[a * M + j]; Lf[a * M + j] = Lf[b * M + j]; Lf[b * M + j] = t; }
+  if (threadIdx.x == 0) { int t = perm[a]; perm[a] = perm[b]; perm[b] = t; }
+  __syncthreads();
+}
+
+__global__ void k_bunch_parlett(int M, double* __restrict__ A, double* __restrict__ Lf, int* __restrict__ perm,
                                 int* __restrict__ blk, double* __restrict__ dval, int* __restrict__ nullp,
-                                double kernel_eps, double kernel_gap, int* __restrict__ kdim_out,
-                                double* __restrict__ mags_work) {
+                                double kernel_eps, double kernel_gap, const int32_t* __restrict__ lam2,
+                                const int64_t* __restrict__ diagpos, const double* __restrict__ kval,
+                                double noise, int* __restrict__ kdim_out, double* __restrict__ mags_work) {
   __shared__ double rv[32];
-  __shared__ int ri[32];
-  __shared__ int s_size, s_swap_a, s_swap_b;
+  __shared__ long long rk[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   const double alpha = (1.0 + sqrt(17.0)) / 8.0;
   for (int e = tid; e < M * M; e += nt) Lf[e] = ((e / M) == (e % M)) ? 1.0 : 0.0;
@@ -431,62 +463,49 @@ __global__ void k_bunch_kaufman(int M, double* __restrict__ A, double* __restric
   __syncthreads();
   int k = 0;
   while (k < M) {
-    // lambda = max_{i>k} |A(i,k)|, r its row
-    double lam = -1.0;
-    int r = 0x7fffffff;
-    for (int i = k + 1 + tid; i < M; i += nt) {
-      double v = fabs(A[i * M + k]);
-      if (v > lam || (v == lam && i < r)) { lam = v; r = i; }
+    // mu0 = max |a_ii| (ties: smaller i); mu1 = max_{i>j} |a_ij| (ties: smaller j, then i)
+    double mu0 = -1.0;
+    long long i0 = 0x7fffffffffffffffLL;
+    for (int i = k + tid; i < M; i += nt) {
+      double v = fabs(A[i * M + i]);
+      if (v > mu0 || (v == mu0 && i < i0)) { mu0 = v; i0 = i; }
     }
-    bk_block_reduce_max(lam, r, rv, ri);
-    if (lam < 0) { lam = 0.0; r = k; }
-    const double akk = fabs(A[k * M + k]);
-    double sigma = 0.0;
-    bool need_sigma = !(max(akk, lam) == 0.0) && !(akk >= alpha * lam);
-    if (need_sigma) {
-      double sg = -1.0;
-      int dummy = 0;
-      for (int j = k + tid; j < M; j += nt)
-        if (j != r) { double v = fabs(A[r * M + j]); if (v > sg) sg = v; }
-      bk_block_reduce_max(sg, dummy, rv, ri);
-      sigma = max(sg, 0.0);
+    block_argmax(mu0, i0, rv, rk);
+    double mu1 = -1.0;
+    long long key1 = 0x7fffffffffffffffLL;
+    const int n2 = M - k;
+    for (long long e = tid; e < (long long)n2 * n2; e += nt) {
+      int j = k + (int)(e / n2), i = k + (int)(e % n2);
+      if (i <= j) continue;
+      double v = fabs(A[i * M + j]);
+      long long kk = (long long)j * M + i;
+      if (v > mu1 || (v == mu1 && kk < key1)) { mu1 = v; key1 = kk; }
     }
-    if (tid == 0) {
-      int size = 1, sa = k, sb = k;
-      if (max(akk, lam) == 0.0 || akk >= alpha * lam) {
-      } else if (akk * sigma >= alpha * lam * lam) {
-      } else if (fabs(A[r * M + r]) >= alpha * sigma) {
-        sa = k; sb = r;
-      } else {
-        size = 2; sa = k + 1; sb = r;
-      }
-      s_size = size; s_swap_a = sa; s_swap_b = sb;
-    }
-    __syncthreads();
-    const int size = s_size, sa = s_swap_a, sb = s_swap_b;
-    if (sa != sb) {
-      for (int j = tid; j < M; j += nt) { double tmp = A[sa * M + j]; A[sa * M + j] = A[sb * M + j]; A[sb * M + j] = tmp; }
+    block_argmax(mu1, key1, rv, rk);
+    if (mu1 < 0) mu1 = 0.0;
+    if (mu0 == 0.0 && mu1 == 0.0) {                 // the rest is exactly zero: zero 1x1 pivots
+      if (tid == 0) { blk[k] = 1; dval[2 * k] = 0.0; }
       __syncthreads();
-      for (int i = tid; i < M; i += nt) { double tmp = A[i * M + sa]; A[i * M + sa] = A[i * M + sb]; A[i * M + sb] = tmp; }
-      for (int j = tid; j < sa; j += nt) { double tmp = Lf[sa * M + j]; Lf[sa * M + j] = Lf[sb * M + j]; Lf[sb * M + j] = tmp; }
-      if (tid == 0) { int tp = perm[sa]; perm[sa] = perm[sb]; perm[sb] = tp; }
-      __syncthreads();
+      k += 1;
+      continue;
     }
-    if (size == 1) {
+    if (mu0 >= alpha * mu1) {
+      bp_swap(A, Lf, perm, M, k, (int)i0);
       const double dk = A[k * M + k];
       if (tid == 0) { blk[k] = 1; dval[2 * k] = dk; }
-      if (dk != 0.0) {
-        for (int i = k + 1 + tid; i < M; i += nt) Lf[i * M + k] = A[i * M + k] / dk;
-        __syncthreads();
-        const int n2 = M - k - 1;
-        for (int e = tid; e < n2 * n2; e += nt) {
-          int i = k + 1 + e / n2, j = k + 1 + e % n2;
-          A[i * M + j] -= Lf[i * M + k] * A[j * M + k];
-        }
+      for (int i = k + 1 + tid; i < M; i += nt) Lf[i * M + k] = A[i * M + k] / dk;
+      __syncthreads();
+      const int m2 = M - k - 1;
+      for (int e = tid; e < m2 * m2; e += nt) {
+        int i = k + 1 + e / m2, j = k + 1 + e % m2;
+        A[i * M + j] -= Lf[i * M + k] * A[j * M + k];
       }
       __syncthreads();
       k += 1;
     } else {
+      const int bj = (int)(key1 / M), bi = (int)(key1 % M);
+      bp_swap(A, Lf, perm, M, k, bj);
+      bp_swap(A, Lf, perm, M, k + 1, bi);
       const double a = A[k * M + k], b = A[(k + 1) * M + k], c = A[(k + 1) * M + k + 1];
       const double det = a * c - b * b;
       if (tid == 0) { blk[k] = 2; blk[k + 1] = 0; dval[2 * k] = a; dval[2 * k + 1] = b; dval[2 * (k + 1)] = c; }
@@ -496,9 +515,9 @@ __global__ void k_bunch_kaufman(int M, double* __restrict__ A, double* __restric
         Lf[i * M + k + 1] = (x1 * a - x0 * b) / det;
       }
       __syncthreads();
-      const int n2 = M - k - 2;
-      for (int e = tid; e < n2 * n2; e += nt) {
-        int i = k + 2 + e / n2, j = k + 2 + e % n2;
+      const int m2 = M - k - 2;
+      for (int e = tid; e < m2 * m2; e += nt) {
+        int i = k + 2 + e / m2, j = k + 2 + e % m2;
         A[i * M + j] -= Lf[i * M + k] * A[j * M + k] + Lf[i * M + k + 1] * A[j * M + k + 1];
       }
       __syncthreads();
@@ -507,6 +526,8 @@ __global__ void k_bunch_kaufman(int M, double* __restrict__ A, double* __restric
   }
   // kernel detection (reading R10): magnitudes per 1x1 pivot / 2x2 eigenvalue
   if (tid == 0) {
+    double ref = 0.0;                // max |K_ii| over Lambda_2: the unit reference
+    for (int i = 0; i < M; ++i) ref = fmax(ref, fabs(kval[diagpos[lam2[i]]]));
     double* mg = mags_work;          // M magnitudes, then M sorted copies
     for (int i = 0; i < M;) {
       if (blk[i] == 1) { mg[i] = fabs(dval[2 * i]); ++i; }
@@ -526,11 +547,13 @@ __global__ void k_bunch_kaufman(int M, double* __restrict__ A, double* __restric
     }
     int dim = 0;
     if (M > 0) {
-      if (s[0] == 0.0) dim = M;
+      const double scale = fmax(s[0], ref);
+      const double thr = fmax(kernel_eps * scale, noise);
+      if (scale == 0.0 || s[0] <= thr) dim = M;
       else {
         double best = 0.0;
         for (int i = 1; i < M; ++i) {
-          if (s[i] > kernel_eps * s[0]) continue;
+          if (s[i] > thr) continue;
           double ratio = (s[i] == 0.0) ? INFINITY : s[i - 1] / s[i];
           if (ratio >= kernel_gap && ratio > best) { best = ratio; dim = M - i; }
         }
@@ -653,7 +676,8 @@ struct Work {
 
 static int ensure_vec(hf_ctx* c, int m, size_t esz) {
   size_t need = (size_t)c->row_elems * m * esz + 64;
-  return hf_ensure(c->d_vec, need);
+  int rc = hf_ensure(c->d_vec, need);
+  return rc ? rc : hf_ensure(c->d_vec2, need);
 }
 
 // Apply the triangular solves with the front factor (TF) in vector precision TV.
@@ -671,7 +695,8 @@ static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const 
   TV* vec = (TV*)c->d_vec.p;
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
-    k_fwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, cbmap, vec, Bin, Ytmp, m);
+    k_fwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, (const int32_t*)c->d_pos0.p, cbmap, vec,
+                                      (TV*)c->d_vec2.p, Bin, Ytmp, m);
   }
   HF_CUDA_TRY(cudaGetLastError());
   const int M = (int)c->M;
@@ -778,13 +803,16 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   const size_t mm = (size_t)m * m;
   std::vector<double> hnorm(m), bnorm(m);
   DevBuf& sm = c->d_gsmall;
-  size_t small_need = ((size_t)(maxit + 2) * mm * 2 + 4 * mm + 2 * (size_t)m + 64) * 8 + (mm + m) * 8;
+  size_t small_need = ((size_t)(maxit + 2) * mm * 2 + 6 * mm + 4 * (size_t)m + 64) * 8;
   if ((rc = hf_ensure(sm, small_need))) return rc;
   double* Mstore = (double*)sm.p;                 // (maxit+1) Gram matrices M_n
   double* Gm = Mstore + (size_t)(maxit + 1) * mm;
   double* Cm = Gm + mm;
   double* wk = Cm + mm;                           // small solve work (m*m + m)
   double* diag = wk + mm + m + 8;                 // m x m scratch for norms
+  int* dmask = (int*)(diag + mm);                 // converged-column mask (m ints)
+  std::vector<int> hmask(m, 0);
+  std::vector<double> hist_res;
   const unsigned nb = nblk((int64_t)blk, 256);
   const int use_smem = mm * 8 <= 48 * 1024;
   const size_t axpy_smem = use_smem ? mm * 8 : 0;
@@ -800,6 +828,8 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   };
   if ((rc = colnorms(B, bnorm))) return rc;
   for (auto& v : bnorm) if (v == 0) v = 1.0;
+  const char* ve = std::getenv("HF_VERBOSE");
+  const bool verbose = ve && ve[0] == '1';
   // X0 = Q^-1 B, R0 = B - K11 X0, W0 = Q^-1 R0, P0 = W0, Q0 = K11 P0
   if ((rc = precond(c, m, B, X, tmp))) return rc;
   spmm(c, m, X, Z);
@@ -821,8 +851,26 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     if ((rc = colnorms(R, hnorm))) return rc;
     res = 0;
     for (int i = 0; i < m; ++i) res = std::max(res, hnorm[i] / bnorm[i]);
+    if (verbose) std::fprintf(stderr, "[hf] block GCR m=%d iter %d max |r|/|b| = %.3e\n", m, it, res);
+    hist_res.push_back(res);
     if (!(res > c->opts.gcr_tol)) { conv = true; break; }
     if (n + 1 >= maxit) break;
+    // stagnation: less than a 2x reduction over three iterations
+    const size_t h = hist_res.size();
+    if (h >= 4 && hist_res[h - 1] > 0.5 * hist_res[h - 4]) {
+      conv = res <= 100.0 * c->opts.gcr_tol;
+      break;
+    }
+    // deflation: converged columns stop contributing search directions
+    bool any = false;
+    for (int i = 0; i < m; ++i) {
+      int mk = !(hnorm[i] / bnorm[i] > c->opts.gcr_tol);
+      any |= (mk != hmask[i]);
+      hmask[i] = mk;
+    }
+    if (any) HF_CUDA_TRY(cudaMemcpyAsync(dmask, hmask.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (std::count(hmask.begin(), hmask.end(), 1) > 0)
+      k_zero_cols<<<nb, 256, 0, s>>>(L, m, dmask, R);
     if ((rc = precond(c, m, R, W, tmp))) return rc;
     spmm(c, m, W, Z);
     double* Pn = Pm(n + 1);
@@ -854,9 +902,10 @@ static int bk_factor(hf_ctx* c) {
   HF_CUDA_TRY(cudaMemcpyAsync(A, c->d_s22.p, (size_t)M * M * 8, cudaMemcpyDeviceToDevice, s));
   int* kd = (int*)((int*)c->d_flags.p + FLAG_COUNT + 8);
   double* mags = (double*)c->d_bk_dval.p + 2 * M;
-  k_bunch_kaufman<<<1, 256, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
+  k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
                                     (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
-                                    c->opts.kernel_gap, kd, mags);
+                                    c->opts.kernel_gap, (const int32_t*)c->d_lam2.p, (const int64_t*)c->d_diagpos.p,
+                                    (const double*)c->d_kval.p, c->s22_noise, kd, mags);
   HF_CUDA_TRY(cudaGetLastError());
   int h = 0;
   HF_CUDA_TRY(cudaMemcpyAsync(&h, kd, 4, cudaMemcpyDeviceToHost, s));
@@ -890,14 +939,38 @@ int hf_schur_impl(hf_ctx* c) {
                                       (const int32_t*)c->d_lam2pos.p, B);
       grc = block_gcr(c, M, B, X12, &c->gcr_iters, &c->gcr_relres);
       if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
+      // error estimate of S22 for the kernel rule: E = K21 Q^-1 (K12 - K11 X12)
+      {
+        const size_t blk = (size_t)L * M;
+        double* Rt = (double*)c->d_work.p;
+        double* Wt = Rt + blk;
+        double* Zt = Wt + blk;
+        double* tmp = Zt + blk;
+        spmm(c, M, X12, Zt);
+        k_sub<<<nblk((int64_t)blk, 256), 256, 0, s>>>((int64_t)blk, B, Zt, Rt);
+        if ((rc = precond(c, M, Rt, Wt, tmp))) return rc;
+        double* E = (double*)c->d_gsmall.p;
+        k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
+                                                            (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
+                                                            (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
+                                                            Wt, nullptr, 0, E, 2);
+        std::vector<double> hE((size_t)M * M);
+        HF_CUDA_TRY(cudaMemcpyAsync(hE.data(), E, hE.size() * 8, cudaMemcpyDeviceToHost, s));
+        HF_CUDA_TRY(cudaStreamSynchronize(s));
+        double mx = 0;
+        for (double v : hE) mx = std::max(mx, std::fabs(v));
+        c->s22_noise = 100.0 * mx;
+      }
       k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
                                                           (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
                                                           (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
-                                                          X12, nullptr, 0, (double*)c->d_s22.p);
+                                                          X12, nullptr, 0, (double*)c->d_s22.p, 0);
       k_symmetrize<<<nblk((int64_t)M * M, 256), 256, 0, s>>>(M, (double*)c->d_s22.p);
       HF_CUDA_TRY(cudaGetLastError());
     } else {
       if ((rc = hf_s22_from_factor(c))) return rc;
+      // S22 from the factor: its error is the unit roundoff of the factor's precision
+      c->s22_noise = 100.0 * (c->prec == HF_PREC_FP64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
     }
   }
   if ((rc = bk_factor(c))) return rc;
@@ -940,7 +1013,7 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
       k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, m, (const int64_t*)c->d_rowptr.p,
                                                           (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
                                                           (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
-                                                          y1, bi, m, y2);
+                                                          y1, bi, m, y2, 1);
       s22_solve();
       k_backsub_x1<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, M, m, (const double*)c->d_x12.p, x2,
                                                             (const int32_t*)c->d_lam2pos.p, y1);
@@ -975,4 +1048,15 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
   HF_CUDA_TRY(cudaGetLastError());
   HF_CUDA_TRY(cudaStreamSynchronize(s));
   return grc;
+}
+
+int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W) {
+  if (!c || m < 1 || !R || !W) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  const size_t blk = (size_t)c->L * m;
+  int rc;
+  if ((rc = hf_ensure(c->d_solve, (blk * 3 + 64) * 8))) return rc;
+  if ((rc = precond(c, m, R, W, c->d_solve.p))) return rc;
+  HF_CUDA_TRY(cudaStreamSynchronize(hf_stream(c)));
+  return HF_OK;
 }

@@ -22,7 +22,7 @@ HF_PREC_MIXED, HF_PREC_FP64, HF_PREC_FP32 = 0, 1, 2
 EXPORTED = (
     "hf_default_opts", "hf_error_string", "hf_analyze", "hf_factorize", "hf_schur", "hf_solve",
     "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
-    "hf_get_s22", "hf_get_s22_factor", "hf_free",
+    "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_free",
 )
 
 
@@ -78,6 +78,8 @@ def lib():
     L.hf_get_tree.argtypes = [vp, vp, vp, vp]
     L.hf_get_pivots.argtypes = [vp, vp, vp, vp, vp]
     L.hf_get_factor.argtypes = [vp, vp, vp, vp, vp]
+    L.hf_get_pivot_events.argtypes = [vp, vp, vp, vp]
+    L.hf_precond.argtypes = [vp, i32, vp, vp]
     L.hf_get_x12.argtypes = [vp, vp, i64]
     L.hf_get_s22.argtypes = [vp, vp]
     L.hf_get_s22_factor.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -156,6 +158,11 @@ class HybridFactor:
         return _check(lib().hf_solve(self._h, nrhs, _ptr(b_dev), self.L, _ptr(x_dev), self.L),
                       "hf_solve", allow=(HF_ERR_NOT_CONVERGED,))
 
+    def precond(self, R_dev, W_dev):
+        """W = Q^-1 R (Sec. 3.2) on row-major L x m torch float64 CUDA tensors (scaled unknowns)."""
+        m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
+        _check(lib().hf_precond(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond")
+
     # -- getters -----------------------------------------------------------
     def info(self) -> dict:
         inf = hf_info()
@@ -186,6 +193,21 @@ class HybridFactor:
         _check(lib().hf_get_pivots(self._h, _ptr(ptr), _ptr(piv), _ptr(moved), C.byref(nm)), "hf_get_pivots")
         per = [piv[ptr[t]:ptr[t + 1]].astype(np.int64) for t in range(nn + 1)]
         return per[:nn], per[nn], moved[:nm.value].astype(np.int64)
+
+    def pivot_events(self):
+        """Per front (tree nodes, then the Lambda_0 stage): (eliminated, stopped, skipped) index arrays."""
+        nn = self.info()["n_nodes"]
+        ptr = np.zeros(nn + 2, np.int64)
+        _check(lib().hf_get_pivot_events(self._h, _ptr(ptr), None, None), "hf_get_pivot_events")
+        cand = np.zeros(max(int(ptr[-1]), 1), np.int32)
+        cnt = np.zeros(2 * (nn + 1), np.int32)
+        _check(lib().hf_get_pivot_events(self._h, _ptr(ptr), _ptr(cand), _ptr(cnt)), "hf_get_pivot_events")
+        out = []
+        for t in range(nn + 1):
+            c = cand[ptr[t]:ptr[t + 1]].astype(np.int64)
+            k, na = int(cnt[2 * t]), int(cnt[2 * t + 1])
+            out.append((c[:k], c[k:na], c[na:][::-1]))
+        return out
 
     def factor(self):
         per, sr, _ = self.pivots()

@@ -27,13 +27,15 @@ def run_gpu(system, tau=1e-2, nrhs=1, rhs_seed=3, rhs_mode="uniform", solve=True
     return out
 
 
-def replay(system, H, tau, n_enlarge=4, slack=1e-4):
+def replay(system, H, tau, n_enlarge=4, slack=1e-4, dtype=np.float32):
     """Oracle factorization on the GPU's tree, following the GPU's pivot decisions."""
     _, sets = H.tree()
-    per, lam0_piv, moved = H.pivots()
+    ev = H.pivot_events()
+    _, _, moved = H.pivots()
     q, K = O.scale_matrix(system.to_scipy())
-    fac = O.threshold_factorize(K, sets, tau, n_enlarge,
-                                replay={"node_pivots": per, "lam0_pivots": lam0_piv}, slack=slack)
+    rp = {"node_pivots": [e[0] for e in ev[:-1]], "node_skipped": [e[2] for e in ev[:-1]],
+          "lam0_pivots": ev[-1][0], "lam0_skipped": ev[-1][2]}
+    fac = O.threshold_factorize(K, sets, tau, n_enlarge, replay=rp, slack=slack, dtype=dtype)
     return q, K, fac, moved
 
 
