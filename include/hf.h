@@ -93,7 +93,18 @@ typedef struct {
   int64_t front_bytes;    /* device bytes of the front arena */
   int32_t delay_retries;  /* times the delay capacity had to be grown */
   int32_t precision;      /* form used */
+  double  trailing_flops; /* algorithmic flops of the trailing (Schur) updates of the fronts:
+                             sum over panels of 2 x width x (lower-triangle entries updated) */
+  int64_t solve_factor_entries; /* factor entries one forward (or backward) sweep of the K11
+                             solve reads */
 } hf_info;
+
+/* Kernel classes of the profile (hf_get_profile). */
+enum {
+  HF_PROF_SCALE = 0, HF_PROF_ASSEMBLE, HF_PROF_PANEL, HF_PROF_TRAILING, HF_PROF_LAMBDA,
+  HF_PROF_TRSV_FWD, HF_PROF_TRSV_BWD, HF_PROF_SPMM, HF_PROF_GRAM, HF_PROF_BLOCK_UPDATE,
+  HF_PROF_SCHUR, HF_PROF_DENSE_LDLT, HF_PROF_VECTOR, HF_NPROF
+};
 
 /* Fill *opts with the defaults listed above.  Returns HF_ERR_ARG if opts is NULL. */
 int hf_default_opts(hf_opts* opts);
@@ -162,6 +173,20 @@ int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int
  * Errors: HF_ERR_STATE (before hf_factorize), HF_ERR_ARG, HF_ERR_CUDA, HF_ERR_OOM.
  */
 int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
+
+/*
+ * Adjoint of the solve with respect to the matrix values.  For x = Kbar^-1 b and an
+ * objective J(x), with lam = Kbar^-T dJ/dx (Kbar is symmetric, so lam comes from
+ * hf_solve with the same factor), dJ/dKbar_ij = -sum_r lam_i^r x_j^r for every stored
+ * entry (i, j).  Writes that gradient in CSR order (the order given to hf_analyze).
+ *   nrhs       number of columns of x and lam (>= 1)
+ *   x, ldx     device, column-major L x nrhs, ldx >= L
+ *   lam, ldl   device, column-major L x nrhs, ldl >= L
+ *   grad_vals  device, rowptr[L] doubles (overwritten)
+ * Errors: HF_ERR_ARG, HF_ERR_STATE (before hf_factorize), HF_ERR_CUDA.
+ */
+int hf_values_adjoint(hf_ctx* ctx, int nrhs, const double* x, int64_t ldx, const double* lam, int64_t ldl,
+                      double* grad_vals);
 
 /*
  * The split of Alg. 1 step 1 (host outputs, any may be NULL):
@@ -236,6 +261,19 @@ int hf_get_s22(hf_ctx* ctx, double* s22);
  *   null   M entries: 1 where the pivot magnitude was declared null (kernel)
  */
 int hf_get_s22_factor(hf_ctx* ctx, int32_t* perm, double* lf, int32_t* dblk, double* dval, int32_t* null_piv);
+
+/*
+ * Tracing.  Kernel launches are always counted per class.  With hf_profile(ctx, 1) every
+ * launch is also bracketed by CUDA events recorded on the context's stream; hf_get_profile
+ * synchronises that stream, returns per class the summed device time (ms, HF_NPROF
+ * entries), the launch count, and the algorithmic flops and bytes of those launches (what
+ * the operation must compute and move: e.g. 2 N M^2 for an N x M by M x M block update,
+ * the factor entries read by a triangular sweep) since the last call, and resets them.
+ * Any output may be NULL.  hf_profile_name gives the class names (static strings).
+ */
+int hf_profile(hf_ctx* ctx, int enable);
+int hf_get_profile(hf_ctx* ctx, double* ms, int64_t* launches, double* flops, double* bytes);
+const char* hf_profile_name(int cls);
 
 /* Release every device and host buffer of the context.  NULL is ignored. */
 void hf_free(hf_ctx* ctx);

@@ -30,6 +30,11 @@ the design notes):
       postponed on its own (skipped) and the elimination of the set goes on.
       Without it, float32 noise pivots of a singular K pass the ratio test
       and the kernel never reaches S22 (Sec. 3 requires it there).
+  R14 The GPU path forms q_{n+1} = A p_{n+1} by a product with A instead of the
+      recurrence q_{n+1} = z_{n+1} + sum beta q_m (Sec. 3.4 keeps the
+      recurrence to save one SpMV for a single rhs; with M rhs the recurrence
+      costs N M^2 n flops against nnz M for the product).  Both equal A p;
+      the oracle keeps the paper's recurrence.
   R10 Kernel detection: pivot magnitudes of the S22 LDL^T sorted; the kernel
       is the tail after the largest ratio gap >= gap_min whose tail lies
       below kernel_eps * max.

@@ -1,0 +1,44 @@
+"""Differentiable hybrid solve (adjoint through the same factorization).
+
+``HybridSolve.apply(H, vals, b)`` factorizes K-bar (CSR values ``vals`` on the
+pattern of ``H``), forms the Schur complement (Alg. 1) and returns x = K-bar^-1 b
+(Alg. 2).  Backward: lam = K-bar^-T dJ/dx is one more hf_solve with the factor
+kept by the context (K-bar is symmetric), dJ/db = lam, and dJ/dvals comes from
+hf_values_adjoint (dJ/dK-bar_ij = -lam_i x_j).  Only the context (factor, X12,
+S22 factors) and x are kept for the backward pass.
+"""
+from __future__ import annotations
+
+import torch
+
+from .hf import HybridFactor
+
+
+class HybridSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, H: HybridFactor, vals: torch.Tensor, b: torch.Tensor, tau: float = 1e-2):
+        vals_c = vals.detach().contiguous()
+        H.factorize(vals_c, tau)
+        H.schur()
+        bt = b.detach().reshape(-1, H.L).contiguous()          # (nrhs, L) = column-major L x nrhs
+        x = torch.zeros_like(bt)
+        H.solve(bt, x)
+        ctx.H = H
+        ctx.b_shape = b.shape
+        ctx.save_for_backward(x)
+        return x.reshape(b.shape)
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        H = ctx.H
+        g = gx.detach().reshape(-1, H.L).contiguous()
+        lam = torch.zeros_like(g)
+        H.solve(g, lam)                                      # K-bar^T = K-bar: the same factor
+        gvals = torch.empty(H._col.shape[0], dtype=torch.float64, device=x.device)
+        H.values_adjoint(x, lam, gvals)
+        return None, gvals, lam.reshape(ctx.b_shape), None
+
+
+def hybrid_solve(H: HybridFactor, vals: torch.Tensor, b: torch.Tensor, tau: float = 1e-2) -> torch.Tensor:
+    return HybridSolve.apply(H, vals, b, tau)

@@ -12,6 +12,8 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau);
 int hf_schur_impl(hf_ctx* c);
 int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W);
+int hf_values_adjoint_impl(hf_ctx* c, int m, const double* x, int64_t ldx, const double* lam, int64_t ldl,
+                           double* grad);
 
 static thread_local char g_cuda_msg[256] = "";
 
@@ -38,7 +40,65 @@ void hf_release(DevBuf& b) {
   b.bytes = 0;
 }
 
+ProfScope::ProfScope(hf_ctx* ctx, int k) : c(ctx), cls(k), idx(0), on(ctx && ctx->prof_on) {
+  if (!c) return;
+  c->launches[cls]++;
+  if (!on) return;
+  while (c->ev_pool.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+    c->ev_pool.push_back(e);
+  }
+  idx = c->ev_used;
+  c->ev_used += 2;
+  cudaEventRecord(c->ev_pool[idx], (cudaStream_t)c->opts.cuda_stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!on) return;
+  cudaEventRecord(c->ev_pool[idx + 1], (cudaStream_t)c->opts.cuda_stream);
+  c->prof_recs.push_back({cls, idx});
+}
+
 extern "C" {
+
+int hf_profile(hf_ctx* c, int enable) {
+  if (!c) return HF_ERR_ARG;
+  c->prof_on = enable != 0;
+  c->prof_recs.clear();
+  c->ev_used = 0;
+  for (auto& v : c->launches) v = 0;
+  for (auto& v : c->work_flops) v = 0;
+  for (auto& v : c->work_bytes) v = 0;
+  return HF_OK;
+}
+
+int hf_get_profile(hf_ctx* c, double* ms, int64_t* launches, double* flops, double* bytes) {
+  if (!c) return HF_ERR_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)c->opts.cuda_stream) != cudaSuccess) return HF_ERR_CUDA;
+  double acc[HF_NPROF] = {0};
+  for (auto& r : c->prof_recs) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, c->ev_pool[r.second], c->ev_pool[r.second + 1]) == cudaSuccess) acc[r.first] += t;
+  }
+  if (ms) for (int i = 0; i < HF_NPROF; ++i) ms[i] = acc[i];
+  if (launches) for (int i = 0; i < HF_NPROF; ++i) launches[i] = c->launches[i];
+  if (flops) for (int i = 0; i < HF_NPROF; ++i) flops[i] = c->work_flops[i];
+  if (bytes) for (int i = 0; i < HF_NPROF; ++i) bytes[i] = c->work_bytes[i];
+  c->prof_recs.clear();
+  c->ev_used = 0;
+  for (auto& v : c->launches) v = 0;
+  for (auto& v : c->work_flops) v = 0;
+  for (auto& v : c->work_bytes) v = 0;
+  return HF_OK;
+}
+
+const char* hf_profile_name(int cls) {
+  static const char* names[HF_NPROF] = {"scale", "assemble", "panel", "trailing", "lambda0",
+                                        "trsv_fwd", "trsv_bwd", "spmm", "gram", "block_update",
+                                        "schur", "dense_ldlt", "vector"};
+  return (cls >= 0 && cls < HF_NPROF) ? names[cls] : "unknown";
+}
 
 int hf_default_opts(hf_opts* o) {
   if (!o) return HF_ERR_ARG;
@@ -104,6 +164,12 @@ int hf_precond(hf_ctx* c, int m, const double* R, double* W) {
   return hf_precond_impl(c, m, R, W);
 }
 
+int hf_values_adjoint(hf_ctx* c, int nrhs, const double* x, int64_t ldx, const double* lam, int64_t ldl,
+                      double* grad_vals) {
+  if (!c) return HF_ERR_ARG;
+  return hf_values_adjoint_impl(c, nrhs, x, ldx, lam, ldl, grad_vals);
+}
+
 int hf_get_info(hf_ctx* c, hf_info* info) {
   if (!c || !info) return HF_ERR_ARG;
   std::memset(info, 0, sizeof(*info));
@@ -126,6 +192,21 @@ int hf_get_info(hf_ctx* c, hf_info* info) {
     fl += 2.0 * (k * (f - 1) * (f - 1) - (f - 1) * k * (k - 1) + k * (k - 1) * (2 * k - 1) / 6.0) / 2.0;
   }
   info->factor_flops = fl;
+  {
+    const double nb = std::max(1, std::min(c->opts.panel, 256));
+    double tf = 0;
+    int64_t se = 0;
+    for (size_t t = 0; t < c->state_host.size(); ++t) {
+      const double k = c->state_host[t].k, f = c->state_host[t].f, ks = c->state_host[t].ksolve;
+      for (double k0 = 0; k0 < k; k0 += nb) {
+        double k1 = std::min(k, k0 + nb), n = f - k1;
+        tf += (k1 - k0) * n * (n + 1);
+      }
+      se += (int64_t)(f * ks - ks * (ks + 1) / 2);
+    }
+    info->trailing_flops = tf;
+    info->solve_factor_entries = se;
+  }
   info->front_bytes = c->d_front.p ? (int64_t)c->d_front.bytes : 0;
   info->delay_retries = c->delay_retries;
   info->precision = c->prec;
@@ -297,8 +378,9 @@ void hf_free(hf_ctx* c) {
                     &c->d_front, &c->d_flags, &c->d_lam2pos, &c->d_lam2, &c->d_vec, &c->d_x12,
                     &c->d_s22, &c->d_bk_lf, &c->d_bk_perm, &c->d_bk_blk, &c->d_bk_dval, &c->d_bk_null,
                     &c->d_work, &c->d_small, &c->d_gsmall, &c->d_k12, &c->d_solve, &c->d_gmag,
-                    &c->d_pos0, &c->d_vec2};
+                    &c->d_pos0, &c->d_invpos};
   for (DevBuf* b : bufs) hf_release(*b);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 

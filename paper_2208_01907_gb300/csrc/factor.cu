@@ -394,6 +394,28 @@ __global__ void __launch_bounds__(256) k_trailing(const NodeDesc* __restrict__ n
   }
 }
 
+// After the factorization the contribution maps of every child are re-expressed in the
+// parent's pivoted row order (the solves work in that order).
+__global__ void k_cbmap_post(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                             const int32_t* __restrict__ pos0, int32_t* __restrict__ inv,
+                             int32_t* __restrict__ cbmap) {
+  const int p = blockIdx.x;
+  const NodeDesc d = nd[p];
+  const int nperm = d.cand_all ? st[p].f : d.n;
+  for (int i = threadIdx.x; i < nperm; i += blockDim.x) inv[d.row_off + pos0[d.row_off + i]] = i;
+  __syncthreads();
+  for (int slot = 0; slot < 2; ++slot) {
+    const int ch = slot == 0 ? d.child0 : d.child1;
+    if (ch < 0) continue;
+    const NodeDesc dc = nd[ch];
+    const int mc = st[ch].f - st[ch].k;
+    for (int a = threadIdx.x; a < mc; a += blockDim.x) {
+      int tg = cbmap[dc.row_off + a];
+      if (tg >= 0 && tg < nperm) cbmap[dc.row_off + a] = inv[d.row_off + tg];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Enlargement (Sec. 2.2, reading R13) and collection of Lambda_2
 // ---------------------------------------------------------------------------
@@ -511,39 +533,54 @@ int run_levels(hf_ctx* c) {
       maxasm = std::max<int64_t>(maxasm, d.asm_cnt);
       has_children |= (d.child0 >= 0);
     }
-    k_level_prep<<<(cnt + 127) / 128, 128, 0, s>>>(nd, st, t0, cnt, flags);
+    HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_prep<<<(cnt + 127) / 128, 128, 0, s>>>(nd, st, t0, cnt, flags));
     if (has_children)
-      k_level_maps<<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_smap.p, (int32_t*)c->d_cbmap.p);
+      HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_maps<<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_smap.p, (int32_t*)c->d_cbmap.p));
     {
       int bx = std::min(std::max(1, maxld), 512);
-      k_front_zero<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, st, t0, arena);
+      HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_front_zero<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, st, t0, arena));
     }
     if (maxasm > 0) {
       int bx = (int)std::min<int64_t>((maxasm + 255) / 256, 1024);
-      k_front_asm<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, t0, (const AsmEntry*)c->d_asm.p,
-                                                   (const double*)c->d_kval.p, arena);
+      HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_front_asm<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, t0, (const AsmEntry*)c->d_asm.p,
+                                                   (const double*)c->d_kval.p, arena));
     }
     if (has_children) {
       int bx = std::min(std::max(1, maxld), 1024);
       for (int slot = 0; slot < 2; ++slot)
-        k_extend_add<T><<<dim3(bx, cnt), 128, 0, s>>>(nd, st, t0, slot, (const int32_t*)c->d_cbmap.p, arena);
+        HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_extend_add<T><<<dim3(bx, cnt), 128, 0, s>>>(nd, st, t0, slot, (const int32_t*)c->d_cbmap.p, arena));
     }
-    k_g_assemble<T><<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_cbmap.p,
+    HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_g_assemble<T><<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_cbmap.p,
                                         (const int64_t*)c->d_diagpos.p, (const double*)c->d_kval.p, gmag,
-                                        (int32_t*)c->d_pos0.p);
+                                        (int32_t*)c->d_pos0.p));
     const int npan = (maxn + nb - 1) / nb;
     const size_t smem = (size_t)nb * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
     if (smem > 220 * 1024) return HF_ERR_ARG;
     const int pthreads = maxld > 1024 ? 1024 : 256;
     const int tiles = (maxld + TB - 1) / TB;
     for (int p = 0; p < npan; ++p) {
-      k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag, (int32_t*)c->d_pos0.p, nb, c->tau);
-      k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena);
+      HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag, (int32_t*)c->d_pos0.p, nb, c->tau));
+      HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena));
     }
     HF_CUDA_TRY(cudaGetLastError());
   }
   (void)nn;
   return HF_OK;
+}
+
+// algorithmic work of the trailing updates of a finished factorization (host state)
+static void trailing_work(hf_ctx* c, size_t esz) {
+  const double nb = std::max(1, std::min(c->opts.panel, 256));
+  double fl = 0, by = 0;
+  for (const NodeState& S : c->state_host) {
+    for (double k0 = 0; k0 < S.k; k0 += nb) {
+      double k1 = std::min<double>(S.k, k0 + nb), n = S.f - k1;
+      fl += (k1 - k0) * n * (n + 1);
+      by += n * (n + 1) / 2 * 2 * esz + n * (k1 - k0) * esz;   // C read+write, panel read
+    }
+  }
+  c->work_flops[HF_PROF_TRAILING] += fl;
+  c->work_bytes[HF_PROF_TRAILING] += by;
 }
 
 }  // namespace
@@ -596,20 +633,26 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     if ((rc = hf_ensure(c->d_front, (size_t)c->front_elems * esz + 64))) return rc;
     if ((rc = hf_ensure(c->d_gmag, (size_t)c->row_elems * esz + 64))) return rc;
     if ((rc = hf_ensure(c->d_pos0, (size_t)c->row_elems * 4 + 64))) return rc;
+    if ((rc = hf_ensure(c->d_invpos, (size_t)c->row_elems * 4 + 64))) return rc;
     HF_CUDA_TRY(cudaMemsetAsync(c->d_flags.p, 0, FLAG_COUNT * sizeof(int) + 64, s));
     HF_CUDA_TRY(cudaMemcpyAsync(c->d_rowid.p, c->d_rowid_static.p, c->rowid_static.size() * 4,
                                 cudaMemcpyDeviceToDevice, s));
     const int64_t L = c->L;
-    k_scale_diag<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_diagpos.p, vals, (double*)c->d_q.p);
-    k_scale_vals<<<(unsigned)((L * 32 + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
+    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_diag<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_diagpos.p, vals, (double*)c->d_q.p));
+    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_vals<<<(unsigned)((L * 32 + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
                                                           vals, (const double*)c->d_q.p, (double*)c->d_kval.p,
-                                                          (int*)c->d_flags.p);
+                                                          (int*)c->d_flags.p));
     HF_CUDA_TRY(cudaGetLastError());
     rc = dbl ? run_levels<double>(c) : run_levels<float>(c);
     if (rc) return rc;
+    HF_LAUNCH(c, HF_PROF_LAMBDA, k_cbmap_post<<<c->n_nodes + 1, 256, 0, s>>>((const NodeDesc*)c->d_nodes.p,
+                                                                            (const NodeState*)c->d_state.p,
+                                                                            (const int32_t*)c->d_pos0.p,
+                                                                            (int32_t*)c->d_invpos.p,
+                                                                            (int32_t*)c->d_cbmap.p));
     int64_t* counts = (int64_t*)((int*)c->d_flags.p + FLAG_COUNT);
-    k_finalize<<<1, 256, 0, s>>>((const NodeDesc*)c->d_nodes.p, (NodeState*)c->d_state.p, c->n_nodes,
-                                 c->opts.n_enlarge, (const int32_t*)c->d_rowid.p, (int32_t*)c->d_lam2.p, counts);
+    HF_LAUNCH(c, HF_PROF_LAMBDA, k_finalize<<<1, 256, 0, s>>>((const NodeDesc*)c->d_nodes.p, (NodeState*)c->d_state.p, c->n_nodes,
+                                 c->opts.n_enlarge, (const int32_t*)c->d_rowid.p, (int32_t*)c->d_lam2.p, counts));
     HF_CUDA_TRY(cudaGetLastError());
     int hflags[FLAG_COUNT];
     int64_t hcounts[3];
@@ -648,6 +691,7 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     c->nnz_factor = nz;
     c->front_prec = c->prec;
     c->factored = true;
+    trailing_work(c, dbl ? 8 : 4);
     return HF_OK;
   }
   return HF_ERR_OOM;
@@ -661,15 +705,15 @@ int hf_s22_from_factor(hf_ctx* c) {
   if ((rc = hf_ensure(c->d_s22, (size_t)M * M * 8 + 16))) return rc;
   if (M == 0) return HF_OK;
   if (c->prec == HF_PREC_FP64)
-    k_s22_from_factor<double><<<1, 1024, 0, s>>>((const NodeDesc*)c->d_nodes.p, (const NodeState*)c->d_state.p,
+    HF_LAUNCH(c, HF_PROF_LAMBDA, k_s22_from_factor<double><<<1, 1024, 0, s>>>((const NodeDesc*)c->d_nodes.p, (const NodeState*)c->d_state.p,
                                                  c->n_nodes, (const double*)c->d_front.p, (const int32_t*)c->d_rowid.p,
                                                  (const int32_t*)c->d_lam2pos.p, M, (double*)c->d_s22.p,
-                                                 (int*)c->d_flags.p);
+                                                 (int*)c->d_flags.p));
   else
-    k_s22_from_factor<float><<<1, 1024, 0, s>>>((const NodeDesc*)c->d_nodes.p, (const NodeState*)c->d_state.p,
+    HF_LAUNCH(c, HF_PROF_LAMBDA, k_s22_from_factor<float><<<1, 1024, 0, s>>>((const NodeDesc*)c->d_nodes.p, (const NodeState*)c->d_state.p,
                                                 c->n_nodes, (const float*)c->d_front.p, (const int32_t*)c->d_rowid.p,
                                                 (const int32_t*)c->d_lam2pos.p, M, (double*)c->d_s22.p,
-                                                (int*)c->d_flags.p);
+                                                (int*)c->d_flags.p));
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
 }

@@ -2,6 +2,8 @@
 #pragma once
 #include "hf.h"
 
+#include <cuda_runtime_api.h>
+
 #include <cstdint>
 #include <cstddef>
 #include <string>
@@ -82,7 +84,7 @@ struct hf_ctx {
   DevBuf d_front;                    // front arena (float or double)
   DevBuf d_gmag;                     // per front row: |K_ii| + accumulated |l|^2 |d| (null-pivot test)
   DevBuf d_pos0;                     // per front row: its position before pivoting
-  DevBuf d_vec2;                     // per-front solve scratch (rows before pivoting)
+  DevBuf d_invpos;                   // inverse of d_pos0 (scratch)
   int front_prec = -1;               // precision the arena was sized for
   DevBuf d_flags;                    // int flags: [0] delay overflow, [1] numeric error
   DevBuf d_lam2pos;                  // L ints: position in Lambda_2 or -1
@@ -107,6 +109,14 @@ struct hf_ctx {
   size_t work_cap = 0;
   DevBuf d_small;                    // small matrices / partial sums
   size_t small_cap = 0;
+  // ---- tracing ----
+  bool prof_on = false;
+  int64_t launches[HF_NPROF] = {0};
+  double work_flops[HF_NPROF] = {0};   // algorithmic flops of the counted launches
+  double work_bytes[HF_NPROF] = {0};   // algorithmic bytes of the counted launches
+  std::vector<cudaEvent_t> ev_pool;   // recycled start/stop events
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> prof_recs;   // (class, index of the start event)
   DevBuf d_gsmall;                   // block GCR small matrices (M_n, coefficients)
   DevBuf d_k12;                      // K12 block (L x M), the right-hand sides of Alg. 1 step 3
   DevBuf d_solve;                    // hf_solve scratch
@@ -116,3 +126,18 @@ struct hf_ctx {
 int hf_analyze_impl(int64_t L, const int64_t* rowptr, const int32_t* col, const double* coords,
                     int dim, const hf_opts* opts, hf_ctx** out);
 void hf_layout_fronts(hf_ctx* c);   // capacities, ld, offsets (depends on opts.delay_cap)
+
+// Counts a kernel launch of class `cls` and, when profiling, brackets it with events.
+struct ProfScope {
+  hf_ctx* c;
+  int cls;
+  size_t idx;
+  bool on;
+  ProfScope(hf_ctx* ctx, int k);
+  ~ProfScope();
+};
+#define HF_LAUNCH(ctx, cls, ...)        \
+  do {                                  \
+    ProfScope hf_ps_(ctx, cls);         \
+    __VA_ARGS__;                        \
+  } while (0)

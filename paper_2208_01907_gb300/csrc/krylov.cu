@@ -19,155 +19,217 @@ namespace {
 constexpr int SB = 32;       // column block of the triangular solves
 
 // ---------------------------------------------------------------------------
-// Multifrontal forward substitution, one CTA per front (levels bottom-up).
-// V_t rows [0, n) start from b, the other rows from 0; the children's update
-// rows are added; then y = L11^-1 V over the K11 columns [0, ksolve) with the
-// contribution rows updated on the way.  Pivot rows leave y_i / d_i (the D^-1
-// step) in the global array Y; rows of Lambda_2 leave their value unscaled.
+// Multifrontal triangular solves with the stored factor, level by level.
+// Forward (levels bottom-up): V_t rows [0, n) start from b, the other rows from 0,
+// the children's update rows are added (maps in pivoted order), then
+// V = L11^-1 V over the K11 columns [0, ksolve), blocked by SB columns: a diagonal
+// triangular solve and a GEMM update of every row below.  Pivot rows leave
+// y_i / d_i (the D^-1 step) in Y; rows of Lambda_2 leave their value unscaled.
+// Backward (levels top-down): rows [ks, f) take the solution of later unknowns from
+// X, then x = L11^-T (y - L21^T x2) blocked from the bottom.
 // ---------------------------------------------------------------------------
+constexpr int TS = 64;       // row tile / diagonal block of the triangular solves
+constexpr int TR = 64;       // right-hand-side tile
+constexpr int TKK = 16;      // k chunk of the GEMM updates
+
+template <typename TV>
+__global__ void k_fwd_init(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                           const int32_t* __restrict__ rowid, TV* __restrict__ vec, const TV* __restrict__ B, int m) {
+  const int t = t0 + blockIdx.y;
+  const NodeDesc d = nd[t];
+  const int f = st[t].f;
+  const int nown = d.cand_all ? 0 : d.n;
+  TV* V = vec + d.row_off * m;
+  const int32_t* rid = rowid + d.row_off;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)f * m; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
+    V[e] = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
+  }
+}
+
+template <typename TV>
+__global__ void k_fwd_child(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0, int slot,
+                            const int32_t* __restrict__ cbmap, TV* __restrict__ vec, int m) {
+  const int t = t0 + blockIdx.y;
+  const NodeDesc d = nd[t];
+  const int ch = slot == 0 ? d.child0 : d.child1;
+  if (ch < 0) return;
+  const NodeDesc dc = nd[ch];
+  const int kc = st[ch].k, mc = st[ch].f - kc;
+  const TV* U = vec + (dc.row_off + kc) * m;
+  const int32_t* map = cbmap + dc.row_off;
+  TV* V = vec + d.row_off * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)mc * m; e += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(e / m), c = (int)(e - (int64_t)a * m);
+    int tg = map[a];
+    if (tg >= 0) V[(int64_t)tg * m + c] += U[e];
+  }
+}
+
+// pivot rows -> Y (scaled by 1/d for the K11 pivots); moved / unfactorized rows unscaled
 template <typename TF, typename TV>
-__global__ void k_fwd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
-                      const TF* __restrict__ arena, const int32_t* __restrict__ rowid,
-                      const int32_t* __restrict__ pos0all, const int32_t* __restrict__ cbmap,
-                      TV* __restrict__ vec, TV* __restrict__ vec2, const TV* __restrict__ B,
-                      TV* __restrict__ Y, int m) {
-  __shared__ TF Ls[SB][SB + 1];
-  const int t = t0 + blockIdx.x;
+__global__ void k_fwd_store(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                           const TF* __restrict__ arena, const int32_t* __restrict__ rowid,
+                           const TV* __restrict__ vec, TV* __restrict__ Y, int m) {
+  const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const NodeState S = st[t];
-  const int f = S.f, k = S.k, ks = S.ksolve;
-  const int64_t ld = d.ld;
+  const int hi = d.cand_all ? S.f : S.k;
   const TF* F = arena + d.front_off;
+  const TV* V = vec + d.row_off * m;
   const int32_t* rid = rowid + d.row_off;
-  const int32_t* pos0 = pos0all + d.row_off;
-  TV* V = vec + d.row_off * m;
-  TV* Vpre = vec2 + d.row_off * m;               // rows in the order before pivoting
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int nown = d.cand_all ? 0 : d.n;
-  const int nperm = d.cand_all ? f : d.n;        // rows [0, nperm) were permuted by pivoting
-  for (int e = tid; e < f * m; e += nt) Vpre[e] = TV(0);
-  __syncthreads();
-  // children's update rows land where the extend-add put them: before this front's pivoting
-  for (int slot = 0; slot < 2; ++slot) {
-    const int ch = slot == 0 ? d.child0 : d.child1;
-    if (ch < 0) continue;
-    const NodeDesc dc = nd[ch];
-    const int kc = st[ch].k, mc = st[ch].f - kc;
-    const TV* U = vec + (dc.row_off + kc) * m;
-    const int32_t* map = cbmap + dc.row_off;
-    for (int e = tid; e < mc * m; e += nt) {
-      int a = e / m, c = e - a * m;
-      int tg = map[a];
-      if (tg >= 0) Vpre[(int64_t)tg * m + c] += U[e];
-    }
-    __syncthreads();
-  }
-  // into pivoted order, plus b on the rows of Lambda_t
-  for (int e = tid; e < f * m; e += nt) {
-    int i = e / m, c = e - i * m;
-    int src = (i < nperm) ? pos0[i] : i;
-    TV v = Vpre[(int64_t)src * m + c];
-    if (i < nown) v += B[(int64_t)rid[i] * m + c];
-    V[e] = v;
-  }
-  __syncthreads();
-  for (int j0 = 0; j0 < ks; j0 += SB) {
-    const int jb = min(SB, ks - j0);
-    for (int e = tid; e < SB * SB; e += nt) {
-      int r = e % SB, c = e / SB;
-      Ls[r][c] = (r < jb && c < jb && r > c) ? F[(j0 + r) + (j0 + c) * ld] : TF(0);
-    }
-    __syncthreads();
-    // triangular block: one thread per right-hand side
-    for (int c = tid; c < m; c += nt) {
-      for (int r = 1; r < jb; ++r) {
-        TV acc = V[(int64_t)(j0 + r) * m + c];
-        for (int q = 0; q < r; ++q) acc -= (TV)Ls[r][q] * V[(int64_t)(j0 + q) * m + c];
-        V[(int64_t)(j0 + r) * m + c] = acc;
-      }
-    }
-    __syncthreads();
-    // rows below the block
-    for (int e = tid; e < (f - j0 - jb) * m; e += nt) {
-      int i = j0 + jb + e / m, c = e % m;
-      TV acc = V[(int64_t)i * m + c];
-      for (int q = 0; q < jb; ++q) acc -= (TV)F[i + (j0 + q) * ld] * V[(int64_t)(j0 + q) * m + c];
-      V[(int64_t)i * m + c] = acc;
-    }
-    __syncthreads();
-  }
-  // pivots of K11: y_i / d_i; moved pivots and unfactorized Lambda_0 rows: value as is
-  const int hi = d.cand_all ? f : k;
-  for (int e = tid; e < hi * m; e += nt) {
-    int i = e / m, c = e - i * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)hi * m; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
     TV v = V[e];
-    if (i < ks) v = v / (TV)F[i + i * ld];
+    if (i < S.ksolve) v = v / (TV)F[i + (int64_t)i * d.ld];
     Y[(int64_t)rid[i] * m + c] = v;
   }
 }
 
-// Backward substitution, one CTA per front (levels top-down): rows [ks, f) take the
-// solution of later unknowns from X (ancestors, or Lambda_2 values), then
-// x = L11^-T (y - L21^T x2) on [0, ks).
-template <typename TF, typename TV>
-__global__ void k_bwd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
-                      const TF* __restrict__ arena, const int32_t* __restrict__ rowid, TV* __restrict__ vec,
-                      const TV* __restrict__ Y, TV* __restrict__ X, int m) {
-  __shared__ TF Ls[SB][SB + 1];
-  const int t = t0 + blockIdx.x;
+template <typename TV>
+__global__ void k_bwd_init(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                           const int32_t* __restrict__ rowid, TV* __restrict__ vec, const TV* __restrict__ Y,
+                           const TV* __restrict__ X, int m) {
+  const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const NodeState S = st[t];
-  const int f = S.f, ks = S.ksolve;
-  if (ks == 0) return;
-  const int64_t ld = d.ld;
-  const TF* F = arena + d.front_off;
-  const int32_t* rid = rowid + d.row_off;
+  if (S.ksolve == 0) return;
   TV* V = vec + d.row_off * m;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < f * m; e += nt) {
-    int i = e / m, c = e - i * m;
-    V[e] = (i < ks) ? Y[(int64_t)rid[i] * m + c] : X[(int64_t)rid[i] * m + c];
+  const int32_t* rid = rowid + d.row_off;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)S.f * m; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
+    V[e] = (i < S.ksolve) ? Y[(int64_t)rid[i] * m + c] : X[(int64_t)rid[i] * m + c];
   }
-  __syncthreads();
-  // w_j -= sum_{i >= ks} L(i, j) x_i
-  if (f > ks) {
-    for (int e = tid; e < ks * m; e += nt) {
-      int j = e / m, c = e - j * m;
-      TV acc = V[e];
-      const TF* col = F + j * ld;
-      for (int i = ks; i < f; ++i) acc -= (TV)col[i] * V[(int64_t)i * m + c];
-      V[e] = acc;
-    }
-    __syncthreads();
-  }
-  // blocks from the bottom
-  for (int j1 = ks; j1 > 0; j1 -= SB) {
-    const int j0 = max(0, j1 - SB), jb = j1 - j0;
-    for (int e = tid; e < SB * SB; e += nt) {
-      int r = e % SB, c = e / SB;
-      Ls[r][c] = (r < jb && c < jb && r > c) ? F[(j0 + r) + (j0 + c) * ld] : TF(0);
-    }
-    __syncthreads();
-    for (int c = tid; c < m; c += nt) {
-      for (int r = jb - 2; r >= 0; --r) {
-        TV acc = V[(int64_t)(j0 + r) * m + c];
-        for (int q = r + 1; q < jb; ++q) acc -= (TV)Ls[q][r] * V[(int64_t)(j0 + q) * m + c];
-        V[(int64_t)(j0 + r) * m + c] = acc;
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < j0 * m; e += nt) {
-      int j = e / m, c = e - j * m;
-      TV acc = V[e];
-      const TF* col = F + j * ld;
-      for (int q = 0; q < jb; ++q) acc -= (TV)col[j0 + q] * V[(int64_t)(j0 + q) * m + c];
-      V[e] = acc;
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < ks * m; e += nt) {
-    int i = e / m, c = e - i * m;
+}
+
+template <typename TV>
+__global__ void k_bwd_store(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                            const int32_t* __restrict__ rowid, const TV* __restrict__ vec, TV* __restrict__ X, int m) {
+  const int t = t0 + blockIdx.y;
+  const NodeDesc d = nd[t];
+  const int ks = st[t].ksolve;
+  const TV* V = vec + d.row_off * m;
+  const int32_t* rid = rowid + d.row_off;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)ks * m; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
     X[(int64_t)rid[i] * m + c] = V[e];
+  }
+}
+
+// Diagonal block solve of block step b: forward (unit L, columns [b*TS, ...)) or
+// backward (unit L^T, blocks counted from ksolve down).  One thread per rhs; the
+// block of L and the rhs columns are staged in shared memory.
+template <typename TV> struct TrsmThreads { static constexpr int value = sizeof(TV) == 8 ? 32 : 64; };
+
+template <typename TF, typename TV, bool FWD>
+__global__ void __launch_bounds__(TrsmThreads<TV>::value) k_trsm_diag(const NodeDesc* __restrict__ nd,
+                                                                        const NodeState* __restrict__ st, int t0,
+                                                                        const TF* __restrict__ arena,
+                                                                        TV* __restrict__ vec, int m, int b) {
+  constexpr int NT = TrsmThreads<TV>::value;
+  __shared__ TF Ls[TS][TS];
+  __shared__ TV Vs[TS][NT];
+  const int t = t0 + blockIdx.y;
+  const NodeDesc d = nd[t];
+  const int ks = st[t].ksolve;
+  int j0, jb;
+  if (FWD) { j0 = b * TS; if (j0 >= ks) return; jb = min(TS, ks - j0); }
+  else { int j1 = ks - b * TS; if (j1 <= 0) return; j0 = max(0, j1 - TS); jb = j1 - j0; }
+  const TF* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  for (int e = threadIdx.x; e < TS * TS; e += NT) {
+    int r = e % TS, c = e / TS;
+    Ls[r][c] = (r < jb && c < jb && r > c) ? F[(j0 + r) + (int64_t)(j0 + c) * ld] : TF(0);
+  }
+  const int tx = threadIdx.x;
+  const int c = blockIdx.x * NT + tx;
+  TV* V = vec + (d.row_off + j0) * m + c;
+  for (int r = 0; r < jb; ++r) Vs[r][tx] = (c < m) ? V[(int64_t)r * m] : TV(0);
+  __syncthreads();
+  if (FWD) {
+    for (int r = 1; r < jb; ++r) {
+      TV acc = Vs[r][tx];
+      for (int q = 0; q < r; ++q) acc -= (TV)Ls[r][q] * Vs[q][tx];
+      Vs[r][tx] = acc;
+    }
+  } else {
+    for (int r = jb - 2; r >= 0; --r) {
+      TV acc = Vs[r][tx];
+      for (int q = r + 1; q < jb; ++q) acc -= (TV)Ls[q][r] * Vs[q][tx];
+      Vs[r][tx] = acc;
+    }
+  }
+  if (c < m)
+    for (int r = 0; r < jb; ++r) V[(int64_t)r * m] = Vs[r][tx];
+}
+
+// GEMM update C -= A B on the front vectors of a level.
+//  MODE 0 (forward, block step b):  rows [j0+jb, f),  A(i,q) = L(i, j0+q),  B = V rows [j0, j0+jb)
+//  MODE 1 (backward, block step b): rows [0, j0),     A(i,q) = L(j0+q, i),  B = V rows [j0, j1)
+//  MODE 2 (backward start):         rows [0, ks),     A(i,q) = L(ks+q, i),  B = V rows [ks, f)
+template <typename TF, typename TV, int MODE>
+__global__ void __launch_bounds__(256) k_gemm_upd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                  int t0, const TF* __restrict__ arena, TV* __restrict__ vec, int m, int b) {
+  const int t = t0 + blockIdx.z;
+  const NodeDesc d = nd[t];
+  const int ks = st[t].ksolve, f = st[t].f;
+  int r_lo, r_hi, k_lo, k_hi;
+  if (MODE == 0) { int j0 = b * TS; if (j0 >= ks) return; int jb = min(TS, ks - j0); r_lo = j0 + jb; r_hi = f; k_lo = j0; k_hi = j0 + jb; }
+  else if (MODE == 1) { int j1 = ks - b * TS; if (j1 <= 0) return; int j0 = max(0, j1 - TS); r_lo = 0; r_hi = j0; k_lo = j0; k_hi = j1; }
+  else { r_lo = 0; r_hi = ks; k_lo = ks; k_hi = f; }
+  const int r0 = r_lo + blockIdx.x * TS;
+  const int c0 = blockIdx.y * TR;
+  if (r0 >= r_hi || c0 >= m || k_hi <= k_lo) return;
+  const TF* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  TV* V = vec + d.row_off * m;
+  __shared__ TV As[TKK][TS + 1];
+  __shared__ TV Bs[TKK][TR + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  TV acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = TV(0);
+  for (int kc = k_lo; kc < k_hi; kc += TKK) {
+    for (int e = threadIdx.x; e < TKK * TS; e += 256) {
+      int kk, rr;
+      if (MODE == 0) { kk = e / TS; rr = e % TS; }      // rows contiguous in column k
+      else { rr = e / TKK; kk = e % TKK; }               // k contiguous in column i
+      int q = kc + kk, i = r0 + rr;
+      TV a = TV(0);
+      if (q < k_hi && i < r_hi) a = (TV)(MODE == 0 ? F[i + (int64_t)q * ld] : F[q + (int64_t)i * ld]);
+      As[kk][rr] = a;
+    }
+    for (int e = threadIdx.x; e < TKK * TR; e += 256) {
+      int kk = e / TR, cc = e % TR;
+      int q = kc + kk, c = c0 + cc;
+      Bs[kk][cc] = (q < k_hi && c < m) ? V[(int64_t)q * m + c] : TV(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TKK; ++kk) {
+      TV av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int r = r0 + ty + 16 * i;
+    if (r >= r_hi) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = c0 + tx + 16 * j;
+      if (c < m) V[(int64_t)r * m + c] -= acc[i][j];
+    }
   }
 }
 
@@ -252,12 +314,13 @@ constexpr int GR = 32;     // rows per tile
 constexpr int GO = 32;     // output block edge
 
 __global__ void k_gram_partial(int64_t L, int ma, int mb, const double* __restrict__ A, const double* __restrict__ B,
-                               double* __restrict__ part, int nchunks) {
+                               double* __restrict__ part, int nchunks, int sym) {
   __shared__ double As[GR][GO + 1];
   __shared__ double Bs[GR][GO + 1];
   const int ob = blockIdx.y;                       // output block
   const int nbb = (mb + GO - 1) / GO;
   const int a0 = (ob / nbb) * GO, b0 = (ob % nbb) * GO;
+  if (sym && a0 > b0) return;                      // A^T A: lower blocks mirror the upper ones
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
   double acc[4] = {0, 0, 0, 0};
   const int64_t rows_per = (L + nchunks - 1) / nchunks;
@@ -284,64 +347,86 @@ __global__ void k_gram_partial(int64_t L, int ma, int mb, const double* __restri
 }
 
 __global__ void k_gram_reduce(int ma, int mb, int nchunks, const double* __restrict__ part, double* __restrict__ G,
-                              double scale) {
+                              double scale, int sym) {
   const int nbb = (mb + GO - 1) / GO;
   const int nob = ((ma + GO - 1) / GO) * nbb;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nob * GO * GO) return;
   int ob = e / (GO * GO), w = e % (GO * GO);
-  int a = (ob / nbb) * GO + w / GO, b = (ob % nbb) * GO + w % GO;
+  int ab = ob / nbb, bb = ob % nbb;
+  if (sym && ab > bb) return;
+  int a = ab * GO + w / GO, b = bb * GO + w % GO;
   if (a >= ma || b >= mb) return;
   double s = 0.0;
   const double* P = part + (int64_t)ob * nchunks * GO * GO + w;
   for (int c = 0; c < nchunks; ++c) s += P[(int64_t)c * GO * GO];
   G[a * mb + b] = scale * s;
+  if (sym && ab < bb) G[b * mb + a] = scale * s;
 }
 
 // ---------------------------------------------------------------------------
-// Small SPD solve C = Mg^-1 Y (m x m) by Cholesky; a pivot that falls below
-// 1e-13 of its own diagonal marks a dependent direction, which is dropped
-// (its coefficients are zero).  One CTA.
+// Small SPD matrices of block GCR: M = Q^T Q = R^T R by a right-looking Cholesky in
+// one CTA (in place, upper triangle R); a pivot below 1e-13 of its own diagonal marks a
+// dependent direction, which is dropped (its row of R is zero and its coefficients are 0).
+// Solves R^T R C = Y run one warp per column of Y with warp-shuffle dot products.
 // ---------------------------------------------------------------------------
-__global__ void k_small_solve(int m, int ny, const double* __restrict__ Mg, const double* __restrict__ Y,
-                              double* __restrict__ C, double* __restrict__ work) {
-  double* R = work;                 // m x m
-  int* drop = (int*)(work + m * m);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < m * m; e += blockDim.x) R[e] = Mg[e];
-  for (int e = tid; e < m * ny; e += blockDim.x) C[e] = Y[e];
+__global__ void k_chol(int m, double* __restrict__ A, int* __restrict__ drop) {
+  __shared__ double s_rjj;
+  __shared__ int s_drop;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // keep the original diagonal in the lower triangle's first column slots is not possible
+  // (it is referenced); store it in drop[m + j] as bits of a double instead
+  double* dref = (double*)(drop + 2 * ((m + 1) / 2) + 2);
+  for (int j = tid; j < m; j += nt) dref[j] = A[j * m + j];
   __syncthreads();
   for (int j = 0; j < m; ++j) {
-    // R(j, j) = sqrt(M_jj - sum_k R(k, j)^2)
     if (tid == 0) {
-      double s = Mg[j * m + j];
-      for (int k = 0; k < j; ++k) s -= R[k * m + j] * R[k * m + j];
-      double ref = Mg[j * m + j];
-      bool dz = !(s > 1e-13 * ref) || !(ref > 0);
+      double sj = A[j * m + j];
+      const double ref = dref[j];
+      int dz = !(sj > 1e-13 * ref) || !(ref > 0);
       drop[j] = dz;
-      R[j * m + j] = dz ? 0.0 : sqrt(s);
+      s_drop = dz;
+      s_rjj = dz ? 0.0 : sqrt(sj);
+      A[j * m + j] = s_rjj;
     }
     __syncthreads();
-    const double rjj = R[j * m + j];
-    for (int l = j + 1 + tid; l < m; l += blockDim.x) {
-      double s = Mg[j * m + l];
-      for (int k = 0; k < j; ++k) s -= R[k * m + j] * R[k * m + l];
-      R[j * m + l] = drop[j] ? 0.0 : s / rjj;
+    const double rjj = s_rjj;
+    const int dz = s_drop;
+    for (int l = j + 1 + tid; l < m; l += nt) A[j * m + l] = dz ? 0.0 : A[j * m + l] / rjj;
+    __syncthreads();
+    if (!dz) {
+      const int n2 = m - j - 1;
+      for (int e = tid; e < n2 * n2; e += nt) {
+        int a = j + 1 + e / n2, b = j + 1 + e % n2;
+        if (b >= a) A[a * m + b] -= A[j * m + a] * A[j * m + b];
+      }
     }
     __syncthreads();
   }
-  // R^T z = y (forward), R c = z (backward), per column of Y
-  for (int c = tid; c < ny; c += blockDim.x) {
-    for (int j = 0; j < m; ++j) {
-      double s = C[j * ny + c];
-      for (int k = 0; k < j; ++k) s -= R[k * m + j] * C[k * ny + c];
-      C[j * ny + c] = drop[j] ? 0.0 : s / R[j * m + j];
-    }
-    for (int j = m - 1; j >= 0; --j) {
-      double s = C[j * ny + c];
-      for (int k = j + 1; k < m; ++k) s -= R[j * m + k] * C[k * ny + c];
-      C[j * ny + c] = drop[j] ? 0.0 : s / R[j * m + j];
-    }
+}
+
+// C = R^-1 R^-T Y (dropped directions give zero rows); one warp per column of Y
+__global__ void k_chol_solve(int m, int ny, const double* __restrict__ R, const int* __restrict__ drop,
+                             const double* __restrict__ Y, double* __restrict__ C) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= ny) return;
+  const int c = warp;
+  // forward: R^T z = y  (z_j = (y_j - sum_{k<j} R_kj z_k) / R_jj)
+  for (int j = 0; j < m; ++j) {
+    double part = 0.0;
+    for (int k = lane; k < j; k += 32) part += R[k * m + j] * C[k * ny + c];
+    part = warp_sum(part);
+    if (lane == 0) C[j * ny + c] = drop[j] ? 0.0 : (Y[j * ny + c] - part) / R[j * m + j];
+    __syncwarp();
+  }
+  // backward: R x = z  (x_j = (z_j - sum_{k>j} R_jk x_k) / R_jj)
+  for (int j = m - 1; j >= 0; --j) {
+    double part = 0.0;
+    for (int k = j + 1 + lane; k < m; k += 32) part += R[j * m + k] * C[k * ny + c];
+    part = warp_sum(part);
+    if (lane == 0) C[j * ny + c] = drop[j] ? 0.0 : (C[j * ny + c] - part) / R[j * m + j];
+    __syncwarp();
   }
 }
 
@@ -676,41 +761,114 @@ struct Work {
 
 static int ensure_vec(hf_ctx* c, int m, size_t esz) {
   size_t need = (size_t)c->row_elems * m * esz + 64;
-  int rc = hf_ensure(c->d_vec, need);
-  return rc ? rc : hf_ensure(c->d_vec2, need);
+  return hf_ensure(c->d_vec, need);
 }
 
 // Apply the triangular solves with the front factor (TF) in vector precision TV.
 //  mode 0: K11 preconditioner (Lambda_2 rows are zero in and out)
 //  mode 1: full solve with S22 handled by the BK factors (non-mixed forms)
+struct LevelDims {
+  int maxf = 0, maxks = 0, maxcb = 0;
+};
+
+static LevelDims level_dims(const hf_ctx* c, int lev) {
+  LevelDims L;
+  const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+  for (int t = t0; t < t0 + cnt; ++t) {
+    const NodeState& S = c->state_host[t];
+    L.maxf = std::max(L.maxf, S.f);
+    L.maxks = std::max(L.maxks, S.ksolve);
+    for (int ch : {c->nodes[t].child0, c->nodes[t].child1})
+      if (ch >= 0) L.maxcb = std::max(L.maxcb, c->state_host[ch].f - c->state_host[ch].k);
+  }
+  return L;
+}
+
+static void sweep_work(hf_ctx* c, int cls, int m, size_t esz) {
+  double ent = 0;
+  for (const NodeState& S : c->state_host) ent += (double)S.f * S.ksolve - 0.5 * (double)S.ksolve * (S.ksolve + 1);
+  c->work_flops[cls] += 2.0 * ent * m;
+  c->work_bytes[cls] += ent * esz;
+}
+
 template <typename TF, typename TV>
-static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const double* x2_dev, bool full,
-                     double* y2_dev) {
+static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp) {
   cudaStream_t s = hf_stream(c);
+  sweep_work(c, HF_PROF_TRSV_FWD, m, sizeof(TF));
   const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
   const NodeState* st = (const NodeState*)c->d_state.p;
   const TF* arena = (const TF*)c->d_front.p;
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
   const int32_t* cbmap = (const int32_t*)c->d_cbmap.p;
   TV* vec = (TV*)c->d_vec.p;
+  const unsigned rt = (unsigned)((m + TR - 1) / TR);
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
-    k_fwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, (const int32_t*)c->d_pos0.p, cbmap, vec,
-                                      (TV*)c->d_vec2.p, Bin, Ytmp, m);
+    const LevelDims D = level_dims(c, lev);
+    const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
+    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m));
+    if (D.maxcb > 0) {
+      const unsigned cx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxcb * m / 1024), 512);
+      for (int slot = 0; slot < 2; ++slot)
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m));
+    }
+    const int nbk = (D.maxks + TS - 1) / TS;
+    for (int b = 0; b < nbk; ++b) {
+      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_trsm_diag<TF, TV, true><<<dim3((m + TrsmThreads<TV>::value - 1) / TrsmThreads<TV>::value, cnt), TrsmThreads<TV>::value, 0, s>>>(nd, st, t0, arena, vec, m, b));
+      const unsigned rx = (unsigned)((D.maxf - b * TS + TS - 1) / TS);
+      if (rx > 0)
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0><<<dim3(rx, rt, cnt), 256, 0, s>>>(nd, st, t0, arena, vec, m, b));
+    }
+    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m));
   }
+}
+
+template <typename TF, typename TV>
+static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout) {
+  cudaStream_t s = hf_stream(c);
+  sweep_work(c, HF_PROF_TRSV_BWD, m, sizeof(TF));
+  const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
+  const NodeState* st = (const NodeState*)c->d_state.p;
+  const TF* arena = (const TF*)c->d_front.p;
+  const int32_t* rowid = (const int32_t*)c->d_rowid.p;
+  TV* vec = (TV*)c->d_vec.p;
+  const unsigned rt = (unsigned)((m + TR - 1) / TR);
+  for (int lev = 0; lev <= c->m; ++lev) {
+    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+    const LevelDims D = level_dims(c, lev);
+    if (D.maxks == 0) continue;
+    const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m));
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 2><<<dim3((D.maxks + TS - 1) / TS, rt, cnt), 256, 0, s>>>(nd, st, t0, arena, vec, m, 0));
+    const int nbk = (D.maxks + TS - 1) / TS;
+    for (int b = 0; b < nbk; ++b) {
+      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_trsm_diag<TF, TV, false><<<dim3((m + TrsmThreads<TV>::value - 1) / TrsmThreads<TV>::value, cnt), TrsmThreads<TV>::value, 0, s>>>(nd, st, t0, arena, vec, m, b));
+      const unsigned rx = (unsigned)((D.maxks - (b + 1) * TS + TS - 1) / TS);
+      if ((int)rx > 0)
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1><<<dim3(rx, rt, cnt), 256, 0, s>>>(nd, st, t0, arena, vec, m, b));
+    }
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m));
+  }
+}
+
+// Apply the triangular solves with the front factor (TF) in vector precision TV.
+//  full = false: K11 preconditioner (Lambda_2 rows are zero in and out)
+//  full = true : forward sweep only; y2 = the Lambda_2 rows, for the S22 solve
+template <typename TF, typename TV>
+static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const double* x2_dev, bool full,
+                     double* y2_dev) {
+  cudaStream_t s = hf_stream(c);
+  fwd_sweep<TF, TV>(c, m, Bin, Ytmp);
   HF_CUDA_TRY(cudaGetLastError());
   const int M = (int)c->M;
   if (M) {
     if (full) {
-      k_get_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, Ytmp, y2_dev);
+      HF_LAUNCH(c, HF_PROF_VECTOR, k_get_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, Ytmp, y2_dev));
       return 1;   // caller solves S22 and calls tri_solve_back
     }
-    k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, nullptr, Xout);
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, nullptr, Xout));
   }
-  for (int lev = 0; lev <= c->m; ++lev) {
-    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
-    k_bwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, Xout, m);
-  }
+  bwd_sweep<TF, TV>(c, m, Ytmp, Xout);
   HF_CUDA_TRY(cudaGetLastError());
   (void)x2_dev;
   return HF_OK;
@@ -719,31 +877,26 @@ static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const 
 template <typename TF, typename TV>
 static int tri_solve_back(hf_ctx* c, int m, TV* Ytmp, TV* Xout, const double* x2_dev) {
   cudaStream_t s = hf_stream(c);
-  const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
-  const NodeState* st = (const NodeState*)c->d_state.p;
-  const TF* arena = (const TF*)c->d_front.p;
-  const int32_t* rowid = (const int32_t*)c->d_rowid.p;
-  TV* vec = (TV*)c->d_vec.p;
   const int M = (int)c->M;
-  if (M) k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, x2_dev, Xout);
-  for (int lev = 0; lev <= c->m; ++lev) {
-    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
-    k_bwd<TF, TV><<<cnt, 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, Xout, m);
-  }
+  if (M) HF_LAUNCH(c, HF_PROF_VECTOR, k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, x2_dev, Xout));
+  bwd_sweep<TF, TV>(c, m, Ytmp, Xout);
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
 }
 
 // Gram G = scale * A^T B
 static int gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale) {
+  const int sym = (A == B && ma == mb) ? 1 : 0;
+  c->work_flops[HF_PROF_GRAM] += 2.0 * (double)L * ma * mb * (sym ? 0.5 : 1.0);
+  c->work_bytes[HF_PROF_GRAM] += 8.0 * (double)L * (sym ? ma : ma + mb);
   cudaStream_t s = hf_stream(c);
   const int nob = ((ma + GO - 1) / GO) * ((mb + GO - 1) / GO);
   int nchunks = (int)std::min<int64_t>(std::max<int64_t>(1, L / 256), 304);
   size_t need = (size_t)nob * nchunks * GO * GO * 8 + 64;
   int rc = hf_ensure(c->d_small, std::max(need, (size_t)(1 << 20)));
   if (rc) return rc;
-  k_gram_partial<<<dim3(nchunks, nob), 256, 0, s>>>(L, ma, mb, A, B, (double*)c->d_small.p, nchunks);
-  k_gram_reduce<<<nblk((int64_t)nob * GO * GO, 256), 256, 0, s>>>(ma, mb, nchunks, (const double*)c->d_small.p, G, scale);
+  HF_LAUNCH(c, HF_PROF_GRAM, k_gram_partial<<<dim3(nchunks, nob), 256, 0, s>>>(L, ma, mb, A, B, (double*)c->d_small.p, nchunks, sym));
+  HF_LAUNCH(c, HF_PROF_GRAM, k_gram_reduce<<<nblk((int64_t)nob * GO * GO, 256), 256, 0, s>>>(ma, mb, nchunks, (const double*)c->d_small.p, G, scale, sym));
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
 }
@@ -758,7 +911,7 @@ static int precond(hf_ctx* c, int m, const double* R, double* W, void* tmp32) {
     int rc;
     if ((rc = ensure_vec(c, m, 8))) return rc;
     HF_CUDA_TRY(cudaMemcpyAsync(W, R, L * m * 8, cudaMemcpyDeviceToDevice, s));
-    k_zero_lam2_rows<<<nblk(c->M * m, 256), 256, 0, s>>>((int)c->M, m, (const int32_t*)c->d_lam2.p, W);
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_zero_lam2_rows<<<nblk(c->M * m, 256), 256, 0, s>>>((int)c->M, m, (const int32_t*)c->d_lam2.p, W));
     rc = tri_solve<double, double>(c, m, W, y, W, nullptr, false, nullptr);
     return rc;
   }
@@ -767,17 +920,19 @@ static int precond(hf_ctx* c, int m, const double* R, double* W, void* tmp32) {
   float* x32 = y32 + L * m;
   int rc;
   if ((rc = ensure_vec(c, m, 4))) return rc;
-  k_cast_in<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, R, l2p, b32);
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_cast_in<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, R, l2p, b32));
   if ((rc = tri_solve<float, float>(c, m, b32, y32, x32, nullptr, false, nullptr))) return rc;
-  k_cast_out<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, x32, l2p, W);
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_cast_out<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, x32, l2p, W));
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
 }
 
 static void spmm(hf_ctx* c, int m, const double* W, double* Z) {
   cudaStream_t s = hf_stream(c);
-  k_spmm<<<nblk(c->L * 32, 256), 256, 0, s>>>(c->L, m, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
-                                              (const double*)c->d_kval.p, (const int32_t*)c->d_lam2pos.p, W, Z);
+  c->work_flops[HF_PROF_SPMM] += 2.0 * (double)c->nnz * m;
+  c->work_bytes[HF_PROF_SPMM] += 12.0 * (double)c->nnz + 16.0 * (double)c->L * m + 8.0 * (double)c->L;
+  HF_LAUNCH(c, HF_PROF_SPMM, k_spmm<<<nblk(c->L * 32, 256), 256, 0, s>>>(c->L, m, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
+                                              (const double*)c->d_kval.p, (const int32_t*)c->d_lam2pos.p, W, Z));
 }
 
 // Block GCR for K11 X = B (Sec. 3.5, readings R7/R8).  B, X: L x m row-major, Lambda_2 rows 0.
@@ -803,7 +958,8 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   const size_t mm = (size_t)m * m;
   std::vector<double> hnorm(m), bnorm(m);
   DevBuf& sm = c->d_gsmall;
-  size_t small_need = ((size_t)(maxit + 2) * mm * 2 + 6 * mm + 4 * (size_t)m + 64) * 8;
+  size_t small_need = ((size_t)(maxit + 2) * mm * 2 + 6 * mm + 4 * (size_t)m + 64) * 8 +
+                      (size_t)(maxit + 2) * (4 * ((size_t)m + 1) + 8) * 4 + 4096;
   if ((rc = hf_ensure(sm, small_need))) return rc;
   double* Mstore = (double*)sm.p;                 // (maxit+1) Gram matrices M_n
   double* Gm = Mstore + (size_t)(maxit + 1) * mm;
@@ -811,11 +967,15 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   double* wk = Cm + mm;                           // small solve work (m*m + m)
   double* diag = wk + mm + m + 8;                 // m x m scratch for norms
   int* dmask = (int*)(diag + mm);                 // converged-column mask (m ints)
+  const size_t meven = (size_t)(m + 1) / 2 * 2;
+  const size_t dstride = 4 * meven + 8;           // per M_n: m drop flags, then m doubles (8-byte aligned)
+  int* dropv = dmask + meven + 8;
   std::vector<int> hmask(m, 0);
   std::vector<double> hist_res;
   const unsigned nb = nblk((int64_t)blk, 256);
   const int use_smem = mm * 8 <= 48 * 1024;
   const size_t axpy_smem = use_smem ? mm * 8 : 0;
+  const double axpy_flops = 2.0 * (double)L * m * m, axpy_bytes = 8.0 * (double)L * m * 3;
 
   auto colnorms = [&](const double* A, std::vector<double>& out) -> int {
     int r = gram(c, L, m, m, A, A, diag, 1.0);
@@ -833,19 +993,26 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   // X0 = Q^-1 B, R0 = B - K11 X0, W0 = Q^-1 R0, P0 = W0, Q0 = K11 P0
   if ((rc = precond(c, m, B, X, tmp))) return rc;
   spmm(c, m, X, Z);
-  k_sub<<<nb, 256, 0, s>>>((int64_t)blk, B, Z, R);
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_sub<<<nb, 256, 0, s>>>((int64_t)blk, B, Z, R));
   if ((rc = precond(c, m, R, Pm(0), tmp))) return rc;
   spmm(c, m, Pm(0), Qm(0));
   int it = 0;
   double res = 0;
   bool conv = false;
+  auto msolve = [&](int q, const double* Y, double* C) {
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_chol_solve<<<nblk((int64_t)m * 32, 256), 256, 0, s>>>(m, m, Mstore + (size_t)q * mm,
+                                                                                    dropv + (size_t)q * dstride, Y, C));
+  };
   for (int n = 0; n < maxit; ++n) {
     double* Mn = Mstore + (size_t)n * mm;
     if ((rc = gram(c, L, m, m, Qm(n), Qm(n), Mn, 1.0))) return rc;
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_chol<<<1, 1024, 0, s>>>(m, Mn, dropv + (size_t)n * dstride));   // M_n = R^T R
     if ((rc = gram(c, L, m, m, Qm(n), R, Gm, 1.0))) return rc;
-    k_small_solve<<<1, 256, 0, s>>>(m, m, Mn, Gm, Cm, wk);
-    k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(n), Cm, X, nullptr, 1.0, use_smem);
-    k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Qm(n), Cm, R, nullptr, -1.0, use_smem);
+    msolve(n, Gm, Cm);
+    HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(n), Cm, X, nullptr, 1.0, use_smem));
+    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops; c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
+    HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Qm(n), Cm, R, nullptr, -1.0, use_smem));
+    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops; c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
     HF_CUDA_TRY(cudaGetLastError());
     it = n + 1;
     if ((rc = colnorms(R, hnorm))) return rc;
@@ -870,17 +1037,19 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     }
     if (any) HF_CUDA_TRY(cudaMemcpyAsync(dmask, hmask.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
     if (std::count(hmask.begin(), hmask.end(), 1) > 0)
-      k_zero_cols<<<nb, 256, 0, s>>>(L, m, dmask, R);
+      HF_LAUNCH(c, HF_PROF_VECTOR, k_zero_cols<<<nb, 256, 0, s>>>(L, m, dmask, R));
     if ((rc = precond(c, m, R, W, tmp))) return rc;
     spmm(c, m, W, Z);
     double* Pn = Pm(n + 1);
     double* Qn = Qm(n + 1);
     for (int q = 0; q <= n; ++q) {
       if ((rc = gram(c, L, m, m, Qm(q), Z, Gm, -1.0))) return rc;      // B_qn = -Q_q^T Z
-      k_small_solve<<<1, 256, 0, s>>>(m, m, Mstore + (size_t)q * mm, Gm, Cm, wk);
-      k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0, use_smem);
-      k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Qm(q), Cm, Qn, q == 0 ? Z : nullptr, 1.0, use_smem);
+      msolve(q, Gm, Cm);
+      HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0, use_smem));
+    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops; c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
     }
+    // Q_{n+1} = K11 P_{n+1}: one FP64 SpMM instead of the n+1 dense recurrence terms (reading R14)
+    spmm(c, m, Pn, Qn);
     HF_CUDA_TRY(cudaGetLastError());
   }
   *iters = it;
@@ -902,10 +1071,10 @@ static int bk_factor(hf_ctx* c) {
   HF_CUDA_TRY(cudaMemcpyAsync(A, c->d_s22.p, (size_t)M * M * 8, cudaMemcpyDeviceToDevice, s));
   int* kd = (int*)((int*)c->d_flags.p + FLAG_COUNT + 8);
   double* mags = (double*)c->d_bk_dval.p + 2 * M;
-  k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
+  HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
                                     (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
                                     c->opts.kernel_gap, (const int32_t*)c->d_lam2.p, (const int64_t*)c->d_diagpos.p,
-                                    (const double*)c->d_kval.p, c->s22_noise, kd, mags);
+                                    (const double*)c->d_kval.p, c->s22_noise, kd, mags));
   HF_CUDA_TRY(cudaGetLastError());
   int h = 0;
   HF_CUDA_TRY(cudaMemcpyAsync(&h, kd, 4, cudaMemcpyDeviceToHost, s));
@@ -934,9 +1103,9 @@ int hf_schur_impl(hf_ctx* c) {
       if ((rc = hf_ensure(c->d_k12, (size_t)L * M * 8 + 64))) return rc;
       double* B = (double*)c->d_k12.p;
       HF_CUDA_TRY(cudaMemsetAsync(B, 0, (size_t)L * M * 8, s));
-      k_extract_k12<<<M, 128, 0, s>>>(M, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
+      HF_LAUNCH(c, HF_PROF_SCHUR, k_extract_k12<<<M, 128, 0, s>>>(M, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
                                       (const double*)c->d_kval.p, (const int32_t*)c->d_lam2.p,
-                                      (const int32_t*)c->d_lam2pos.p, B);
+                                      (const int32_t*)c->d_lam2pos.p, B));
       grc = block_gcr(c, M, B, X12, &c->gcr_iters, &c->gcr_relres);
       if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
       // error estimate of S22 for the kernel rule: E = K21 Q^-1 (K12 - K11 X12)
@@ -947,13 +1116,13 @@ int hf_schur_impl(hf_ctx* c) {
         double* Zt = Wt + blk;
         double* tmp = Zt + blk;
         spmm(c, M, X12, Zt);
-        k_sub<<<nblk((int64_t)blk, 256), 256, 0, s>>>((int64_t)blk, B, Zt, Rt);
+        HF_LAUNCH(c, HF_PROF_VECTOR, k_sub<<<nblk((int64_t)blk, 256), 256, 0, s>>>((int64_t)blk, B, Zt, Rt));
         if ((rc = precond(c, M, Rt, Wt, tmp))) return rc;
         double* E = (double*)c->d_gsmall.p;
-        k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
+        HF_LAUNCH(c, HF_PROF_SCHUR, k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
                                                             (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
                                                             (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
-                                                            Wt, nullptr, 0, E, 2);
+                                                            Wt, nullptr, 0, E, 2));
         std::vector<double> hE((size_t)M * M);
         HF_CUDA_TRY(cudaMemcpyAsync(hE.data(), E, hE.size() * 8, cudaMemcpyDeviceToHost, s));
         HF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -961,11 +1130,11 @@ int hf_schur_impl(hf_ctx* c) {
         for (double v : hE) mx = std::max(mx, std::fabs(v));
         c->s22_noise = 100.0 * mx;
       }
-      k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
+      HF_LAUNCH(c, HF_PROF_SCHUR, k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, M, (const int64_t*)c->d_rowptr.p,
                                                           (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
                                                           (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
-                                                          X12, nullptr, 0, (double*)c->d_s22.p, 0);
-      k_symmetrize<<<nblk((int64_t)M * M, 256), 256, 0, s>>>(M, (double*)c->d_s22.p);
+                                                          X12, nullptr, 0, (double*)c->d_s22.p, 0));
+      HF_LAUNCH(c, HF_PROF_SCHUR, k_symmetrize<<<nblk((int64_t)M * M, 256), 256, 0, s>>>(M, (double*)c->d_s22.p));
       HF_CUDA_TRY(cudaGetLastError());
     } else {
       if ((rc = hf_s22_from_factor(c))) return rc;
@@ -996,29 +1165,29 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
   double* y2 = scratch + blk;
   double* x2 = y2 + (size_t)M * m;
   double* zt = x2 + (size_t)M * m;
-  k_scale_in<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, b, ldb, (const double*)c->d_q.p, bi);
+  HF_LAUNCH(c, HF_PROF_SCALE, k_scale_in<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, b, ldb, (const double*)c->d_q.p, bi));
   int grc = HF_OK;
   auto s22_solve = [&]() {
-    k_bk_solve<<<1, 128, 0, s>>>(M, m, (const double*)c->d_bk_lf.p, (const int*)c->d_bk_perm.p,
+    HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bk_solve<<<1, 128, 0, s>>>(M, m, (const double*)c->d_bk_lf.p, (const int*)c->d_bk_perm.p,
                                  (const int*)c->d_bk_blk.p, (const double*)c->d_bk_dval.p,
-                                 (const int*)c->d_bk_null.p, y2, x2, zt);
+                                 (const int*)c->d_bk_null.p, y2, x2, zt));
   };
   if (c->prec == HF_PREC_MIXED) {
     // Alg. 2: y1 by block GCR on K11, y2 = b2 - K21 y1, S22 x2 = y2, x1 = y1 - X12 x2
     HF_CUDA_TRY(cudaMemcpyAsync(y, bi, blk * 8, cudaMemcpyDeviceToDevice, s));
-    if (M) k_zero_lam2_rows<<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, y);
+    if (M) HF_LAUNCH(c, HF_PROF_VECTOR, k_zero_lam2_rows<<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, y));
     grc = block_gcr(c, m, y, y1, &c->solve_iters, &c->solve_relres);
     if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
     if (M) {
-      k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, m, (const int64_t*)c->d_rowptr.p,
+      HF_LAUNCH(c, HF_PROF_SCHUR, k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, m, (const int64_t*)c->d_rowptr.p,
                                                           (const int32_t*)c->d_col.p, (const double*)c->d_kval.p,
                                                           (const int32_t*)c->d_lam2.p, (const int32_t*)c->d_lam2pos.p,
-                                                          y1, bi, m, y2, 1);
+                                                          y1, bi, m, y2, 1));
       s22_solve();
-      k_backsub_x1<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, M, m, (const double*)c->d_x12.p, x2,
-                                                            (const int32_t*)c->d_lam2pos.p, y1);
+      HF_LAUNCH(c, HF_PROF_SCHUR, k_backsub_x1<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, M, m, (const double*)c->d_x12.p, x2,
+                                                            (const int32_t*)c->d_lam2pos.p, y1));
     }
-    k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx);
+    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx));
   } else if (c->prec == HF_PREC_FP64) {
     // block substitution with the stored FP64 factor (Eq. 1): forward, S22 solve, backward
     if ((rc = ensure_vec(c, m, 8))) return rc;
@@ -1028,22 +1197,22 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
       s22_solve();
       if ((rc = tri_solve_back<double, double>(c, m, y, y1, x2))) return rc;
     }
-    k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx);
+    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx));
   } else {
     // FP32 form: the same substitution with the FP32 factor (S22 solved in FP64)
     if ((rc = ensure_vec(c, m, 4))) return rc;
     float* b32 = (float*)scratch;
     float* y32 = (float*)y;
     float* x32 = y32 + blk;
-    k_cast_in<float><<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, bi, nullptr, b32);
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_cast_in<float><<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, bi, nullptr, b32));
     rc = tri_solve<float, float>(c, m, b32, y32, x32, nullptr, M > 0, y2);
     if (rc != HF_OK && rc != 1) return rc;
     if (M) {
       s22_solve();
       if ((rc = tri_solve_back<float, float>(c, m, y32, x32, x2))) return rc;
     }
-    k_cast_out<float><<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, x32, nullptr, y1);
-    k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx);
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_cast_out<float><<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, x32, nullptr, y1));
+    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx));
   }
   HF_CUDA_TRY(cudaGetLastError());
   HF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1058,5 +1227,33 @@ int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W) {
   if ((rc = hf_ensure(c->d_solve, (blk * 3 + 64) * 8))) return rc;
   if ((rc = precond(c, m, R, W, c->d_solve.p))) return rc;
   HF_CUDA_TRY(cudaStreamSynchronize(hf_stream(c)));
+  return HF_OK;
+}
+
+// dJ/dKbar_ij = -sum_r lam_i^r x_j^r on the stored pattern (adjoint of the solve); one warp per row
+__global__ void k_values_adjoint(int64_t L, int m, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                 const double* __restrict__ x, int64_t ldx, const double* __restrict__ lam,
+                                 int64_t ldl, double* __restrict__ grad) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= L) return;
+  for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
+    const int j = col[e];
+    double g = 0.0;
+    for (int r = 0; r < m; ++r) g += lam[row + r * ldl] * x[j + r * ldx];
+    grad[e] = -g;
+  }
+}
+
+int hf_values_adjoint_impl(hf_ctx* c, int m, const double* x, int64_t ldx, const double* lam, int64_t ldl,
+                           double* grad) {
+  if (!c || m < 1 || !x || !lam || !grad || ldx < c->L || ldl < c->L) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  cudaStream_t s = hf_stream(c);
+  c->work_flops[HF_PROF_SCHUR] += 2.0 * (double)c->nnz * m;
+  HF_LAUNCH(c, HF_PROF_SCHUR, k_values_adjoint<<<nblk(c->L * 32, 256), 256, 0, s>>>(c->L, m, (const int64_t*)c->d_rowptr.p,
+                                                                                  (const int32_t*)c->d_col.p, x, ldx, lam, ldl, grad));
+  HF_CUDA_TRY(cudaGetLastError());
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
   return HF_OK;
 }

@@ -22,8 +22,10 @@ HF_PREC_MIXED, HF_PREC_FP64, HF_PREC_FP32 = 0, 1, 2
 EXPORTED = (
     "hf_default_opts", "hf_error_string", "hf_analyze", "hf_factorize", "hf_schur", "hf_solve",
     "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
-    "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_free",
+    "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
+    "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_free",
 )
+HF_NPROF = 13
 
 
 class hf_opts(C.Structure):
@@ -42,6 +44,7 @@ class hf_info(C.Structure):
         ("kernel_dim", C.c_int32), ("gcr_iters", C.c_int32), ("solve_iters", C.c_int32),
         ("gcr_relres", C.c_double), ("solve_relres", C.c_double), ("factor_flops", C.c_double),
         ("front_bytes", C.c_int64), ("delay_retries", C.c_int32), ("precision", C.c_int32),
+        ("trailing_flops", C.c_double), ("solve_factor_entries", C.c_int64),
     ]
 
     def as_dict(self):
@@ -80,13 +83,18 @@ def lib():
     L.hf_get_factor.argtypes = [vp, vp, vp, vp, vp]
     L.hf_get_pivot_events.argtypes = [vp, vp, vp, vp]
     L.hf_precond.argtypes = [vp, i32, vp, vp]
+    L.hf_profile.argtypes = [vp, i32]
+    L.hf_values_adjoint.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+    L.hf_get_profile.argtypes = [vp, vp, vp, vp, vp]
+    L.hf_profile_name.argtypes = [i32]
+    L.hf_profile_name.restype = C.c_char_p
     L.hf_get_x12.argtypes = [vp, vp, i64]
     L.hf_get_s22.argtypes = [vp, vp]
     L.hf_get_s22_factor.argtypes = [vp, vp, vp, vp, vp, vp]
     L.hf_free.argtypes = [vp]
     L.hf_free.restype = None
     for name in EXPORTED:
-        if name not in ("hf_error_string", "hf_free"):
+        if name not in ("hf_error_string", "hf_free", "hf_profile_name"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -162,6 +170,25 @@ class HybridFactor:
         """W = Q^-1 R (Sec. 3.2) on row-major L x m torch float64 CUDA tensors (scaled unknowns)."""
         m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
         _check(lib().hf_precond(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond")
+
+    def profile(self, enable=True):
+        _check(lib().hf_profile(self._h, 1 if enable else 0), "hf_profile")
+
+    def get_profile(self):
+        """{class: (device ms, launches, algorithmic flops, algorithmic bytes)} since the last call."""
+        ms = np.zeros(HF_NPROF)
+        ln = np.zeros(HF_NPROF, np.int64)
+        fl = np.zeros(HF_NPROF)
+        by = np.zeros(HF_NPROF)
+        _check(lib().hf_get_profile(self._h, _ptr(ms), _ptr(ln), _ptr(fl), _ptr(by)), "hf_get_profile")
+        return {lib().hf_profile_name(i).decode(): (float(ms[i]), int(ln[i]), float(fl[i]), float(by[i]))
+                for i in range(HF_NPROF)}
+
+    def values_adjoint(self, x_dev, lam_dev, grad_dev):
+        """grad[e] = -sum_r lam[row_e, r] x[col_e, r] (tensors (nrhs, L) contiguous = column-major L x nrhs)."""
+        nrhs = 1 if x_dev.dim() == 1 else x_dev.shape[0]
+        _check(lib().hf_values_adjoint(self._h, nrhs, _ptr(x_dev), self.L, _ptr(lam_dev), self.L, _ptr(grad_dev)),
+               "hf_values_adjoint")
 
     # -- getters -----------------------------------------------------------
     def info(self) -> dict:

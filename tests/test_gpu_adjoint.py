@@ -1,0 +1,73 @@
+"""Adjoint of the hybrid solve (autograd through the same factorization) on the
+cfg-5 model: per-cell log coefficient theta, J = 1/2 |x - x*|^2.
+
+Checked against central finite differences (h = 1e-6, 32 directions) and against
+the oracle's adjoint formula evaluated with an FP64 direct solve.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import adjoint_diffusion2d, diffusion2d_structure
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _model(n, seed=5):
+    import paper_2208_01907_gb300 as hf
+    s, theta, b, xs, dirs = adjoint_diffusion2d(n, seed=seed)
+    st = {k: torch.tensor(v, device="cuda") for k, v in diffusion2d_structure(s).items()}
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    return s, theta, b, xs, dirs, st, H
+
+
+def _vals(theta, st, nnz):
+    k = torch.exp(theta)
+    ka, kb = k[st["a"]], k[st["b"]]
+    t = 2.0 * ka * kb / (ka + kb)
+    v = torch.zeros(nnz, dtype=torch.float64, device=theta.device)
+    v = v.index_add(0, st["p_aa"], t).index_add(0, st["p_bb"], t)
+    v = v.index_add(0, st["p_ab"], -t).index_add(0, st["p_ba"], -t)
+    return v.index_add(0, st["p_gg"], 2.0 * k[st["ghost"]])
+
+
+def _J(H, theta, st, s, bt, xst):
+    from paper_2208_01907_gb300.autograd import hybrid_solve
+    x = hybrid_solve(H, _vals(theta, st, s.nnz), bt)
+    return 0.5 * ((x - xst) ** 2).sum(), x
+
+
+def test_adjoint_matches_central_differences():
+    s, theta, b, xs, dirs, st, H = _model(32)
+    th = torch.tensor(theta, device="cuda", requires_grad=True)
+    bt = torch.tensor(b, device="cuda")
+    xst = torch.tensor(xs, device="cuda")
+    J, _ = _J(H, th, st, s, bt, xst)
+    (g,) = torch.autograd.grad(J, th)
+    h = 1e-6
+    worst = 0.0
+    with torch.no_grad():
+        for d in dirs:
+            dt = torch.tensor(d, device="cuda")
+            jp, _ = _J(H, th + h * dt, st, s, bt, xst)
+            jm, _ = _J(H, th - h * dt, st, s, bt, xst)
+            fd = float(jp - jm) / (2 * h)
+            ad = float(g @ dt)
+            worst = max(worst, abs(fd - ad) / max(abs(fd), 1e-12 * float(J)))
+    assert worst <= 1e-5
+
+
+@pytest.mark.parametrize("n", [32, 256])
+def test_adjoint_matches_oracle_gradient(n):
+    import scipy.sparse.linalg as spla
+    s, theta, b, xs, dirs, st, H = _model(n)
+    th = torch.tensor(theta, device="cuda", requires_grad=True)
+    J, x = _J(H, th, st, s, torch.tensor(b, device="cuda"), torch.tensor(xs, device="cuda"))
+    (g,) = torch.autograd.grad(J, th)
+    lu = spla.splu(s.to_scipy().tocsc())
+    xo = lu.solve(b)
+    lam = lu.solve(xo - xs)                      # K symmetric
+    go = O.adjoint_gradient(n, n, theta, xo, lam)
+    assert np.abs(x.detach().cpu().numpy() - xo).max() <= 1e-9 * np.abs(xo).max()
+    assert np.linalg.norm(g.cpu().numpy() - go) <= 1e-9 * np.linalg.norm(go)

@@ -13,6 +13,7 @@ from .gen import (  # noqa: F401
     darcy2d,
     batched_systems,
     adjoint_diffusion2d,
+    diffusion2d_structure,
     consistent_rhs,
     config_system,
 )

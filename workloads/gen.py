@@ -389,6 +389,33 @@ def adjoint_diffusion2d(n=256, seed=5, theta=None):
     return sys_, theta, b, xs, dirs
 
 
+def diffusion2d_structure(system: CsrSystem) -> dict:
+    """CSR positions of each face's four entries for a ``diffusion2d`` system.
+
+    Returns index arrays: cells a, b of every interior face; positions of (a,a), (b,b),
+    (a,b), (b,a) in the CSR value array; Dirichlet ghost cells and their diagonal
+    positions.  With them any (differentiable) cell-coefficient model can assemble the
+    values: t_f on the diagonals, -t_f off them, 2 k_c on ghost diagonals.
+    """
+    nx, ny = system.meta["nx"], system.meta["ny"]
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    a = np.concatenate([idx[:, :-1].ravel(), idx[:-1, :].ravel()])
+    b = np.concatenate([idx[:, 1:].ravel(), idx[1:, :].ravel()])
+    L = system.L
+    prow = np.repeat(np.arange(L, dtype=np.int64), np.diff(system.rowptr))
+    key = prow * L + system.col.astype(np.int64)
+
+    def pos(r, c):
+        return np.searchsorted(key, r.astype(np.int64) * L + c.astype(np.int64))
+    out = dict(a=a, b=b, p_aa=pos(a, a), p_bb=pos(b, b), p_ab=pos(a, b), p_ba=pos(b, a))
+    if system.meta.get("dirichlet_x"):
+        g = np.concatenate([idx[:, 0], idx[:, -1]])
+        out.update(ghost=g, p_gg=pos(g, g))
+    else:
+        out.update(ghost=np.zeros(0, np.int64), p_gg=np.zeros(0, np.int64))
+    return out
+
+
 def consistent_rhs(system: CsrSystem, seed: int, nrhs: int = 1, mode: str = "uniform") -> np.ndarray:
     """Right-hand sides (L x nrhs, float64) orthogonal to the known kernel.
 
