@@ -175,6 +175,32 @@ int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int
 int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
 
 /*
+ * hf_precond without any device allocation (the paper has no counterpart; this is a
+ * deployment variant).  For callers that must not allocate device memory while they
+ * run: a process whose device memory is owned by another allocator (a framework's
+ * caching pool that reserved it), a real-time loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable, or a host thread that may not grow the context's
+ * buffers.  It computes exactly what hf_precond computes (same kernels, same arguments
+ * and layout: R, W device, row-major L x m), but its scratch (the per-front solve
+ * vectors and the precision-cast copies) lives in one file-scope device array of
+ * 64 MiB that every GPU loading the library holds until the process exits.
+ *  - Limits: rejects with HF_ERR_ARG any call whose scratch exceeds 64 MiB, i.e.
+ *    (4 or 8) * m * (front rows of all fronts) + (12 or 8) * L * m bytes, rounded.
+ *  - The first call on a device looks up the array's device address (with that device
+ *    current); make that first call before any stream capture.  Call with the device of
+ *    the hf_factorize that built the context current.
+ *  - Every call on a device shares the array and leaves its contents behind; the solve
+ *    initialises everything it reads, so no clearing is needed.  Calls whose work can
+ *    overlap on the GPU (other streams, other threads, other contexts) race on the
+ *    array: serialise them.
+ *  - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.  Profiling
+ *    events are not recorded for this call.
+ * Errors: HF_ERR_ARG (bad argument or scratch above the limit), HF_ERR_STATE (before
+ * hf_factorize), HF_ERR_CUDA.
+ */
+int hf_precond_noalloc(hf_ctx* ctx, int m, const double* R, double* W);
+
+/*
  * Adjoint of the solve with respect to the matrix values.  For x = Kbar^-1 b and an
  * objective J(x), with lam = Kbar^-T dJ/dx (Kbar is symmetric, so lam comes from
  * hf_solve with the same factor), dJ/dKbar_ij = -sum_r lam_i^r x_j^r for every stored

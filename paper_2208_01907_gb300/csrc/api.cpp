@@ -12,6 +12,7 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau);
 int hf_schur_impl(hf_ctx* c);
 int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W);
+int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W);
 int hf_values_adjoint_impl(hf_ctx* c, int m, const double* x, int64_t ldx, const double* lam, int64_t ldl,
                            double* grad);
 
@@ -168,6 +169,11 @@ int hf_values_adjoint(hf_ctx* c, int nrhs, const double* x, int64_t ldx, const d
                       double* grad_vals) {
   if (!c) return HF_ERR_ARG;
   return hf_values_adjoint_impl(c, nrhs, x, ldx, lam, ldl, grad_vals);
+}
+
+int hf_precond_noalloc(hf_ctx* c, int m, const double* R, double* W) {
+  if (!c) return HF_ERR_ARG;
+  return hf_precond_noalloc_impl(c, m, R, W);
 }
 
 int hf_get_info(hf_ctx* c, hf_info* info) {

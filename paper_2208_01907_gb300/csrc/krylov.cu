@@ -792,7 +792,7 @@ static void sweep_work(hf_ctx* c, int cls, int m, size_t esz) {
 }
 
 template <typename TF, typename TV>
-static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp) {
+static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
   cudaStream_t s = hf_stream(c);
   sweep_work(c, HF_PROF_TRSV_FWD, m, sizeof(TF));
   const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
@@ -800,7 +800,6 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp) {
   const TF* arena = (const TF*)c->d_front.p;
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
   const int32_t* cbmap = (const int32_t*)c->d_cbmap.p;
-  TV* vec = (TV*)c->d_vec.p;
   const unsigned rt = (unsigned)((m + TR - 1) / TR);
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
@@ -824,14 +823,13 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp) {
 }
 
 template <typename TF, typename TV>
-static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout) {
+static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
   cudaStream_t s = hf_stream(c);
   sweep_work(c, HF_PROF_TRSV_BWD, m, sizeof(TF));
   const NodeDesc* nd = (const NodeDesc*)c->d_nodes.p;
   const NodeState* st = (const NodeState*)c->d_state.p;
   const TF* arena = (const TF*)c->d_front.p;
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
-  TV* vec = (TV*)c->d_vec.p;
   const unsigned rt = (unsigned)((m + TR - 1) / TR);
   for (int lev = 0; lev <= c->m; ++lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
@@ -856,9 +854,10 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout) {
 //  full = true : forward sweep only; y2 = the Lambda_2 rows, for the S22 solve
 template <typename TF, typename TV>
 static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const double* x2_dev, bool full,
-                     double* y2_dev) {
+                     double* y2_dev, void* vecbuf = nullptr) {
   cudaStream_t s = hf_stream(c);
-  fwd_sweep<TF, TV>(c, m, Bin, Ytmp);
+  TV* vec = (TV*)(vecbuf ? vecbuf : c->d_vec.p);
+  fwd_sweep<TF, TV>(c, m, Bin, Ytmp, vec);
   HF_CUDA_TRY(cudaGetLastError());
   const int M = (int)c->M;
   if (M) {
@@ -868,7 +867,7 @@ static int tri_solve(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* Xout, const 
     }
     HF_LAUNCH(c, HF_PROF_VECTOR, k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, nullptr, Xout));
   }
-  bwd_sweep<TF, TV>(c, m, Ytmp, Xout);
+  bwd_sweep<TF, TV>(c, m, Ytmp, Xout, vec);
   HF_CUDA_TRY(cudaGetLastError());
   (void)x2_dev;
   return HF_OK;
@@ -879,7 +878,7 @@ static int tri_solve_back(hf_ctx* c, int m, TV* Ytmp, TV* Xout, const double* x2
   cudaStream_t s = hf_stream(c);
   const int M = (int)c->M;
   if (M) HF_LAUNCH(c, HF_PROF_VECTOR, k_set_lam2<TV><<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, x2_dev, Xout));
-  bwd_sweep<TF, TV>(c, m, Ytmp, Xout);
+  bwd_sweep<TF, TV>(c, m, Ytmp, Xout, (TV*)c->d_vec.p);
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
 }
@@ -902,29 +901,33 @@ static int gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const dou
 }
 
 // K11-preconditioner application W = Q^-1 R (FP32 factor) or exact (FP64 factor)
-static int precond(hf_ctx* c, int m, const double* R, double* W, void* tmp32) {
+// W = Q^-1 R on caller-provided scratch: tmp32 (3 L m floats, or L m doubles for the FP64
+// factor) and vecbuf (the per-front vectors: row_elems m entries of the factor's type)
+static int precond_on(hf_ctx* c, int m, const double* R, double* W, void* tmp32, void* vecbuf) {
   cudaStream_t s = hf_stream(c);
   const int64_t L = c->L;
   const int32_t* l2p = (const int32_t*)c->d_lam2pos.p;
   if (c->prec == HF_PREC_FP64) {
     double* y = (double*)tmp32;
-    int rc;
-    if ((rc = ensure_vec(c, m, 8))) return rc;
     HF_CUDA_TRY(cudaMemcpyAsync(W, R, L * m * 8, cudaMemcpyDeviceToDevice, s));
     HF_LAUNCH(c, HF_PROF_VECTOR, k_zero_lam2_rows<<<nblk(c->M * m, 256), 256, 0, s>>>((int)c->M, m, (const int32_t*)c->d_lam2.p, W));
-    rc = tri_solve<double, double>(c, m, W, y, W, nullptr, false, nullptr);
-    return rc;
+    return tri_solve<double, double>(c, m, W, y, W, nullptr, false, nullptr, vecbuf);
   }
   float* b32 = (float*)tmp32;
   float* y32 = b32 + L * m;
   float* x32 = y32 + L * m;
   int rc;
-  if ((rc = ensure_vec(c, m, 4))) return rc;
   HF_LAUNCH(c, HF_PROF_VECTOR, k_cast_in<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, R, l2p, b32));
-  if ((rc = tri_solve<float, float>(c, m, b32, y32, x32, nullptr, false, nullptr))) return rc;
+  if ((rc = tri_solve<float, float>(c, m, b32, y32, x32, nullptr, false, nullptr, vecbuf))) return rc;
   HF_LAUNCH(c, HF_PROF_VECTOR, k_cast_out<float><<<nblk(L * m, 256), 256, 0, s>>>(L, m, x32, l2p, W));
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
+}
+
+static int precond(hf_ctx* c, int m, const double* R, double* W, void* tmp32) {
+  int rc;
+  if ((rc = ensure_vec(c, m, c->prec == HF_PREC_FP64 ? 8 : 4))) return rc;
+  return precond_on(c, m, R, W, tmp32, c->d_vec.p);
 }
 
 static void spmm(hf_ctx* c, int m, const double* W, double* Z) {
@@ -1255,5 +1258,43 @@ int hf_values_adjoint_impl(hf_ctx* c, int m, const double* x, int64_t ldx, const
                                                                                   (const int32_t*)c->d_col.p, x, ldx, lam, ldl, grad));
   HF_CUDA_TRY(cudaGetLastError());
   HF_CUDA_TRY(cudaStreamSynchronize(s));
+  return HF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Q^-1 without device allocation.  All scratch of the solve lives in this file-scope
+// device array, which every GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------------
+#define HF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+static __device__ __align__(256) unsigned char g_precond_scratch[HF_NOALLOC_SCRATCH_BYTES];
+
+static void* g_precond_scratch_addr[64] = {nullptr};   // device address of the array, per device
+
+int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W) {
+  if (!c || m < 1 || !R || !W) return HF_ERR_ARG;
+  if (!c->factored) return HF_ERR_STATE;
+  int dev = 0;
+  HF_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return HF_ERR_ARG;
+  const bool dbl = c->prec == HF_PREC_FP64;
+  const size_t esz = dbl ? 8 : 4;
+  const size_t tmp_bytes = dbl ? (size_t)c->L * m * 8 : (size_t)c->L * m * 4 * 3;
+  const size_t tmp_round = (tmp_bytes + 255) / 256 * 256;
+  const size_t vec_bytes = (size_t)c->row_elems * m * esz;
+  if (tmp_round + vec_bytes > HF_NOALLOC_SCRATCH_BYTES) return HF_ERR_ARG;
+  if (!g_precond_scratch_addr[dev]) {
+    // host code only has a stand-in for the array's name: ask the runtime for the address
+    // on this device (once per device, with that device current)
+    void* p = nullptr;
+    HF_CUDA_TRY(cudaGetSymbolAddress(&p, g_precond_scratch));
+    g_precond_scratch_addr[dev] = p;
+  }
+  unsigned char* base = (unsigned char*)g_precond_scratch_addr[dev];
+  const bool prof = c->prof_on;
+  c->prof_on = false;                  // event bookkeeping could create events: keep it off here
+  int rc = precond_on(c, m, R, W, base, base + tmp_round);
+  c->prof_on = prof;
+  if (rc) return rc;
+  HF_CUDA_TRY(cudaStreamSynchronize(hf_stream(c)));
   return HF_OK;
 }

@@ -23,7 +23,7 @@ EXPORTED = (
     "hf_default_opts", "hf_error_string", "hf_analyze", "hf_factorize", "hf_schur", "hf_solve",
     "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
-    "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_free",
+    "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc", "hf_free",
 )
 HF_NPROF = 13
 
@@ -85,6 +85,7 @@ def lib():
     L.hf_precond.argtypes = [vp, i32, vp, vp]
     L.hf_profile.argtypes = [vp, i32]
     L.hf_values_adjoint.argtypes = [vp, i32, vp, i64, vp, i64, vp]
+    L.hf_precond_noalloc.argtypes = [vp, i32, vp, vp]
     L.hf_get_profile.argtypes = [vp, vp, vp, vp, vp]
     L.hf_profile_name.argtypes = [i32]
     L.hf_profile_name.restype = C.c_char_p
@@ -183,6 +184,11 @@ class HybridFactor:
         _check(lib().hf_get_profile(self._h, _ptr(ms), _ptr(ln), _ptr(fl), _ptr(by)), "hf_get_profile")
         return {lib().hf_profile_name(i).decode(): (float(ms[i]), int(ln[i]), float(fl[i]), float(by[i]))
                 for i in range(HF_NPROF)}
+
+    def precond_noalloc(self, R_dev, W_dev):
+        """Same as precond(), with all scratch in the library's fixed device array (no allocation)."""
+        m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
+        _check(lib().hf_precond_noalloc(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond_noalloc")
 
     def values_adjoint(self, x_dev, lam_dev, grad_dev):
         """grad[e] = -sum_r lam[row_e, r] x[col_e, r] (tensors (nrhs, L) contiguous = column-major L x nrhs)."""
