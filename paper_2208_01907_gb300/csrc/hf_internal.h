@@ -119,6 +119,7 @@ struct hf_ctx {
   std::vector<std::pair<int, size_t>> prof_recs;   // (class, index of the start event)
   DevBuf d_gsmall;                   // block GCR small matrices (M_n, coefficients)
   DevBuf d_k12;                      // K12 block (L x M), the right-hand sides of Alg. 1 step 3
+  DevBuf d_ozint;                    // scaling exponents of the emulated FP64 products
   DevBuf d_solve;                    // hf_solve scratch
 };
 

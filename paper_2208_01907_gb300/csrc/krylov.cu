@@ -747,6 +747,19 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
+int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale,
+               double* scratch, size_t scratch_bytes, int* iscratch, int* err);
+int hf_oz_update(hf_ctx* c, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
+                 double sgn, int* iscratch, int* err);
+
+static int* oz_err(hf_ctx* c) { return (int*)c->d_flags.p + FLAG_COUNT + 10; }
+
+static int oz_iscratch(hf_ctx* c, size_t n, int** p) {
+  int rc = hf_ensure(c->d_ozint, n * 4 + 256);
+  *p = (int*)c->d_ozint.p;
+  return rc;
+}
+
 // ============================================================================
 // Host drivers
 // ============================================================================
@@ -886,6 +899,18 @@ static int tri_solve_back(hf_ctx* c, int m, TV* Ytmp, TV* Xout, const double* x2
 // Gram G = scale * A^T B
 static int gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale) {
   const int sym = (A == B && ma == mb) ? 1 : 0;
+  if (c->opts.fp64_gemm == 0) {
+    // FP64-accurate product on the tensor cores (all 2 L ma mb multiply-adds are done)
+    c->work_flops[HF_PROF_GRAM] += 2.0 * (double)L * ma * mb;
+    c->work_bytes[HF_PROF_GRAM] += 8.0 * (double)L * (ma + mb);
+    const int tiles = ((ma + 127) / 128) * ((mb + 63) / 64);
+    const size_t nch = (size_t)std::max(1, (2 * 152 + tiles - 1) / tiles) + 2;
+    int rc = hf_ensure(c->d_small, std::max(nch * (size_t)ma * mb * 8 + 64, (size_t)(1 << 20)));
+    if (rc) return rc;
+    int* is = nullptr;
+    if ((rc = oz_iscratch(c, (size_t)ma + mb + 64, &is))) return rc;
+    return hf_oz_gram(c, L, ma, mb, A, B, G, scale, (double*)c->d_small.p, c->d_small.bytes, is, oz_err(c));
+  }
   c->work_flops[HF_PROF_GRAM] += 2.0 * (double)L * ma * mb * (sym ? 0.5 : 1.0);
   c->work_bytes[HF_PROF_GRAM] += 8.0 * (double)L * (sym ? ma : ma + mb);
   cudaStream_t s = hf_stream(c);
@@ -979,6 +1004,19 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   const int use_smem = mm * 8 <= 48 * 1024;
   const size_t axpy_smem = use_smem ? mm * 8 : 0;
   const double axpy_flops = 2.0 * (double)L * m * m, axpy_bytes = 8.0 * (double)L * m * 3;
+  int* ozis = nullptr;
+  if (c->opts.fp64_gemm == 0) {
+    if ((rc = oz_iscratch(c, (size_t)L + m + 64, &ozis))) return rc;
+    HF_CUDA_TRY(cudaMemsetAsync(oz_err(c), 0, sizeof(int), s));
+  }
+  // Y = (Yinit ? Yinit : Y) + sgn * A C, FP64-accurate
+  auto block_update = [&](const double* A, const double* Cmat, double* Y, const double* Yinit, double sgn) -> int {
+    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops;
+    c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
+    if (c->opts.fp64_gemm == 0) return hf_oz_update(c, L, m, A, Cmat, Y, Yinit, sgn, ozis, oz_err(c));
+    HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, A, Cmat, Y, Yinit, sgn, use_smem));
+    return HF_OK;
+  };
 
   auto colnorms = [&](const double* A, std::vector<double>& out) -> int {
     int r = gram(c, L, m, m, A, A, diag, 1.0);
@@ -1012,10 +1050,8 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     HF_LAUNCH(c, HF_PROF_VECTOR, k_chol<<<1, 1024, 0, s>>>(m, Mn, dropv + (size_t)n * dstride));   // M_n = R^T R
     if ((rc = gram(c, L, m, m, Qm(n), R, Gm, 1.0))) return rc;
     msolve(n, Gm, Cm);
-    HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(n), Cm, X, nullptr, 1.0, use_smem));
-    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops; c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
-    HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Qm(n), Cm, R, nullptr, -1.0, use_smem));
-    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops; c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
+    if ((rc = block_update(Pm(n), Cm, X, nullptr, 1.0))) return rc;
+    if ((rc = block_update(Qm(n), Cm, R, nullptr, -1.0))) return rc;
     HF_CUDA_TRY(cudaGetLastError());
     it = n + 1;
     if ((rc = colnorms(R, hnorm))) return rc;
@@ -1048,8 +1084,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     for (int q = 0; q <= n; ++q) {
       if ((rc = gram(c, L, m, m, Qm(q), Z, Gm, -1.0))) return rc;      // B_qn = -Q_q^T Z
       msolve(q, Gm, Cm);
-      HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0, use_smem));
-    c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops; c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
+      if ((rc = block_update(Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0))) return rc;
     }
     // Q_{n+1} = K11 P_{n+1}: one FP64 SpMM instead of the n+1 dense recurrence terms (reading R14)
     spmm(c, m, Pn, Qn);
@@ -1057,6 +1092,12 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   }
   *iters = it;
   *relres = res;
+  if (c->opts.fp64_gemm == 0) {
+    int h = 0;
+    HF_CUDA_TRY(cudaMemcpyAsync(&h, oz_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
+    HF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return HF_ERR_TIMEOUT;     // a tensor-core wait gave up: the products are not valid
+  }
   return conv ? HF_OK : HF_ERR_NOT_CONVERGED;
 }
 

@@ -154,6 +154,25 @@ def test_fp64_form_schur_and_solve():
     assert out["info"]["kernel_dim"] == 1
 
 
+@pytest.mark.parametrize("name", ["cfg1_diffusion48", "stokes8", "elasticity6"])
+def test_emulated_fp64_products_match_native(name):
+    """Block GCR (Sec. 3.5) with its Grams and updates on the tensor cores (sliced
+    BF16 products, FP64-accurate) against the same iteration on native FP64 kernels:
+    same pivots, so X12 and S22 agree to the iteration's own rounding."""
+    make, _, opts = CASES[name]
+    s = make()
+    emu = run_gpu(s, tau=1e-2, fp64_gemm=0, **opts)
+    nat = run_gpu(s, tau=1e-2, fp64_gemm=1, **opts)
+    assert emu["schur_rc"] == 0 and nat["schur_rc"] == 0
+    assert emu["H"].split()[1].tolist() == nat["H"].split()[1].tolist()
+    Xe, Xn = emu["H"].x12(torch).cpu().numpy(), nat["H"].x12(torch).cpu().numpy()
+    assert np.abs(Xe - Xn).max() <= 1e-12 * max(np.abs(Xn).max(), 1.0)
+    Se, Sn = emu["H"].s22(torch).cpu().numpy(), nat["H"].s22(torch).cpu().numpy()
+    assert rel_fro(Se, Sn) <= 1e-12
+    assert emu["info"]["gcr_iters"] == nat["info"]["gcr_iters"]
+    assert O.backward_error(s.to_scipy(), emu["x"], emu["b"]) <= BWD_TOL
+
+
 @pytest.mark.parametrize("name", ["dirichlet20", "cfg1_diffusion48", "stokes8"])
 def test_fp64_form_precond_is_exact_inverse(name):
     """With the FP64 factor the multifrontal solve is a direct solve of K11."""
