@@ -76,7 +76,7 @@ typedef struct {
   void*  cuda_stream;    /* cudaStream_t; NULL = default stream */
   int    fp64_gemm;      /* FP64 Grams and block updates of block GCR: 0 = emulated on the BF16
                             tensor cores with exact slice products (FP64 accuracy), 1 = FP64
-                            units; default 1 */
+                            units; default 0 */
 } hf_opts;
 
 typedef struct {

@@ -107,6 +107,7 @@ struct hf_ctx {
   int64_t nnz_factor = 0;
   DevBuf d_work;                     // Krylov workspace
   size_t work_cap = 0;
+  DevBuf d_ozslice;                  // BF16 slices of the operands of the emulated FP64 products
   DevBuf d_small;                    // small matrices / partial sums
   size_t small_cap = 0;
   // ---- tracing ----

@@ -346,6 +346,26 @@ __global__ void k_gram_partial(int64_t L, int ma, int mb, const double* __restri
   for (int q = 0; q < 4; ++q) P[(ty + 8 * q) * GO + tx] = acc[q];
 }
 
+// Column sums of squares of a row-major L x m block: per row-chunk partials (pass 1),
+// then a fixed-order reduction (pass 2), so the result does not depend on scheduling.
+__global__ void k_colsq_partial(int64_t L, int m, const double* __restrict__ A, double* __restrict__ part) {
+  const int j = blockIdx.y * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int64_t rows = (L + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows, r1 = min(L, r0 + rows);
+  double s = 0.0;
+  for (int64_t r = r0; r < r1; ++r) { const double v = A[r * m + j]; s += v * v; }
+  part[(int64_t)blockIdx.x * m + j] = s;
+}
+
+__global__ void k_colsq_reduce(int m, int nchunks, const double* __restrict__ part, double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += part[(int64_t)c * m + j];
+  out[j] = s;
+}
+
 __global__ void k_gram_reduce(int ma, int mb, int nchunks, const double* __restrict__ part, double* __restrict__ G,
                               double scale, int sym) {
   const int nbb = (mb + GO - 1) / GO;
@@ -748,9 +768,11 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 }  // namespace
 
 int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale,
-               double* scratch, size_t scratch_bytes, int* iscratch, int* err);
+               double* scratch, size_t scratch_bytes, void* slices, size_t slice_bytes, int* iscratch, int* err);
 int hf_oz_update(hf_ctx* c, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
-                 double sgn, int* iscratch, int* err);
+                 double sgn, void* slices, size_t slice_bytes, int* iscratch, int* err);
+size_t hf_oz_slice_bytes(int64_t R, int64_t K);
+int64_t hf_oz_gram_chunks(int64_t L, int ma, int mb);
 
 static int* oz_err(hf_ctx* c) { return (int*)c->d_flags.p + FLAG_COUNT + 10; }
 
@@ -903,13 +925,15 @@ static int gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const dou
     // FP64-accurate product on the tensor cores (all 2 L ma mb multiply-adds are done)
     c->work_flops[HF_PROF_GRAM] += 2.0 * (double)L * ma * mb;
     c->work_bytes[HF_PROF_GRAM] += 8.0 * (double)L * (ma + mb);
-    const int tiles = ((ma + 127) / 128) * ((mb + 63) / 64);
-    const size_t nch = (size_t)std::max(1, (2 * 152 + tiles - 1) / tiles) + 2;
+    const size_t nch = (size_t)hf_oz_gram_chunks(L, ma, mb);
     int rc = hf_ensure(c->d_small, std::max(nch * (size_t)ma * mb * 8 + 64, (size_t)(1 << 20)));
     if (rc) return rc;
     int* is = nullptr;
     if ((rc = oz_iscratch(c, (size_t)ma + mb + 64, &is))) return rc;
-    return hf_oz_gram(c, L, ma, mb, A, B, G, scale, (double*)c->d_small.p, c->d_small.bytes, is, oz_err(c));
+    const size_t sl = hf_oz_slice_bytes(ma, L) + (A == B && ma == mb ? 0 : hf_oz_slice_bytes(mb, L));
+    if ((rc = hf_ensure(c->d_ozslice, sl + 256))) return rc;
+    return hf_oz_gram(c, L, ma, mb, A, B, G, scale, (double*)c->d_small.p, c->d_small.bytes, c->d_ozslice.p,
+                      c->d_ozslice.bytes, is, oz_err(c));
   }
   c->work_flops[HF_PROF_GRAM] += 2.0 * (double)L * ma * mb * (sym ? 0.5 : 1.0);
   c->work_bytes[HF_PROF_GRAM] += 8.0 * (double)L * (sym ? ma : ma + mb);
@@ -1007,24 +1031,35 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   int* ozis = nullptr;
   if (c->opts.fp64_gemm == 0) {
     if ((rc = oz_iscratch(c, (size_t)L + m + 64, &ozis))) return rc;
+    const size_t sl = std::max(hf_oz_slice_bytes(L, m) + hf_oz_slice_bytes(m, m), 2 * hf_oz_slice_bytes(m, L));
+    if ((rc = hf_ensure(c->d_ozslice, sl + 256))) return rc;
     HF_CUDA_TRY(cudaMemsetAsync(oz_err(c), 0, sizeof(int), s));
   }
   // Y = (Yinit ? Yinit : Y) + sgn * A C, FP64-accurate
   auto block_update = [&](const double* A, const double* Cmat, double* Y, const double* Yinit, double sgn) -> int {
     c->work_flops[HF_PROF_BLOCK_UPDATE] += axpy_flops;
     c->work_bytes[HF_PROF_BLOCK_UPDATE] += axpy_bytes;
-    if (c->opts.fp64_gemm == 0) return hf_oz_update(c, L, m, A, Cmat, Y, Yinit, sgn, ozis, oz_err(c));
+    if (c->opts.fp64_gemm == 0)
+      return hf_oz_update(c, L, m, A, Cmat, Y, Yinit, sgn, c->d_ozslice.p, c->d_ozslice.bytes, ozis, oz_err(c));
     HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nb, 256, axpy_smem, s>>>(L, m, A, Cmat, Y, Yinit, sgn, use_smem));
     return HF_OK;
   };
 
+  // column 2-norms; row-chunk partials in the small scratch buffer
+  const int ncs = (int)std::max<int64_t>(1, std::min<int64_t>(L / 1024, 152));
   auto colnorms = [&](const double* A, std::vector<double>& out) -> int {
-    int r = gram(c, L, m, m, A, A, diag, 1.0);
+    c->work_flops[HF_PROF_VECTOR] += 2.0 * (double)L * m;
+    c->work_bytes[HF_PROF_VECTOR] += 8.0 * (double)L * m;
+    int r = hf_ensure(c->d_small, std::max((size_t)ncs * m * 8 + 64, (size_t)(1 << 20)));
     if (r) return r;
-    std::vector<double> g(mm);
-    HF_CUDA_TRY(cudaMemcpyAsync(g.data(), diag, mm * 8, cudaMemcpyDeviceToHost, s));
+    double* part = (double*)c->d_small.p;
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_partial<<<dim3(ncs, (m + 127) / 128), 128, 0, s>>>(L, m, A, part));
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_reduce<<<(m + 127) / 128, 128, 0, s>>>(m, ncs, part, diag));
+    HF_CUDA_TRY(cudaGetLastError());
+    std::vector<double> g(m);
+    HF_CUDA_TRY(cudaMemcpyAsync(g.data(), diag, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
     HF_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int i = 0; i < m; ++i) out[i] = std::sqrt(std::max(0.0, g[i * m + i]));
+    for (int i = 0; i < m; ++i) out[i] = std::sqrt(std::max(0.0, g[i]));
     return HF_OK;
   };
   if ((rc = colnorms(B, bnorm))) return rc;
