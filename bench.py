@@ -257,17 +257,23 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs", 6800.0)
     fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12          # derived: SMs x FP32 lanes x FMA x max clock
     fp64_peak = 1.25                                    # nominal GB300 FP64 (profiling recipe table)
+    bf16_sus = peaks.get("bf16_tflops_sustained", 1700.0)
     kinds = {
+        "panel": ("alu", fp32_simt, "k_panel_cl (pivoted left-looking panel, cluster/DSMEM resident)",
+                  "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
         "trailing": ("alu", fp32_simt, "k_trailing (FP32 SIMT rank-nb Schur update)",
                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "gram": ("alu", fp64_peak, "k_gram_partial (FP64 block Gram Q^T Z)", "nominal FP64 1.25 TFLOP/s"),
-        "block_update": ("alu", fp64_peak, "k_block_axpy (FP64 N x M by M x M update)",
-                         "nominal FP64 1.25 TFLOP/s"),
+        "gram": ("tensor", bf16_sus, "k_oz_mma (FP64 Gram Q^T Z emulated: 36 BF16 slice products)",
+                 "MEASURED_PEAKS.json bf16_tflops_sustained"),
+        "block_update": ("tensor", bf16_sus, "k_oz_mma (FP64 update P C emulated: 36 BF16 slice products)",
+                         "MEASURED_PEAKS.json bf16_tflops_sustained"),
         "trsv_fwd": ("hbm", hbm, "k_trsm_diag/k_gemm_upd forward sweep (FP32 factor)", "MEASURED_PEAKS.json hbm_gbs"),
         "trsv_bwd": ("hbm", hbm, "k_trsm_diag/k_gemm_upd backward sweep (FP32 factor)", "MEASURED_PEAKS.json hbm_gbs"),
         "spmm": ("hbm", hbm, "k_spmm (FP64 CSR x block)", "MEASURED_PEAKS.json hbm_gbs"),
     }
     bound, peak, kname, psrc = kinds.get(dom, ("alu", None, dom, None))
+    if dom in ("gram", "block_update") and not info.get("fp64_native", False):
+        dom_flops = 36.0 * dom_flops      # tensor work: 36 slice products per FP64 multiply-add
     if bound == "hbm":
         achieved = dom_bytes / (dom_ms / 1e3) / 1e9
         unit = "GB/s"

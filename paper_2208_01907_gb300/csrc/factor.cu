@@ -11,8 +11,10 @@
 // contribution passed to the parent by extend-add.
 #include "common.cuh"
 
+#include <cooperative_groups.h>
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 namespace {
@@ -203,7 +205,7 @@ __device__ __forceinline__ void sym_swap(T* F, int64_t ld, int f, int a, int b, 
 template <typename T>
 __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0,
                         T* __restrict__ arena, int32_t* __restrict__ rowid, T* __restrict__ Gall,
-                        int32_t* __restrict__ pos0all, int nb, double tau) {
+                        int32_t* __restrict__ pos0all, int nb, double tau, int cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red_k[32];
   __shared__ int red_i[32], red_p[32];
@@ -216,6 +218,7 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
   const int k0 = S->k;
   int nact = S->nact;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (f - k0 <= cap) return;               // handled by the shared-memory cluster kernel
   if (S->stopped || k0 >= nact) {
     if (tid == 0) S->kp0 = k0;
     return;
@@ -326,6 +329,329 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
     S->nact = nact;
     if (stopped) S->stopped = 1;
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same panel step with the panel resident in distributed shared memory: a
+// cluster of C CTAs per front, CTA r owning the front positions
+// [k0 + r R, k0 + (r+1) R) of the rows [k0, f).  Each CTA keeps, for its rows, the
+// panel columns computed so far (row-major, stride nb+1) and the per-row data
+// (running candidate diagonal, diagonal entry, term magnitude, ids).
+//
+// One cluster barrier per pivot.  Before it, every CTA pushes into every CTA's
+// (double-buffered) slots: its best candidate (key, id, G, diagonal, panel row),
+// and the owners of positions k and nact-1 push those rows.  After it, every CTA
+// takes the same decision (R2, R3, R3b, R5) from its local slots, forms
+// w_c = d_c L(q, c), computes d_k itself (same operations, same order as the
+// owner would) and processes its own rows: the symmetric swap k <-> q is fused into
+// the load of the new column k, then L(i, k), the diagonals and the magnitudes.
+// The arithmetic per element is that of k_panel, in the same order.  A front larger
+// than C * Rcap rows is left to k_panel (which skips the fronts handled here).
+// ---------------------------------------------------------------------------
+constexpr int PCL_THREADS = 512;
+constexpr int PCL_CMAX = 8;
+constexpr int PCL_SLOTS = PCL_CMAX + 2;       // candidates of C CTAs, row k, row nact-1
+
+template <typename T> struct PclLayout {
+  // bytes of dynamic shared memory for Rcap rows and panel width nb
+  static size_t bytes(int Rcap, int nb) {
+    const size_t per_row = (size_t)(nb + 1) * sizeof(T) + 3 * sizeof(T) + 3 * sizeof(int);
+    return (size_t)Rcap * per_row + 2 * (size_t)nb * sizeof(T) + push_bytes(nb) + 64;
+  }
+  static size_t push_bytes(int nb) {
+    return 2 * (size_t)PCL_SLOTS * ((size_t)nb * sizeof(T) + 3 * sizeof(T) + sizeof(double) + 4 * sizeof(int));
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(PCL_THREADS, 1)
+k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, T* __restrict__ arena,
+           int32_t* __restrict__ rowid, T* __restrict__ Gall, int32_t* __restrict__ pos0all, int nb, double tau,
+           int C, int Rcap) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red_k[32];
+  __shared__ int red_i[32], red_p[32];
+  __shared__ int s_act, s_q, s_w;
+  __shared__ T s_dk;
+  const int rank = (int)cl.block_rank();
+  const int t = t0 + (int)(blockIdx.x / (unsigned)C);
+  const NodeDesc d = nd[t];
+  NodeState* S = st + t;
+  const int f = S->f;
+  const int k0 = S->k;
+  int nact = S->nact;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // the same decisions in every CTA of the cluster
+  if (S->stopped || k0 >= nact || f - k0 > C * Rcap) {
+    if (rank == 0 && tid == 0 && (S->stopped || k0 >= nact)) S->kp0 = k0;
+    return;
+  }
+  T* F = arena + d.front_off;
+  T* Gg = Gall + d.row_off;
+  const int64_t ld = d.ld;
+  int32_t* rid = rowid + d.row_off;
+  int32_t* pos0 = pos0all + d.row_off;
+  const int ps = nb + 1;
+  // dynamic shared memory
+  T* P = (T*)smem_raw;                         // Rcap x ps: panel rows
+  T* dgl = P + (size_t)Rcap * ps;              // running candidate diagonal
+  T* Gl = dgl + Rcap;                          // term magnitudes
+  T* diagl = Gl + Rcap;                        // diagonal entries F(p, p)
+  T* wv = diagl + Rcap;                        // nb
+  T* dpiv = wv + nb;                           // nb: pivots of this panel
+  T* prow = dpiv + nb;                         // [2][SLOTS][nb] pushed panel rows
+  T* pG = prow + 2 * PCL_SLOTS * nb;           // [2][SLOTS]
+  T* pdiag = pG + 2 * PCL_SLOTS;
+  T* pdg = pdiag + 2 * PCL_SLOTS;
+  double* pkey = (double*)(((uintptr_t)(pdg + 2 * PCL_SLOTS) + 7) & ~(uintptr_t)7);   // [2][SLOTS]
+  int* psid = (int*)(pkey + 2 * PCL_SLOTS);    // [2][SLOTS]
+  int* ppos = psid + 2 * PCL_SLOTS;
+  int* prid = ppos + 2 * PCL_SLOTS;
+  int* pp0 = prid + 2 * PCL_SLOTS;
+  int* sidl = pp0 + 2 * PCL_SLOTS;             // Rcap
+  int* ridl = sidl + Rcap;                     // Rcap
+  int* pos0l = ridl + Rcap;                    // Rcap
+  const int R = (f - k0 + C - 1) / C;
+  const int p0 = k0 + rank * R, p1 = min(f, p0 + R);
+  auto owner = [&](int p) { return (p - k0) / R; };
+  for (int p = p0 + tid; p < p1; p += nt) {
+    const int l = p - p0;
+    const T dv = F[p + (int64_t)p * ld];
+    diagl[l] = dv;
+    dgl[l] = dv;
+    Gl[l] = Gg[p];
+    sidl[l] = rid[p];
+    ridl[l] = rid[p];
+    pos0l[l] = pos0[p];
+  }
+  double dref = S->dref;
+  int k = k0;
+  bool stopped = false;
+  int it = 0;
+  cl.sync();
+  // push the row at own position p into slot `slot` of buffer `buf` of every CTA
+  auto push_row = [&](int buf, int slot, int p, double key, int kk) {
+    const int l = p - p0;
+    const int base = buf * PCL_SLOTS + slot;
+    for (int e = tid; e < C * kk; e += nt) {
+      const int r = e / kk, c = e - r * kk;
+      cl.map_shared_rank(prow, r)[(size_t)base * nb + c] = P[(size_t)l * ps + c];
+    }
+    if (tid < C) {
+      const int r = tid;
+      cl.map_shared_rank(pkey, r)[base] = key;
+      cl.map_shared_rank(psid, r)[base] = sidl[l];
+      cl.map_shared_rank(ppos, r)[base] = p;
+      cl.map_shared_rank(prid, r)[base] = ridl[l];
+      cl.map_shared_rank(pp0, r)[base] = pos0l[l];
+      cl.map_shared_rank(pG, r)[base] = Gl[l];
+      cl.map_shared_rank(pdiag, r)[base] = diagl[l];
+      cl.map_shared_rank(pdg, r)[base] = dgl[l];
+    }
+  };
+  while (k < k0 + nb && k < nact) {
+    const int buf = it & 1;
+    const int kk = k - k0;
+    // 1. local argmax over the own candidates [k, nact), ties to the smaller original index (R5)
+    double bk = -2.0;
+    int bi = 0x7fffffff, bp = -1;
+    for (int p = max(k, p0) + tid; p < min(nact, p1); p += nt) {
+      const double kv = piv_key(dgl[p - p0]);
+      const int si = sidl[p - p0];
+      if (better(kv, si, bk, bi)) { bk = kv; bi = si; bp = p; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (better(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
+    }
+    if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; red_p[tid >> 5] = bp; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w2 = 1; w2 < (nt + 31) / 32; ++w2)
+        if (better(red_k[w2], red_i[w2], bk, bi)) { bk = red_k[w2]; bi = red_i[w2]; bp = red_p[w2]; }
+      red_k[0] = bk; red_i[0] = bi; red_p[0] = bp;
+    }
+    __syncthreads();
+    // 2. pushes: own candidate, and rows k / nact-1 by their owners
+    {
+      const int pbest = red_p[0];
+      const int base = buf * PCL_SLOTS + rank;
+      if (pbest >= 0) {
+        push_row(buf, rank, pbest, red_k[0], kk);
+      } else if (tid < C) {
+        cl.map_shared_rank(pkey, tid)[base] = -2.0;
+        cl.map_shared_rank(psid, tid)[base] = 0x7fffffff;
+        cl.map_shared_rank(ppos, tid)[base] = -1;
+      }
+      if (owner(k) == rank) push_row(buf, PCL_CMAX, k, 0.0, kk);
+      if (owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, 0.0, kk);
+    }
+    cl.sync();                                                             // the only cluster barrier
+    // 3. the decision, identical in every CTA
+    const int sb = buf * PCL_SLOTS;
+    if (tid == 0) {
+      double gk = -2.0;
+      int gi = 0x7fffffff, gw = -1;
+      for (int r = 0; r < C; ++r)
+        if (ppos[sb + r] >= 0 && better(pkey[sb + r], psid[sb + r], gk, gi)) { gk = pkey[sb + r]; gi = psid[sb + r]; gw = r; }
+      int act = 0;
+      if (!(gk >= tau * dref)) act = 1;                                          // ratio test (R2/R3)
+      else if (!(gk >= tau * (double)pG[sb + gw])) act = 2;                     // null pivot (R3b)
+      s_act = act;
+      s_w = gw;
+      s_q = gw >= 0 ? ppos[sb + gw] : -1;
+    }
+    __syncthreads();
+    const int act = s_act, q = s_q, wsl = sb + s_w;
+    if (act == 1) { stopped = true; break; }
+    if (act == 2) {
+      // 4a. postpone the null candidate: swap q <-> b = nact-1 (both candidates)
+      const int b = nact - 1;
+      if (q != b) {
+        const int bsl = sb + PCL_CMAX + 1;
+        // rows q and b over the columns outside the computed panel: [0, k0) and [k, q), spread
+        // over the cluster (ordered before any later use by the next cluster barrier)
+        {
+          const int nL = k0, nM = q - k;
+          for (int e = rank * nt + tid; e < nL + nM; e += C * nt) {
+            const int j = e < nL ? e : k + (e - nL);
+            const int64_t x = q + (int64_t)j * ld, y = b + (int64_t)j * ld;
+            const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+          }
+        }
+        if (owner(q) == rank) {
+          const int l = q - p0;
+          for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = prow[(size_t)bsl * nb + c];
+          if (tid == 0) {
+            dgl[l] = pdg[bsl]; Gl[l] = pG[bsl]; diagl[l] = pdiag[bsl];
+            sidl[l] = psid[bsl]; ridl[l] = prid[bsl]; pos0l[l] = pp0[bsl];
+          }
+        }
+        if (owner(b) == rank) {
+          const int l = b - p0;
+          for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = prow[(size_t)wsl * nb + c];
+          if (tid == 0) {
+            dgl[l] = pdg[wsl]; Gl[l] = pG[wsl]; diagl[l] = pdiag[wsl];
+            sidl[l] = psid[wsl]; ridl[l] = prid[wsl]; pos0l[l] = pp0[wsl];
+          }
+        }
+        // middle (j in (q, b): (j, q) <-> (b, j)) and lower (i > b: (i, q) <-> (i, b)) parts by row owners
+        for (int p = max(q + 1, p0) + tid; p < p1; p += nt) {
+          if (p == b) continue;
+          int64_t x, y;
+          if (p < b) { x = p + (int64_t)q * ld; y = b + (int64_t)p * ld; }
+          else { x = p + (int64_t)q * ld; y = p + (int64_t)b * ld; }
+          const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+        }
+      }
+      --nact;
+      ++it;
+      __syncthreads();
+      continue;
+    }
+    // 4b. pivot q -> position k.  w from the winner's row; d_k computed locally
+    const T* rq = prow + (size_t)wsl * nb;
+    const int ksl = sb + PCL_CMAX;
+    const T* rk = prow + (size_t)ksl * nb;
+    for (int c = tid; c < kk; c += nt) wv[c] = dpiv[c] * rq[c];
+    // new contents of positions k and q (own rows only)
+    if (owner(k) == rank) {
+      const int l = k - p0;
+      for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rq[c];
+      if (tid == 0) {
+        sidl[l] = psid[wsl]; ridl[l] = prid[wsl]; pos0l[l] = pp0[wsl]; Gl[l] = pG[wsl];
+      }
+    }
+    if (q != k && owner(q) == rank) {
+      const int l = q - p0;
+      for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rk[c];
+      if (tid == 0) {
+        dgl[l] = pdg[ksl]; Gl[l] = pG[ksl]; diagl[l] = pdiag[ksl];
+        sidl[l] = psid[ksl]; ridl[l] = prid[ksl]; pos0l[l] = pp0[ksl];
+      }
+    }
+    __syncthreads();
+    // 5. warp 0: d_k (every CTA, the owner's operations); warps 1..: rows k and q over the
+    // earlier panels' columns [0, k0) (spread over the cluster, not read again in this
+    // panel), and column k of the own rows with the swap fused into its load
+    if (tid < 32) {
+      if (tid == 0) {
+        T acc = pdiag[wsl];
+        for (int c = 0; c < kk; ++c) acc -= rq[c] * wv[c];
+        s_dk = acc;
+      }
+    } else {
+      const int t2 = tid - 32, n2 = nt - 32;
+      if (q != k)
+        for (int j = rank * n2 + t2; j < k0; j += C * n2) {
+          const int64_t x = k + (int64_t)j * ld, y = q + (int64_t)j * ld;
+          const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+        }
+      for (int p = max(k + 1, p0) + t2; p < p1; p += n2) {
+        T v;
+        if (q == k) {
+          v = F[p + (int64_t)k * ld];
+        } else if (p > q) {
+          const int64_t x = p + (int64_t)k * ld, y = p + (int64_t)q * ld;
+          v = F[y];
+          F[y] = F[x];
+        } else if (p < q) {
+          const int64_t x = p + (int64_t)k * ld, y = q + (int64_t)p * ld;
+          v = F[y];
+          F[y] = F[x];
+        } else {
+          v = F[q + (int64_t)k * ld];
+        }
+        T* Pr = P + (size_t)(p - p0) * ps;
+        T acc = v;
+        for (int c = 0; c < kk; ++c) acc -= Pr[c] * wv[c];
+        Pr[kk] = acc;
+      }
+    }
+    __syncthreads();
+    // 6. L(i, k) = c_i / d_k, the candidates' diagonals and the term magnitudes
+    const T dk = s_dk;
+    if (owner(k) == rank && tid == 0) P[(size_t)(k - p0) * ps + kk] = dk;
+    for (int p = max(k + 1, p0) + tid; p < p1; p += nt) {
+      const int l = p - p0;
+      T* e = P + (size_t)l * ps + kk;
+      const T acc = *e;
+      const T lv = acc / dk;
+      *e = lv;
+      if (p < nact) dgl[l] -= lv * acc;
+      Gl[l] += fabs(lv * acc);
+    }
+    if (tid == 0) dpiv[kk] = dk;
+    dref = fabs((double)dk);
+    ++k;
+    ++it;
+    __syncthreads();
+  }
+  // write back: computed panel columns (lower part), diagonals of the unpivoted rows, row data
+  const int kdone = k - k0;
+  for (int c = 0; c < kdone; ++c)
+    for (int p = max(p0, k0 + c) + tid; p < p1; p += nt)
+      F[p + (int64_t)(k0 + c) * ld] = P[(size_t)(p - p0) * ps + c];
+  for (int p = max(p0, k) + tid; p < p1; p += nt) F[p + (int64_t)p * ld] = diagl[p - p0];
+  for (int p = p0 + tid; p < p1; p += nt) {
+    const int l = p - p0;
+    Gg[p] = Gl[l];
+    rid[p] = ridl[l];
+    pos0[p] = pos0l[l];
+  }
+  if (rank == 0 && tid == 0) {
+    S->kp0 = k0;
+    S->k = k;
+    S->dref = dref;
+    S->nact = nact;
+    if (stopped) S->stopped = 1;
+  }
+  cl.sync();                               // no CTA leaves while its shared memory may be written
 }
 
 // ---------------------------------------------------------------------------
@@ -516,11 +842,38 @@ int run_levels(hf_ctx* c) {
   int* flags = (int*)c->d_flags.p;
   const int nb = std::max(1, std::min(c->opts.panel, 256));
   const int nn = c->n_nodes;
+  constexpr size_t PCL_SMEM = 220 * 1024;
   static bool attr_set[2] = {false, false};
+  static int max_cluster[2] = {0, 0};
   if (!attr_set[sizeof(T) == 8]) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCL_SMEM));
+    // largest cluster (<= 8) that can be resident with the full shared-memory panel
+    for (int cs = 8; cs >= 1; cs /= 2) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(cs);
+      q.blockDim = dim3(PCL_THREADS);
+      q.dynamicSmemBytes = PCL_SMEM;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+      q.attrs = at; q.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_panel_cl<T>, &q) == cudaSuccess && ncl > 0) {
+        max_cluster[sizeof(T) == 8] = cs;
+        break;
+      }
+      (void)cudaGetLastError();
+    }
     attr_set[sizeof(T) == 8] = true;
   }
+  const int cmax = max_cluster[sizeof(T) == 8];
+  // HF_LEVEL_TIMES=1: time the panel and trailing launches of every level (diagnostic)
+  const char* lt = std::getenv("HF_LEVEL_TIMES");
+  const bool level_times = lt && lt[0] == '1';
+  // HF_PANEL_KERNEL=global: one CTA per front with the panel in global memory (for comparison)
+  const char* pk = std::getenv("HF_PANEL_KERNEL");
+  const bool panel_global = pk && pk[0] == 'g';
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
     int maxn = 0, maxld = 0;
@@ -553,14 +906,55 @@ int run_levels(hf_ctx* c) {
     HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_g_assemble<T><<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_cbmap.p,
                                         (const int64_t*)c->d_diagpos.p, (const double*)c->d_kval.p, gmag,
                                         (int32_t*)c->d_pos0.p));
-    const int npan = (maxn + nb - 1) / nb;
-    const size_t smem = (size_t)nb * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
-    if (smem > 220 * 1024) return HF_ERR_ARG;
+    // panel in distributed shared memory for the fronts a cluster of <= cmax CTAs can hold;
+    // larger ones (if any) by the global-memory kernel in the same step
+    const int nbc = sizeof(T) == 8 ? std::min(nb, 32) : nb;
+    const size_t per_row = (size_t)(nbc + 1) * sizeof(T) + 3 * sizeof(T) + 3 * sizeof(int);
+    const size_t fixed = PclLayout<T>::bytes(0, nbc);
+    const int Rcap = (int)((PCL_SMEM - fixed) / per_row);
+    const int C = std::max(1, std::min(cmax, (maxld + Rcap - 1) / Rcap));
+    const bool use_cl = cmax > 0 && maxld > 0 && !panel_global;
+    const int cap = use_cl ? C * Rcap : -1;
+    const bool use_gl = !use_cl || maxld > cap;
+    const int nbl = use_cl ? nbc : nb;
+    const int npan = (maxn + nbl - 1) / nbl;
+    const size_t smem = (size_t)nbl * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
+    if (use_gl && smem > 220 * 1024) return HF_ERR_ARG;
     const int pthreads = maxld > 1024 ? 1024 : 256;
     const int tiles = (maxld + TB - 1) / TB;
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute la[1];
+    if (use_cl) {
+      lc.gridDim = dim3((unsigned)(cnt * C));
+      lc.blockDim = dim3(PCL_THREADS);
+      lc.dynamicSmemBytes = PCL_SMEM;
+      lc.stream = s;
+      la[0].id = cudaLaunchAttributeClusterDimension;
+      la[0].val.clusterDim.x = (unsigned)C; la[0].val.clusterDim.y = 1; la[0].val.clusterDim.z = 1;
+      lc.attrs = la; lc.numAttrs = 1;
+    }
+    cudaEvent_t lev_e0 = nullptr, lev_e1 = nullptr;
+    if (level_times) {
+      cudaEventCreate(&lev_e0); cudaEventCreate(&lev_e1);
+      cudaEventRecord(lev_e0, s);
+    }
     for (int p = 0; p < npan; ++p) {
-      HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag, (int32_t*)c->d_pos0.p, nb, c->tau));
+      if (use_cl)
+        HF_LAUNCH(c, HF_PROF_PANEL, HF_CUDA_TRY(cudaLaunchKernelEx(&lc, k_panel_cl<T>, nd, st, t0, arena, rowid, gmag,
+                                                                   (int32_t*)c->d_pos0.p, nbl, c->tau, C, Rcap)));
+      if (use_gl)
+        HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag,
+                                                                           (int32_t*)c->d_pos0.p, nbl, c->tau, cap));
       HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena));
+    }
+    if (level_times) {
+      float ms = 0;
+      cudaEventRecord(lev_e1, s);
+      cudaEventSynchronize(lev_e1);
+      cudaEventElapsedTime(&ms, lev_e0, lev_e1);
+      std::fprintf(stderr, "level %d: fronts %d max n %d max ld %d cluster %d (cap %d) global %d panels %d: %.3f ms\n",
+                   lev, cnt, maxn, maxld, use_cl ? C : 0, cap, use_gl ? 1 : 0, npan, ms);
+      cudaEventDestroy(lev_e0); cudaEventDestroy(lev_e1);
     }
     HF_CUDA_TRY(cudaGetLastError());
   }
@@ -581,6 +975,19 @@ static void trailing_work(hf_ctx* c, size_t esz) {
   }
   c->work_flops[HF_PROF_TRAILING] += fl;
   c->work_bytes[HF_PROF_TRAILING] += by;
+  // panels: column k of a panel costs 2 (f - k) (k - k0) for the left-looking products plus
+  // 3 (f - k) for the division, diagonal and magnitude updates; the panel block is read and
+  // written once
+  double pf = 0, pb = 0;
+  for (const NodeState& S : c->state_host) {
+    for (double k = 0; k < S.k; k += 1) {
+      const double kk = std::fmod(k, nb), rows = S.f - k;
+      pf += 2.0 * rows * kk + 3.0 * rows;
+      if (kk == 0) pb += 2.0 * rows * std::min(nb, (double)S.k - k) * esz;
+    }
+  }
+  c->work_flops[HF_PROF_PANEL] += pf;
+  c->work_bytes[HF_PROF_PANEL] += pb;
 }
 
 }  // namespace
