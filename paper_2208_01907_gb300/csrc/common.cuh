@@ -39,3 +39,13 @@ template <typename T> __device__ __forceinline__ double piv_key(T x) {
 __device__ __forceinline__ bool better(double ka, int ia, double kb, int ib) {
   return ka > kb || (ka == kb && ia < ib);
 }
+
+// The same key and order in the factor's own type: |x| of an FP32 value is exact in FP32,
+// so comparisons agree with the FP64 ones while staying off GB300's narrow FP64 pipe.
+template <typename T> __device__ __forceinline__ T piv_key_t(T x) {
+  const T a = fabs(x);
+  return (a == a) ? a : T(-1);
+}
+template <typename T> __device__ __forceinline__ bool better_t(T ka, int ia, T kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}

@@ -207,7 +207,7 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
                         T* __restrict__ arena, int32_t* __restrict__ rowid, T* __restrict__ Gall,
                         int32_t* __restrict__ pos0all, int nb, double tau, int cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_k[32];
+  __shared__ T red_k[32];
   __shared__ int red_i[32], red_p[32];
   __shared__ int s_q, s_act;
   const int t = t0 + blockIdx.x;
@@ -241,29 +241,29 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
   __syncthreads();
   while (k < k0 + nb && k < nact) {
     // 1. argmax |dg| over the active candidates, ties to the smaller original index (R5)
-    double bk = -2.0;
+    T bk = T(-2);
     int bi = 0x7fffffff, bp = -1;
     for (int i = k + tid; i < nact; i += nt) {
-      double kk = piv_key(dg[i]);
-      if (better(kk, sid[i], bk, bi)) { bk = kk; bi = sid[i]; bp = i; }
+      const T kk = piv_key_t(dg[i]);
+      if (better_t(kk, sid[i], bk, bi)) { bk = kk; bi = sid[i]; bp = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      T ok = __shfl_xor_sync(0xffffffffu, bk, o);
       int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (better(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
+      if (better_t(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
     }
     if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; red_p[tid >> 5] = bp; }
     __syncthreads();
     if (tid == 0) {
       for (int wv = 1; wv < (nt + 31) / 32; ++wv)
-        if (better(red_k[wv], red_i[wv], bk, bi)) { bk = red_k[wv]; bi = red_i[wv]; bp = red_p[wv]; }
+        if (better_t(red_k[wv], red_i[wv], bk, bi)) { bk = red_k[wv]; bi = red_i[wv]; bp = red_p[wv]; }
       // ratio test |d_{i+1} / d_i| < tau stops the set (R2/R3; NaN fails it);
       // the null-pivot test |d| < tau * G postpones this candidate alone (R3b)
       int act = 0;
-      if (!(bk >= tau * dref)) act = 1;
-      else if (!(bk >= tau * (double)G[bp])) act = 2;
+      if (!((double)bk >= tau * dref)) act = 1;
+      else if (!((double)bk >= tau * (double)G[bp])) act = 2;
       s_act = act;
       s_q = bp;
     }
@@ -318,7 +318,7 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
       if (i < nact) dg[i] -= l * c;
       G[i] += fabs(l * c);
     }
-    dref = fabs((double)dk);
+    if (tid == 0) dref = fabs((double)dk);     // used by the deciding thread only
     ++k;
     __syncthreads();
   }
@@ -348,8 +348,25 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
 // The arithmetic per element is that of k_panel, in the same order.  A front larger
 // than C * Rcap rows is left to k_panel (which skips the fronts handled here).
 // ---------------------------------------------------------------------------
+// acc - sum_{c < n} a[c] * b[c], accumulated in order c = 0, 1, ...; the shared-memory
+// loads are issued eight at a time so that their latency overlaps
+template <typename T>
+__device__ __forceinline__ T dot_sub_seq(T acc, const T* __restrict__ a, const T* __restrict__ b, int n) {
+  int c = 0;
+  for (; c + 8 <= n; c += 8) {
+    T x[8], y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { x[u] = a[c + u]; y[u] = b[c + u]; }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc -= x[u] * y[u];
+  }
+  for (; c < n; ++c) acc -= a[c] * b[c];
+  return acc;
+}
+
 constexpr int PCL_THREADS = 512;
-constexpr int PCL_CMAX = 8;
+constexpr int PCL_RPT = 2;                    // rows per thread: Rcap <= PCL_RPT * PCL_THREADS
+constexpr int PCL_CMAX = 16;
 constexpr int PCL_SLOTS = PCL_CMAX + 2;       // candidates of C CTAs, row k, row nact-1
 
 template <typename T> struct PclLayout {
@@ -371,10 +388,10 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_k[32];
+  __shared__ T red_k[32];
   __shared__ int red_i[32], red_p[32];
-  __shared__ int s_act, s_q, s_w;
-  __shared__ T s_dk;
+  __shared__ T s_bk;
+  __shared__ int s_bp, s_act, s_w;
   const int rank = (int)cl.block_rank();
   const int t = t0 + (int)(blockIdx.x / (unsigned)C);
   const NodeDesc d = nd[t];
@@ -405,7 +422,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   T* pG = prow + 2 * PCL_SLOTS * nb;           // [2][SLOTS]
   T* pdiag = pG + 2 * PCL_SLOTS;
   T* pdg = pdiag + 2 * PCL_SLOTS;
-  double* pkey = (double*)(((uintptr_t)(pdg + 2 * PCL_SLOTS) + 7) & ~(uintptr_t)7);   // [2][SLOTS]
+  T* pkey = pdg + 2 * PCL_SLOTS;               // [2][SLOTS]
   int* psid = (int*)(pkey + 2 * PCL_SLOTS);    // [2][SLOTS]
   int* ppos = psid + 2 * PCL_SLOTS;
   int* prid = ppos + 2 * PCL_SLOTS;
@@ -432,7 +449,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   int it = 0;
   cl.sync();
   // push the row at own position p into slot `slot` of buffer `buf` of every CTA
-  auto push_row = [&](int buf, int slot, int p, double key, int kk) {
+  auto push_row = [&](int buf, int slot, int p, T key, int kk) {
     const int l = p - p0;
     const int base = buf * PCL_SLOTS + slot;
     for (int e = tid; e < C * kk; e += nt) {
@@ -451,63 +468,79 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       cl.map_shared_rank(pdg, r)[base] = dgl[l];
     }
   };
+  // rows are owned by fixed threads: position p belongs to thread (p - p0) % nt, so the
+  // column updates of one pivot and the argmax of the next touch only the thread's rows
   while (k < k0 + nb && k < nact) {
     const int buf = it & 1;
     const int kk = k - k0;
-    // 1. local argmax over the own candidates [k, nact), ties to the smaller original index (R5)
-    double bk = -2.0;
+    // 1. argmax over the own candidates [k, nact), ties to the smaller original index (R5)
+    T bk = T(-2);
     int bi = 0x7fffffff, bp = -1;
-    for (int p = max(k, p0) + tid; p < min(nact, p1); p += nt) {
-      const double kv = piv_key(dgl[p - p0]);
-      const int si = sidl[p - p0];
-      if (better(kv, si, bk, bi)) { bk = kv; bi = si; bp = p; }
+#pragma unroll
+    for (int j = 0; j < PCL_RPT; ++j) {
+      const int p = p0 + tid + j * nt;
+      if (p >= k && p < nact && p < p1) {
+        const T kv = piv_key_t(dgl[p - p0]);
+        const int si = sidl[p - p0];
+        if (better_t(kv, si, bk, bi)) { bk = kv; bi = si; bp = p; }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ok = __shfl_xor_sync(0xffffffffu, bk, o);
+      T ok = __shfl_xor_sync(0xffffffffu, bk, o);
       int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (better(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
+      if (better_t(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
     }
     if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; red_p[tid >> 5] = bp; }
     __syncthreads();
-    if (tid == 0) {
-      for (int w2 = 1; w2 < (nt + 31) / 32; ++w2)
-        if (better(red_k[w2], red_i[w2], bk, bi)) { bk = red_k[w2]; bi = red_i[w2]; bp = red_p[w2]; }
-      red_k[0] = bk; red_i[0] = bi; red_p[0] = bp;
+    if (tid < 32) {
+      const int nw = (nt + 31) / 32;
+      bk = tid < nw ? red_k[tid] : T(-2);
+      bi = tid < nw ? red_i[tid] : 0x7fffffff;
+      bp = tid < nw ? red_p[tid] : -1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        T ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (better_t(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
+      }
+      if (tid == 0) { s_bk = bk; s_bp = bp; }
     }
     __syncthreads();
     // 2. pushes: own candidate, and rows k / nact-1 by their owners
     {
-      const int pbest = red_p[0];
+      const int pbest = s_bp;
       const int base = buf * PCL_SLOTS + rank;
       if (pbest >= 0) {
-        push_row(buf, rank, pbest, red_k[0], kk);
+        push_row(buf, rank, pbest, s_bk, kk);
       } else if (tid < C) {
-        cl.map_shared_rank(pkey, tid)[base] = -2.0;
+        cl.map_shared_rank(pkey, tid)[base] = T(-2);
         cl.map_shared_rank(psid, tid)[base] = 0x7fffffff;
         cl.map_shared_rank(ppos, tid)[base] = -1;
       }
-      if (owner(k) == rank) push_row(buf, PCL_CMAX, k, 0.0, kk);
-      if (owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, 0.0, kk);
+      if (owner(k) == rank) push_row(buf, PCL_CMAX, k, T(0), kk);
+      if (owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, T(0), kk);
     }
-    cl.sync();                                                             // the only cluster barrier
-    // 3. the decision, identical in every CTA
+    if (C > 1) cl.sync(); else __syncthreads();                            // the only cluster barrier
+    // 3. the decision from the local slots (the same in every CTA): one thread, so that the
+    // two FP64 threshold tests do not occupy the FP64 pipe for the whole block
     const int sb = buf * PCL_SLOTS;
     if (tid == 0) {
-      double gk = -2.0;
+      T gk = T(-2);
       int gi = 0x7fffffff, gw = -1;
       for (int r = 0; r < C; ++r)
-        if (ppos[sb + r] >= 0 && better(pkey[sb + r], psid[sb + r], gk, gi)) { gk = pkey[sb + r]; gi = psid[sb + r]; gw = r; }
-      int act = 0;
-      if (!(gk >= tau * dref)) act = 1;                                          // ratio test (R2/R3)
-      else if (!(gk >= tau * (double)pG[sb + gw])) act = 2;                     // null pivot (R3b)
-      s_act = act;
+        if (ppos[sb + r] >= 0 && better_t(pkey[sb + r], psid[sb + r], gk, gi)) { gk = pkey[sb + r]; gi = psid[sb + r]; gw = r; }
+      int a2 = 0;
+      if (!((double)gk >= tau * dref)) a2 = 1;                                   // ratio test (R2/R3)
+      else if (!((double)gk >= tau * (double)pG[sb + gw])) a2 = 2;              // null pivot (R3b)
+      s_act = a2;
       s_w = gw;
-      s_q = gw >= 0 ? ppos[sb + gw] : -1;
     }
     __syncthreads();
-    const int act = s_act, q = s_q, wsl = sb + s_w;
+    const int act = s_act, wsl = sb + s_w;
+    const int q = s_w >= 0 ? ppos[wsl] : -1;
     if (act == 1) { stopped = true; break; }
     if (act == 2) {
       // 4a. postpone the null candidate: swap q <-> b = nact-1 (both candidates)
@@ -541,12 +574,14 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
           }
         }
         // middle (j in (q, b): (j, q) <-> (b, j)) and lower (i > b: (i, q) <-> (i, b)) parts by row owners
-        for (int p = max(q + 1, p0) + tid; p < p1; p += nt) {
-          if (p == b) continue;
-          int64_t x, y;
-          if (p < b) { x = p + (int64_t)q * ld; y = b + (int64_t)p * ld; }
-          else { x = p + (int64_t)q * ld; y = p + (int64_t)b * ld; }
-          const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+#pragma unroll
+        for (int j = 0; j < PCL_RPT; ++j) {
+          const int p = p0 + tid + j * nt;
+          if (p > q && p < p1 && p != b) {
+            const int64_t x = p + (int64_t)q * ld;
+            const int64_t y = p < b ? b + (int64_t)p * ld : p + (int64_t)b * ld;
+            const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+          }
         }
       }
       --nact;
@@ -554,12 +589,11 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       __syncthreads();
       continue;
     }
-    // 4b. pivot q -> position k.  w from the winner's row; d_k computed locally
+    // 4b. pivot q -> position k: w from the winner's row, new contents of positions k and q
     const T* rq = prow + (size_t)wsl * nb;
     const int ksl = sb + PCL_CMAX;
     const T* rk = prow + (size_t)ksl * nb;
     for (int c = tid; c < kk; c += nt) wv[c] = dpiv[c] * rq[c];
-    // new contents of positions k and q (own rows only)
     if (owner(k) == rank) {
       const int l = k - p0;
       for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rq[c];
@@ -576,63 +610,60 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       }
     }
     __syncthreads();
-    // 5. warp 0: d_k (every CTA, the owner's operations); warps 1..: rows k and q over the
-    // earlier panels' columns [0, k0) (spread over the cluster, not read again in this
-    // panel), and column k of the own rows with the swap fused into its load
-    if (tid < 32) {
-      if (tid == 0) {
-        T acc = pdiag[wsl];
-        for (int c = 0; c < kk; ++c) acc -= rq[c] * wv[c];
-        s_dk = acc;
-      }
-    } else {
-      const int t2 = tid - 32, n2 = nt - 32;
-      if (q != k)
-        for (int j = rank * n2 + t2; j < k0; j += C * n2) {
-          const int64_t x = k + (int64_t)j * ld, y = q + (int64_t)j * ld;
-          const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
-        }
-      for (int p = max(k + 1, p0) + t2; p < p1; p += n2) {
-        T v;
+    // 5. loads first: rows k and q over the earlier panels' columns [0, k0) (spread over the
+    // cluster; not read again in this panel) and the new column k of the own rows (swap fused)
+    T v[PCL_RPT];
+    int64_t wy[PCL_RPT];
+    T wx[PCL_RPT];
+#pragma unroll
+    for (int j = 0; j < PCL_RPT; ++j) {
+      const int p = p0 + tid + j * nt;
+      wy[j] = -1;
+      v[j] = T(0);
+      if (p > k && p < p1) {
         if (q == k) {
-          v = F[p + (int64_t)k * ld];
-        } else if (p > q) {
-          const int64_t x = p + (int64_t)k * ld, y = p + (int64_t)q * ld;
-          v = F[y];
-          F[y] = F[x];
-        } else if (p < q) {
-          const int64_t x = p + (int64_t)k * ld, y = q + (int64_t)p * ld;
-          v = F[y];
-          F[y] = F[x];
+          v[j] = F[p + (int64_t)k * ld];
+        } else if (p != q) {
+          const int64_t x = p + (int64_t)k * ld;
+          wy[j] = p > q ? p + (int64_t)q * ld : q + (int64_t)p * ld;
+          v[j] = F[wy[j]];
+          wx[j] = F[x];
         } else {
-          v = F[q + (int64_t)k * ld];
+          v[j] = F[q + (int64_t)k * ld];
         }
-        T* Pr = P + (size_t)(p - p0) * ps;
-        T acc = v;
-        for (int c = 0; c < kk; ++c) acc -= Pr[c] * wv[c];
-        Pr[kk] = acc;
       }
     }
-    __syncthreads();
-    // 6. L(i, k) = c_i / d_k, the candidates' diagonals and the term magnitudes
-    const T dk = s_dk;
-    if (owner(k) == rank && tid == 0) P[(size_t)(k - p0) * ps + kk] = dk;
-    for (int p = max(k + 1, p0) + tid; p < p1; p += nt) {
-      const int l = p - p0;
-      T* e = P + (size_t)l * ps + kk;
-      const T acc = *e;
-      const T lv = acc / dk;
-      *e = lv;
-      if (p < nact) dgl[l] -= lv * acc;
-      Gl[l] += fabs(lv * acc);
+    if (q != k)
+      for (int j = rank * nt + tid; j < k0; j += C * nt) {
+        const int64_t x = k + (int64_t)j * ld, y = q + (int64_t)j * ld;
+        const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
+      }
+    // d_k by every thread: the owner's operations on the winner's row
+    const T dk = dot_sub_seq(pdiag[wsl], rq, wv, kk);
+    // 6. c_i = A(i, k) - sum_c L(i, c) w_c; L(i, k) = c_i / d_k; diagonals and magnitudes
+#pragma unroll
+    for (int j = 0; j < PCL_RPT; ++j) {
+      const int p = p0 + tid + j * nt;
+      if (p > k && p < p1) {
+        if (wy[j] >= 0) F[wy[j]] = wx[j];
+        const int l = p - p0;
+        T* Pr = P + (size_t)l * ps;
+        const T acc = dot_sub_seq(v[j], Pr, wv, kk);
+        const T lv = acc / dk;
+        Pr[kk] = lv;
+        if (p < nact) dgl[l] -= lv * acc;
+        Gl[l] += fabs(lv * acc);
+      } else if (p == k) {
+        P[(size_t)(k - p0) * ps + kk] = dk;
+      }
     }
     if (tid == 0) dpiv[kk] = dk;
-    dref = fabs((double)dk);
+    if (tid == 0) dref = fabs((double)dk);     // used by the deciding thread only
     ++k;
     ++it;
-    __syncthreads();
   }
   // write back: computed panel columns (lower part), diagonals of the unpivoted rows, row data
+  __syncthreads();
   const int kdone = k - k0;
   for (int c = 0; c < kdone; ++c)
     for (int p = max(p0, k0 + c) + tid; p < p1; p += nt)
@@ -848,8 +879,10 @@ int run_levels(hf_ctx* c) {
   if (!attr_set[sizeof(T) == 8]) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCL_SMEM));
-    // largest cluster (<= 8) that can be resident with the full shared-memory panel
-    for (int cs = 8; cs >= 1; cs /= 2) {
+    if (cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      (void)cudaGetLastError();
+    // largest cluster (<= 16) that can be resident with the full shared-memory panel
+    for (int cs = PCL_CMAX; cs >= 1; cs /= 2) {
       cudaLaunchConfig_t q = {};
       q.gridDim = dim3(cs);
       q.blockDim = dim3(PCL_THREADS);
@@ -911,7 +944,7 @@ int run_levels(hf_ctx* c) {
     const int nbc = sizeof(T) == 8 ? std::min(nb, 32) : nb;
     const size_t per_row = (size_t)(nbc + 1) * sizeof(T) + 3 * sizeof(T) + 3 * sizeof(int);
     const size_t fixed = PclLayout<T>::bytes(0, nbc);
-    const int Rcap = (int)((PCL_SMEM - fixed) / per_row);
+    const int Rcap = std::min((int)((PCL_SMEM - fixed) / per_row), PCL_RPT * PCL_THREADS);
     const int C = std::max(1, std::min(cmax, (maxld + Rcap - 1) / Rcap));
     const bool use_cl = cmax > 0 && maxld > 0 && !panel_global;
     const int cap = use_cl ? C * Rcap : -1;
