@@ -117,18 +117,22 @@ __global__ void k_bwd_store(const NodeDesc* __restrict__ nd, const NodeState* __
 }
 
 // Diagonal block solve of block step b: forward (unit L, columns [b*TS, ...)) or
-// backward (unit L^T, blocks counted from ksolve down).  One thread per rhs; the
-// block of L and the rhs columns are staged in shared memory.
-template <typename TV> struct TrsmThreads { static constexpr int value = sizeof(TV) == 8 ? 32 : 64; };
+// backward (unit L^T, blocks counted from ksolve down), for a tile of DR right-hand
+// sides.  The block of L and the right-hand sides are staged in shared memory; the
+// block is processed in sub-blocks of DSB rows: a sub-block is solved by one thread
+// per right-hand side in registers, then the rows after it (before it, backward) are
+// updated by all threads.
+template <typename TV> struct DiagRhs { static constexpr int value = sizeof(TV) == 8 ? 16 : 64; };  // rhs per CTA
+constexpr int DSB = 16;      // sub-block rows
+constexpr int DTH = 256;     // threads
 
 template <typename TF, typename TV, bool FWD>
-__global__ void __launch_bounds__(TrsmThreads<TV>::value) k_trsm_diag(const NodeDesc* __restrict__ nd,
-                                                                        const NodeState* __restrict__ st, int t0,
-                                                                        const TF* __restrict__ arena,
-                                                                        TV* __restrict__ vec, int m, int b) {
-  constexpr int NT = TrsmThreads<TV>::value;
-  __shared__ TF Ls[TS][TS];
-  __shared__ TV Vs[TS][NT];
+__global__ void __launch_bounds__(DTH) k_trsm_diag(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                  int t0, const TF* __restrict__ arena, TV* __restrict__ vec, int m,
+                                                  int b) {
+  constexpr int DR = DiagRhs<TV>::value;
+  __shared__ TV Ls[TS][TS + 1];
+  __shared__ TV Vs[TS][DR + 1];
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const int ks = st[t].ksolve;
@@ -137,39 +141,84 @@ __global__ void __launch_bounds__(TrsmThreads<TV>::value) k_trsm_diag(const Node
   else { int j1 = ks - b * TS; if (j1 <= 0) return; j0 = max(0, j1 - TS); jb = j1 - j0; }
   const TF* F = arena + d.front_off;
   const int64_t ld = d.ld;
-  for (int e = threadIdx.x; e < TS * TS; e += NT) {
-    int r = e % TS, c = e / TS;
-    Ls[r][c] = (r < jb && c < jb && r > c) ? F[(j0 + r) + (int64_t)(j0 + c) * ld] : TF(0);
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * DR;
+  for (int e = tid; e < TS * TS; e += DTH) {
+    const int r = e % TS, c = e / TS;                     // r fastest: contiguous in column c of F
+    Ls[r][c] = (r < jb && c < jb && r > c) ? (TV)F[(j0 + r) + (int64_t)(j0 + c) * ld] : TV(0);
   }
-  const int tx = threadIdx.x;
-  const int c = blockIdx.x * NT + tx;
-  TV* V = vec + (d.row_off + j0) * m + c;
-  for (int r = 0; r < jb; ++r) Vs[r][tx] = (c < m) ? V[(int64_t)r * m] : TV(0);
+  TV* V = vec + (d.row_off + j0) * m;
+  for (int e = tid; e < TS * DR; e += DTH) {
+    const int r = e / DR, c = e % DR;
+    Vs[r][c] = (r < jb && c0 + c < m) ? V[(int64_t)r * m + c0 + c] : TV(0);
+  }
   __syncthreads();
-  if (FWD) {
-    for (int r = 1; r < jb; ++r) {
-      TV acc = Vs[r][tx];
-      for (int q = 0; q < r; ++q) acc -= (TV)Ls[r][q] * Vs[q][tx];
-      Vs[r][tx] = acc;
+  const int nsb = (jb + DSB - 1) / DSB;
+  for (int sbi = 0; sbi < nsb; ++sbi) {
+    const int s = FWD ? sbi : nsb - 1 - sbi;             // sub-block index
+    const int r0 = s * DSB, r1 = min(jb, r0 + DSB);
+    if (tid < DR) {
+      TV x[DSB];
+#pragma unroll
+      for (int i = 0; i < DSB; ++i) x[i] = (r0 + i < r1) ? Vs[r0 + i][tid] : TV(0);
+      if (FWD) {
+#pragma unroll
+        for (int i = 1; i < DSB; ++i)
+#pragma unroll
+          for (int q = 0; q < i; ++q) x[i] -= Ls[r0 + i][r0 + q] * x[q];
+      } else {
+#pragma unroll
+        for (int i = DSB - 2; i >= 0; --i)
+#pragma unroll
+          for (int q = i + 1; q < DSB; ++q) x[i] -= Ls[r0 + q][r0 + i] * x[q];
+      }
+#pragma unroll
+      for (int i = 0; i < DSB; ++i)
+        if (r0 + i < r1) Vs[r0 + i][tid] = x[i];
     }
-  } else {
-    for (int r = jb - 2; r >= 0; --r) {
-      TV acc = Vs[r][tx];
-      for (int q = r + 1; q < jb; ++q) acc -= (TV)Ls[q][r] * Vs[q][tx];
-      Vs[r][tx] = acc;
+    __syncthreads();
+    // rows after (forward) / before (backward) the sub-block
+    const int u0 = FWD ? r1 : 0, u1 = FWD ? jb : r0;
+    for (int e = tid; e < (u1 - u0) * DR; e += DTH) {
+      const int r = u0 + e / DR, c = e % DR;
+      TV acc = Vs[r][c];
+      if (FWD) {
+#pragma unroll
+        for (int q = 0; q < DSB; ++q)
+          if (r0 + q < r1) acc -= Ls[r][r0 + q] * Vs[r0 + q][c];
+      } else {
+#pragma unroll
+        for (int q = 0; q < DSB; ++q)
+          if (r0 + q < r1) acc -= Ls[r0 + q][r] * Vs[r0 + q][c];
+      }
+      Vs[r][c] = acc;
     }
+    __syncthreads();
   }
-  if (c < m)
-    for (int r = 0; r < jb; ++r) V[(int64_t)r * m] = Vs[r][tx];
+  for (int e = tid; e < jb * DR; e += DTH) {
+    const int r = e / DR, c = e % DR;
+    if (c0 + c < m) V[(int64_t)r * m + c0 + c] = Vs[r][c];
+  }
 }
 
 // GEMM update C -= A B on the front vectors of a level.
 //  MODE 0 (forward, block step b):  rows [j0+jb, f),  A(i,q) = L(i, j0+q),  B = V rows [j0, j0+jb)
 //  MODE 1 (backward, block step b): rows [0, j0),     A(i,q) = L(j0+q, i),  B = V rows [j0, j1)
 //  MODE 2 (backward start):         rows [0, ks),     A(i,q) = L(ks+q, i),  B = V rows [ks, f)
+// CTA tile SGR rows x SGC right-hand sides, 128 threads with 8 x 8 outputs each; the k
+// chunks are double-buffered (the next chunk is loaded into registers while the
+// current one is multiplied from shared memory).
+constexpr int SGR = 128;      // rows per CTA
+constexpr int SGC = 64;       // right-hand sides per CTA
+constexpr int SGTH = 128;     // threads
+template <typename TV> struct GemmK { static constexpr int value = sizeof(TV) == 8 ? 8 : 16; };
+
 template <typename TF, typename TV, int MODE>
-__global__ void __launch_bounds__(256) k_gemm_upd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+__global__ void __launch_bounds__(SGTH) k_gemm_upd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
                                                   int t0, const TF* __restrict__ arena, TV* __restrict__ vec, int m, int b) {
+  constexpr int GK = GemmK<TV>::value;
+  constexpr int AL = GK * SGR / SGTH;          // A elements per thread per chunk
+  constexpr int BL = GK * SGC / SGTH;          // B elements per thread per chunk
   const int t = t0 + blockIdx.z;
   const NodeDesc d = nd[t];
   const int ks = st[t].ksolve, f = st[t].f;
@@ -177,57 +226,85 @@ __global__ void __launch_bounds__(256) k_gemm_upd(const NodeDesc* __restrict__ n
   if (MODE == 0) { int j0 = b * TS; if (j0 >= ks) return; int jb = min(TS, ks - j0); r_lo = j0 + jb; r_hi = f; k_lo = j0; k_hi = j0 + jb; }
   else if (MODE == 1) { int j1 = ks - b * TS; if (j1 <= 0) return; int j0 = max(0, j1 - TS); r_lo = 0; r_hi = j0; k_lo = j0; k_hi = j1; }
   else { r_lo = 0; r_hi = ks; k_lo = ks; k_hi = f; }
-  const int r0 = r_lo + blockIdx.x * TS;
-  const int c0 = blockIdx.y * TR;
+  const int r0 = r_lo + blockIdx.x * SGR;
+  const int c0 = blockIdx.y * SGC;
   if (r0 >= r_hi || c0 >= m || k_hi <= k_lo) return;
   const TF* F = arena + d.front_off;
   const int64_t ld = d.ld;
   TV* V = vec + d.row_off * m;
-  __shared__ TV As[TKK][TS + 1];
-  __shared__ TV Bs[TKK][TR + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  TV acc[4][4];
+  __shared__ __align__(16) TV As[2][GK][SGR + 4];
+  __shared__ __align__(16) TV Bs[2][GK][SGC + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 7, ty = tid >> 3;     // 8 rhs groups x 16 row groups
+  TV pa[AL], pb[BL];
+  auto load = [&](int kc) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = TV(0);
-  for (int kc = k_lo; kc < k_hi; kc += TKK) {
-    for (int e = threadIdx.x; e < TKK * TS; e += 256) {
+    for (int u = 0; u < AL; ++u) {
       int kk, rr;
-      if (MODE == 0) { kk = e / TS; rr = e % TS; }      // rows contiguous in column k
-      else { rr = e / TKK; kk = e % TKK; }               // k contiguous in column i
-      int q = kc + kk, i = r0 + rr;
+      if (MODE == 0) { const int e = tid + u * SGTH; kk = e / SGR; rr = e % SGR; }   // rows contiguous in column q
+      else { rr = tid; kk = u; }                                                 // k contiguous in column i
+      const int q = kc + kk, i = r0 + rr;
       TV a = TV(0);
       if (q < k_hi && i < r_hi) a = (TV)(MODE == 0 ? F[i + (int64_t)q * ld] : F[q + (int64_t)i * ld]);
-      As[kk][rr] = a;
+      pa[u] = a;
     }
-    for (int e = threadIdx.x; e < TKK * TR; e += 256) {
-      int kk = e / TR, cc = e % TR;
-      int q = kc + kk, c = c0 + cc;
-      Bs[kk][cc] = (q < k_hi && c < m) ? V[(int64_t)q * m + c] : TV(0);
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int e = tid + u * SGTH;
+      const int kk = e / SGC, cc = e % SGC;
+      const int q = kc + kk, c = c0 + cc;
+      pb[u] = (q < k_hi && c < m) ? V[(int64_t)q * m + c] : TV(0);
     }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < AL; ++u) {
+      int kk, rr;
+      if (MODE == 0) { const int e = tid + u * SGTH; kk = e / SGR; rr = e % SGR; }
+      else { rr = tid; kk = u; }
+      As[buf][kk][rr] = pa[u];
+    }
+#pragma unroll
+    for (int u = 0; u < BL; ++u) {
+      const int e = tid + u * SGTH;
+      Bs[buf][e / SGC][e % SGC] = pb[u];
+    }
+  };
+  TV acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = TV(0);
+  load(k_lo);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int kc = k_lo; kc < k_hi; kc += GK) {
+    const bool more = kc + GK < k_hi;
+    if (more) load(kc + GK);
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      TV av[8], bv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) av[i] = As[buf][kk][ty * 8 + i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) bv[j] = Bs[buf][kk][tx * 8 + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    if (more) store(buf ^ 1);
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < TKK; ++kk) {
-      TV av[4], bv[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
-    }
-    __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int r = r0 + ty + 16 * i;
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + ty * 8 + i;
     if (r >= r_hi) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int c = c0 + tx + 16 * j;
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + tx * 8 + j;
       if (c < m) V[(int64_t)r * m + c] -= acc[i][j];
     }
   }
@@ -799,9 +876,32 @@ static int ensure_vec(hf_ctx* c, int m, size_t esz) {
   return hf_ensure(c->d_vec, need);
 }
 
-// Apply the triangular solves with the front factor (TF) in vector precision TV.
-//  mode 0: K11 preconditioner (Lambda_2 rows are zero in and out)
-//  mode 1: full solve with S22 handled by the BK factors (non-mixed forms)
+// HF_LEVEL_TIMES=1: device time of every level of the sweeps (diagnostic)
+struct SweepTimer {
+  cudaStream_t s;
+  const char* name;
+  int m;
+  bool on;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SweepTimer(cudaStream_t st, const char* nm, int mm) : s(st), name(nm), m(mm) {
+    const char* v = std::getenv("HF_LEVEL_TIMES");
+    on = v && v[0] == '1';
+    if (on) { cudaEventCreate(&e0); cudaEventCreate(&e1); }
+  }
+  ~SweepTimer() { if (on) { cudaEventDestroy(e0); cudaEventDestroy(e1); } }
+  void begin() { if (on) cudaEventRecord(e0, s); }
+  void end(int lev, int cnt, int maxf, int maxks) {
+    if (!on) return;
+    float ms = 0;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    std::fprintf(stderr, "sweep %s m %d level %d: fronts %d max f %d max ks %d: %.3f ms\n", name, m, lev, cnt, maxf,
+                 maxks, ms);
+  }
+};
+
+// Largest front order, solved columns and contribution block of a level (host state)
 struct LevelDims {
   int maxf = 0, maxks = 0, maxcb = 0;
 };
@@ -835,10 +935,12 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
   const TF* arena = (const TF*)c->d_front.p;
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
   const int32_t* cbmap = (const int32_t*)c->d_cbmap.p;
-  const unsigned rt = (unsigned)((m + TR - 1) / TR);
+  const unsigned gt = (unsigned)((m + SGC - 1) / SGC);
+  SweepTimer tm(s, "fwd", m);
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
     const LevelDims D = level_dims(c, lev);
+    tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
     HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m));
     if (D.maxcb > 0) {
@@ -848,12 +950,13 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
     }
     const int nbk = (D.maxks + TS - 1) / TS;
     for (int b = 0; b < nbk; ++b) {
-      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_trsm_diag<TF, TV, true><<<dim3((m + TrsmThreads<TV>::value - 1) / TrsmThreads<TV>::value, cnt), TrsmThreads<TV>::value, 0, s>>>(nd, st, t0, arena, vec, m, b));
-      const unsigned rx = (unsigned)((D.maxf - b * TS + TS - 1) / TS);
+      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_trsm_diag<TF, TV, true><<<dim3((m + DiagRhs<TV>::value - 1) / DiagRhs<TV>::value, cnt), DTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
+      const unsigned rx = (unsigned)((D.maxf - b * TS + SGR - 1) / SGR);
       if (rx > 0)
-        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0><<<dim3(rx, rt, cnt), 256, 0, s>>>(nd, st, t0, arena, vec, m, b));
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
     HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m));
+    tm.end(lev, cnt, D.maxf, D.maxks);
   }
 }
 
@@ -865,22 +968,25 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
   const NodeState* st = (const NodeState*)c->d_state.p;
   const TF* arena = (const TF*)c->d_front.p;
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
-  const unsigned rt = (unsigned)((m + TR - 1) / TR);
+  const unsigned gt = (unsigned)((m + SGC - 1) / SGC);
+  SweepTimer tm(s, "bwd", m);
   for (int lev = 0; lev <= c->m; ++lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
     const LevelDims D = level_dims(c, lev);
     if (D.maxks == 0) continue;
+    tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
     HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m));
-    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 2><<<dim3((D.maxks + TS - 1) / TS, rt, cnt), 256, 0, s>>>(nd, st, t0, arena, vec, m, 0));
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 2><<<dim3((D.maxks + SGR - 1) / SGR, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, 0));
     const int nbk = (D.maxks + TS - 1) / TS;
     for (int b = 0; b < nbk; ++b) {
-      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_trsm_diag<TF, TV, false><<<dim3((m + TrsmThreads<TV>::value - 1) / TrsmThreads<TV>::value, cnt), TrsmThreads<TV>::value, 0, s>>>(nd, st, t0, arena, vec, m, b));
-      const unsigned rx = (unsigned)((D.maxks - (b + 1) * TS + TS - 1) / TS);
+      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_trsm_diag<TF, TV, false><<<dim3((m + DiagRhs<TV>::value - 1) / DiagRhs<TV>::value, cnt), DTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
+      const unsigned rx = (unsigned)((D.maxks - (b + 1) * TS + SGR - 1) / SGR);
       if ((int)rx > 0)
-        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1><<<dim3(rx, rt, cnt), 256, 0, s>>>(nd, st, t0, arena, vec, m, b));
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
     HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m));
+    tm.end(lev, cnt, D.maxf, D.maxks);
   }
 }
 
