@@ -304,6 +304,28 @@ int hf_profile(hf_ctx* ctx, int enable);
 int hf_get_profile(hf_ctx* ctx, double* ms, int64_t* launches, double* flops, double* bytes);
 const char* hf_profile_name(int cls);
 
+/*
+ * Batched form: the same step on n independent systems (distinct contexts, each from its
+ * own hf_analyze), run concurrently.  A pool of host worker threads takes the contexts
+ * in order; a context created with cuda_stream = NULL runs on the worker's own
+ * non-blocking stream for the duration of the call, otherwise on its own stream.  Every
+ * context's work is complete when the call returns.  The per-system semantics are those
+ * of hf_factorize / hf_schur / hf_solve on the same context (Alg. 1 and 2 per system,
+ * each with its own tau and its own Lambda_2); systems do not interact.
+ *   ctxs      n distinct contexts
+ *   vals_dev  n device pointers (K values of system i, CSR order of its pattern)
+ *   b_dev, x_dev  n device pointers: right-hand sides / solutions (as hf_solve), with
+ *             leading dimensions ldb[i], ldx[i] (NULL: system i's L)
+ *   status    optional, n entries: the HF_* status of each system
+ * Returns HF_OK if every system succeeded, else the first non-OK status in index order
+ * (HF_ERR_ARG for NULL or repeated contexts, nothing run).  Workers: HF_BATCH_WORKERS
+ * environment variable (default 8).
+ */
+int hf_factorize_batched(hf_ctx* const* ctxs, int n, const double* const* vals_dev, double tau, int32_t* status);
+int hf_schur_batched(hf_ctx* const* ctxs, int n, int32_t* status);
+int hf_solve_batched(hf_ctx* const* ctxs, int n, int nrhs, const double* const* b_dev, const int64_t* ldb,
+                     double* const* x_dev, const int64_t* ldx, int32_t* status);
+
 /* Release every device and host buffer of the context.  NULL is ignored. */
 void hf_free(hf_ctx* ctx);
 

@@ -6,4 +6,5 @@ include/hf.h); this package only marshals arguments to it.
 from .hf import (  # noqa: F401
     HybridFactor, HFError, default_opts, lib, LIB_PATH, EXPORTED,
     HF_PREC_MIXED, HF_PREC_FP64, HF_PREC_FP32, HF_OK, HF_ERR_NOT_CONVERGED,
+    factorize_batched, schur_batched, solve_batched,
 )

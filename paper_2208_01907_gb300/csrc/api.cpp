@@ -6,6 +6,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 int hf_factorize_impl(hf_ctx* c, const double* vals, double tau);
@@ -60,6 +63,72 @@ ProfScope::~ProfScope() {
   cudaEventRecord(c->ev_pool[idx + 1], (cudaStream_t)c->opts.cuda_stream);
   c->prof_recs.push_back({cls, idx});
 }
+
+namespace {
+
+int batch_workers(int n) {
+  int w = 8;
+  if (const char* e = std::getenv("HF_BATCH_WORKERS")) w = std::max(1, std::atoi(e));
+  return std::max(1, std::min(w, n));
+}
+
+// Runs op(i) for the n contexts on a pool of host threads.  Each worker owns a
+// non-blocking stream, used by contexts created on the default stream.
+template <typename Op>
+int run_batched(hf_ctx* const* ctxs, int n, int32_t* status, Op op) {
+  if (!ctxs || n < 0) return HF_ERR_ARG;
+  if (n == 0) return HF_OK;
+  {
+    std::vector<hf_ctx*> v(ctxs, ctxs + n);
+    for (hf_ctx* c : v) if (!c) return HF_ERR_ARG;
+    std::sort(v.begin(), v.end());
+    if (std::adjacent_find(v.begin(), v.end()) != v.end()) return HF_ERR_ARG;
+  }
+  int dev = 0;
+  {
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return hf_cuda_error(e);
+  }
+  const int W = batch_workers(n);
+  std::vector<cudaStream_t> streams(W, nullptr);
+  for (int w = 0; w < W; ++w) {
+    cudaError_t e = cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      for (int u = 0; u < w; ++u) cudaStreamDestroy(streams[u]);
+      return hf_cuda_error(e);
+    }
+  }
+  std::vector<int32_t> st(n, HF_OK);
+  std::atomic<int> next(0);
+  auto worker = [&](int w) {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      hf_ctx* c = ctxs[i];
+      void* saved = c->opts.cuda_stream;
+      if (!saved) c->opts.cuda_stream = streams[w];
+      int rc = op(i);
+      const cudaError_t e = cudaStreamSynchronize((cudaStream_t)c->opts.cuda_stream);
+      if (rc == HF_OK && e != cudaSuccess) rc = hf_cuda_error(e);
+      c->opts.cuda_stream = saved;
+      st[i] = rc;
+    }
+  };
+  std::vector<std::thread> threads;
+  threads.reserve(W);
+  for (int w = 0; w < W; ++w) threads.emplace_back(worker, w);
+  for (auto& t : threads) t.join();
+  for (int w = 0; w < W; ++w) cudaStreamDestroy(streams[w]);
+  int first = HF_OK;
+  for (int i = 0; i < n; ++i) {
+    if (status) status[i] = st[i];
+    if (first == HF_OK && st[i] != HF_OK) first = st[i];
+  }
+  return first;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -378,6 +447,24 @@ int hf_get_s22_factor(hf_ctx* c, int32_t* perm, double* lf, int32_t* dblk, doubl
   return e == cudaSuccess ? HF_OK : hf_cuda_error(e);
 }
 
+int hf_factorize_batched(hf_ctx* const* ctxs, int n, const double* const* vals_dev, double tau, int32_t* status) {
+  if (!vals_dev) return HF_ERR_ARG;
+  return run_batched(ctxs, n, status, [&](int i) { return hf_factorize(ctxs[i], vals_dev[i], tau); });
+}
+
+int hf_schur_batched(hf_ctx* const* ctxs, int n, int32_t* status) {
+  return run_batched(ctxs, n, status, [&](int i) { return hf_schur(ctxs[i]); });
+}
+
+int hf_solve_batched(hf_ctx* const* ctxs, int n, int nrhs, const double* const* b_dev, const int64_t* ldb,
+                     double* const* x_dev, const int64_t* ldx, int32_t* status) {
+  if (!b_dev || !x_dev) return HF_ERR_ARG;
+  return run_batched(ctxs, n, status, [&](int i) {
+    const int64_t lb = ldb ? ldb[i] : ctxs[i]->L, lx = ldx ? ldx[i] : ctxs[i]->L;
+    return hf_solve(ctxs[i], nrhs, b_dev[i], lb, x_dev[i], lx);
+  });
+}
+
 void hf_free(hf_ctx* c) {
   if (!c) return;
   DevBuf* bufs[] = {&c->d_rowptr, &c->d_col, &c->d_diagpos, &c->d_nodes, &c->d_state, &c->d_rowid,
@@ -387,6 +474,7 @@ void hf_free(hf_ctx* c) {
                     &c->d_work, &c->d_small, &c->d_ozslice, &c->d_gsmall, &c->d_k12, &c->d_solve, &c->d_gmag,
                     &c->d_pos0, &c->d_invpos, &c->d_ozint};
   for (DevBuf* b : bufs) hf_release(*b);
+  for (DevBuf& b : c->d_hist) hf_release(b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 namespace {
@@ -876,6 +877,8 @@ int run_levels(hf_ctx* c) {
   constexpr size_t PCL_SMEM = 220 * 1024;
   static bool attr_set[2] = {false, false};
   static int max_cluster[2] = {0, 0};
+  static std::mutex attr_mu;                 // contexts may be driven from several host threads
+  std::lock_guard<std::mutex> attr_lock(attr_mu);
   if (!attr_set[sizeof(T) == 8]) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCL_SMEM));

@@ -106,6 +106,7 @@ struct hf_ctx {
   double gcr_relres = 0, solve_relres = 0;
   int64_t nnz_factor = 0;
   DevBuf d_work;                     // Krylov workspace
+  std::vector<DevBuf> d_hist;        // block-GCR history P_0, Q_0, P_1, Q_1, ... (grown on demand)
   size_t work_cap = 0;
   DevBuf d_ozslice;                  // BF16 slices of the operands of the emulated FP64 products
   DevBuf d_small;                    // small matrices / partial sums

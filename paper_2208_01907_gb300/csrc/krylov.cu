@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 namespace {
@@ -1099,9 +1100,10 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   const int64_t L = c->L;
   const int maxit = std::max(1, c->opts.gcr_maxit);
   const size_t blk = (size_t)L * m;
-  // workspace: R, W, Z, tmp(3 x L x m floats or 1 x L x m doubles), 2 * (maxit+1) history blocks
+  // workspace: R, W, Z, tmp(3 x L x m floats or 1 x L x m doubles); the history blocks
+  // P_i, Q_i are allocated when an iteration first needs them (kept for later calls)
   const size_t tmp_doubles = (blk * 3 + 1) / 2 + blk;
-  size_t need = (blk * 3 + tmp_doubles + blk * 2 * (size_t)(maxit + 1)) * 8 + 1024;
+  size_t need = (blk * 3 + tmp_doubles) * 8 + 1024;
   int rc;
   if ((rc = hf_ensure(c->d_work, need))) return rc;
   double* base = (double*)c->d_work.p;
@@ -1109,9 +1111,14 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   double* W = R + blk;
   double* Z = W + blk;
   double* tmp = Z + blk;
-  double* hist = tmp + tmp_doubles;
-  auto Pm = [&](int i) { return hist + (size_t)(2 * i) * blk; };
-  auto Qm = [&](int i) { return hist + (size_t)(2 * i + 1) * blk; };
+  auto ensure_hist = [&](int i) -> int {           // P_i and Q_i
+    if ((int)c->d_hist.size() < 2 * i + 2) c->d_hist.resize(2 * i + 2);
+    int r = hf_ensure(c->d_hist[2 * i], blk * 8 + 256);
+    if (!r) r = hf_ensure(c->d_hist[2 * i + 1], blk * 8 + 256);
+    return r;
+  };
+  auto Pm = [&](int i) { return (double*)c->d_hist[2 * i].p; };
+  auto Qm = [&](int i) { return (double*)c->d_hist[2 * i + 1].p; };
   // small matrices in pinned / device memory
   const size_t mm = (size_t)m * m;
   std::vector<double> hnorm(m), bnorm(m);
@@ -1176,6 +1183,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   if ((rc = precond(c, m, B, X, tmp))) return rc;
   spmm(c, m, X, Z);
   HF_LAUNCH(c, HF_PROF_VECTOR, k_sub<<<nb, 256, 0, s>>>((int64_t)blk, B, Z, R));
+  if ((rc = ensure_hist(0))) return rc;
   if ((rc = precond(c, m, R, Pm(0), tmp))) return rc;
   spmm(c, m, Pm(0), Qm(0));
   int it = 0;
@@ -1220,6 +1228,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
       HF_LAUNCH(c, HF_PROF_VECTOR, k_zero_cols<<<nb, 256, 0, s>>>(L, m, dmask, R));
     if ((rc = precond(c, m, R, W, tmp))) return rc;
     spmm(c, m, W, Z);
+    if ((rc = ensure_hist(n + 1))) return rc;
     double* Pn = Pm(n + 1);
     double* Qn = Qm(n + 1);
     for (int q = 0; q <= n; ++q) {
@@ -1464,6 +1473,8 @@ int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W) {
   const size_t tmp_round = (tmp_bytes + 255) / 256 * 256;
   const size_t vec_bytes = (size_t)c->row_elems * m * esz;
   if (tmp_round + vec_bytes > HF_NOALLOC_SCRATCH_BYTES) return HF_ERR_ARG;
+  static std::mutex addr_mu;
+  std::lock_guard<std::mutex> addr_lock(addr_mu);
   if (!g_precond_scratch_addr[dev]) {
     // host code only has a stand-in for the array's name: ask the runtime for the address
     // on this device (once per device, with that device current)

@@ -37,6 +37,7 @@
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 namespace {
 
@@ -436,15 +437,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+EncodeTiledFn lookup_encode() {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    return (EncodeTiledFn)f;
+  return nullptr;
+}
+
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)f;
-  }
+  static const EncodeTiledFn fn = lookup_encode();    // thread-safe one-time initialisation
   return fn;
 }
 
@@ -464,8 +467,10 @@ int slice_map(CUtensorMap* map, const void* base, int64_t R, int64_t Kg, int box
 }
 
 bool oz_attr_done = false;
+std::mutex oz_attr_mu;
 
 int oz_setup() {
+  std::lock_guard<std::mutex> lk(oz_attr_mu);
   if (!oz_attr_done) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     oz_attr_done = true;

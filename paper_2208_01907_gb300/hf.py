@@ -23,7 +23,8 @@ EXPORTED = (
     "hf_default_opts", "hf_error_string", "hf_analyze", "hf_factorize", "hf_schur", "hf_solve",
     "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
-    "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc", "hf_free",
+    "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc",
+    "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_free",
 )
 HF_NPROF = 13
 
@@ -95,6 +96,10 @@ def lib():
     L.hf_get_s22_factor.argtypes = [vp, vp, vp, vp, vp, vp]
     L.hf_free.argtypes = [vp]
     L.hf_free.restype = None
+    pp = C.POINTER(C.c_void_p)
+    L.hf_factorize_batched.argtypes = [pp, i32, pp, dbl, vp]
+    L.hf_schur_batched.argtypes = [pp, i32, vp]
+    L.hf_solve_batched.argtypes = [pp, i32, i32, pp, vp, pp, vp, vp]
     for name in EXPORTED:
         if name not in ("hf_error_string", "hf_free", "hf_profile_name"):
             getattr(L, name).restype = i32
@@ -277,3 +282,44 @@ class HybridFactor:
         _check(lib().hf_get_s22_factor(self._h, _ptr(perm), _ptr(lf), _ptr(blk), _ptr(dval), _ptr(nul)),
                "hf_get_s22_factor")
         return perm[:M], lf[:M, :M], blk[:M], dval[:M], nul[:M]
+
+
+# -- batched form ---------------------------------------------------------
+def _ptrs(items):
+    return (C.c_void_p * len(items))(*[int(x) for x in items])
+
+
+def _batched_check(rc, st, where, allow=()):
+    bad = [(i, int(v)) for i, v in enumerate(st) if v != HF_OK and v not in allow]
+    if bad:
+        i, v = bad[0]
+        raise HFError(v, f"{where} (system {i})")
+    if rc != HF_OK and rc not in allow:
+        raise HFError(rc, where)            # rejected before any system ran
+    return [int(v) for v in st]
+
+
+def factorize_batched(factors, vals_list, tau=1e-2):
+    """hf_factorize on every (HybridFactor, CUDA values) pair, run concurrently."""
+    n = len(factors)
+    st = np.zeros(n, np.int32)
+    rc = lib().hf_factorize_batched(_ptrs([f._h.value for f in factors]), n,
+                                    _ptrs([v.data_ptr() for v in vals_list]), float(tau), _ptr(st))
+    return _batched_check(rc, st, "hf_factorize_batched")
+
+
+def schur_batched(factors):
+    n = len(factors)
+    st = np.zeros(n, np.int32)
+    rc = lib().hf_schur_batched(_ptrs([f._h.value for f in factors]), n, _ptr(st))
+    return _batched_check(rc, st, "hf_schur_batched", allow=(HF_ERR_NOT_CONVERGED,))
+
+
+def solve_batched(factors, bs, xs):
+    """bs[i], xs[i]: CUDA float64 tensors of shape (nrhs, L_i), the same nrhs for all."""
+    n = len(factors)
+    nrhs = 1 if bs[0].dim() == 1 else bs[0].shape[0]
+    st = np.zeros(n, np.int32)
+    rc = lib().hf_solve_batched(_ptrs([f._h.value for f in factors]), n, nrhs, _ptrs([b.data_ptr() for b in bs]),
+                                None, _ptrs([x.data_ptr() for x in xs]), None, _ptr(st))
+    return _batched_check(rc, st, "hf_solve_batched", allow=(HF_ERR_NOT_CONVERGED,))
