@@ -77,6 +77,10 @@ typedef struct {
   int    fp64_gemm;      /* FP64 Grams and block updates of block GCR: 0 = emulated on the BF16
                             tensor cores with exact slice products (FP64 accuracy), 1 = FP64
                             units; default 0 */
+  int    trailing;       /* trailing updates of the FP32 factor: 0 = tensor cores with the exact
+                            3 x BF16 split of FP32 (six products, FP32 accumulate per product
+                            order), 1 = FP32 SIMT; default 1 (faster here: the rank-64 update
+                            is memory-bound); the FP64 form always uses FP64 SIMT */
 } hf_opts;
 
 typedef struct {

@@ -16,7 +16,7 @@ int hf_cuda_error(cudaError_t e);       // maps to HF_ERR_OOM / HF_ERR_CUDA, kee
 const char* hf_last_cuda_message();
 
 // flag slots in ctx->d_flags
-enum { FLAG_DELAY_OVERFLOW = 0, FLAG_NUMERIC = 1, FLAG_SMEM = 2, FLAG_COUNT = 8 };
+enum { FLAG_DELAY_OVERFLOW = 0, FLAG_NUMERIC = 1, FLAG_SMEM = 2, FLAG_TC_TIMEOUT = 3, FLAG_COUNT = 8 };
 
 inline cudaStream_t hf_stream(const hf_ctx* c) { return (cudaStream_t)c->opts.cuda_stream; }
 

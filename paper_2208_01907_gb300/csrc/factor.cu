@@ -10,6 +10,9 @@
 // factor (unit L below the diagonal, D on it) and the trailing block [k, f)^2 is the
 // contribution passed to the parent by extend-add.
 #include "common.cuh"
+#include "tcgen05.cuh"
+
+#include <cuda_bf16.h>
 
 #include <cooperative_groups.h>
 #include <algorithm>
@@ -752,6 +755,171 @@ __global__ void __launch_bounds__(256) k_trailing(const NodeDesc* __restrict__ n
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same trailing update on the tensor cores (the precision form of the FP32 factor):
+// each FP32 operand is split exactly into three BF16 parts, x = x0 + x1 + x2 with
+// x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1) (24 significant bits), and
+// the six products of total order <= 2 accumulate in three FP32 TMEM accumulators, one
+// per order.  The dropped products are below 2^-24 of |W| |D| |W|^T,
+// the rounding level of the FP32 SIMT update.  One 128 x 64 tile of the lower trailing
+// block per CTA of 128 threads; K = the panel width (<= 64) in one shared-memory stage.
+// ---------------------------------------------------------------------------
+constexpr int TT_M = 128, TT_N = 64, TT_K = 64, TT_THREADS = 128;
+constexpr int TT_A = 3 * TT_M * TT_K * 2;          // 48 KB: three BF16 parts of W rows
+constexpr int TT_B = 3 * TT_N * TT_K * 2;          // 24 KB: three BF16 parts of (W D) rows
+constexpr int TT_SMEM = TT_A + TT_B + 128;
+constexpr uint32_t TT_IDESC = tc::bf16_idesc(TT_M, TT_N);
+constexpr int TT_COLS = 256;                        // TMEM columns: three accumulators of TT_N
+
+__device__ __forceinline__ void split3(float x, uint32_t& h0, uint32_t& h1, uint32_t& h2) {
+  const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(b0);
+  const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b1);
+  const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+  h0 = __bfloat16_as_ushort(b0);
+  h1 = __bfloat16_as_ushort(b1);
+  h2 = __bfloat16_as_ushort(b2);
+}
+
+// Split of the panel, once per panel step: rows [k1, f) of W = L[:, k0:k1) and of W D
+// into three BF16 parts each, stored per front as [part 0..5][k-group 0..7][row][8 BF16]
+// (16 bytes per row and k-group; row = front position), i.e. already in the K-major
+// core-matrix layout of a tile, so that a tile of consecutive rows is one contiguous
+// block per part and k-group.
+__global__ void k_trailing_split(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                                 const float* __restrict__ arena, uint4* __restrict__ parts) {
+  const int t = t0 + blockIdx.y;
+  const int k0 = st[t].kp0, k1 = st[t].k, f = st[t].f;
+  if (k1 <= k0) return;
+  const NodeDesc d = nd[t];
+  const float* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  const int K = min(k1 - k0, TT_K);
+  uint4* P = parts + d.row_off * 48;                           // 6 parts x 8 k-groups per row
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (f - k1) * 8; e += gridDim.x * blockDim.x) {
+    const int r = k1 + e / 8, kg = e % 8;                      // 8 threads per row
+    float w[8], b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = kg * 8 + q;
+      const float x = k < K ? F[r + (int64_t)(k0 + k) * ld] : 0.f;
+      w[q] = x;
+      b[q] = k < K ? x * F[(k0 + k) + (int64_t)(k0 + k) * ld] : 0.f;
+    }
+    uint32_t p[6][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t a0, a1, a2, c0, c1, c2;
+      split3(w[2 * q], a0, a1, a2);
+      split3(w[2 * q + 1], c0, c1, c2);
+      p[0][q] = a0 | (c0 << 16); p[1][q] = a1 | (c1 << 16); p[2][q] = a2 | (c2 << 16);
+      split3(b[2 * q], a0, a1, a2);
+      split3(b[2 * q + 1], c0, c1, c2);
+      p[3][q] = a0 | (c0 << 16); p[4][q] = a1 | (c1 << 16); p[5][q] = a2 | (c2 << 16);
+    }
+#pragma unroll
+    for (int part = 0; part < 6; ++part)
+      P[((int64_t)(part * 8 + kg)) * ld + r] = make_uint4(p[part][0], p[part][1], p[part][2], p[part][3]);
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(TT_THREADS) k_trailing_tc(const NodeDesc* __restrict__ nd,
+                                                          const NodeState* __restrict__ st, int t0,
+                                                          float* __restrict__ arena, const uint4* __restrict__ parts,
+                                                          int* __restrict__ flags) {
+  const int t = t0 + blockIdx.z;
+  const int k0 = st[t].kp0, k1 = st[t].k, f = st[t].f;
+  if (k1 <= k0) return;
+  const int i0 = k1 + blockIdx.x * TT_M, j0 = k1 + blockIdx.y * TT_N;
+  if (i0 >= f || j0 >= f || j0 > i0 + TT_M - 1) return;       // outside the front or strictly upper
+  const NodeDesc d = nd[t];
+  float* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  const uint4* P = parts + d.row_off * 48;
+  extern __shared__ __align__(128) unsigned char tt_raw[];
+  unsigned char* sA = (unsigned char*)(((uintptr_t)tt_raw + 127) & ~(uintptr_t)127);
+  unsigned char* sB = sA + TT_A;
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc::smem_u32(&tslot)), "r"(TT_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::smem_u32(&bar_ld)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::smem_u32(&bar_mma)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  // bulk copies of the pre-split parts: A = parts 0..2 of rows [i0, i0+128), B = parts 3..5 of
+  // rows [j0, j0+64), each k-group one contiguous block (rows past f are masked in the epilogue)
+  if (tid == 0) {
+    const uint32_t bl = tc::smem_u32(&bar_ld);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bl), "r"(TT_A + TT_B) : "memory");
+    for (int part = 0; part < 3; ++part)
+      for (int kg = 0; kg < 8; ++kg) {
+        bulk_g2s(tc::smem_u32(sA + part * (TT_M * TT_K * 2) + kg * (TT_M * 16)), P + (int64_t)(part * 8 + kg) * ld + i0,
+                 TT_M * 16, bl);
+        bulk_g2s(tc::smem_u32(sB + part * (TT_N * TT_K * 2) + kg * (TT_N * 16)),
+                 P + (int64_t)((part + 3) * 8 + kg) * ld + j0, TT_N * 16, bl);
+      }
+  }
+  bool ok = false;
+  for (int it = 0; it < (1 << 22) && !ok; ++it) ok = tc::mbar_try(tc::smem_u32(&bar_ld), 0u);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  if (tid == 0 && ok) {
+    // one accumulator per order of the products (x0y0 | x0y1 + x1y0 | x0y2 + x1y1 + x2y0),
+    // added in registers afterwards: the tensor core's FP32 accumulation then never adds
+    // terms of very different magnitude
+    const int ps[6] = {0, 1, 0, 2, 1, 0}, qs[6] = {0, 0, 1, 0, 1, 2}, os[6] = {0, 1, 1, 2, 2, 2};
+    for (int ks = 0; ks < TT_K / 16; ++ks)
+      for (int u = 0; u < 6; ++u) {
+        const uint64_t ad = tc::smem_desc(tc::smem_u32(sA + ps[u] * (TT_M * TT_K * 2) + ks * (2 * TT_M * 16)), 16 * TT_M, 128);
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(sB + qs[u] * (TT_N * TT_K * 2) + ks * (2 * TT_N * 16)), 16 * TT_N, 128);
+        const bool first = ks == 0 && (u == 0 || u == 1 || u == 3);
+        tc::mma_bf16(tmem + (uint32_t)(os[u] * TT_N), ad, bd, TT_IDESC, first ? 0u : 1u);
+      }
+    tc::mma_commit(tc::smem_u32(&bar_mma));
+  }
+  bool done = false;
+  if (ok)
+    for (int it = 0; it < (1 << 22) && !done; ++it) done = tc::mbar_try(tc::smem_u32(&bar_mma), 0u);
+  if (!done && lane == 0) atomicExch(flags + FLAG_TC_TIMEOUT, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (done) {
+    const int i = i0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TT_N; c0 += 32) {
+      uint32_t r0[32], r1[32], r2[32];
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      tc::tmem_ld32(tl, r0);
+      tc::tmem_ld32(tl + TT_N, r1);
+      tc::tmem_ld32(tl + 2 * TT_N, r2);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = j0 + c0 + q;
+        const float v = __uint_as_float(r0[q]) + (__uint_as_float(r1[q]) + __uint_as_float(r2[q]));
+        if (i < f && j < f && i >= j) F[i + (int64_t)j * ld] -= v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TT_COLS));
+  }
+}
+
 // After the factorization the contribution maps of every child are re-expressed in the
 // parent's pivoted row order (the solves work in that order).
 __global__ void k_cbmap_post(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
@@ -882,6 +1050,7 @@ int run_levels(hf_ctx* c) {
   if (!attr_set[sizeof(T) == 8]) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCL_SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM));
     if (cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
       (void)cudaGetLastError();
     // largest cluster (<= 16) that can be resident with the full shared-memory panel
@@ -904,6 +1073,8 @@ int run_levels(hf_ctx* c) {
     attr_set[sizeof(T) == 8] = true;
   }
   const int cmax = max_cluster[sizeof(T) == 8];
+  // trailing updates of the FP32 factor on the tensor cores (3 x BF16 split) when selected
+  const bool use_tc = sizeof(T) == 4 && c->opts.trailing == 0;
   // HF_LEVEL_TIMES=1: time the panel and trailing launches of every level (diagnostic)
   const char* lt = std::getenv("HF_LEVEL_TIMES");
   const bool level_times = lt && lt[0] == '1';
@@ -981,7 +1152,14 @@ int run_levels(hf_ctx* c) {
       if (use_gl)
         HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag,
                                                                            (int32_t*)c->d_pos0.p, nbl, c->tau, cap));
-      HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena));
+      if (use_tc) {
+        uint4* parts = (uint4*)c->d_tparts.p;
+        HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_split<<<dim3((unsigned)std::min(1024, (maxld * 8 + 255) / 256), cnt), 256, 0, s>>>(
+                                           nd, st, t0, (const float*)arena, parts));
+        HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_tc<<<dim3((maxld + TT_M - 1) / TT_M, (maxld + TT_N - 1) / TT_N, cnt),
+                                                       TT_THREADS, TT_SMEM, s>>>(nd, st, t0, (float*)arena, parts, flags));
+      } else
+        HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena));
     }
     if (level_times) {
       float ms = 0;
@@ -1075,6 +1253,9 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     const size_t esz = dbl ? 8 : 4;
     if ((rc = hf_ensure(c->d_front, (size_t)c->front_elems * esz + 64))) return rc;
     if ((rc = hf_ensure(c->d_gmag, (size_t)c->row_elems * esz + 64))) return rc;
+    // pre-split panel parts of the tensor-core trailing update: 768 bytes per front row, plus
+    // one tile of rows past the last front (tiles may read beyond a front's rows)
+    if (!dbl && c->opts.trailing == 0 && (rc = hf_ensure(c->d_tparts, ((size_t)c->row_elems + TT_M) * 768 + 256))) return rc;
     if ((rc = hf_ensure(c->d_pos0, (size_t)c->row_elems * 4 + 64))) return rc;
     if ((rc = hf_ensure(c->d_invpos, (size_t)c->row_elems * 4 + 64))) return rc;
     HF_CUDA_TRY(cudaMemsetAsync(c->d_flags.p, 0, FLAG_COUNT * sizeof(int) + 64, s));
@@ -1103,6 +1284,7 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     HF_CUDA_TRY(cudaMemcpyAsync(hcounts, counts, sizeof(hcounts), cudaMemcpyDeviceToHost, s));
     HF_CUDA_TRY(cudaStreamSynchronize(s));
     if (hflags[FLAG_NUMERIC]) return HF_ERR_NUMERIC;
+    if (hflags[FLAG_TC_TIMEOUT]) return HF_ERR_TIMEOUT;
     if (hflags[FLAG_DELAY_OVERFLOW]) {
       // grow the capacity for postponed rows and lay the fronts out again
       c->opts.delay_cap = std::max(1, c->opts.delay_cap) * 2;

@@ -35,7 +35,7 @@ class hf_opts(C.Structure):
         ("gcr_tol", C.c_double), ("gcr_maxit", C.c_int), ("kernel_eps", C.c_double),
         ("kernel_gap", C.c_double), ("nd_leaf", C.c_int), ("nd_levels", C.c_int),
         ("delay_cap", C.c_int), ("panel", C.c_int), ("cuda_stream", C.c_void_p),
-        ("fp64_gemm", C.c_int),
+        ("fp64_gemm", C.c_int), ("trailing", C.c_int),
     ]
 
 

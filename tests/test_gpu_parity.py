@@ -154,6 +154,35 @@ def test_fp64_form_schur_and_solve():
     assert out["info"]["kernel_dim"] == 1
 
 
+@pytest.mark.parametrize("name", ["cfg1_diffusion48", "stokes8", "elasticity6", "darcy16"])
+def test_trailing_tensor_cores_match_fp32_simt(name):
+    """Precision form: the trailing updates on the tensor cores (exact 3 x BF16 split of
+    FP32, six products, FP32 accumulate) against the FP32 SIMT updates: the same pivots,
+    pivots and factor entries within FP32 rounding, the same S22 to the GCR tolerance."""
+    make, _, opts = CASES[name]
+    s = make()
+    tc_ = run_gpu(s, tau=1e-2, trailing=0, **opts)
+    sm_ = run_gpu(s, tau=1e-2, trailing=1, **opts)
+    Ht, Hs = tc_["H"], sm_["H"]
+    ev_t, ev_s = Ht.pivot_events(), Hs.pivot_events()
+    same = all(np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2]) for a, b in zip(ev_t, ev_s))
+    if same:
+        _, _, _, dt = Ht.factor()
+        _, _, _, ds = Hs.factor()
+        assert np.max(np.abs(dt - ds) / np.maximum(np.abs(ds), 1e-30)) <= 1e-4
+        St, Ss = Ht.s22(torch).cpu().numpy(), Hs.s22(torch).cpu().numpy()
+        assert rel_fro(St, Ss) <= 1e-12
+    else:
+        # near-ties of max |diag| resolved differently by the two roundings: each form must
+        # then pass the oracle replay (admissible pivots) and the S22 parity on its own
+        for out in (tc_, sm_):
+            q, K, fac, _ = replay(s, out["H"], 1e-2)
+            assert fac.violations == []
+            assert rel_fro(out["H"].s22(torch).cpu().numpy(), O.schur_direct(K, fac.lambda2)) <= S22_TOL
+    for out in (tc_, sm_):
+        assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
+
+
 @pytest.mark.parametrize("name", ["cfg1_diffusion48", "stokes8", "elasticity6"])
 def test_emulated_fp64_products_match_native(name):
     """Block GCR (Sec. 3.5) with its Grams and updates on the tensor cores (sliced
