@@ -127,6 +127,56 @@ template <typename TV> struct DiagRhs { static constexpr int value = sizeof(TV) 
 constexpr int DSB = 16;      // sub-block rows
 constexpr int DTH = 256;     // threads
 
+// Unit-triangular solve of a jb x jb diagonal block (forward: L, backward: L^T) for the
+// NR right-hand sides staged in Vs; sub-blocks of DSB rows are solved by one thread per
+// right-hand side in registers, the rows after (before) them updated by all NTH threads.
+template <typename TV, bool FWD, int NR, int NTH, int LS, int VS>
+__device__ __forceinline__ void diag_solve(const TV (*Ls)[LS], TV (*Vs)[VS], int jb, int tid) {
+  constexpr int DR = NR;
+  const int nsb = (jb + DSB - 1) / DSB;
+  for (int sbi = 0; sbi < nsb; ++sbi) {
+    const int s = FWD ? sbi : nsb - 1 - sbi;             // sub-block index
+    const int r0 = s * DSB, r1 = min(jb, r0 + DSB);
+    if (tid < DR) {
+      TV x[DSB];
+#pragma unroll
+      for (int i = 0; i < DSB; ++i) x[i] = (r0 + i < r1) ? Vs[r0 + i][tid] : TV(0);
+      if (FWD) {
+#pragma unroll
+        for (int i = 1; i < DSB; ++i)
+#pragma unroll
+          for (int q = 0; q < i; ++q) x[i] -= Ls[r0 + i][r0 + q] * x[q];
+      } else {
+#pragma unroll
+        for (int i = DSB - 2; i >= 0; --i)
+#pragma unroll
+          for (int q = i + 1; q < DSB; ++q) x[i] -= Ls[r0 + q][r0 + i] * x[q];
+      }
+#pragma unroll
+      for (int i = 0; i < DSB; ++i)
+        if (r0 + i < r1) Vs[r0 + i][tid] = x[i];
+    }
+    __syncthreads();
+    // rows after (forward) / before (backward) the sub-block
+    const int u0 = FWD ? r1 : 0, u1 = FWD ? jb : r0;
+    for (int e = tid; e < (u1 - u0) * DR; e += NTH) {
+      const int r = u0 + e / DR, c = e % DR;
+      TV acc = Vs[r][c];
+      if (FWD) {
+#pragma unroll
+        for (int q = 0; q < DSB; ++q)
+          if (r0 + q < r1) acc -= Ls[r][r0 + q] * Vs[r0 + q][c];
+      } else {
+#pragma unroll
+        for (int q = 0; q < DSB; ++q)
+          if (r0 + q < r1) acc -= Ls[r0 + q][r] * Vs[r0 + q][c];
+      }
+      Vs[r][c] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename TF, typename TV, bool FWD>
 __global__ void __launch_bounds__(DTH) k_trsm_diag(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
                                                   int t0, const TF* __restrict__ arena, TV* __restrict__ vec, int m,
@@ -154,48 +204,7 @@ __global__ void __launch_bounds__(DTH) k_trsm_diag(const NodeDesc* __restrict__ 
     Vs[r][c] = (r < jb && c0 + c < m) ? V[(int64_t)r * m + c0 + c] : TV(0);
   }
   __syncthreads();
-  const int nsb = (jb + DSB - 1) / DSB;
-  for (int sbi = 0; sbi < nsb; ++sbi) {
-    const int s = FWD ? sbi : nsb - 1 - sbi;             // sub-block index
-    const int r0 = s * DSB, r1 = min(jb, r0 + DSB);
-    if (tid < DR) {
-      TV x[DSB];
-#pragma unroll
-      for (int i = 0; i < DSB; ++i) x[i] = (r0 + i < r1) ? Vs[r0 + i][tid] : TV(0);
-      if (FWD) {
-#pragma unroll
-        for (int i = 1; i < DSB; ++i)
-#pragma unroll
-          for (int q = 0; q < i; ++q) x[i] -= Ls[r0 + i][r0 + q] * x[q];
-      } else {
-#pragma unroll
-        for (int i = DSB - 2; i >= 0; --i)
-#pragma unroll
-          for (int q = i + 1; q < DSB; ++q) x[i] -= Ls[r0 + q][r0 + i] * x[q];
-      }
-#pragma unroll
-      for (int i = 0; i < DSB; ++i)
-        if (r0 + i < r1) Vs[r0 + i][tid] = x[i];
-    }
-    __syncthreads();
-    // rows after (forward) / before (backward) the sub-block
-    const int u0 = FWD ? r1 : 0, u1 = FWD ? jb : r0;
-    for (int e = tid; e < (u1 - u0) * DR; e += DTH) {
-      const int r = u0 + e / DR, c = e % DR;
-      TV acc = Vs[r][c];
-      if (FWD) {
-#pragma unroll
-        for (int q = 0; q < DSB; ++q)
-          if (r0 + q < r1) acc -= Ls[r][r0 + q] * Vs[r0 + q][c];
-      } else {
-#pragma unroll
-        for (int q = 0; q < DSB; ++q)
-          if (r0 + q < r1) acc -= Ls[r0 + q][r] * Vs[r0 + q][c];
-      }
-      Vs[r][c] = acc;
-    }
-    __syncthreads();
-  }
+  diag_solve<TV, FWD, DR, DTH>(Ls, Vs, jb, tid);
   for (int e = tid; e < jb * DR; e += DTH) {
     const int r = e / DR, c = e % DR;
     if (c0 + c < m) V[(int64_t)r * m + c0 + c] = Vs[r][c];
@@ -214,7 +223,11 @@ constexpr int SGC = 64;       // right-hand sides per CTA
 constexpr int SGTH = 128;     // threads
 template <typename TV> struct GemmK { static constexpr int value = sizeof(TV) == 8 ? 8 : 16; };
 
-template <typename TF, typename TV, int MODE>
+// With SOLVE (MODE 0 / 1), the CTAs of the row tile that holds the next diagonal block
+// (forward: rows [j0+jb, ...), the first tile; backward: rows [.., j0), the first tile,
+// tiles counted from the top) also solve that block after their update, so that the next
+// block step needs no separate diagonal-solve launch.
+template <typename TF, typename TV, int MODE, bool SOLVE>
 __global__ void __launch_bounds__(SGTH) k_gemm_upd(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
                                                   int t0, const TF* __restrict__ arena, TV* __restrict__ vec, int m, int b) {
   constexpr int GK = GemmK<TV>::value;
@@ -227,14 +240,16 @@ __global__ void __launch_bounds__(SGTH) k_gemm_upd(const NodeDesc* __restrict__ 
   if (MODE == 0) { int j0 = b * TS; if (j0 >= ks) return; int jb = min(TS, ks - j0); r_lo = j0 + jb; r_hi = f; k_lo = j0; k_hi = j0 + jb; }
   else if (MODE == 1) { int j1 = ks - b * TS; if (j1 <= 0) return; int j0 = max(0, j1 - TS); r_lo = 0; r_hi = j0; k_lo = j0; k_hi = j1; }
   else { r_lo = 0; r_hi = ks; k_lo = ks; k_hi = f; }
-  const int r0 = r_lo + blockIdx.x * SGR;
+  // row tile: forward / start from the first row, backward block steps from the last
+  const int r0 = MODE == 1 ? r_hi - (int)(blockIdx.x + 1) * SGR : r_lo + (int)blockIdx.x * SGR;
   const int c0 = blockIdx.y * SGC;
-  if (r0 >= r_hi || c0 >= m || k_hi <= k_lo) return;
+  if (r0 >= r_hi || r0 + SGR <= r_lo || c0 >= m || k_hi <= k_lo) return;
   const TF* F = arena + d.front_off;
   const int64_t ld = d.ld;
   TV* V = vec + d.row_off * m;
   __shared__ __align__(16) TV As[2][GK][SGR + 4];
   __shared__ __align__(16) TV Bs[2][GK][SGC + 4];
+  __shared__ TV Ls[SOLVE ? TS : 1][SOLVE ? TS + 1 : 1];   // next diagonal block (SOLVE)
   const int tid = threadIdx.x;
   const int tx = tid & 7, ty = tid >> 3;     // 8 rhs groups x 16 row groups
   TV pa[AL], pb[BL];
@@ -246,7 +261,7 @@ __global__ void __launch_bounds__(SGTH) k_gemm_upd(const NodeDesc* __restrict__ 
       else { rr = tid; kk = u; }                                                 // k contiguous in column i
       const int q = kc + kk, i = r0 + rr;
       TV a = TV(0);
-      if (q < k_hi && i < r_hi) a = (TV)(MODE == 0 ? F[i + (int64_t)q * ld] : F[q + (int64_t)i * ld]);
+      if (q < k_hi && i < r_hi && i >= r_lo) a = (TV)(MODE == 0 ? F[i + (int64_t)q * ld] : F[q + (int64_t)i * ld]);
       pa[u] = a;
     }
 #pragma unroll
@@ -299,14 +314,37 @@ __global__ void __launch_bounds__(SGTH) k_gemm_upd(const NodeDesc* __restrict__ 
     __syncthreads();
     buf ^= 1;
   }
+  // next diagonal block held by this tile (SOLVE): rows [nb0, nb0 + njb)
+  int nb0 = 0, njb = 0;
+  if (SOLVE && blockIdx.x == 0) {
+    if (MODE == 0 && r_lo < ks) { nb0 = r_lo; njb = min(TS, ks - r_lo); }
+    if (MODE == 1 && r_hi > 0) { njb = min(TS, r_hi); nb0 = r_hi - njb; }
+  }
+  static_assert(!SOLVE || (SGR + 4) * 2 * GK >= TS * (SGC + 1), "block staging reuses As");
+  TV (*Vs)[SGC + 1] = (TV (*)[SGC + 1])&As[0][0][0];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = r0 + ty * 8 + i;
-    if (r >= r_hi) continue;
+    if (r >= r_hi || r < r_lo) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int c = c0 + tx * 8 + j;
-      if (c < m) V[(int64_t)r * m + c] -= acc[i][j];
+      if (c >= m) continue;
+      const TV v = V[(int64_t)r * m + c] - acc[i][j];
+      if (SOLVE && njb > 0 && r >= nb0 && r < nb0 + njb) Vs[r - nb0][tx * 8 + j] = v;
+      else V[(int64_t)r * m + c] = v;
+    }
+  }
+  if (SOLVE && njb > 0) {                   // uniform across the CTA
+    for (int e = tid; e < TS * TS; e += SGTH) {
+      const int r = e % TS, c = e / TS;
+      Ls[r][c] = (r < njb && c < njb && r > c) ? (TV)F[(nb0 + r) + (int64_t)(nb0 + c) * ld] : TV(0);
+    }
+    __syncthreads();
+    diag_solve<TV, MODE == 0, SGC, SGTH>(Ls, Vs, njb, tid);
+    for (int e = tid; e < njb * SGC; e += SGTH) {
+      const int r = e / SGC, c = e % SGC;
+      if (c0 + c < m) V[(int64_t)(nb0 + r) * m + c0 + c] = Vs[r][c];
     }
   }
 }
@@ -950,11 +988,13 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
         HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m));
     }
     const int nbk = (D.maxks + TS - 1) / TS;
+    constexpr bool fused = sizeof(TV) == 4;          // next diagonal block solved inside the GEMM
     for (int b = 0; b < nbk; ++b) {
-      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_trsm_diag<TF, TV, true><<<dim3((m + DiagRhs<TV>::value - 1) / DiagRhs<TV>::value, cnt), DTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
+      if (b == 0 || !fused)
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_trsm_diag<TF, TV, true><<<dim3((m + DiagRhs<TV>::value - 1) / DiagRhs<TV>::value, cnt), DTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
       const unsigned rx = (unsigned)((D.maxf - b * TS + SGR - 1) / SGR);
       if (rx > 0)
-        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0, fused><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
     HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m));
     tm.end(lev, cnt, D.maxf, D.maxks);
@@ -978,13 +1018,15 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
     HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m));
-    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 2><<<dim3((D.maxks + SGR - 1) / SGR, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, 0));
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 2, false><<<dim3((D.maxks + SGR - 1) / SGR, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, 0));
     const int nbk = (D.maxks + TS - 1) / TS;
+    constexpr bool fused = sizeof(TV) == 4;          // next diagonal block solved inside the GEMM
     for (int b = 0; b < nbk; ++b) {
-      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_trsm_diag<TF, TV, false><<<dim3((m + DiagRhs<TV>::value - 1) / DiagRhs<TV>::value, cnt), DTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
+      if (b == 0 || !fused)
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_trsm_diag<TF, TV, false><<<dim3((m + DiagRhs<TV>::value - 1) / DiagRhs<TV>::value, cnt), DTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
       const unsigned rx = (unsigned)((D.maxks - (b + 1) * TS + SGR - 1) / SGR);
       if ((int)rx > 0)
-        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1, fused><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
     HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m));
     tm.end(lev, cnt, D.maxf, D.maxks);
