@@ -274,8 +274,11 @@ def run_ours(args):
                  "MEASURED_PEAKS.json bf16_tflops_sustained"),
         "block_update": ("tensor", bf16_sus, "k_oz_mma (FP64 update P C emulated: 36 BF16 slice products)",
                          "MEASURED_PEAKS.json bf16_tflops_sustained"),
-        "trsv_fwd": ("hbm", hbm, "k_trsm_diag/k_gemm_upd forward sweep (FP32 factor)", "MEASURED_PEAKS.json hbm_gbs"),
-        "trsv_bwd": ("hbm", hbm, "k_trsm_diag/k_gemm_upd backward sweep (FP32 factor)", "MEASURED_PEAKS.json hbm_gbs"),
+        # with M ~ 400 right-hand sides the sweeps do 2 M flops per factor entry read: FP32 ALU-bound
+        "trsv_fwd": ("alu", fp32_simt, "k_gemm_upd (+ fused diagonal solves) forward sweep, FP32",
+                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
+        "trsv_bwd": ("alu", fp32_simt, "k_gemm_upd (+ fused diagonal solves) backward sweep, FP32",
+                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
         "spmm": ("hbm", hbm, "k_spmm (FP64 CSR x block)", "MEASURED_PEAKS.json hbm_gbs"),
     }
     bound, peak, kname, psrc = kinds.get(dom, ("alu", None, dom, None))
