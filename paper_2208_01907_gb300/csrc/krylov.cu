@@ -8,6 +8,8 @@
 // indexed by original unknown; rows of Lambda_2 are kept at zero in K11 blocks.
 #include "common.cuh"
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -506,63 +508,146 @@ __global__ void k_gram_reduce(int ma, int mb, int nchunks, const double* __restr
 // dependent direction, which is dropped (its row of R is zero and its coefficients are 0).
 // Solves R^T R C = Y run one warp per column of Y with warp-shuffle dot products.
 // ---------------------------------------------------------------------------
-__global__ void k_chol(int m, double* __restrict__ A, int* __restrict__ drop) {
+// ---------------------------------------------------------------------------
+// Cholesky M = R^T R of the small SPD Gram (upper R, row-major), dropping directions whose
+// pivot fell below 1e-13 of the original diagonal (reading R8), and the two triangular
+// solves C = R^-1 R^-T Y; blocked by CB rows and spread over all SMs: cooperative kernels with grid-wide barriers between
+// the phases of a block step (GB300 runs about two FP64 FMAs per clock per SM, so the
+// O(m^3) FP64 work of one SM took milliseconds at m ~ 400).
+// ---------------------------------------------------------------------------
+constexpr int CB = 32;
+
+__global__ void __launch_bounds__(256) k_chol_coop(int m, double* __restrict__ A, int* __restrict__ drop) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
   __shared__ double s_rjj;
   __shared__ int s_drop;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // keep the original diagonal in the lower triangle's first column slots is not possible
-  // (it is referenced); store it in drop[m + j] as bits of a double instead
+  const int gtid = blockIdx.x * nt + tid, gnt = gridDim.x * nt;
   double* dref = (double*)(drop + 2 * ((m + 1) / 2) + 2);
-  for (int j = tid; j < m; j += nt) dref[j] = A[j * m + j];
-  __syncthreads();
-  for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      double sj = A[j * m + j];
-      const double ref = dref[j];
-      int dz = !(sj > 1e-13 * ref) || !(ref > 0);
-      drop[j] = dz;
-      s_drop = dz;
-      s_rjj = dz ? 0.0 : sqrt(sj);
-      A[j * m + j] = s_rjj;
-    }
-    __syncthreads();
-    const double rjj = s_rjj;
-    const int dz = s_drop;
-    for (int l = j + 1 + tid; l < m; l += nt) A[j * m + l] = dz ? 0.0 : A[j * m + l] / rjj;
-    __syncthreads();
-    if (!dz) {
-      const int n2 = m - j - 1;
-      for (int e = tid; e < n2 * n2; e += nt) {
-        int a = j + 1 + e / n2, b = j + 1 + e % n2;
-        if (b >= a) A[a * m + b] -= A[j * m + a] * A[j * m + b];
+  for (int j = gtid; j < m; j += gnt) dref[j] = A[j * m + j];
+  grid.sync();
+  for (int jb = 0; jb < m; jb += CB) {
+    const int je = min(m, jb + CB);
+    // 1. the diagonal block, right-looking inside the block (block 0)
+    if (blockIdx.x == 0) {
+      for (int j = jb; j < je; ++j) {
+        if (tid == 0) {
+          const double sj = A[j * m + j];
+          const double ref = dref[j];
+          const int dz = !(sj > 1e-13 * ref) || !(ref > 0);
+          drop[j] = dz;
+          s_drop = dz;
+          s_rjj = dz ? 0.0 : sqrt(sj);
+          A[j * m + j] = s_rjj;
+        }
+        __syncthreads();
+        const double rjj = s_rjj;
+        const int dz = s_drop;
+        for (int l = j + 1 + tid; l < je; l += nt) A[j * m + l] = dz ? 0.0 : A[j * m + l] / rjj;
+        __syncthreads();
+        if (!dz) {
+          const int n2 = je - j - 1;
+          for (int e = tid; e < n2 * n2; e += nt) {
+            const int a = j + 1 + e / n2, b = j + 1 + e % n2;
+            if (b >= a) A[a * m + b] -= A[j * m + a] * A[j * m + b];
+          }
+        }
+        __syncthreads();
       }
     }
-    __syncthreads();
+    grid.sync();
+    // 2. rows [jb, je) right of the block: forward substitution with the block, per column
+    for (int l = je + gtid; l < m; l += gnt) {
+      double x[CB];
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const int j = jb + u;
+        if (j < je) {
+          double v = A[j * m + l];
+#pragma unroll
+          for (int w = 0; w < u; ++w) v -= A[(jb + w) * m + j] * x[w];
+          x[u] = drop[j] ? 0.0 : v / A[j * m + j];
+          A[j * m + l] = x[u];
+        }
+      }
+    }
+    grid.sync();
+    // 3. trailing update of the upper triangle [je, m)^2
+    const int n2 = m - je;
+    for (int64_t e = gtid; e < (int64_t)n2 * n2; e += gnt) {
+      const int a = je + (int)(e / n2), b = je + (int)(e % n2);
+      if (b < a) continue;
+      double acc = 0.0;
+      for (int k = jb; k < je; ++k) acc += A[k * m + a] * A[k * m + b];
+      A[a * m + b] -= acc;
+    }
+    grid.sync();
   }
 }
 
-// C = R^-1 R^-T Y (dropped directions give zero rows); one warp per column of Y
-__global__ void k_chol_solve(int m, int ny, const double* __restrict__ R, const int* __restrict__ drop,
-                             const double* __restrict__ Y, double* __restrict__ C) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= ny) return;
-  const int c = warp;
-  // forward: R^T z = y  (z_j = (y_j - sum_{k<j} R_kj z_k) / R_jj)
-  for (int j = 0; j < m; ++j) {
-    double part = 0.0;
-    for (int k = lane; k < j; k += 32) part += R[k * m + j] * C[k * ny + c];
-    part = warp_sum(part);
-    if (lane == 0) C[j * ny + c] = drop[j] ? 0.0 : (Y[j * ny + c] - part) / R[j * m + j];
-    __syncwarp();
+// C = R^-1 R^-T Y (dropped directions give zero rows), m x ny row-major, blocked
+__global__ void __launch_bounds__(256) k_chol_solve_coop(int m, int ny, const double* __restrict__ R,
+                                                       const int* __restrict__ drop, const double* __restrict__ Y,
+                                                       double* __restrict__ C) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gnt = gridDim.x * blockDim.x;
+  for (int64_t e = gtid; e < (int64_t)m * ny; e += gnt) C[e] = Y[e];
+  grid.sync();
+  // forward: R^T z = y
+  for (int jb = 0; jb < m; jb += CB) {
+    const int je = min(m, jb + CB);
+    for (int c = gtid; c < ny; c += gnt) {
+      double x[CB];
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const int j = jb + u;
+        if (j < je) {
+          double v = C[(int64_t)j * ny + c];
+#pragma unroll
+          for (int w = 0; w < u; ++w) v -= R[(jb + w) * m + j] * x[w];
+          x[u] = drop[j] ? 0.0 : v / R[j * m + j];
+          C[(int64_t)j * ny + c] = x[u];
+        }
+      }
+    }
+    grid.sync();
+    const int nr = m - je;
+    for (int64_t e = gtid; e < (int64_t)nr * ny; e += gnt) {
+      const int i = je + (int)(e / ny), c = (int)(e % ny);
+      double acc = 0.0;
+      for (int k = jb; k < je; ++k) acc += R[k * m + i] * C[(int64_t)k * ny + c];
+      C[(int64_t)i * ny + c] -= acc;
+    }
+    grid.sync();
   }
-  // backward: R x = z  (x_j = (z_j - sum_{k>j} R_jk x_k) / R_jj)
-  for (int j = m - 1; j >= 0; --j) {
-    double part = 0.0;
-    for (int k = j + 1 + lane; k < m; k += 32) part += R[j * m + k] * C[k * ny + c];
-    part = warp_sum(part);
-    if (lane == 0) C[j * ny + c] = drop[j] ? 0.0 : (C[j * ny + c] - part) / R[j * m + j];
-    __syncwarp();
+  // backward: R x = z, blocks from the bottom
+  for (int je = m; je > 0; je -= CB) {
+    const int jb = max(0, je - CB);
+    for (int c = gtid; c < ny; c += gnt) {
+      double x[CB];
+#pragma unroll
+      for (int u = CB - 1; u >= 0; --u) {
+        const int j = jb + u;
+        if (j < je) {
+          double v = C[(int64_t)j * ny + c];
+#pragma unroll
+          for (int w = u + 1; w < CB; ++w)
+            if (jb + w < je) v -= R[j * m + jb + w] * x[w];
+          x[u] = drop[j] ? 0.0 : v / R[j * m + j];
+          C[(int64_t)j * ny + c] = x[u];
+        }
+      }
+    }
+    grid.sync();
+    for (int64_t e = gtid; e < (int64_t)jb * ny; e += gnt) {
+      const int i = (int)(e / ny), c = (int)(e % ny);
+      double acc = 0.0;
+      for (int k = jb; k < je; ++k) acc += R[i * m + k] * C[(int64_t)k * ny + c];
+      C[(int64_t)i * ny + c] -= acc;
+    }
+    grid.sync();
   }
 }
 
@@ -1137,6 +1222,25 @@ static void spmm(hf_ctx* c, int m, const double* W, double* Z) {
 }
 
 // Block GCR for K11 X = B (Sec. 3.5, readings R7/R8).  B, X: L x m row-major, Lambda_2 rows 0.
+// Grid of the cooperative kernels: every block must be resident at once
+static int coop_grid(hf_ctx* c) {
+  static std::mutex mu;
+  static int blocks = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!blocks) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int p1 = 0, p2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_chol_coop, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_chol_solve_coop, 256, 0);
+    per = std::min(p1, p2);
+    blocks = std::max(1, sms * std::min(per, 2));
+  }
+  (void)c;
+  return blocks;
+}
+
 static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, double* relres) {
   cudaStream_t s = hf_stream(c);
   const int64_t L = c->L;
@@ -1231,16 +1335,26 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   int it = 0;
   double res = 0;
   bool conv = false;
-  auto msolve = [&](int q, const double* Y, double* C) {
-    HF_LAUNCH(c, HF_PROF_VECTOR, k_chol_solve<<<nblk((int64_t)m * 32, 256), 256, 0, s>>>(m, m, Mstore + (size_t)q * mm,
-                                                                                    dropv + (size_t)q * dstride, Y, C));
+  const int cgrid = coop_grid(c);
+  auto msolve = [&](int q, const double* Y, double* C) -> int {
+    const double* Rq = Mstore + (size_t)q * mm;
+    const int* dq = dropv + (size_t)q * dstride;
+    int mm_ = m, ny = m;
+    void* args[] = {&mm_, &ny, (void*)&Rq, (void*)&dq, (void*)&Y, (void*)&C};
+    HF_LAUNCH(c, HF_PROF_VECTOR, HF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_solve_coop, cgrid, 256, args, 0, s)));
+    return HF_OK;
   };
   for (int n = 0; n < maxit; ++n) {
     double* Mn = Mstore + (size_t)n * mm;
     if ((rc = gram(c, L, m, m, Qm(n), Qm(n), Mn, 1.0))) return rc;
-    HF_LAUNCH(c, HF_PROF_VECTOR, k_chol<<<1, 1024, 0, s>>>(m, Mn, dropv + (size_t)n * dstride));   // M_n = R^T R
+    {                                                                                       // M_n = R^T R
+      int mm_ = m;
+      int* dn = dropv + (size_t)n * dstride;
+      void* args[] = {&mm_, (void*)&Mn, (void*)&dn};
+      HF_LAUNCH(c, HF_PROF_VECTOR, HF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_coop, cgrid, 256, args, 0, s)));
+    }
     if ((rc = gram(c, L, m, m, Qm(n), R, Gm, 1.0))) return rc;
-    msolve(n, Gm, Cm);
+    if ((rc = msolve(n, Gm, Cm))) return rc;
     if ((rc = block_update(Pm(n), Cm, X, nullptr, 1.0))) return rc;
     if ((rc = block_update(Qm(n), Cm, R, nullptr, -1.0))) return rc;
     HF_CUDA_TRY(cudaGetLastError());
@@ -1275,7 +1389,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     double* Qn = Qm(n + 1);
     for (int q = 0; q <= n; ++q) {
       if ((rc = gram(c, L, m, m, Qm(q), Z, Gm, -1.0))) return rc;      // B_qn = -Q_q^T Z
-      msolve(q, Gm, Cm);
+      if ((rc = msolve(q, Gm, Cm))) return rc;
       if ((rc = block_update(Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0))) return rc;
     }
     // Q_{n+1} = K11 P_{n+1}: one FP64 SpMM instead of the n+1 dense recurrence terms (reading R14)
