@@ -82,6 +82,7 @@ struct hf_ctx {
   DevBuf d_cbmap;                    // per front: parent row of each contribution row (ld entries)
   DevBuf d_q, d_kval;                // scaling diag(Q) and scaled K values (FP64)
   DevBuf d_front;                    // front arena (float or double)
+  DevBuf d_bpart;                    // per-block partial maxima of the cooperative S22 LDL^T
   DevBuf d_tparts;                   // BF16 parts of the current panel (tensor-core trailing update)
   DevBuf d_gmag;                     // per front row: |K_ii| + accumulated |l|^2 |d| (null-pivot test)
   DevBuf d_pos0;                     // per front row: its position before pivoting

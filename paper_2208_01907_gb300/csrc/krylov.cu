@@ -755,6 +755,57 @@ __device__ void bp_swap(double* A, double* Lf, int* perm, int M, int a, int b) {
   __syncthreads();
 }
 
+// Kernel detection after the S22 LDL^T (reading R10): magnitudes per 1x1 pivot / 2x2
+// eigenvalue, sorted; the kernel is the tail after the largest ratio gap >= kernel_gap
+// whose entries are below max(kernel_eps * scale, noise); one thread.
+__device__ void bp_kernel_rule(int M, const int* __restrict__ blk, const double* __restrict__ dval,
+                               int* __restrict__ nullp, double kernel_eps, double kernel_gap,
+                               const int32_t* __restrict__ lam2, const int64_t* __restrict__ diagpos,
+                               const double* __restrict__ kval, double noise, int* __restrict__ kdim_out,
+                               double* __restrict__ mags_work) {
+  double ref = 0.0;                // max |K_ii| over Lambda_2: the unit reference
+  for (int i = 0; i < M; ++i) ref = fmax(ref, fabs(kval[diagpos[lam2[i]]]));
+  double* mg = mags_work;          // M magnitudes, then M sorted copies
+  for (int i = 0; i < M;) {
+    if (blk[i] == 1) { mg[i] = fabs(dval[2 * i]); ++i; }
+    else {
+      double a = dval[2 * i], b = dval[2 * i + 1], c = dval[2 * (i + 1)];
+      double mean = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + b * b);
+      mg[i] = fabs(mean + rad); mg[i + 1] = fabs(mean - rad);
+      i += 2;
+    }
+  }
+  double* s = mg + M;
+  for (int i = 0; i < M; ++i) s[i] = mg[i];
+  for (int i = 1; i < M; ++i) {               // insertion sort, descending
+    double v = s[i]; int j = i - 1;
+    while (j >= 0 && s[j] < v) { s[j + 1] = s[j]; --j; }
+    s[j + 1] = v;
+  }
+  int dim = 0;
+  if (M > 0) {
+    const double scale = fmax(s[0], ref);
+    const double thr = fmax(kernel_eps * scale, noise);
+    if (scale == 0.0 || s[0] <= thr) dim = M;
+    else {
+      double best = 0.0;
+      for (int i = 1; i < M; ++i) {
+        if (s[i] > thr) continue;
+        double ratio = (s[i] == 0.0) ? INFINITY : s[i - 1] / s[i];
+        if (ratio >= kernel_gap && ratio > best) { best = ratio; dim = M - i; }
+      }
+    }
+  }
+  *kdim_out = dim;
+  // mark the `dim` smallest magnitudes as null pivots (ties: later position first)
+  for (int cnt = 0; cnt < dim; ++cnt) {
+    int bi = -1; double bv = INFINITY;
+    for (int i = 0; i < M; ++i)
+      if (!nullp[i] && (mg[i] < bv || (mg[i] == bv && i > bi))) { bv = mg[i]; bi = i; }
+    if (bi >= 0) nullp[bi] = 1;
+  }
+}
+
 __global__ void k_bunch_parlett(int M, double* __restrict__ A, double* __restrict__ Lf, int* __restrict__ perm,
                                 int* __restrict__ blk, double* __restrict__ dval, int* __restrict__ nullp,
                                 double kernel_eps, double kernel_gap, const int32_t* __restrict__ lam2,
@@ -830,50 +881,175 @@ __global__ void k_bunch_parlett(int M, double* __restrict__ A, double* __restric
       k += 2;
     }
   }
-  // kernel detection (reading R10): magnitudes per 1x1 pivot / 2x2 eigenvalue
-  if (tid == 0) {
-    double ref = 0.0;                // max |K_ii| over Lambda_2: the unit reference
-    for (int i = 0; i < M; ++i) ref = fmax(ref, fabs(kval[diagpos[lam2[i]]]));
-    double* mg = mags_work;          // M magnitudes, then M sorted copies
-    for (int i = 0; i < M;) {
-      if (blk[i] == 1) { mg[i] = fabs(dval[2 * i]); ++i; }
-      else {
-        double a = dval[2 * i], b = dval[2 * i + 1], c = dval[2 * (i + 1)];
-        double mean = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + b * b);
-        mg[i] = fabs(mean + rad); mg[i + 1] = fabs(mean - rad);
-        i += 2;
-      }
-    }
-    double* s = mg + M;
-    for (int i = 0; i < M; ++i) s[i] = mg[i];
-    for (int i = 1; i < M; ++i) {               // insertion sort, descending
-      double v = s[i]; int j = i - 1;
-      while (j >= 0 && s[j] < v) { s[j + 1] = s[j]; --j; }
-      s[j + 1] = v;
-    }
-    int dim = 0;
-    if (M > 0) {
-      const double scale = fmax(s[0], ref);
-      const double thr = fmax(kernel_eps * scale, noise);
-      if (scale == 0.0 || s[0] <= thr) dim = M;
-      else {
-        double best = 0.0;
-        for (int i = 1; i < M; ++i) {
-          if (s[i] > thr) continue;
-          double ratio = (s[i] == 0.0) ? INFINITY : s[i - 1] / s[i];
-          if (ratio >= kernel_gap && ratio > best) { best = ratio; dim = M - i; }
+  if (tid == 0)
+    bp_kernel_rule(M, blk, dval, nullp, kernel_eps, kernel_gap, lam2, diagpos, kval, noise, kdim_out, mags_work);
+}
+
+// ---------------------------------------------------------------------------
+// The same Bunch-Parlett LDL^T (complete pivoting, alpha = (1+sqrt 17)/8, the same tie
+// rules and the same physical row/column swaps, so the same pivot order), spread over all
+// SMs: a cooperative kernel with grid-wide barriers between the phases of a pivot step.
+// The two maxima use the bit patterns of |a| as integer keys (non-negative FP64 values
+// order like their bit patterns; NaN is never chosen, as with the FP64 comparisons), so
+// the O(M^2) search per step runs on the integer units instead of the FP64 pipe.
+// ---------------------------------------------------------------------------
+struct BpPart {
+  long long v0, i0, v1, j1;      // max |a_ii| key and i; max |a_ij| (i > j) key and j*M+i
+};
+
+__device__ __forceinline__ long long abs_key(double x) {
+  const long long b = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  return b > 0x7FF0000000000000LL ? -1LL : b;
+}
+
+__device__ __forceinline__ void bp_better(long long& v, long long& k, long long ov, long long ok) {
+  if (ov > v || (ov == v && ok < k)) { v = ov; k = ok; }
+}
+
+constexpr int BP_THREADS = 256;
+constexpr int BP_MAX_M = 2048;   // Lf columns of a step staged in shared memory (2 x M doubles)
+
+__global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restrict__ A, double* __restrict__ Lf,
+                                                        int* __restrict__ perm, int* __restrict__ blk,
+                                                        double* __restrict__ dval, int* __restrict__ nullp,
+                                                        double kernel_eps, double kernel_gap,
+                                                        const int32_t* __restrict__ lam2,
+                                                        const int64_t* __restrict__ diagpos,
+                                                        const double* __restrict__ kval, double noise,
+                                                        int* __restrict__ kdim_out, double* __restrict__ mags_work,
+                                                        BpPart* __restrict__ parts) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ double lcol[];                 // 2 x M: the new Lf column(s) of the step
+  __shared__ long long w0[BP_THREADS / 32], wi0[BP_THREADS / 32], w1[BP_THREADS / 32], wj1[BP_THREADS / 32];
+  __shared__ int s_act, s_a, s_b;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int gtid = blockIdx.x * nt + tid, gnt = gridDim.x * nt;
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  for (int64_t e = gtid; e < (int64_t)M * M; e += gnt) Lf[e] = ((e / M) == (e % M)) ? 1.0 : 0.0;
+  for (int i = gtid; i < M; i += gnt) { perm[i] = i; blk[i] = 0; dval[2 * i] = 0; dval[2 * i + 1] = 0; nullp[i] = 0; }
+  grid.sync();
+  // the symmetric swap of positions a < b (rows, then columns, as one set of disjoint pair
+  // exchanges), the rows of Lf left of a, and perm
+  auto swap_pos = [&](int a, int b) {
+    if (a == b) return;
+    const int np = 2 * M + a;
+    for (int e = gtid; e < np; e += gnt) {
+      int64_t x, y;
+      if (e < M) {                                 // row pairs (a, j) <-> (b, j), j not in {a, b}
+        const int j = e;
+        if (j == a || j == b) continue;
+        x = (int64_t)a * M + j; y = (int64_t)b * M + j;
+      } else if (e < 2 * M) {                      // column pairs (i, a) <-> (i, b)
+        const int i = e - M;
+        if (i == a || i == b) {
+          if (i != a) continue;                    // the 2 x 2 corner once: (a,a)<->(b,b), (a,b)<->(b,a)
+          double t = A[(int64_t)a * M + a]; A[(int64_t)a * M + a] = A[(int64_t)b * M + b]; A[(int64_t)b * M + b] = t;
+          t = A[(int64_t)a * M + b]; A[(int64_t)a * M + b] = A[(int64_t)b * M + a]; A[(int64_t)b * M + a] = t;
+          continue;
         }
+        x = (int64_t)i * M + a; y = (int64_t)i * M + b;
+      } else {                                     // Lf rows left of a
+        const int j = e - 2 * M;
+        const double t = Lf[(int64_t)a * M + j]; Lf[(int64_t)a * M + j] = Lf[(int64_t)b * M + j]; Lf[(int64_t)b * M + j] = t;
+        continue;
       }
+      const double t = A[x]; A[x] = A[y]; A[y] = t;
     }
-    *kdim_out = dim;
-    // mark the `dim` smallest magnitudes as null pivots (ties: later position first)
-    for (int cnt = 0; cnt < dim; ++cnt) {
-      int bi = -1; double bv = INFINITY;
-      for (int i = 0; i < M; ++i)
-        if (!nullp[i] && (mg[i] < bv || (mg[i] == bv && i > bi))) { bv = mg[i]; bi = i; }
-      if (bi >= 0) nullp[bi] = 1;
+    if (gtid == 0) { const int t = perm[a]; perm[a] = perm[b]; perm[b] = t; }
+  };
+  int k = 0, it = 0;
+  while (k < M) {
+    BpPart* pp = parts + (it & 1) * gridDim.x;
+    // 1. the two maxima, per block
+    long long v0 = -1, i0 = 0x7fffffffffffffffLL, v1 = -1, j1 = 0x7fffffffffffffffLL;
+    for (int i = k + gtid; i < M; i += gnt) bp_better(v0, i0, abs_key(A[(int64_t)i * M + i]), i);
+    const int n2 = M - k;
+    for (long long e = gtid; e < (long long)n2 * n2; e += gnt) {
+      const int j = k + (int)(e / n2), i = k + (int)(e % n2);
+      if (i <= j) continue;
+      bp_better(v1, j1, abs_key(A[(int64_t)i * M + j]), (long long)j * M + i);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bp_better(v0, i0, __shfl_xor_sync(0xffffffffu, v0, o), __shfl_xor_sync(0xffffffffu, i0, o));
+      bp_better(v1, j1, __shfl_xor_sync(0xffffffffu, v1, o), __shfl_xor_sync(0xffffffffu, j1, o));
+    }
+    if ((tid & 31) == 0) { w0[tid >> 5] = v0; wi0[tid >> 5] = i0; w1[tid >> 5] = v1; wj1[tid >> 5] = j1; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < nt / 32; ++w) { bp_better(v0, i0, w0[w], wi0[w]); bp_better(v1, j1, w1[w], wj1[w]); }
+      pp[blockIdx.x] = BpPart{v0, i0, v1, j1};
+    }
+    grid.sync();
+    // 2. the decision, the same in every block
+    if (tid == 0) {
+      long long g0 = -1, gi = 0x7fffffffffffffffLL, g1 = -1, gj = 0x7fffffffffffffffLL;
+      for (int b = 0; b < (int)gridDim.x; ++b) { bp_better(g0, gi, pp[b].v0, pp[b].i0); bp_better(g1, gj, pp[b].v1, pp[b].j1); }
+      const double mu0 = g0 < 0 ? -1.0 : __longlong_as_double(g0);
+      double mu1 = g1 < 0 ? -1.0 : __longlong_as_double(g1);
+      if (mu1 < 0) mu1 = 0.0;
+      int act;
+      if (mu0 == 0.0 && mu1 == 0.0) act = 0;            // the rest is exactly zero: zero 1x1 pivots
+      else if (mu0 >= alpha * mu1) act = 1;
+      else act = 2;
+      s_act = act;
+      s_a = act == 1 ? (int)gi : (int)(gj / M);
+      s_b = act == 2 ? (int)(gj % M) : 0;
+    }
+    __syncthreads();
+    const int act = s_act;
+    if (act == 0) {
+      if (gtid == 0) { blk[k] = 1; dval[2 * k] = 0.0; }
+      k += 1; ++it;
+      continue;
+    }
+    if (act == 1) {
+      swap_pos(k, s_a);
+      grid.sync();
+      const double dk = A[(int64_t)k * M + k];
+      if (gtid == 0) { blk[k] = 1; dval[2 * k] = dk; }
+      for (int i = k + 1 + tid; i < M; i += nt) {
+        const double l = A[(int64_t)i * M + k] / dk;
+        lcol[i] = l;
+        if (blockIdx.x == 0) Lf[(int64_t)i * M + k] = l;
+      }
+      __syncthreads();
+      const int m2 = M - k - 1;
+      for (long long e = gtid; e < (long long)m2 * m2; e += gnt) {
+        const int i = k + 1 + (int)(e / m2), j = k + 1 + (int)(e % m2);
+        A[(int64_t)i * M + j] -= lcol[i] * A[(int64_t)j * M + k];
+      }
+      grid.sync();
+      k += 1; ++it;
+    } else {
+      swap_pos(k, s_a);
+      grid.sync();
+      swap_pos(k + 1, s_b);
+      grid.sync();
+      const double a = A[(int64_t)k * M + k], b = A[(int64_t)(k + 1) * M + k], cc = A[(int64_t)(k + 1) * M + k + 1];
+      const double det = a * cc - b * b;
+      if (gtid == 0) { blk[k] = 2; blk[k + 1] = 0; dval[2 * k] = a; dval[2 * k + 1] = b; dval[2 * (k + 1)] = cc; }
+      for (int i = k + 2 + tid; i < M; i += nt) {
+        const double x0 = A[(int64_t)i * M + k], x1 = A[(int64_t)i * M + k + 1];
+        const double l0 = (x0 * cc - x1 * b) / det, l1 = (x1 * a - x0 * b) / det;
+        lcol[i] = l0;
+        lcol[M + i] = l1;
+        if (blockIdx.x == 0) { Lf[(int64_t)i * M + k] = l0; Lf[(int64_t)i * M + k + 1] = l1; }
+      }
+      __syncthreads();
+      const int m2 = M - k - 2;
+      for (long long e = gtid; e < (long long)m2 * m2; e += gnt) {
+        const int i = k + 2 + (int)(e / m2), j = k + 2 + (int)(e % m2);
+        A[(int64_t)i * M + j] -= lcol[i] * A[(int64_t)j * M + k] + lcol[M + i] * A[(int64_t)j * M + k + 1];
+      }
+      grid.sync();
+      k += 2; ++it;
     }
   }
+  grid.sync();
+  if (blockIdx.x == 0 && tid == 0)
+    bp_kernel_rule(M, blk, dval, nullp, kernel_eps, kernel_gap, lam2, diagpos, kval, noise, kdim_out, mags_work);
 }
 
 // x = S22^+ y with null pivots treated as zero; y, x: M x m row-major. One CTA.
@@ -1421,10 +1597,43 @@ static int bk_factor(hf_ctx* c) {
   HF_CUDA_TRY(cudaMemcpyAsync(A, c->d_s22.p, (size_t)M * M * 8, cudaMemcpyDeviceToDevice, s));
   int* kd = (int*)((int*)c->d_flags.p + FLAG_COUNT + 8);
   double* mags = (double*)c->d_bk_dval.p + 2 * M;
-  HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
-                                    (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
-                                    c->opts.kernel_gap, (const int32_t*)c->d_lam2.p, (const int64_t*)c->d_diagpos.p,
-                                    (const double*)c->d_kval.p, c->s22_noise, kd, mags));
+  if (M <= BP_MAX_M) {
+    // over all SMs (cooperative); partial maxima of two steps in flight per block
+    static std::mutex bp_mu;
+    static int bp_blocks = 0;
+    {
+      std::lock_guard<std::mutex> lk(bp_mu);
+      if (!bp_blocks) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        HF_CUDA_TRY(cudaFuncSetAttribute(k_bp_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BP_MAX_M * 8));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bp_coop, BP_THREADS, 2 * BP_MAX_M * 8);
+        bp_blocks = std::max(1, sms * std::min(std::max(per, 1), 2));
+      }
+    }
+    if ((rc = hf_ensure(c->d_bpart, (size_t)2 * bp_blocks * sizeof(BpPart) + 64))) return rc;
+    double* Lf = (double*)c->d_bk_lf.p;
+    int* pm = (int*)c->d_bk_perm.p;
+    int* bk = (int*)c->d_bk_blk.p;
+    double* dv = (double*)c->d_bk_dval.p;
+    int* nl = (int*)c->d_bk_null.p;
+    double keps = c->opts.kernel_eps, kgap = c->opts.kernel_gap, noise = c->s22_noise;
+    const int32_t* l2 = (const int32_t*)c->d_lam2.p;
+    const int64_t* dp = (const int64_t*)c->d_diagpos.p;
+    const double* kv = (const double*)c->d_kval.p;
+    BpPart* parts = (BpPart*)c->d_bpart.p;
+    int Mi = M;
+    void* args[] = {&Mi, (void*)&A, (void*)&Lf, (void*)&pm, (void*)&bk, (void*)&dv, (void*)&nl, &keps, &kgap,
+                    (void*)&l2, (void*)&dp, (void*)&kv, &noise, (void*)&kd, (void*)&mags, (void*)&parts};
+    HF_LAUNCH(c, HF_PROF_DENSE_LDLT, HF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bp_coop, bp_blocks, BP_THREADS,
+                                                                             args, 2 * (size_t)M * 8, s)));
+  } else {
+    HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
+                                      (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
+                                      c->opts.kernel_gap, (const int32_t*)c->d_lam2.p, (const int64_t*)c->d_diagpos.p,
+                                      (const double*)c->d_kval.p, c->s22_noise, kd, mags));
+  }
   HF_CUDA_TRY(cudaGetLastError());
   int h = 0;
   HF_CUDA_TRY(cudaMemcpyAsync(&h, kd, 4, cudaMemcpyDeviceToHost, s));
