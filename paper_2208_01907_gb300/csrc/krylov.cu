@@ -1411,7 +1411,7 @@ static int coop_grid(hf_ctx* c) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_chol_coop, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_chol_solve_coop, 256, 0);
     per = std::min(p1, p2);
-    blocks = std::max(1, sms * std::min(per, 2));
+    blocks = std::max(1, sms * std::min(per, 1));
   }
   (void)c;
   return blocks;
@@ -1609,7 +1609,7 @@ static int bk_factor(hf_ctx* c) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         HF_CUDA_TRY(cudaFuncSetAttribute(k_bp_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BP_MAX_M * 8));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bp_coop, BP_THREADS, 2 * BP_MAX_M * 8);
-        bp_blocks = std::max(1, sms * std::min(std::max(per, 1), 2));
+        bp_blocks = std::max(1, sms * std::min(std::max(per, 1), 1));
       }
     }
     if ((rc = hf_ensure(c->d_bpart, (size_t)2 * bp_blocks * sizeof(BpPart) + 64))) return rc;
