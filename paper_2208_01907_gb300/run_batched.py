@@ -51,6 +51,38 @@ def main():
         hf.schur_batched(bat)
         hf.solve_batched(bat, bs, xs)
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        # one process per GPU (torchrun): LPT shares of the systems, no collective in the
+        # data path, results gathered on rank 0 (paper_2208_01907_gb300.shard)
+        import torch.distributed as dist
+        from paper_2208_01907_gb300.shard import estimated_cost, run_sharded
+        rank = int(os.environ["RANK"])
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+        costs = [estimated_cost(s.L) for s in systems]
+
+        def share(idx):
+            hs = [bat[i] for i in idx]
+            hf.factorize_batched(hs, [vals[i] for i in idx], 1e-2)
+            hf.schur_batched(hs)
+            hf.solve_batched(hs, [bs[i] for i in idx], [xs[i] for i in idx])
+            return {i: int(bat[i].info()["M"]) for i in idx}
+
+        dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ms = run_sharded(len(systems), costs, share, rank, world)
+        torch.cuda.synchronize()
+        dist.barrier()
+        dt = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"workload": f"batched_{args.count}_2d_L{args.lmin}-{args.lmax}_nrhs{args.nrhs}",
+                              "systems": args.count, "n_gpus": world, "ms": dt * 1e3,
+                              "systems_per_s": args.count / dt, "M_total": int(sum(Ms))}))
+        dist.destroy_process_group()
+        return
+
     res = {}
     for name, fn in (("one_by_one", run_one), ("batched", run_batched)):
         fn()                                   # warm-up (allocations, delayed-row capacity)
