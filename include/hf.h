@@ -283,6 +283,17 @@ int hf_get_factor(hf_ctx* ctx, int64_t* col_ptr, int32_t* row_idx, double* val, 
  *   s22  M x M row-major, rows/cols in ascending Lambda_2 order
  */
 int hf_get_x12(hf_ctx* ctx, double* x12, int64_t ldx12);
+
+/*
+ * Kernel basis of K-bar (mixed form, after hf_schur; Sec. 3: the null pivots of the S22
+ * LDL^T carry the kernel of K).  For each of the info.kernel_dim null pivot directions v
+ * of the S22 factorization, n2 = P Lf^-T v is a null vector of S22 and
+ * Q [-X12 n2 ; n2] (Lambda_2 rows from n2, the others from -X12 n2, unscaled by Q) is a
+ * null vector of K-bar.  basis: device, L x kernel_dim column-major, ldb >= L (not
+ * normalised, not orthogonalised).  HF_ERR_STATE before hf_schur or for the FP64 / FP32
+ * forms (no X12 is kept there); nothing is written when kernel_dim = 0.
+ */
+int hf_get_kernel_basis(hf_ctx* ctx, double* basis, int64_t ldb);
 int hf_get_s22(hf_ctx* ctx, double* s22);
 
 /*

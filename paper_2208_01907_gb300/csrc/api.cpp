@@ -16,6 +16,7 @@ int hf_schur_impl(hf_ctx* c);
 int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W);
 int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W);
+int hf_kernel_basis_impl(hf_ctx* c, double* basis, int64_t ldb);
 int hf_values_adjoint_impl(hf_ctx* c, int m, const double* x, int64_t ldx, const double* lam, int64_t ldl,
                            double* grad);
 
@@ -424,6 +425,11 @@ int hf_get_x12(hf_ctx* c, double* x12, int64_t ldx12) {
   if (c->M == 0) return HF_OK;
   cudaError_t e = cudaMemcpy2D(x12, ldx12 * 8, c->d_x12.p, c->M * 8, c->M * 8, c->L, cudaMemcpyDeviceToDevice);
   return e == cudaSuccess ? HF_OK : hf_cuda_error(e);
+}
+
+int hf_get_kernel_basis(hf_ctx* c, double* basis, int64_t ldb) {
+  if (!c) return HF_ERR_ARG;
+  return hf_kernel_basis_impl(c, basis, ldb);
 }
 
 int hf_get_s22(hf_ctx* c, double* s22) {

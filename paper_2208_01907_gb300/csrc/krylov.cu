@@ -1052,6 +1052,75 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restric
     bp_kernel_rule(M, blk, dval, nullp, kernel_eps, kernel_gap, lam2, diagpos, kval, noise, kdim_out, mags_work);
 }
 
+// Null vectors of S22 from its LDL^T (one CTA): for every null pivot direction v (e_i for
+// a 1x1 null pivot, the eigenvector of the null eigenvalue of a 2x2 block), y = Lf^-T v
+// and n2 = P y, so that S22 n2 = P Lf D v = 0 up to the null pivot.  N2: M x kdim,
+// column-major; w: M doubles of work.
+__global__ void k_s22_nullvecs(int M, const double* __restrict__ Lf, const int* __restrict__ perm,
+                               const int* __restrict__ blk, const double* __restrict__ dval,
+                               const int* __restrict__ nullp, int kdim, double* __restrict__ N2,
+                               double* __restrict__ w) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int s_pos;
+  int d = 0;
+  for (int i = 0; i < M && d < kdim; ++i) {
+    if (!nullp[i]) continue;
+    // v: the null direction at position i (within its pivot block)
+    for (int e = tid; e < M; e += nt) w[e] = 0.0;
+    __syncthreads();
+    if (tid == 0) {
+      const int start = (blk[i] == 0) ? i - 1 : i;   // second row of a 2x2 belongs to the block at i-1
+      if (blk[start] == 1) {
+        w[i] = 1.0;
+      } else {
+        const double a = dval[2 * start], b = dval[2 * start + 1], cc = dval[2 * (start + 1)];
+        const double mean = 0.5 * (a + cc), rad = sqrt(0.25 * (a - cc) * (a - cc) + b * b);
+        const int q = i - start;                       // eigenvalue mean + rad (q = 0) or mean - rad
+        const double ev = q == 0 ? mean + rad : mean - rad;
+        double vx = b, vy = ev - a;
+        if (fabs(vx) + fabs(vy) < 1e-300) { vx = ev - cc; vy = b; }
+        if (fabs(vx) + fabs(vy) < 1e-300) { vx = (q == 0) ? 1.0 : 0.0; vy = (q == 0) ? 0.0 : 1.0; }
+        const double nr = sqrt(vx * vx + vy * vy);
+        w[start] = vx / nr;
+        w[start + 1] = vy / nr;
+      }
+      s_pos = d;
+    }
+    __syncthreads();
+    // y = Lf^-T w, from the last row up (Lf unit lower, row-major)
+    for (int j = M - 1; j >= 0; --j) {
+      const double yj = w[j];
+      __syncthreads();
+      for (int r = tid; r < j; r += nt) w[r] -= Lf[(int64_t)j * M + r] * yj;
+      __syncthreads();
+    }
+    for (int r = tid; r < M; r += nt) N2[(int64_t)s_pos * M + perm[r]] = w[r];
+    __syncthreads();
+    ++d;
+  }
+}
+
+// Kernel basis of K-bar: column c = Q [-X12 n2_c ; n2_c] in original unknowns
+// (X12: L x M row-major, zero on Lambda_2 rows; basis: L x kdim column-major, ld ldb).
+__global__ void k_kernel_basis(int64_t L, int M, int kdim, const double* __restrict__ X12,
+                               const double* __restrict__ N2, const int32_t* __restrict__ lam2pos,
+                               const double* __restrict__ q, double* __restrict__ basis, int64_t ldb) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (r >= L || c >= kdim) return;
+  const double* n2 = N2 + (int64_t)c * M;
+  double x;
+  const int p = lam2pos[r];
+  if (p >= 0) {
+    x = n2[p];
+  } else {
+    double acc = 0.0;
+    for (int j = 0; j < M; ++j) acc += X12[r * M + j] * n2[j];
+    x = -acc;
+  }
+  basis[(int64_t)c * ldb + r] = q[r] * x;
+}
+
 // x = S22^+ y with null pivots treated as zero; y, x: M x m row-major. One CTA.
 __global__ void k_bk_solve(int M, int m, const double* __restrict__ Lf, const int* __restrict__ perm,
                            const int* __restrict__ blk, const double* __restrict__ dval, const int* __restrict__ nullp,
@@ -1854,5 +1923,28 @@ int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W) {
   c->prof_on = prof;
   if (rc) return rc;
   HF_CUDA_TRY(cudaStreamSynchronize(hf_stream(c)));
+  return HF_OK;
+}
+
+// Kernel basis of K-bar (mixed form; after hf_schur): L x kernel_dim column-major on the device.
+int hf_kernel_basis_impl(hf_ctx* c, double* basis, int64_t ldb) {
+  if (!c->schured) return HF_ERR_STATE;
+  if (c->prec != HF_PREC_MIXED) return HF_ERR_STATE;
+  const int M = (int)c->M, kd = c->kernel_dim;
+  if (kd == 0) return HF_OK;
+  if (!basis || ldb < c->L) return HF_ERR_ARG;
+  cudaStream_t s = hf_stream(c);
+  int rc;
+  if ((rc = hf_ensure(c->d_small, ((size_t)M * kd + M + 64) * 8))) return rc;
+  double* N2 = (double*)c->d_small.p;
+  double* w = N2 + (size_t)M * kd;
+  HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_s22_nullvecs<<<1, 256, 0, s>>>(M, (const double*)c->d_bk_lf.p, (const int*)c->d_bk_perm.p,
+                                                               (const int*)c->d_bk_blk.p, (const double*)c->d_bk_dval.p,
+                                                               (const int*)c->d_bk_null.p, kd, N2, w));
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_kernel_basis<<<dim3(nblk(c->L, 256), kd), 256, 0, s>>>(c->L, M, kd, (const double*)c->d_x12.p, N2,
+                                                                              (const int32_t*)c->d_lam2pos.p,
+                                                                              (const double*)c->d_q.p, basis, ldb));
+  HF_CUDA_TRY(cudaGetLastError());
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
   return HF_OK;
 }

@@ -24,7 +24,7 @@ EXPORTED = (
     "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
     "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc",
-    "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_free",
+    "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis", "hf_free",
 )
 HF_NPROF = 13
 
@@ -96,6 +96,7 @@ def lib():
     L.hf_get_s22_factor.argtypes = [vp, vp, vp, vp, vp, vp]
     L.hf_free.argtypes = [vp]
     L.hf_free.restype = None
+    L.hf_get_kernel_basis.argtypes = [vp, vp, i64]
     pp = C.POINTER(C.c_void_p)
     L.hf_factorize_batched.argtypes = [pp, i32, pp, dbl, vp]
     L.hf_schur_batched.argtypes = [pp, i32, vp]
@@ -172,6 +173,14 @@ class HybridFactor:
         nrhs = 1 if b_dev.dim() == 1 else b_dev.shape[0]
         return _check(lib().hf_solve(self._h, nrhs, _ptr(b_dev), self.L, _ptr(x_dev), self.L),
                       "hf_solve", allow=(HF_ERR_NOT_CONVERGED,))
+
+    def kernel_basis(self, torch):
+        """Kernel basis of K-bar as a (kernel_dim, L) CUDA float64 tensor (rows = basis vectors)."""
+        kd = self.info()["kernel_dim"]
+        out = torch.zeros((max(kd, 0), self.L), dtype=torch.float64, device="cuda")
+        if kd:
+            _check(lib().hf_get_kernel_basis(self._h, _ptr(out), self.L), "hf_get_kernel_basis")
+        return out
 
     def precond(self, R_dev, W_dev):
         """W = Q^-1 R (Sec. 3.2) on row-major L x m torch float64 CUDA tensors (scaled unknowns)."""

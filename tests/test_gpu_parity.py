@@ -332,3 +332,30 @@ def test_full_size_stokes32_properties():
     S22 = H.s22(torch).cpu().numpy()
     Sh = K[lam2][:, lam2].toarray() - K[lam2][:, lam1] @ X12[lam1]
     assert rel_fro(S22, 0.5 * (Sh + Sh.T)) <= 1e-13
+
+
+@pytest.mark.parametrize("name", ["cfg1_diffusion48", "stokes8", "elasticity6", "darcy16"])
+def test_kernel_basis(name):
+    """The exported kernel basis spans the kernel of K-bar: K-bar B = 0 to the accuracy of
+    the iterative X12 (normwise 1e-8; the tiny flux entries of the Darcy kernel carry the
+    GCR error amplified by the unscaling), full rank kernel_dim, and it contains the known
+    kernel of the generator (constants, rigid modes, translations)."""
+    make, kdim, opts = CASES[name]
+    s = make()
+    out = run_gpu(s, tau=1e-2, solve=False, **opts)
+    H = out["H"]
+    B = H.kernel_basis(torch).cpu().numpy().T          # L x kdim
+    assert B.shape[1] == kdim
+    K = s.to_scipy()
+    nK = abs(K).sum(axis=1).max()
+    for j in range(kdim):
+        b = B[:, j]
+        assert np.abs(K @ b).max() <= 1e-8 * nK * np.abs(b).max()
+    sv = np.linalg.svd(B / np.linalg.norm(B, axis=0), compute_uv=False)
+    assert sv[-1] > 1e-6 * sv[0]
+    V = s.kernel
+    if V is not None and V.shape[1] == kdim:
+        # the generator's kernel lies in span(B)
+        Qb, _ = np.linalg.qr(B)
+        resid = V - Qb @ (Qb.T @ V)
+        assert np.linalg.norm(resid) <= 1e-6 * np.linalg.norm(V)
