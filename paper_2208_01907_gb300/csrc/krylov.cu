@@ -806,6 +806,68 @@ __device__ void bp_kernel_rule(int M, const int* __restrict__ blk, const double*
   }
 }
 
+// The same rule with all threads of one CTA and shared-memory scratch (3 M doubles):
+// magnitudes in parallel, a stable descending sort by ranks (rank of i = number of
+// magnitudes larger, or equal at a smaller position), and the `dim` last entries of that
+// order marked null -- the same positions the one-thread loop picks (smallest
+// magnitudes, ties to the later position).
+__device__ void bp_kernel_rule_block(int M, const int* __restrict__ blk, const double* __restrict__ dval,
+                                     int* __restrict__ nullp, double kernel_eps, double kernel_gap,
+                                     const int32_t* __restrict__ lam2, const int64_t* __restrict__ diagpos,
+                                     const double* __restrict__ kval, double noise, int* __restrict__ kdim_out,
+                                     double* __restrict__ scratch) {
+  __shared__ double red[32];
+  __shared__ int s_dim;
+  double* mg = scratch;                 // M: magnitude per position
+  double* srt = scratch + M;            // M: descending order
+  int* rk = (int*)(scratch + 2 * M);    // M: rank of each position
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double ref = 0.0;                     // max |K_ii| over Lambda_2: the unit reference
+  for (int i = tid; i < M; i += nt) ref = fmax(ref, fabs(kval[diagpos[lam2[i]]]));
+  for (int o = 16; o > 0; o >>= 1) ref = fmax(ref, __shfl_xor_sync(0xffffffffu, ref, o));
+  if ((tid & 31) == 0) red[tid >> 5] = ref;
+  for (int i = tid; i < M; i += nt) {
+    if (blk[i] == 1) {
+      mg[i] = fabs(dval[2 * i]);
+    } else if (blk[i] == 2) {
+      const double a = dval[2 * i], b = dval[2 * i + 1], c = dval[2 * (i + 1)];
+      const double mean = 0.5 * (a + c), rad = sqrt(0.25 * (a - c) * (a - c) + b * b);
+      mg[i] = fabs(mean + rad);
+      mg[i + 1] = fabs(mean - rad);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) for (int w = 1; w < (nt + 31) / 32; ++w) ref = fmax(ref, red[w]);
+  for (int i = tid; i < M; i += nt) {
+    const double v = mg[i];
+    int r = 0;
+    for (int j = 0; j < M; ++j) r += (mg[j] > v || (mg[j] == v && j < i)) ? 1 : 0;
+    rk[i] = r;
+    srt[r] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int dim = 0;
+    if (M > 0) {
+      const double scale = fmax(srt[0], ref);
+      const double thr = fmax(kernel_eps * scale, noise);
+      if (scale == 0.0 || srt[0] <= thr) dim = M;
+      else {
+        double best = 0.0;
+        for (int i = 1; i < M; ++i) {
+          if (srt[i] > thr) continue;
+          const double ratio = (srt[i] == 0.0) ? INFINITY : srt[i - 1] / srt[i];
+          if (ratio >= kernel_gap && ratio > best) { best = ratio; dim = M - i; }
+        }
+      }
+    }
+    *kdim_out = dim;
+    s_dim = dim;
+  }
+  __syncthreads();
+  for (int i = tid; i < M; i += nt) nullp[i] = rk[i] >= M - s_dim ? 1 : 0;
+}
+
 __global__ void k_bunch_parlett(int M, double* __restrict__ A, double* __restrict__ Lf, int* __restrict__ perm,
                                 int* __restrict__ blk, double* __restrict__ dval, int* __restrict__ nullp,
                                 double kernel_eps, double kernel_gap, const int32_t* __restrict__ lam2,
@@ -920,7 +982,7 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restric
                                                         BpPart* __restrict__ parts) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  extern __shared__ double lcol[];                 // 2 x M: the new Lf column(s) of the step
+  extern __shared__ double lcol[];                 // 3 x M: the new Lf column(s) of the step; rule scratch
   __shared__ long long w0[BP_THREADS / 32], wi0[BP_THREADS / 32], w1[BP_THREADS / 32], wj1[BP_THREADS / 32];
   __shared__ int s_act, s_a, s_b;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -965,8 +1027,8 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restric
     long long v0 = -1, i0 = 0x7fffffffffffffffLL, v1 = -1, j1 = 0x7fffffffffffffffLL;
     for (int i = k + gtid; i < M; i += gnt) bp_better(v0, i0, abs_key(A[(int64_t)i * M + i]), i);
     const int n2 = M - k;
-    for (long long e = gtid; e < (long long)n2 * n2; e += gnt) {
-      const int j = k + (int)(e / n2), i = k + (int)(e % n2);
+    for (int e = gtid; e < n2 * n2; e += gnt) {                   // n2^2 < 2^31 for M <= BP_MAX_M
+      const int j = k + e / n2, i = k + e % n2;
       if (i <= j) continue;
       bp_better(v1, j1, abs_key(A[(int64_t)i * M + j]), (long long)j * M + i);
     }
@@ -1016,8 +1078,8 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restric
       }
       __syncthreads();
       const int m2 = M - k - 1;
-      for (long long e = gtid; e < (long long)m2 * m2; e += gnt) {
-        const int i = k + 1 + (int)(e / m2), j = k + 1 + (int)(e % m2);
+      for (int e = gtid; e < m2 * m2; e += gnt) {
+        const int i = k + 1 + e / m2, j = k + 1 + e % m2;
         A[(int64_t)i * M + j] -= lcol[i] * A[(int64_t)j * M + k];
       }
       grid.sync();
@@ -1039,8 +1101,8 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restric
       }
       __syncthreads();
       const int m2 = M - k - 2;
-      for (long long e = gtid; e < (long long)m2 * m2; e += gnt) {
-        const int i = k + 2 + (int)(e / m2), j = k + 2 + (int)(e % m2);
+      for (int e = gtid; e < m2 * m2; e += gnt) {
+        const int i = k + 2 + e / m2, j = k + 2 + e % m2;
         A[(int64_t)i * M + j] -= lcol[i] * A[(int64_t)j * M + k] + lcol[M + i] * A[(int64_t)j * M + k + 1];
       }
       grid.sync();
@@ -1048,8 +1110,9 @@ __global__ void __launch_bounds__(BP_THREADS) k_bp_coop(int M, double* __restric
     }
   }
   grid.sync();
-  if (blockIdx.x == 0 && tid == 0)
-    bp_kernel_rule(M, blk, dval, nullp, kernel_eps, kernel_gap, lam2, diagpos, kval, noise, kdim_out, mags_work);
+  if (blockIdx.x == 0)
+    bp_kernel_rule_block(M, blk, dval, nullp, kernel_eps, kernel_gap, lam2, diagpos, kval, noise, kdim_out, lcol);
+  (void)mags_work;
 }
 
 // Null vectors of S22 from its LDL^T (one CTA): for every null pivot direction v (e_i for
@@ -1119,6 +1182,222 @@ __global__ void k_kernel_basis(int64_t L, int M, int kdim, const double* __restr
     x = -acc;
   }
   basis[(int64_t)c * ldb + r] = q[r] * x;
+}
+
+// ---------------------------------------------------------------------------
+// The same Bunch-Parlett LDL^T with S22 resident in the distributed shared memory of a
+// thread-block cluster: CTA r holds the rows [r R, (r+1) R) (FP64, row stride M).  Per
+// pivot step two cluster barriers: (1) after every CTA pushed its two maxima (integer keys
+// of |a|, the same tie rules); (2) after the moved rows were sent to their new owners and
+// every CTA pushed, for its rows, the entries of the pivot column(s) before the
+// permutation.  Each CTA then permutes its own rows and columns and updates them with the
+// pivot column exactly as the one-CTA kernel does (same operations per element).
+// ---------------------------------------------------------------------------
+constexpr int BPC_THREADS = 512;
+constexpr int BPC_CMAX = 16;
+constexpr size_t BPC_SMEM = 200 * 1024;
+constexpr int BPC_RMAX = 128;                        // rows per CTA
+
+__global__ void __launch_bounds__(BPC_THREADS, 1)
+k_bp_cluster(int M, int R, const double* __restrict__ S22, double* __restrict__ Lf, int* __restrict__ perm,
+             int* __restrict__ blk, double* __restrict__ dval, int* __restrict__ nullp, double kernel_eps,
+             double kernel_gap, const int32_t* __restrict__ lam2, const int64_t* __restrict__ diagpos,
+             const double* __restrict__ kval, double noise, int* __restrict__ kdim_out,
+             double* __restrict__ mags_work) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) double bpc[];
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* Arow = bpc;                               // R x M: own rows
+  double* rowbuf = Arow + (size_t)R * M;            // 4 x M: incoming rows for own moved positions
+  double* colbuf = rowbuf + 4 * (size_t)M;          // 2 x M: old pivot columns, by old row index
+  double* newcol = colbuf + 2 * (size_t)M;          // 2 x M: new pivot columns, by new row index
+  long long* slots = (long long*)(newcol + 2 * (size_t)M);   // [2][BPC_CMAX][4]
+  __shared__ double ltmp[2 * BPC_RMAX];             // multipliers of the own rows
+  __shared__ long long w0[BPC_THREADS / 32], wi0[BPC_THREADS / 32], w1[BPC_THREADS / 32], wj1[BPC_THREADS / 32];
+  __shared__ int s_act, s_np, s_pos[4], s_src[4], s_colsrc[2];
+  const int p0 = rank * R, p1 = min(M, p0 + R);
+  auto owner = [&](int pos) { return pos / R; };
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  for (int64_t e = tid; e < (int64_t)(p1 - p0) * M; e += nt) Arow[e] = S22[(int64_t)p0 * M + e];
+  for (int64_t e = tid; e < (int64_t)(p1 - p0) * M; e += nt) {
+    const int r = p0 + (int)(e / M), c = (int)(e % M);
+    Lf[(int64_t)r * M + c] = (r == c) ? 1.0 : 0.0;
+  }
+  for (int i = p0 + tid; i < p1; i += nt) { perm[i] = i; blk[i] = 0; dval[2 * i] = 0; dval[2 * i + 1] = 0; nullp[i] = 0; }
+  cl.sync();
+  int k = 0, it = 0;
+  while (k < M) {
+    long long* sl = slots + (it & 1) * BPC_CMAX * 4;
+    // 1. own maxima: max |a_ii| (i >= k, ties: smaller i); max |a_ij|, i > j >= k (ties: smaller j*M+i)
+    long long v0 = -1, i0 = 0x7fffffffffffffffLL, v1 = -1, j1 = 0x7fffffffffffffffLL;
+    for (int i = max(k, p0) + tid; i < p1; i += nt) bp_better(v0, i0, abs_key(Arow[(int64_t)(i - p0) * M + i]), i);
+    {
+      const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;   // warps over rows, lanes over columns
+      for (int i = max(k, p0) + warp; i < p1; i += nw) {
+        const double* row = Arow + (size_t)(i - p0) * M;
+        for (int j = k + lane; j < i; j += 32) bp_better(v1, j1, abs_key(row[j]), (long long)j * M + i);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      bp_better(v0, i0, __shfl_xor_sync(0xffffffffu, v0, o), __shfl_xor_sync(0xffffffffu, i0, o));
+      bp_better(v1, j1, __shfl_xor_sync(0xffffffffu, v1, o), __shfl_xor_sync(0xffffffffu, j1, o));
+    }
+    if ((tid & 31) == 0) { w0[tid >> 5] = v0; wi0[tid >> 5] = i0; w1[tid >> 5] = v1; wj1[tid >> 5] = j1; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < nt / 32; ++w) { bp_better(v0, i0, w0[w], wi0[w]); bp_better(v1, j1, w1[w], wj1[w]); }
+      w0[0] = v0; wi0[0] = i0; w1[0] = v1; wj1[0] = j1;
+    }
+    __syncthreads();
+    if (tid < C) {
+      long long* d = cl.map_shared_rank(sl, tid) + rank * 4;
+      d[0] = w0[0]; d[1] = wi0[0]; d[2] = w1[0]; d[3] = wj1[0];
+    }
+    cl.sync();                                                      // barrier 1
+    // 2. the decision (identical in every CTA) and the position permutation sigma
+    if (tid == 0) {
+      long long g0 = -1, gi = 0x7fffffffffffffffLL, g1 = -1, gj = 0x7fffffffffffffffLL;
+      for (int b = 0; b < C; ++b) { bp_better(g0, gi, sl[b * 4 + 0], sl[b * 4 + 1]); bp_better(g1, gj, sl[b * 4 + 2], sl[b * 4 + 3]); }
+      const double mu0 = g0 < 0 ? -1.0 : __longlong_as_double(g0);
+      double mu1 = g1 < 0 ? -1.0 : __longlong_as_double(g1);
+      if (mu1 < 0) mu1 = 0.0;
+      int act;
+      if (mu0 == 0.0 && mu1 == 0.0) act = 0;
+      else if (mu0 >= alpha * mu1) act = 1;
+      else act = 2;
+      s_act = act;
+      // affected positions and their sources: content at pos[x] after the step = old content at src[x]
+      int pos[4], src[4], np = 0;
+      auto addp = [&](int p) { for (int x = 0; x < np; ++x) if (pos[x] == p) return; pos[np] = p; src[np] = p; ++np; };
+      auto swp = [&](int a, int b) {                  // content exchange of positions a and b
+        int xa = -1, xb = -1;
+        for (int x = 0; x < np; ++x) { if (pos[x] == a) xa = x; if (pos[x] == b) xb = x; }
+        const int t = src[xa]; src[xa] = src[xb]; src[xb] = t;
+      };
+      if (act == 1) { const int a = (int)gi; addp(k); addp(a); swp(k, a); }
+      if (act == 2) {
+        const int bj = (int)(gj / M), bi = (int)(gj % M);
+        addp(k); addp(bj); addp(k + 1); addp(bi);
+        swp(k, bj);
+        swp(k + 1, bi);
+      }
+      s_np = act == 0 ? 0 : np;
+      for (int x = 0; x < np; ++x) { s_pos[x] = pos[x]; s_src[x] = src[x]; }
+      int ck = k, ck1 = k + 1;
+      for (int x = 0; x < np; ++x) { if (pos[x] == k) ck = src[x]; if (pos[x] == k + 1) ck1 = src[x]; }
+      s_colsrc[0] = ck;
+      s_colsrc[1] = ck1;
+    }
+    __syncthreads();
+    const int act = s_act, np = s_np;
+    if (act == 0) {
+      if (rank == 0 && tid == 0) { blk[k] = 1; dval[2 * k] = 0.0; }
+      k += 1; ++it;
+      continue;
+    }
+    const int ncol = act;                                           // pivot columns: 1 or 2
+    // 3. pushes: moved rows to their new owners, old pivot columns (own rows) to everyone
+    for (int x = 0; x < np; ++x) {
+      const int pd = s_pos[x], ps = s_src[x];
+      if (pd == ps || owner(ps) != rank) continue;
+      double* dst = cl.map_shared_rank(rowbuf, owner(pd)) + (size_t)x * M;
+      const double* srcrow = Arow + (size_t)(ps - p0) * M;
+      for (int c = tid; c < M; c += nt) dst[c] = srcrow[c];
+    }
+    for (int e = tid; e < C * ncol * (p1 - p0); e += nt) {
+      const int r = e / (ncol * (p1 - p0)), rem = e % (ncol * (p1 - p0));
+      const int cidx = rem / (p1 - p0), i = p0 + rem % (p1 - p0);
+      cl.map_shared_rank(colbuf, r)[(size_t)cidx * M + i] = Arow[(size_t)(i - p0) * M + s_colsrc[cidx]];
+    }
+    cl.sync();                                                      // barrier 2
+    // 4. permute own rows (moved rows from rowbuf) and the affected columns of all own rows
+    for (int x = 0; x < np; ++x) {
+      const int pd = s_pos[x], ps = s_src[x];
+      if (pd == ps || owner(pd) != rank) continue;
+      double* drow = Arow + (size_t)(pd - p0) * M;
+      for (int c = tid; c < M; c += nt) drow[c] = rowbuf[(size_t)x * M + c];
+    }
+    __syncthreads();
+    for (int i = p0 + tid; i < p1; i += nt) {
+      double* row = Arow + (size_t)(i - p0) * M;
+      double tmp[4];
+      for (int x = 0; x < np; ++x) tmp[x] = row[s_src[x]];
+      for (int x = 0; x < np; ++x) row[s_pos[x]] = tmp[x];
+    }
+    // the new pivot column(s) for every row j: new A[j][k(+1)] = old A[sigma(j)][sigma(k(+1))]
+    auto src_of = [&](int j) { for (int x = 0; x < np; ++x) if (s_pos[x] == j) return s_src[x]; return j; };
+    __syncthreads();
+    if (rank == 0) {
+      // Lf rows of the moved positions, columns < k (the eliminated part)
+      for (int x = 0; x < np; ++x) {
+        if (s_pos[x] == s_src[x]) continue;
+        for (int c = tid; c < k; c += nt) rowbuf[(size_t)x * M + c] = Lf[(int64_t)s_src[x] * M + c];
+      }
+      __syncthreads();
+      for (int x = 0; x < np; ++x) {
+        if (s_pos[x] == s_src[x]) continue;
+        for (int c = tid; c < k; c += nt) Lf[(int64_t)s_pos[x] * M + c] = rowbuf[(size_t)x * M + c];
+      }
+      if (tid == 0) {
+        int pv[4];
+        for (int x = 0; x < np; ++x) pv[x] = perm[s_src[x]];
+        for (int x = 0; x < np; ++x) perm[s_pos[x]] = pv[x];
+      }
+    }
+    // the new pivot column(s) in old-row order -> new-row order (sigma applied once)
+    for (int j = tid; j < M; j += nt) {
+      const int sj = src_of(j);
+      newcol[j] = colbuf[sj];
+      if (act == 2) newcol[M + j] = colbuf[M + sj];
+    }
+    __syncthreads();
+    const int ib = max(k + act, p0);                               // first own row updated
+    if (act == 1) {
+      const double dk = newcol[k];
+      if (rank == 0 && tid == 0) { blk[k] = 1; dval[2 * k] = dk; }
+      for (int i = ib + tid; i < p1; i += nt) {
+        const double l = Arow[(size_t)(i - p0) * M + k] / dk;
+        ltmp[i - p0] = l;
+        Lf[(int64_t)i * M + k] = l;
+      }
+      __syncthreads();
+      for (int i = ib + (tid >> 5); i < p1; i += nt >> 5) {
+        double* row = Arow + (size_t)(i - p0) * M;
+        const double l = ltmp[i - p0];
+        for (int j = k + 1 + (tid & 31); j < M; j += 32) row[j] -= l * newcol[j];
+      }
+      k += 1;
+    } else {
+      const double a = newcol[k], b = newcol[k + 1], cc = newcol[M + k + 1];
+      const double det = a * cc - b * b;
+      if (rank == 0 && tid == 0) { blk[k] = 2; blk[k + 1] = 0; dval[2 * k] = a; dval[2 * k + 1] = b; dval[2 * (k + 1)] = cc; }
+      for (int i = ib + tid; i < p1; i += nt) {
+        const double* row = Arow + (size_t)(i - p0) * M;
+        const double x0 = row[k], x1 = row[k + 1];
+        const double l0 = (x0 * cc - x1 * b) / det, l1 = (x1 * a - x0 * b) / det;
+        ltmp[i - p0] = l0;
+        ltmp[BPC_RMAX + i - p0] = l1;
+        Lf[(int64_t)i * M + k] = l0;
+        Lf[(int64_t)i * M + k + 1] = l1;
+      }
+      __syncthreads();
+      for (int i = ib + (tid >> 5); i < p1; i += nt >> 5) {
+        double* row = Arow + (size_t)(i - p0) * M;
+        const double l0 = ltmp[i - p0], l1 = ltmp[BPC_RMAX + i - p0];
+        for (int j = k + 2 + (tid & 31); j < M; j += 32) row[j] -= l0 * newcol[j] + l1 * newcol[M + j];
+      }
+      k += 2;
+    }
+    ++it;
+    __syncthreads();
+  }
+  cl.sync();
+  if (rank == 0)
+    bp_kernel_rule_block(M, blk, dval, nullp, kernel_eps, kernel_gap, lam2, diagpos, kval, noise, kdim_out, rowbuf);
+  (void)mags_work;
 }
 
 // x = S22^+ y with null pivots treated as zero; y, x: M x m row-major. One CTA.
@@ -1666,7 +1945,47 @@ static int bk_factor(hf_ctx* c) {
   HF_CUDA_TRY(cudaMemcpyAsync(A, c->d_s22.p, (size_t)M * M * 8, cudaMemcpyDeviceToDevice, s));
   int* kd = (int*)((int*)c->d_flags.p + FLAG_COUNT + 8);
   double* mags = (double*)c->d_bk_dval.p + 2 * M;
-  if (M <= BP_MAX_M) {
+  // S22 in the distributed shared memory of one cluster when it fits, else over all SMs
+  static std::mutex bpc_mu;
+  static int bpc_cmax = -1;
+  {
+    std::lock_guard<std::mutex> lk(bpc_mu);
+    if (bpc_cmax < 0) {
+      bpc_cmax = 0;
+      if (cudaFuncSetAttribute(k_bp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BPC_SMEM) == cudaSuccess &&
+          cudaFuncSetAttribute(k_bp_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        for (int cs = BPC_CMAX; cs >= 2; cs /= 2) {
+          cudaLaunchConfig_t q = {};
+          q.gridDim = dim3(cs); q.blockDim = dim3(BPC_THREADS); q.dynamicSmemBytes = BPC_SMEM;
+          cudaLaunchAttribute at[1];
+          at[0].id = cudaLaunchAttributeClusterDimension;
+          at[0].val.clusterDim.x = cs; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+          q.attrs = at; q.numAttrs = 1;
+          int ncl = 0;
+          if (cudaOccupancyMaxActiveClusters(&ncl, k_bp_cluster, &q) == cudaSuccess && ncl > 0) { bpc_cmax = cs; break; }
+        }
+      }
+      (void)cudaGetLastError();
+    }
+  }
+  const int bpc_C = bpc_cmax;
+  const int bpc_R = bpc_C > 0 ? (M + bpc_C - 1) / bpc_C : 0;
+  const size_t bpc_bytes = ((size_t)bpc_R * M + 8 * (size_t)M) * 8 + 2 * BPC_CMAX * 4 * 8 + 64;
+  if (bpc_C > 0 && bpc_R <= BPC_RMAX && bpc_bytes <= BPC_SMEM) {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(bpc_C); lc.blockDim = dim3(BPC_THREADS); lc.dynamicSmemBytes = bpc_bytes; lc.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = bpc_C; la[0].val.clusterDim.y = 1; la[0].val.clusterDim.z = 1;
+    lc.attrs = la; lc.numAttrs = 1;
+    HF_LAUNCH(c, HF_PROF_DENSE_LDLT, HF_CUDA_TRY(cudaLaunchKernelEx(&lc, k_bp_cluster, M, bpc_R, (const double*)A,
+                                                                    (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p,
+                                                                    (int*)c->d_bk_blk.p, (double*)c->d_bk_dval.p,
+                                                                    (int*)c->d_bk_null.p, c->opts.kernel_eps,
+                                                                    c->opts.kernel_gap, (const int32_t*)c->d_lam2.p,
+                                                                    (const int64_t*)c->d_diagpos.p,
+                                                                    (const double*)c->d_kval.p, c->s22_noise, kd, mags)));
+  } else if (M <= BP_MAX_M) {
     // over all SMs (cooperative); partial maxima of two steps in flight per block
     static std::mutex bp_mu;
     static int bp_blocks = 0;
@@ -1676,8 +1995,8 @@ static int bk_factor(hf_ctx* c) {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        HF_CUDA_TRY(cudaFuncSetAttribute(k_bp_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BP_MAX_M * 8));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bp_coop, BP_THREADS, 2 * BP_MAX_M * 8);
+        HF_CUDA_TRY(cudaFuncSetAttribute(k_bp_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * BP_MAX_M * 8));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bp_coop, BP_THREADS, 3 * BP_MAX_M * 8);
         bp_blocks = std::max(1, sms * std::min(std::max(per, 1), 1));
       }
     }
@@ -1696,7 +2015,7 @@ static int bk_factor(hf_ctx* c) {
     void* args[] = {&Mi, (void*)&A, (void*)&Lf, (void*)&pm, (void*)&bk, (void*)&dv, (void*)&nl, &keps, &kgap,
                     (void*)&l2, (void*)&dp, (void*)&kv, &noise, (void*)&kd, (void*)&mags, (void*)&parts};
     HF_LAUNCH(c, HF_PROF_DENSE_LDLT, HF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bp_coop, bp_blocks, BP_THREADS,
-                                                                             args, 2 * (size_t)M * 8, s)));
+                                                                             args, 3 * (size_t)M * 8, s)));
   } else {
     HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
                                       (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
