@@ -1400,53 +1400,66 @@ k_bp_cluster(int M, int R, const double* __restrict__ S22, double* __restrict__ 
   (void)mags_work;
 }
 
-// x = S22^+ y with null pivots treated as zero; y, x: M x m row-major. One CTA.
-__global__ void k_bk_solve(int M, int m, const double* __restrict__ Lf, const int* __restrict__ perm,
-                           const int* __restrict__ blk, const double* __restrict__ dval, const int* __restrict__ nullp,
-                           const double* __restrict__ y, double* __restrict__ x, double* __restrict__ z) {
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    for (int i = 0; i < M; ++i) z[i * m + c] = y[perm[i] * m + c];
-    for (int i = 0; i < M; ++i) {
-      double s = z[i * m + c];
-      for (int j = 0; j < i; ++j) s -= Lf[i * M + j] * z[j * m + c];
-      z[i * m + c] = s;
-    }
-    for (int i = 0; i < M;) {
-      if (blk[i] == 1) {
-        double dd = dval[2 * i];
-        z[i * m + c] = (nullp[i] || dd == 0.0) ? 0.0 : z[i * m + c] / dd;
-        ++i;
-      } else {
-        double a = dval[2 * i], b = dval[2 * i + 1], cc = dval[2 * (i + 1)];
-        double mean = 0.5 * (a + cc), rad = sqrt(0.25 * (a - cc) * (a - cc) + b * b);
-        double ev[2] = {mean + rad, mean - rad};
-        // eigenvectors of [[a b][b cc]]
-        double v[2][2];
-        for (int q = 0; q < 2; ++q) {
-          double vx = b, vy = ev[q] - a;
-          if (fabs(vx) + fabs(vy) < 1e-300) { vx = ev[q] - cc; vy = b; }
-          if (fabs(vx) + fabs(vy) < 1e-300) { vx = (q == 0) ? 1.0 : 0.0; vy = (q == 0) ? 0.0 : 1.0; }
-          double nr = sqrt(vx * vx + vy * vy);
-          v[q][0] = vx / nr; v[q][1] = vy / nr;
-        }
-        double z0 = z[i * m + c], z1 = z[(i + 1) * m + c];
-        double o0 = 0.0, o1 = 0.0;
-        for (int q = 0; q < 2; ++q) {
-          if (nullp[i + q] || ev[q] == 0.0) continue;
-          double pr = (v[q][0] * z0 + v[q][1] * z1) / ev[q];
-          o0 += v[q][0] * pr; o1 += v[q][1] * pr;
-        }
-        z[i * m + c] = o0; z[(i + 1) * m + c] = o1;
-        i += 2;
-      }
-    }
-    for (int i = M - 1; i >= 0; --i) {
-      double s = z[i * m + c];
-      for (int j = i + 1; j < M; ++j) s -= Lf[j * M + i] * z[j * m + c];
-      z[i * m + c] = s;
-    }
-    for (int i = 0; i < M; ++i) x[perm[i] * m + c] = z[i * m + c];
+constexpr size_t BKS_SMEM_MAX = 200 * 1024;  // largest shared work vector of k_bk_solve
+
+// x = S22^+ y with null pivots treated as zero; y, x: M x m row-major.  One CTA per
+// right-hand side; the work vector z sits in shared memory (zg == nullptr) or, when
+// M doubles do not fit there, in the column c of the global M x m buffer zg.  The
+// substitutions are column-oriented (one barrier per column, the updates of the
+// other rows in parallel).
+__global__ void __launch_bounds__(256) k_bk_solve(int M, int m, const double* __restrict__ Lf,
+                                                const int* __restrict__ perm, const int* __restrict__ blk,
+                                                const double* __restrict__ dval, const int* __restrict__ nullp,
+                                                const double* __restrict__ y, double* __restrict__ x,
+                                                double* zg) {
+  extern __shared__ double zs[];
+  const int c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  if (c >= m) return;
+  double* z = zg ? zg + (int64_t)c * M : zs;
+  for (int i = tid; i < M; i += nt) z[i] = y[(int64_t)perm[i] * m + c];
+  __syncthreads();
+  // Lf z' = z (unit lower): z_i -= Lf_ij z_j for j = 0, 1, ... in order
+  for (int j = 0; j < M; ++j) {
+    const double zj = z[j];
+    for (int i = j + 1 + tid; i < M; i += nt) z[i] -= Lf[(int64_t)i * M + j] * zj;
+    __syncthreads();
   }
+  // D^+ (1x1: divide unless null; 2x2: eigen-decomposition, null eigenvalues dropped)
+  for (int i = tid; i < M; i += nt) {
+    if (blk[i] == 1) {
+      const double dd = dval[2 * i];
+      z[i] = (nullp[i] || dd == 0.0) ? 0.0 : z[i] / dd;
+    } else if (blk[i] == 2) {
+      const double a = dval[2 * i], b = dval[2 * i + 1], cc = dval[2 * (i + 1)];
+      const double mean = 0.5 * (a + cc), rad = sqrt(0.25 * (a - cc) * (a - cc) + b * b);
+      const double ev[2] = {mean + rad, mean - rad};
+      double v[2][2];
+      for (int q = 0; q < 2; ++q) {
+        double vx = b, vy = ev[q] - a;
+        if (fabs(vx) + fabs(vy) < 1e-300) { vx = ev[q] - cc; vy = b; }
+        if (fabs(vx) + fabs(vy) < 1e-300) { vx = (q == 0) ? 1.0 : 0.0; vy = (q == 0) ? 0.0 : 1.0; }
+        const double nr = sqrt(vx * vx + vy * vy);
+        v[q][0] = vx / nr; v[q][1] = vy / nr;
+      }
+      const double z0 = z[i], z1 = z[i + 1];
+      double o0 = 0.0, o1 = 0.0;
+      for (int q = 0; q < 2; ++q) {
+        if (nullp[i + q] || ev[q] == 0.0) continue;
+        const double pr = (v[q][0] * z0 + v[q][1] * z1) / ev[q];
+        o0 += v[q][0] * pr; o1 += v[q][1] * pr;
+      }
+      z[i] = o0;
+      z[i + 1] = o1;
+    }
+  }
+  __syncthreads();
+  // Lf^T z'' = z' (from the last row up)
+  for (int j = M - 1; j >= 0; --j) {
+    const double zj = z[j];
+    for (int i = tid; i < j; i += nt) z[i] -= Lf[(int64_t)j * M + i] * zj;
+    __syncthreads();
+  }
+  for (int i = tid; i < M; i += nt) x[(int64_t)perm[i] * m + c] = z[i];
 }
 
 // x1 = y1 - X12 x2 on Lambda_1 rows; Lambda_2 rows = x2
@@ -2111,13 +2124,20 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
   double* scratch = y1 + blk;
   double* y2 = scratch + blk;
   double* x2 = y2 + (size_t)M * m;
-  double* zt = x2 + (size_t)M * m;
+  double* zt = x2 + (size_t)M * m;  // work vectors of the S22 solve when they do not fit in shared memory
   HF_LAUNCH(c, HF_PROF_SCALE, k_scale_in<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, b, ldb, (const double*)c->d_q.p, bi));
   int grc = HF_OK;
   auto s22_solve = [&]() {
-    HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bk_solve<<<1, 128, 0, s>>>(M, m, (const double*)c->d_bk_lf.p, (const int*)c->d_bk_perm.p,
+    if (M == 0) return;
+    const size_t zbytes = (size_t)M * 8;
+    const bool in_smem = zbytes <= BKS_SMEM_MAX;
+    if (in_smem && zbytes > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_bk_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BKS_SMEM_MAX);
+      if (e != cudaSuccess) { grc = HF_ERR_CUDA; return; }
+    }
+    HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bk_solve<<<m, 256, in_smem ? zbytes : 0, s>>>(M, m, (const double*)c->d_bk_lf.p, (const int*)c->d_bk_perm.p,
                                  (const int*)c->d_bk_blk.p, (const double*)c->d_bk_dval.p,
-                                 (const int*)c->d_bk_null.p, y2, x2, zt));
+                                 (const int*)c->d_bk_null.p, y2, x2, in_smem ? nullptr : zt));
   };
   if (c->prec == HF_PREC_MIXED) {
     // Alg. 2: y1 by block GCR on K11, y2 = b2 - K21 y1, S22 x2 = y2, x1 = y1 - X12 x2
