@@ -1314,6 +1314,7 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
       nz += (int64_t)S.k * (S.f - S.k) + (int64_t)S.k * (S.k - 1) / 2;
     }
     c->nnz_factor = nz;
+    if ((rc = hf_sweep_plan(c))) return rc;
     c->front_prec = c->prec;
     c->factored = true;
     trailing_work(c, dbl ? 8 : 4);

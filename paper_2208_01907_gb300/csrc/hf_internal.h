@@ -91,8 +91,11 @@ struct hf_ctx {
   DevBuf d_flags;                    // int flags: [0] delay overflow, [1] numeric error
   DevBuf d_lam2pos;                  // L ints: position in Lambda_2 or -1
   DevBuf d_lam2;                     // M ints ascending
-  DevBuf d_vec;                      // per-front solve vectors
+  DevBuf d_vec;                      // per-front solve vectors (+ the sweep flags and tickets)
   size_t vec_cap = 0;
+  DevBuf d_swplan;                   // dataflow sweeps: work items (forward, backward), block bases
+  std::vector<int> sw_fwd_start, sw_fwd_cnt, sw_bwd_start, sw_bwd_cnt;   // per level: item range
+  int sw_blocks = 0;                 // 64-row diagonal blocks of all fronts
   // ---- split (host copy) ----
   bool factored = false, schured = false;
   int prec = HF_PREC_MIXED;
@@ -130,7 +133,10 @@ struct hf_ctx {
 // analyze.cpp
 int hf_analyze_impl(int64_t L, const int64_t* rowptr, const int32_t* col, const double* coords,
                     int dim, const hf_opts* opts, hf_ctx** out);
-void hf_layout_fronts(hf_ctx* c);   // capacities, ld, offsets (depends on opts.delay_cap)
+void hf_layout_fronts(hf_ctx* c);
+
+// krylov.cu: work-item lists of the dataflow sweeps, from the host front state
+int hf_sweep_plan(hf_ctx* c);   // capacities, ld, offsets (depends on opts.delay_cap)
 
 // Counts a kernel launch of class `cls` and, when profiling, brackets it with events.
 struct ProfScope {

@@ -351,6 +351,233 @@ __global__ void __launch_bounds__(SGTH) k_gemm_upd(const NodeDesc* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Dataflow sweep of one level (FP32 factor and vectors): one launch per level instead
+// of a launch per diagonal block.
+//
+// Work item = (front t, block, 64-column tile C).  Forward: triangle block R (rows
+// [64R, 64R+64) of [0, ks)) takes y_R = L_RR^-1 (v_R - sum_{b<R} L_Rb y_b); a
+// contribution block j (rows [ks + 64j, ...) of [ks, f)) takes v -= sum_b L_jb y_b.
+// Backward: triangle block R takes x_R = L_RR^-T (v_R - sum_{r>=ks} L_rR^T x_r -
+// sum_{b>R} L_bR^T x_b).  The updates accumulate in registers over the whole k range,
+// so no row is re-read between block steps; a triangle block publishes its columns
+// tile with a flag once solved, and an item waits for the flag of every block it reads.
+//
+// Persistent CTAs take items by ticket (an atomic counter).  Items are listed so that
+// an item only waits for items of lower tickets (forward: blocks by ascending R, then
+// the contribution blocks; backward: descending R).  A ticket is held by a running CTA,
+// so the lowest unfinished item always has its inputs and the level cannot deadlock,
+// whatever the number of resident CTAs.  Every wait is bounded: on timeout the CTA sets
+// the abort word, and every later wait of the launch gives up at once.
+// ---------------------------------------------------------------------------
+constexpr int DF_R = 64;       // rows per item (= TS, the diagonal block)
+constexpr int DF_C = 64;       // right-hand sides per item
+constexpr int DF_TH = 128;     // threads: 8 row groups x 16 column groups, 8 x 4 outputs each
+constexpr int DF_K = 16;       // k chunk of the register double buffer
+constexpr int DF_SPIN = 1 << 22;
+static_assert(DF_R == TS, "the triangle blocks are the diagonal blocks of the solve");
+
+__device__ __forceinline__ int df_ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void df_st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits for *flag != 0 (bounded); false (uniform) on timeout or abort.
+__device__ __forceinline__ bool df_wait(const int* flag, int* abort_word, int* s_ok) {
+  if (threadIdx.x == 0) {
+    int ok = 0;
+    for (int it = 0; it < DF_SPIN; ++it) {
+      if (df_ld_acquire(flag)) { ok = 1; break; }
+      if (*(volatile int*)abort_word) break;
+      __nanosleep(it < 64 ? 32 : 256);
+    }
+    if (!ok) atomicExch(abort_word, 1);
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <bool FWD>
+__global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                   const float* __restrict__ arena, float* vec, int m, int gt,
+                                                   const int2* __restrict__ items, int nitems,
+                                                   const int* __restrict__ blockbase, int* flags, int* counter,
+                                                   int* abort_word) {
+  constexpr int APT = DF_K * DF_R / DF_TH;     // A elements per thread per chunk
+  constexpr int BPT = DF_K * DF_C / DF_TH;     // B elements per thread per chunk
+  struct Gemm { float A[2][DF_K][DF_R + 4]; float B[2][DF_K][DF_C + 4]; };
+  constexpr int VS = DF_C + 1;
+  constexpr size_t UB = sizeof(Gemm) > sizeof(float) * DF_R * VS ? sizeof(Gemm) : sizeof(float) * DF_R * VS;
+  __shared__ __align__(16) unsigned char ubuf[UB];     // GEMM staging, then the block being solved
+  __shared__ float Ls[TS][TS + 1];
+  __shared__ int s_ticket, s_ok;
+  Gemm& G = *reinterpret_cast<Gemm*>(ubuf);
+  float (*Vs)[VS] = reinterpret_cast<float (*)[VS]>(ubuf);
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t total = (int64_t)nitems * gt;
+  for (;;) {
+    if (tid == 0) s_ticket = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ticket = s_ticket;
+    if (ticket >= total) return;
+    const int2 it = items[ticket / gt];
+    const int C = ticket - (ticket / gt) * gt;
+    const int t = it.x, code = it.y;
+    const NodeDesc d = nd[t];
+    const int ks = st[t].ksolve, f = st[t].f;
+    const int nblk = (ks + DF_R - 1) / DF_R;
+    const int64_t ld = d.ld;
+    const float* F = arena + d.front_off;
+    float* V = vec + d.row_off * m;
+    const int c0 = C * DF_C;
+    const bool tri = code >= 0;
+    const int r0 = tri ? code * DF_R : ks + (-1 - code) * DF_R;
+    const int nr = min(DF_R, (tri ? ks : f) - r0);
+    int* fl = flags + (int64_t)blockbase[t] * gt + C;     // flag of block b: fl[b * gt]
+    if (tri) {                                           // diagonal block, staged early
+      for (int e = tid; e < TS * TS; e += DF_TH) {
+        const int r = e % TS, cc = e / TS;
+        Ls[r][cc] = (r < nr && cc < nr && r > cc) ? F[(r0 + r) + (int64_t)(r0 + cc) * ld] : 0.f;
+      }
+    }
+    // blocked summation: acc holds the products of at most DF_R consecutive k, then is
+    // added into tot (the error of a long FP32 dot product grows with its length; this
+    // keeps it at that of the per-block updates)
+    float acc[8][4], tot[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; tot[i][j] = 0.f; }
+    auto flush = [&]() {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { tot[i][j] += acc[i][j]; acc[i][j] = 0.f; }
+    };
+    float pa[APT], pb[BPT];
+    // acc += A(rows of the item, k in [k_lo, k_hi)) * V(k rows, tile columns)
+    auto gemm_range = [&](int k_lo, int k_hi) {
+      auto load = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < APT; ++u) {
+          const int e = tid + u * DF_TH;
+          int kk, rr;
+          if (FWD) { kk = e / DF_R; rr = e % DF_R; }    // rows contiguous in column q
+          else { rr = e / DF_K; kk = e % DF_K; }        // k contiguous in column r0 + rr
+          const int q = kc + kk;
+          float a = 0.f;
+          if (q < k_hi && rr < nr) a = FWD ? __ldg(F + (r0 + rr) + (int64_t)q * ld) : __ldg(F + q + (int64_t)(r0 + rr) * ld);
+          pa[u] = a;
+        }
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+          const int e = tid + u * DF_TH;
+          const int kk = e / DF_C, cc = e % DF_C;
+          const int q = kc + kk, c = c0 + cc;
+          pb[u] = (q < k_hi && c < m) ? __ldcg(V + (int64_t)q * m + c) : 0.f;
+        }
+      };
+      auto stage = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < APT; ++u) {
+          const int e = tid + u * DF_TH;
+          int kk, rr;
+          if (FWD) { kk = e / DF_R; rr = e % DF_R; }
+          else { rr = e / DF_K; kk = e % DF_K; }
+          G.A[buf][kk][rr] = pa[u];
+        }
+#pragma unroll
+        for (int u = 0; u < BPT; ++u) {
+          const int e = tid + u * DF_TH;
+          G.B[buf][e / DF_C][e % DF_C] = pb[u];
+        }
+      };
+      load(k_lo);
+      stage(0);
+      __syncthreads();
+      int buf = 0;
+      for (int kc = k_lo; kc < k_hi; kc += DF_K) {
+        const bool more = kc + DF_K < k_hi;
+        if (more) load(kc + DF_K);
+#pragma unroll
+        for (int kk = 0; kk < DF_K; ++kk) {
+          const float4 a0 = *reinterpret_cast<const float4*>(&G.A[buf][kk][ty * 8]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&G.A[buf][kk][ty * 8 + 4]);
+          const float4 b = *reinterpret_cast<const float4*>(&G.B[buf][kk][tx * 4]);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        if (more) stage(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+        if (!more || ((kc + DF_K - k_lo) % DF_R) == 0) flush();
+      }
+    };
+    bool ok = true;
+    if (FWD) {
+      const int bend = tri ? code : nblk;                 // blocks [0, bend) feed this item
+      for (int b = 0; b < bend && ok; ++b) {
+        ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok);
+        if (ok) gemm_range(b * DF_R, min(ks, (b + 1) * DF_R));
+      }
+    } else {
+      if (f > ks) gemm_range(ks, f);                      // solved rows of the ancestors
+      for (int b = nblk - 1; b > code && ok; --b) {
+        ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok);
+        if (ok) gemm_range(b * DF_R, min(ks, (b + 1) * DF_R));
+      }
+    }
+    if (!ok) return;                                      // uniform: s_ok after a barrier
+    if (!tri) {                                           // contribution rows: v -= acc
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = ty * 8 + i;
+        if (r >= nr) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + tx * 4 + j;
+          if (c < m) {
+            float* p = V + (int64_t)(r0 + r) * m + c;
+            *p = __ldcg(p) - tot[i][j];
+          }
+        }
+      }
+      __syncthreads();
+      continue;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = ty * 8 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int cc = tx * 4 + j, c = c0 + cc;
+        Vs[r][cc] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * m + c) - tot[i][j] : 0.f;
+      }
+    }
+    __syncthreads();
+    diag_solve<float, FWD, DF_C, DF_TH>(Ls, Vs, nr, tid);
+    for (int e = tid; e < nr * DF_C; e += DF_TH) {
+      const int r = e / DF_C, cc = e % DF_C;
+      if (c0 + cc < m) V[(int64_t)(r0 + r) * m + c0 + cc] = Vs[r][cc];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      df_st_release(fl + (int64_t)code * gt, 1);
+    }
+  }
+}
+
 // r (FP64) -> lower precision with Lambda_2 rows zeroed (the cast of Sec. 3.1)
 template <typename TV>
 __global__ void k_cast_in(int64_t n, int m, const double* __restrict__ R, const int32_t* __restrict__ lam2pos,
@@ -1532,9 +1759,99 @@ struct Work {
   int slots;
 };
 
+// The per-front vectors (row_elems x m), then the flags and tickets of the dataflow
+// sweeps: [forward tickets | forward flags | backward tickets | backward flags], one
+// ticket counter per level and one flag per (diagonal block, column tile).
+static size_t sweep_vec_bytes(const hf_ctx* c, int m, size_t esz) {
+  return ((size_t)c->row_elems * m * esz + 255) / 256 * 256;
+}
+static int sweep_tickets(const hf_ctx* c) { return (2 * (c->m + 1) + 63) / 64 * 64 / 2 + 32; }
+static size_t sweep_half_ints(const hf_ctx* c, int m) {
+  const size_t gt = (size_t)((m + DF_C - 1) / DF_C);
+  return ((size_t)sweep_tickets(c) + (size_t)c->sw_blocks * gt + 63) / 64 * 64;
+}
+static size_t sweep_sync_bytes(const hf_ctx* c, int m) { return 2 * sweep_half_ints(c, m) * sizeof(int); }
+static int* sweep_err(hf_ctx* c) { return (int*)c->d_flags.p + FLAG_COUNT + 11; }
+
+// Synchronises the stream; HF_ERR_TIMEOUT once a wait of a dataflow sweep has given up
+// (the word stays set until the next factorization: the solves of this factor are void).
+static int sweep_status(hf_ctx* c) {
+  int h = 0;
+  cudaStream_t s = hf_stream(c);
+  HF_CUDA_TRY(cudaMemcpyAsync(&h, sweep_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  return h ? HF_ERR_TIMEOUT : HF_OK;
+}
+
 static int ensure_vec(hf_ctx* c, int m, size_t esz) {
-  size_t need = (size_t)c->row_elems * m * esz + 64;
+  size_t need = sweep_vec_bytes(c, m, esz) + sweep_sync_bytes(c, m) + 64;
   return hf_ensure(c->d_vec, need);
+}
+
+int hf_sweep_plan(hf_ctx* c) {
+  const int nlev = c->m + 1;
+  const int nt = (int)c->state_host.size();
+  std::vector<int32_t> bb(nt + 1, 0);
+  int blocks = 0;
+  auto nblk = [&](int t) { return (c->state_host[t].ksolve + DF_R - 1) / DF_R; };
+  for (int t = 0; t < nt; ++t) { bb[t] = blocks; blocks += nblk(t); }
+  std::vector<int32_t> it;   // pairs (front, code)
+  c->sw_fwd_start.assign(nlev, 0); c->sw_fwd_cnt.assign(nlev, 0);
+  c->sw_bwd_start.assign(nlev, 0); c->sw_bwd_cnt.assign(nlev, 0);
+  for (int lev = 0; lev < nlev; ++lev) {
+    const int t0 = c->level_start[lev], cnt = c->level_count[lev];
+    int maxb = 0;
+    for (int t = t0; t < t0 + cnt; ++t) maxb = std::max(maxb, nblk(t));
+    // forward: triangle blocks by ascending R, then the contribution blocks
+    c->sw_fwd_start[lev] = (int)(it.size() / 2);
+    for (int R = 0; R < maxb; ++R)
+      for (int t = t0; t < t0 + cnt; ++t)
+        if (nblk(t) > R) { it.push_back(t); it.push_back(R); }
+    for (int t = t0; t < t0 + cnt; ++t) {
+      if (nblk(t) == 0) continue;
+      const int ncb = (c->state_host[t].f - c->state_host[t].ksolve + DF_R - 1) / DF_R;
+      for (int j = 0; j < ncb; ++j) { it.push_back(t); it.push_back(-1 - j); }
+    }
+    c->sw_fwd_cnt[lev] = (int)(it.size() / 2) - c->sw_fwd_start[lev];
+    // backward: triangle blocks by descending R
+    c->sw_bwd_start[lev] = (int)(it.size() / 2);
+    for (int R = maxb - 1; R >= 0; --R)
+      for (int t = t0; t < t0 + cnt; ++t)
+        if (nblk(t) > R) { it.push_back(t); it.push_back(R); }
+    c->sw_bwd_cnt[lev] = (int)(it.size() / 2) - c->sw_bwd_start[lev];
+  }
+  c->sw_blocks = blocks;
+  const size_t ib = it.size() * sizeof(int32_t), bbytes = bb.size() * sizeof(int32_t);
+  int rc;
+  if ((rc = hf_ensure(c->d_swplan, ib + bbytes + 256))) return rc;
+  cudaStream_t s = hf_stream(c);
+  if (ib) HF_CUDA_TRY(cudaMemcpyAsync(c->d_swplan.p, it.data(), ib, cudaMemcpyHostToDevice, s));
+  HF_CUDA_TRY(cudaMemcpyAsync((char*)c->d_swplan.p + ib, bb.data(), bbytes, cudaMemcpyHostToDevice, s));
+  HF_CUDA_TRY(cudaStreamSynchronize(s));   // the host vectors go out of scope
+  return HF_OK;
+}
+
+// first diagonal block of every front (after the item pairs in d_swplan)
+static const int* sweep_bbase(const hf_ctx* c) {
+  size_t pairs = 0;
+  if (!c->sw_bwd_start.empty()) pairs = (size_t)c->sw_bwd_start.back() + c->sw_bwd_cnt.back();
+  return (const int*)((const char*)c->d_swplan.p + pairs * 2 * sizeof(int32_t));
+}
+
+// CTAs of a dataflow sweep launch: all resident at once is not required, only useful
+static int sweep_grid(bool fwd) {
+  static std::mutex mu;
+  static int per[2] = {0, 0}, sms = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sweep_df<false>, DF_TH, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sweep_df<true>, DF_TH, 0);
+    sms = std::max(sms, 1);
+  }
+  return sms * std::max(1, per[fwd ? 1 : 0]);
 }
 
 // HF_LEVEL_TIMES=1: device time of every level of the sweeps (diagnostic)
@@ -1587,6 +1904,13 @@ static void sweep_work(hf_ctx* c, int cls, int m, size_t esz) {
   c->work_bytes[cls] += ent * esz;
 }
 
+// HF_SWEEP_BLOCKED=1: the sweeps launch one GEMM per diagonal block (the form before
+// the dataflow levels; diagnostic comparison)
+static bool sweep_blocked() {
+  const char* v = std::getenv("HF_SWEEP_BLOCKED");
+  return v && v[0] == '1';
+}
+
 template <typename TF, typename TV>
 static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
   cudaStream_t s = hf_stream(c);
@@ -1597,6 +1921,14 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
   const int32_t* cbmap = (const int32_t*)c->d_cbmap.p;
   const unsigned gt = (unsigned)((m + SGC - 1) / SGC);
+  constexpr bool DF = sizeof(TF) == 4 && sizeof(TV) == 4;   // dataflow levels (FP32 factor)
+  static_assert(SGC == DF_C, "column tiles of both sweep forms");
+  const bool use_df = DF && !sweep_blocked();
+  const int2* items = (const int2*)c->d_swplan.p;
+  const int* bbase = sweep_bbase(c);
+  int* sync = (int*)((char*)vec + sweep_vec_bytes(c, m, sizeof(TV)));     // forward half
+  if (use_df) (void)cudaMemsetAsync(sync, 0, sweep_half_ints(c, m) * sizeof(int), s);   // errors: cudaGetLastError
+  int* flags = sync + sweep_tickets(c);
   SweepTimer tm(s, "fwd", m);
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
@@ -1608,6 +1940,17 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
       const unsigned cx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxcb * m / 1024), 512);
       for (int slot = 0; slot < 2; ++slot)
         HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m));
+    }
+    if constexpr (DF) if (use_df) {
+      const int ni = c->sw_fwd_cnt[lev];
+      if (ni > 0) {
+        const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(true));
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, (int)gt, items + c->sw_fwd_start[lev], ni,
+                                                                          bbase, flags, sync + lev, sweep_err(c)));
+      }
+      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m));
+      tm.end(lev, cnt, D.maxf, D.maxks);
+      continue;
     }
     const int nbk = (D.maxks + TS - 1) / TS;
     constexpr bool fused = sizeof(TV) == 4;          // next diagonal block solved inside the GEMM
@@ -1632,6 +1975,13 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
   const TF* arena = (const TF*)c->d_front.p;
   const int32_t* rowid = (const int32_t*)c->d_rowid.p;
   const unsigned gt = (unsigned)((m + SGC - 1) / SGC);
+  constexpr bool DF = sizeof(TF) == 4 && sizeof(TV) == 4;   // dataflow levels (FP32 factor)
+  const bool use_df = DF && !sweep_blocked();
+  const int2* items = (const int2*)c->d_swplan.p;
+  const int* bbase = sweep_bbase(c);
+  int* sync = (int*)((char*)vec + sweep_vec_bytes(c, m, sizeof(TV))) + sweep_half_ints(c, m);   // backward half
+  if (use_df) (void)cudaMemsetAsync(sync, 0, sweep_half_ints(c, m) * sizeof(int), s);   // errors: cudaGetLastError
+  int* flags = sync + sweep_tickets(c);
   SweepTimer tm(s, "bwd", m);
   for (int lev = 0; lev <= c->m; ++lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
@@ -1640,6 +1990,17 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
     HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m));
+    if constexpr (DF) if (use_df) {
+      const int ni = c->sw_bwd_cnt[lev];
+      if (ni > 0) {
+        const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(false));
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, (int)gt, items + c->sw_bwd_start[lev], ni,
+                                                                           bbase, flags, sync + lev, sweep_err(c)));
+      }
+      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m));
+      tm.end(lev, cnt, D.maxf, D.maxks);
+      continue;
+    }
     HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 2, false><<<dim3((D.maxks + SGR - 1) / SGR, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, 0));
     const int nbk = (D.maxks + TS - 1) / TS;
     constexpr bool fused = sizeof(TV) == 4;          // next diagonal block solved inside the GEMM
@@ -1899,7 +2260,14 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     if ((rc = colnorms(R, hnorm))) return rc;
     res = 0;
     for (int i = 0; i < m; ++i) res = std::max(res, hnorm[i] / bnorm[i]);
-    if (verbose) std::fprintf(stderr, "[hf] block GCR m=%d iter %d max |r|/|b| = %.3e\n", m, it, res);
+    if (verbose) {
+      std::vector<double> rr(m);
+      for (int i = 0; i < m; ++i) rr[i] = hnorm[i] / bnorm[i];
+      std::sort(rr.rbegin(), rr.rend());
+      const int above = (int)std::count_if(rr.begin(), rr.end(), [&](double v) { return v > c->opts.gcr_tol; });
+      std::fprintf(stderr, "[hf] block GCR m=%d iter %d max |r|/|b| = %.3e (columns above tol %d; next %.3e %.3e)\n", m, it,
+                   res, above, m > 1 ? rr[1] : 0.0, m > 2 ? rr[2] : 0.0);
+    }
     hist_res.push_back(res);
     if (!(res > c->opts.gcr_tol)) { conv = true; break; }
     if (n + 1 >= maxit) break;
@@ -1941,6 +2309,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     HF_CUDA_TRY(cudaStreamSynchronize(s));
     if (h) return HF_ERR_TIMEOUT;     // a tensor-core wait gave up: the products are not valid
   }
+  if ((rc = sweep_status(c))) return rc;   // a sweep wait gave up: the preconditioner is void
   return conv ? HF_OK : HF_ERR_NOT_CONVERGED;
 }
 
@@ -2182,7 +2551,7 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
     HF_LAUNCH(c, HF_PROF_SCALE, k_scale_out<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, y1, (const double*)c->d_q.p, x, ldx));
   }
   HF_CUDA_TRY(cudaGetLastError());
-  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  if ((rc = sweep_status(c))) return rc;
   return grc;
 }
 
@@ -2193,8 +2562,7 @@ int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W) {
   int rc;
   if ((rc = hf_ensure(c->d_solve, (blk * 3 + 64) * 8))) return rc;
   if ((rc = precond(c, m, R, W, c->d_solve.p))) return rc;
-  HF_CUDA_TRY(cudaStreamSynchronize(hf_stream(c)));
-  return HF_OK;
+  return sweep_status(c);
 }
 
 // dJ/dKbar_ij = -sum_r lam_i^r x_j^r on the stored pattern (adjoint of the solve); one warp per row
@@ -2244,7 +2612,7 @@ int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W) {
   const size_t esz = dbl ? 8 : 4;
   const size_t tmp_bytes = dbl ? (size_t)c->L * m * 8 : (size_t)c->L * m * 4 * 3;
   const size_t tmp_round = (tmp_bytes + 255) / 256 * 256;
-  const size_t vec_bytes = (size_t)c->row_elems * m * esz;
+  const size_t vec_bytes = sweep_vec_bytes(c, m, esz) + sweep_sync_bytes(c, m);
   if (tmp_round + vec_bytes > HF_NOALLOC_SCRATCH_BYTES) return HF_ERR_ARG;
   static std::mutex addr_mu;
   std::lock_guard<std::mutex> addr_lock(addr_mu);
@@ -2261,8 +2629,7 @@ int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W) {
   int rc = precond_on(c, m, R, W, base, base + tmp_round);
   c->prof_on = prof;
   if (rc) return rc;
-  HF_CUDA_TRY(cudaStreamSynchronize(hf_stream(c)));
-  return HF_OK;
+  return sweep_status(c);
 }
 
 // Kernel basis of K-bar (mixed form; after hf_schur): L x kernel_dim column-major on the device.
