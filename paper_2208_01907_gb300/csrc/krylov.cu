@@ -37,35 +37,36 @@ constexpr int TKK = 16;      // k chunk of the GEMM updates
 
 template <typename TV>
 __global__ void k_fwd_init(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
-                           const int32_t* __restrict__ rowid, TV* __restrict__ vec, const TV* __restrict__ B, int m) {
+                           const int32_t* __restrict__ rowid, TV* __restrict__ vec, const TV* __restrict__ B, int m,
+                           int vs) {
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const int f = st[t].f;
   const int nown = d.cand_all ? 0 : d.n;
-  TV* V = vec + d.row_off * m;
+  TV* V = vec + d.row_off * vs;
   const int32_t* rid = rowid + d.row_off;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)f * m; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
-    V[e] = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
+    V[(int64_t)i * vs + c] = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
   }
 }
 
 template <typename TV>
 __global__ void k_fwd_child(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0, int slot,
-                            const int32_t* __restrict__ cbmap, TV* __restrict__ vec, int m) {
+                            const int32_t* __restrict__ cbmap, TV* __restrict__ vec, int m, int vs) {
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const int ch = slot == 0 ? d.child0 : d.child1;
   if (ch < 0) return;
   const NodeDesc dc = nd[ch];
   const int kc = st[ch].k, mc = st[ch].f - kc;
-  const TV* U = vec + (dc.row_off + kc) * m;
+  const TV* U = vec + (dc.row_off + kc) * vs;
   const int32_t* map = cbmap + dc.row_off;
-  TV* V = vec + d.row_off * m;
+  TV* V = vec + d.row_off * vs;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)mc * m; e += (int64_t)gridDim.x * blockDim.x) {
     int a = (int)(e / m), c = (int)(e - (int64_t)a * m);
     int tg = map[a];
-    if (tg >= 0) V[(int64_t)tg * m + c] += U[e];
+    if (tg >= 0) V[(int64_t)tg * vs + c] += U[(int64_t)a * vs + c];
   }
 }
 
@@ -73,17 +74,17 @@ __global__ void k_fwd_child(const NodeDesc* __restrict__ nd, const NodeState* __
 template <typename TF, typename TV>
 __global__ void k_fwd_store(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
                            const TF* __restrict__ arena, const int32_t* __restrict__ rowid,
-                           const TV* __restrict__ vec, TV* __restrict__ Y, int m) {
+                           const TV* __restrict__ vec, TV* __restrict__ Y, int m, int vs) {
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const NodeState S = st[t];
   const int hi = d.cand_all ? S.f : S.k;
   const TF* F = arena + d.front_off;
-  const TV* V = vec + d.row_off * m;
+  const TV* V = vec + d.row_off * vs;
   const int32_t* rid = rowid + d.row_off;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)hi * m; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
-    TV v = V[e];
+    TV v = V[(int64_t)i * vs + c];
     if (i < S.ksolve) v = v / (TV)F[i + (int64_t)i * d.ld];
     Y[(int64_t)rid[i] * m + c] = v;
   }
@@ -92,30 +93,31 @@ __global__ void k_fwd_store(const NodeDesc* __restrict__ nd, const NodeState* __
 template <typename TV>
 __global__ void k_bwd_init(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
                            const int32_t* __restrict__ rowid, TV* __restrict__ vec, const TV* __restrict__ Y,
-                           const TV* __restrict__ X, int m) {
+                           const TV* __restrict__ X, int m, int vs) {
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const NodeState S = st[t];
   if (S.ksolve == 0) return;
-  TV* V = vec + d.row_off * m;
+  TV* V = vec + d.row_off * vs;
   const int32_t* rid = rowid + d.row_off;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)S.f * m; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
-    V[e] = (i < S.ksolve) ? Y[(int64_t)rid[i] * m + c] : X[(int64_t)rid[i] * m + c];
+    V[(int64_t)i * vs + c] = (i < S.ksolve) ? Y[(int64_t)rid[i] * m + c] : X[(int64_t)rid[i] * m + c];
   }
 }
 
 template <typename TV>
 __global__ void k_bwd_store(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
-                            const int32_t* __restrict__ rowid, const TV* __restrict__ vec, TV* __restrict__ X, int m) {
+                            const int32_t* __restrict__ rowid, const TV* __restrict__ vec, TV* __restrict__ X, int m,
+                            int vs) {
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const int ks = st[t].ksolve;
-  const TV* V = vec + d.row_off * m;
+  const TV* V = vec + d.row_off * vs;
   const int32_t* rid = rowid + d.row_off;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)ks * m; e += (int64_t)gridDim.x * blockDim.x) {
     int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
-    X[(int64_t)rid[i] * m + c] = V[e];
+    X[(int64_t)rid[i] * m + c] = V[(int64_t)i * vs + c];
   }
 }
 
@@ -402,30 +404,68 @@ __device__ __forceinline__ bool df_wait(const int* flag, int* abort_word, int* s
   return *s_ok != 0;
 }
 
+// After block `from` is known to be ready: the end of the run of blocks that are
+// ready as well (ascending from+1, from+2, ... below `lim`, or descending from-1, ...
+// above `lim`), looking at up to DF_TH flags at once.  Uniform; one barrier.
+__device__ __forceinline__ int df_ready_run(const int* fl, int gt, int from, int lim, bool up, int* s_e) {
+  const int tid = threadIdx.x;
+  if (tid == 0) *s_e = up ? min(lim, from + 1 + DF_TH) : max(lim, from - 1 - DF_TH);
+  __syncthreads();
+  const int b = up ? from + 1 + tid : from - 1 - tid;
+  if (up ? b < lim : b > lim) {
+    if (!df_ld_acquire(fl + (int64_t)b * gt)) {
+      if (up) atomicMin(s_e, b);
+      else atomicMax(s_e, b);
+    }
+  }
+  __syncthreads();
+  const int e = *s_e;
+  __syncthreads();
+  return e;   // up: blocks [from, e) ready; down: blocks (e, from] ready
+}
+
+// cp.async (global -> shared, no registers): 4-byte copies for the factor (read-only in
+// the sweeps), 16-byte L2-only copies for the vectors (written by other CTAs of the launch)
+__device__ __forceinline__ uint32_t df_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void df_cp4(void* dst, const void* src, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(df_smem(dst)), "l"(src), "r"(pred ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void df_cp16(void* dst, const void* src, bool pred) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(df_smem(dst)), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void df_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void df_wait_copies() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+constexpr int DF_ST = 3;       // cp.async pipeline stages
+
+// vs: row stride of the per-front vectors (m rounded up to 4, so that rows are 16-byte aligned)
 template <bool FWD>
-__global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
-                                                   const float* __restrict__ arena, float* vec, int m, int gt,
+__global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                   const float* __restrict__ arena, float* vec, int m, int vs, int gt,
                                                    const int2* __restrict__ items, int nitems,
                                                    const int* __restrict__ blockbase, int* flags, int* counter,
                                                    int* abort_word) {
-  constexpr int APT = DF_K * DF_R / DF_TH;     // A elements per thread per chunk
-  constexpr int BPT = DF_K * DF_C / DF_TH;     // B elements per thread per chunk
-  struct Gemm { float A[2][DF_K][DF_R + 4]; float B[2][DF_K][DF_C + 4]; };
+  constexpr int APT = DF_K * DF_R / DF_TH;       // 4-byte A copies per thread per chunk
+  constexpr int BPT = DF_K * DF_C / 4 / DF_TH;   // 16-byte B copies per thread per chunk
+  struct Gemm { float A[DF_ST][DF_K][DF_R + 4]; float B[DF_ST][DF_K][DF_C + 4]; };
   constexpr int VS = DF_C + 1;
   constexpr size_t UB = sizeof(Gemm) > sizeof(float) * DF_R * VS ? sizeof(Gemm) : sizeof(float) * DF_R * VS;
-  __shared__ __align__(16) unsigned char ubuf[UB];     // GEMM staging, then the block being solved
+  __shared__ __align__(16) unsigned char ubuf[UB];     // GEMM stages, then the block being solved
   __shared__ float Ls[TS][TS + 1];
-  __shared__ int s_ticket, s_ok;
+  __shared__ int s_ticket, s_ok, s_e;
   Gemm& G = *reinterpret_cast<Gemm*>(ubuf);
   float (*Vs)[VS] = reinterpret_cast<float (*)[VS]>(ubuf);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t total = (int64_t)nitems * gt;
+  int next = 0;
+  if (tid == 0) next = atomicAdd(counter, 1);
   for (;;) {
-    if (tid == 0) s_ticket = atomicAdd(counter, 1);
+    if (tid == 0) s_ticket = next;
     __syncthreads();
     const int ticket = s_ticket;
     if (ticket >= total) return;
+    if (tid == 0) next = atomicAdd(counter, 1);          // the next item's ticket, taken early
     const int2 it = items[ticket / gt];
     const int C = ticket - (ticket / gt) * gt;
     const int t = it.x, code = it.y;
@@ -434,7 +474,7 @@ __global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__
     const int nblk = (ks + DF_R - 1) / DF_R;
     const int64_t ld = d.ld;
     const float* F = arena + d.front_off;
-    float* V = vec + d.row_off * m;
+    float* V = vec + d.row_off * vs;
     const int c0 = C * DF_C;
     const bool tri = code >= 0;
     const int r0 = tri ? code * DF_R : ks + (-1 - code) * DF_R;
@@ -454,16 +494,12 @@ __global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; tot[i][j] = 0.f; }
-    auto flush = [&]() {
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) { tot[i][j] += acc[i][j]; acc[i][j] = 0.f; }
-    };
-    float pa[APT], pb[BPT];
-    // acc += A(rows of the item, k in [k_lo, k_hi)) * V(k rows, tile columns)
+    // acc += A(rows of the item, k in [k_lo, k_hi)) * V(k rows, tile columns); k_lo is a
+    // multiple of DF_R or the start of the ancestors' rows
     auto gemm_range = [&](int k_lo, int k_hi) {
-      auto load = [&](int kc) {
+      const int nch = (k_hi - k_lo + DF_K - 1) / DF_K;
+      auto issue = [&](int ch) {
+        const int kc = k_lo + ch * DF_K, stg = ch % DF_ST;
 #pragma unroll
         for (int u = 0; u < APT; ++u) {
           const int e = tid + u * DF_TH;
@@ -471,45 +507,35 @@ __global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__
           if (FWD) { kk = e / DF_R; rr = e % DF_R; }    // rows contiguous in column q
           else { rr = e / DF_K; kk = e % DF_K; }        // k contiguous in column r0 + rr
           const int q = kc + kk;
-          float a = 0.f;
-          if (q < k_hi && rr < nr) a = FWD ? __ldg(F + (r0 + rr) + (int64_t)q * ld) : __ldg(F + q + (int64_t)(r0 + rr) * ld);
-          pa[u] = a;
+          const bool ok = q < k_hi && rr < nr;
+          const float* src = ok ? (FWD ? F + (r0 + rr) + (int64_t)q * ld : F + q + (int64_t)(r0 + rr) * ld) : F;
+          df_cp4(&G.A[stg][kk][rr], src, ok);
         }
 #pragma unroll
         for (int u = 0; u < BPT; ++u) {
           const int e = tid + u * DF_TH;
-          const int kk = e / DF_C, cc = e % DF_C;
-          const int q = kc + kk, c = c0 + cc;
-          pb[u] = (q < k_hi && c < m) ? __ldcg(V + (int64_t)q * m + c) : 0.f;
+          const int kk = e / (DF_C / 4), c4 = e % (DF_C / 4);
+          const int q = kc + kk, c = c0 + 4 * c4;
+          const bool ok = q < k_hi && c < vs;
+          df_cp16(&G.B[stg][kk][4 * c4], ok ? V + (int64_t)q * vs + c : V, ok);
         }
       };
-      auto stage = [&](int buf) {
 #pragma unroll
-        for (int u = 0; u < APT; ++u) {
-          const int e = tid + u * DF_TH;
-          int kk, rr;
-          if (FWD) { kk = e / DF_R; rr = e % DF_R; }
-          else { rr = e / DF_K; kk = e % DF_K; }
-          G.A[buf][kk][rr] = pa[u];
-        }
-#pragma unroll
-        for (int u = 0; u < BPT; ++u) {
-          const int e = tid + u * DF_TH;
-          G.B[buf][e / DF_C][e % DF_C] = pb[u];
-        }
-      };
-      load(k_lo);
-      stage(0);
-      __syncthreads();
-      int buf = 0;
-      for (int kc = k_lo; kc < k_hi; kc += DF_K) {
-        const bool more = kc + DF_K < k_hi;
-        if (more) load(kc + DF_K);
+      for (int ch = 0; ch < DF_ST - 1; ++ch) {
+        if (ch < nch) issue(ch);
+        df_commit();
+      }
+      for (int ch = 0; ch < nch; ++ch) {
+        df_wait_copies<DF_ST - 2>();                     // chunk ch has landed (this thread's copies)
+        __syncthreads();                                 // ... everyone's; stage of ch-1 is free
+        if (ch + DF_ST - 1 < nch) issue(ch + DF_ST - 1);
+        df_commit();
+        const int stg = ch % DF_ST;
 #pragma unroll
         for (int kk = 0; kk < DF_K; ++kk) {
-          const float4 a0 = *reinterpret_cast<const float4*>(&G.A[buf][kk][ty * 8]);
-          const float4 a1 = *reinterpret_cast<const float4*>(&G.A[buf][kk][ty * 8 + 4]);
-          const float4 b = *reinterpret_cast<const float4*>(&G.B[buf][kk][tx * 4]);
+          const float4 a0 = *reinterpret_cast<const float4*>(&G.A[stg][kk][ty * 8]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&G.A[stg][kk][ty * 8 + 4]);
+          const float4 b = *reinterpret_cast<const float4*>(&G.B[stg][kk][tx * 4]);
           const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
           const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
@@ -517,28 +543,39 @@ __global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
         }
-        if (more) stage(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-        if (!more || ((kc + DF_K - k_lo) % DF_R) == 0) flush();
+        if (ch == nch - 1 || ((ch + 1) * DF_K) % DF_R == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { tot[i][j] += acc[i][j]; acc[i][j] = 0.f; }
+        }
       }
+      __syncthreads();                                   // stages free for the next range / Vs
     };
+    // the blocks an item reads are taken in runs: wait for the next one, then extend the
+    // run over the blocks already published, and multiply the run as one k range
     bool ok = true;
     if (FWD) {
       const int bend = tri ? code : nblk;                 // blocks [0, bend) feed this item
-      for (int b = 0; b < bend && ok; ++b) {
+      for (int b = 0; b < bend && ok;) {
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok);
-        if (ok) gemm_range(b * DF_R, min(ks, (b + 1) * DF_R));
+        if (!ok) break;
+        const int e = df_ready_run(fl, gt, b, bend, true, &s_e);
+        gemm_range(b * DF_R, min(ks, e * DF_R));
+        b = e;
       }
     } else {
       if (f > ks) gemm_range(ks, f);                      // solved rows of the ancestors
-      for (int b = nblk - 1; b > code && ok; --b) {
+      for (int b = nblk - 1; b > code && ok;) {
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok);
-        if (ok) gemm_range(b * DF_R, min(ks, (b + 1) * DF_R));
+        if (!ok) break;
+        const int e = df_ready_run(fl, gt, b, code, false, &s_e);
+        gemm_range((e + 1) * DF_R, min(ks, (b + 1) * DF_R));
+        b = e;
       }
     }
     if (!ok) return;                                      // uniform: s_ok after a barrier
-    if (!tri) {                                           // contribution rows: v -= acc
+    if (!tri) {                                           // contribution rows: v -= tot
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = ty * 8 + i;
@@ -547,7 +584,7 @@ __global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__
         for (int j = 0; j < 4; ++j) {
           const int c = c0 + tx * 4 + j;
           if (c < m) {
-            float* p = V + (int64_t)(r0 + r) * m + c;
+            float* p = V + (int64_t)(r0 + r) * vs + c;
             *p = __ldcg(p) - tot[i][j];
           }
         }
@@ -561,14 +598,14 @@ __global__ void __launch_bounds__(DF_TH) k_sweep_df(const NodeDesc* __restrict__
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int cc = tx * 4 + j, c = c0 + cc;
-        Vs[r][cc] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * m + c) - tot[i][j] : 0.f;
+        Vs[r][cc] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * vs + c) - tot[i][j] : 0.f;
       }
     }
     __syncthreads();
     diag_solve<float, FWD, DF_C, DF_TH>(Ls, Vs, nr, tid);
     for (int e = tid; e < nr * DF_C; e += DF_TH) {
       const int r = e / DF_C, cc = e % DF_C;
-      if (c0 + cc < m) V[(int64_t)(r0 + r) * m + c0 + cc] = Vs[r][cc];
+      if (c0 + cc < m) V[(int64_t)(r0 + r) * vs + c0 + cc] = Vs[r][cc];
     }
     __syncthreads();
     if (tid == 0) {
@@ -1763,7 +1800,8 @@ struct Work {
 // sweeps: [forward tickets | forward flags | backward tickets | backward flags], one
 // ticket counter per level and one flag per (diagonal block, column tile).
 static size_t sweep_vec_bytes(const hf_ctx* c, int m, size_t esz) {
-  return ((size_t)c->row_elems * m * esz + 255) / 256 * 256;
+  const size_t vs = (size_t)(m + 3) / 4 * 4;      // the dataflow sweeps pad the rows to 16 bytes
+  return ((size_t)c->row_elems * vs * esz + 255) / 256 * 256;
 }
 static int sweep_tickets(const hf_ctx* c) { return (2 * (c->m + 1) + 63) / 64 * 64 / 2 + 32; }
 static size_t sweep_half_ints(const hf_ctx* c, int m) {
@@ -1924,6 +1962,7 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
   constexpr bool DF = sizeof(TF) == 4 && sizeof(TV) == 4;   // dataflow levels (FP32 factor)
   static_assert(SGC == DF_C, "column tiles of both sweep forms");
   const bool use_df = DF && !sweep_blocked();
+  const int vs = use_df ? (m + 3) / 4 * 4 : m;     // row stride of the per-front vectors
   const int2* items = (const int2*)c->d_swplan.p;
   const int* bbase = sweep_bbase(c);
   int* sync = (int*)((char*)vec + sweep_vec_bytes(c, m, sizeof(TV)));     // forward half
@@ -1935,20 +1974,20 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
     const LevelDims D = level_dims(c, lev);
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
-    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m));
+    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m, vs));
     if (D.maxcb > 0) {
       const unsigned cx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxcb * m / 1024), 512);
       for (int slot = 0; slot < 2; ++slot)
-        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m));
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m, vs));
     }
     if constexpr (DF) if (use_df) {
       const int ni = c->sw_fwd_cnt[lev];
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(true));
-        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, (int)gt, items + c->sw_fwd_start[lev], ni,
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_fwd_start[lev], ni,
                                                                           bbase, flags, sync + lev, sweep_err(c)));
       }
-      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m));
+      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
       tm.end(lev, cnt, D.maxf, D.maxks);
       continue;
     }
@@ -1961,7 +2000,7 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
       if (rx > 0)
         HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0, fused><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
-    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m));
+    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
     tm.end(lev, cnt, D.maxf, D.maxks);
   }
 }
@@ -1977,6 +2016,7 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
   const unsigned gt = (unsigned)((m + SGC - 1) / SGC);
   constexpr bool DF = sizeof(TF) == 4 && sizeof(TV) == 4;   // dataflow levels (FP32 factor)
   const bool use_df = DF && !sweep_blocked();
+  const int vs = use_df ? (m + 3) / 4 * 4 : m;     // row stride of the per-front vectors
   const int2* items = (const int2*)c->d_swplan.p;
   const int* bbase = sweep_bbase(c);
   int* sync = (int*)((char*)vec + sweep_vec_bytes(c, m, sizeof(TV))) + sweep_half_ints(c, m);   // backward half
@@ -1989,15 +2029,15 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
     if (D.maxks == 0) continue;
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
-    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m));
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m, vs));
     if constexpr (DF) if (use_df) {
       const int ni = c->sw_bwd_cnt[lev];
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(false));
-        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, (int)gt, items + c->sw_bwd_start[lev], ni,
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_bwd_start[lev], ni,
                                                                            bbase, flags, sync + lev, sweep_err(c)));
       }
-      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m));
+      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
       tm.end(lev, cnt, D.maxf, D.maxks);
       continue;
     }
@@ -2011,7 +2051,7 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
       if ((int)rx > 0)
         HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1, fused><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
-    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m));
+    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
     tm.end(lev, cnt, D.maxf, D.maxks);
   }
 }
