@@ -182,6 +182,23 @@ int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int
 int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
 
 /*
+ * The two dense products of the block GCR of Sec. 3.5 (Alg. 5) on their own, computed
+ * the way the iteration computes them (FP64-accurate BF16 tensor-core products when
+ * hf_opts.fp64_gemm == 0, native FP64 kernels otherwise), with ctx's stream and
+ * scratch; ctx is any context from hf_analyze (no factorization needed).
+ *   hf_gram_fp64:   G = scale * A^T B;  A: L x ma, B: L x mb (device, row-major),
+ *                   G: ma x mb (device, row-major, overwritten).
+ *   hf_update_fp64: Y = (Yinit ? Yinit : Y) + sgn * A C;  A, Y, Yinit: L x m, C: m x m
+ *                   (device, row-major); Y may not alias A or C; Yinit may be Y or NULL.
+ * Both synchronise the stream before returning.
+ * Errors: HF_ERR_ARG (sizes), HF_ERR_OOM, HF_ERR_CUDA, HF_ERR_TIMEOUT (a bounded
+ * tensor-core wait gave up; the output is not valid).
+ */
+int hf_gram_fp64(hf_ctx* ctx, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale);
+int hf_update_fp64(hf_ctx* ctx, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
+                   double sgn);
+
+/*
  * hf_precond without any device allocation (the paper has no counterpart; this is a
  * deployment variant).  For callers that must not allocate device memory while they
  * run: a process whose device memory is owned by another allocator (a framework's

@@ -16,6 +16,9 @@ int hf_schur_impl(hf_ctx* c);
 int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W);
 int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W);
+int hf_gram_fp64_impl(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale);
+int hf_update_fp64_impl(hf_ctx* c, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
+                        double sgn);
 int hf_kernel_basis_impl(hf_ctx* c, double* basis, int64_t ldb);
 int hf_values_adjoint_impl(hf_ctx* c, int m, const double* x, int64_t ldx, const double* lam, int64_t ldl,
                            double* grad);
@@ -241,6 +244,17 @@ int hf_values_adjoint(hf_ctx* c, int nrhs, const double* x, int64_t ldx, const d
                       double* grad_vals) {
   if (!c) return HF_ERR_ARG;
   return hf_values_adjoint_impl(c, nrhs, x, ldx, lam, ldl, grad_vals);
+}
+
+int hf_gram_fp64(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale) {
+  if (!c) return HF_ERR_ARG;
+  return hf_gram_fp64_impl(c, L, ma, mb, A, B, G, scale);
+}
+
+int hf_update_fp64(hf_ctx* c, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
+                   double sgn) {
+  if (!c) return HF_ERR_ARG;
+  return hf_update_fp64_impl(c, L, m, A, C, Y, Yinit, sgn);
 }
 
 int hf_precond_noalloc(hf_ctx* c, int m, const double* R, double* W) {

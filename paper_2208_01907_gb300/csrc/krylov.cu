@@ -2595,6 +2595,56 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
   return grc;
 }
 
+// The dense products of the block GCR on their own (public entry points): the same
+// calls as inside the iteration, on a context that may not have been factorized.
+static int products_prepare(hf_ctx* c) {
+  const bool fresh = c->d_flags.p == nullptr;
+  int rc;
+  if ((rc = hf_ensure(c->d_flags, FLAG_COUNT * sizeof(int) + 64))) return rc;
+  cudaStream_t s = hf_stream(c);
+  if (fresh) HF_CUDA_TRY(cudaMemsetAsync(c->d_flags.p, 0, FLAG_COUNT * sizeof(int) + 64, s));
+  HF_CUDA_TRY(cudaMemsetAsync(oz_err(c), 0, sizeof(int), s));
+  return HF_OK;
+}
+
+static int products_status(hf_ctx* c) {
+  int h = 0;
+  cudaStream_t s = hf_stream(c);
+  HF_CUDA_TRY(cudaGetLastError());
+  HF_CUDA_TRY(cudaMemcpyAsync(&h, oz_err(c), sizeof(int), cudaMemcpyDeviceToHost, s));
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  return h ? HF_ERR_TIMEOUT : HF_OK;
+}
+
+int hf_gram_fp64_impl(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale) {
+  if (L < 1 || ma < 1 || mb < 1 || !A || !B || !G) return HF_ERR_ARG;
+  int rc;
+  if ((rc = products_prepare(c))) return rc;
+  if ((rc = gram(c, L, ma, mb, A, B, G, scale))) return rc;
+  return products_status(c);
+}
+
+int hf_update_fp64_impl(hf_ctx* c, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
+                        double sgn) {
+  if (L < 1 || m < 1 || !A || !C || !Y || Y == A || Y == C) return HF_ERR_ARG;
+  int rc;
+  if ((rc = products_prepare(c))) return rc;
+  cudaStream_t s = hf_stream(c);
+  c->work_flops[HF_PROF_BLOCK_UPDATE] += 2.0 * (double)L * m * m;
+  c->work_bytes[HF_PROF_BLOCK_UPDATE] += 8.0 * (double)L * m * 3;
+  if (c->opts.fp64_gemm == 0) {
+    int* is = nullptr;
+    if ((rc = oz_iscratch(c, (size_t)L + m + 64, &is))) return rc;
+    if ((rc = hf_ensure(c->d_ozslice, hf_oz_slice_bytes(L, m) + hf_oz_slice_bytes(m, m) + 256))) return rc;
+    if ((rc = hf_oz_update(c, L, m, A, C, Y, Yinit, sgn, c->d_ozslice.p, c->d_ozslice.bytes, is, oz_err(c)))) return rc;
+  } else {
+    const size_t mm = (size_t)m * m;
+    const int use_smem = mm * 8 <= 48 * 1024;
+    HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nblk(L * m, 256), 256, use_smem ? mm * 8 : 0, s>>>(L, m, A, C, Y, Yinit, sgn, use_smem));
+  }
+  return products_status(c);
+}
+
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W) {
   if (!c || m < 1 || !R || !W) return HF_ERR_ARG;
   if (!c->factored) return HF_ERR_STATE;

@@ -112,7 +112,8 @@ __device__ __forceinline__ void oz_fixed(double x, int e, uint32_t& hi, uint32_t
   const int sh = ex - 1019 - e;                          // F = m 2^sh; sh <= 3 since |x| < 2^e
   unsigned long long F;
   if (sh >= 0) F = m << min(sh, 3);
-  else F = (sh > -64) ? (m >> (-sh)) : 0ull;
+  else F = (sh > -64) ? (((m >> (-sh - 1)) + 1ull) >> 1) : 0ull;   // to nearest (ties away): unbiased
+  // (no overflow: F < 2^56 needs rounding only when sh < 0, where F <= 2^53)
   hi = (uint32_t)(F >> 32);
   lo = (uint32_t)F;
 }

@@ -24,7 +24,8 @@ EXPORTED = (
     "hf_get_split", "hf_get_info", "hf_get_tree", "hf_get_pivots", "hf_get_factor", "hf_get_x12",
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
     "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc",
-    "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis", "hf_free",
+    "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis",
+    "hf_gram_fp64", "hf_update_fp64", "hf_free",
 )
 HF_NPROF = 13
 
@@ -97,6 +98,8 @@ def lib():
     L.hf_free.argtypes = [vp]
     L.hf_free.restype = None
     L.hf_get_kernel_basis.argtypes = [vp, vp, i64]
+    L.hf_gram_fp64.argtypes = [vp, i64, i32, i32, vp, vp, vp, dbl]
+    L.hf_update_fp64.argtypes = [vp, i64, i32, vp, vp, vp, vp, dbl]
     pp = C.POINTER(C.c_void_p)
     L.hf_factorize_batched.argtypes = [pp, i32, pp, dbl, vp]
     L.hf_schur_batched.argtypes = [pp, i32, vp]
@@ -204,6 +207,20 @@ class HybridFactor:
         """Same as precond(), with all scratch in the library's fixed device array (no allocation)."""
         m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
         _check(lib().hf_precond_noalloc(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond_noalloc")
+
+    def gram_fp64(self, A_dev, B_dev, G_dev, scale=1.0):
+        """G = scale * A^T B (Alg. 5's Gram products) on row-major L x ma / L x mb float64 CUDA tensors."""
+        L, ma = A_dev.shape
+        mb = B_dev.shape[1]
+        _check(lib().hf_gram_fp64(self._h, L, ma, mb, _ptr(A_dev), _ptr(B_dev), _ptr(G_dev), float(scale)),
+               "hf_gram_fp64")
+
+    def update_fp64(self, A_dev, C_dev, Y_dev, Yinit_dev=None, sgn=1.0):
+        """Y = (Yinit or Y) + sgn * A C (Alg. 5's block updates), row-major float64 CUDA tensors."""
+        L, m = A_dev.shape
+        yi = _ptr(Yinit_dev) if Yinit_dev is not None else None
+        _check(lib().hf_update_fp64(self._h, L, m, _ptr(A_dev), _ptr(C_dev), _ptr(Y_dev), yi, float(sgn)),
+               "hf_update_fp64")
 
     def values_adjoint(self, x_dev, lam_dev, grad_dev):
         """grad[e] = -sum_r lam[row_e, r] x[col_e, r] (tensors (nrhs, L) contiguous = column-major L x nrhs)."""
