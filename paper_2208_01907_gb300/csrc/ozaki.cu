@@ -56,6 +56,8 @@ constexpr int OZ_STAGE = OZ_A_STAGE + OZ_B_STAGE;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;  // + alignment slack
 constexpr int OZ_THREADS = 320;      // producer warp, MMA warp, 8 flush warps
 constexpr int OZ_WAIT_LIMIT = 1 << 20;
+constexpr int OZ_RG = 32;             // rows per TMA row group: 32 x 8 BF16 = 512 contiguous bytes
+__host__ __device__ constexpr int64_t oz_rows(int64_t R) { return (R + OZ_RG - 1) / OZ_RG * OZ_RG; }
 
 static_assert(OZ_SMEM <= 227 * 1024, "stage ring exceeds shared memory");
 static_assert((OZ_NEXACT + 1) * OZ_BJ <= 512, "accumulators exceed TMEM");
@@ -192,9 +194,15 @@ __global__ void k_fill_int(int* __restrict__ p, int n, int v) {
 // rows, so the 16-byte stores of each slice are contiguous.
 __global__ void k_oz_slice(const double* __restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
                            const int* __restrict__ e, uint4* __restrict__ dst, int64_t Kg) {
-  const int64_t total = R * Kg;
+  const int64_t Rp = oz_rows(R);                 // row stride of the slices; rows [R, Rp) are zero
+  const int64_t total = Rp * Kg;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = t % R, kg = t / R;
+    const int64_t r = t % Rp, kg = t / Rp;
+    if (r >= R) {
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s) dst[((int64_t)s * Kg + kg) * Rp + r] = make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
     const int er = e[r];
     uint32_t hi[8], lo[8], ng[8];
 #pragma unroll
@@ -210,7 +218,7 @@ __global__ void k_oz_slice(const double* __restrict__ X, int64_t R, int64_t K, i
       for (int q = 0; q < 4; ++q)
         w[q] = oz_bf16(oz_digit(hi[2 * q], lo[2 * q], s), s, ng[2 * q]) |
                (oz_bf16(oz_digit(hi[2 * q + 1], lo[2 * q + 1], s), s, ng[2 * q + 1]) << 16);
-      dst[((int64_t)s * Kg + kg) * R + r] = make_uint4(w[0], w[1], w[2], w[3]);
+      dst[((int64_t)s * Kg + kg) * Rp + r] = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -271,8 +279,8 @@ k_oz_mma(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtenso
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(OZ_STAGE) : "memory");
         const uint32_t sa = smem_u32(smem + st * OZ_STAGE);
         const int kg = (int)((s_beg + q) * (OZ_BK / 8));
-        tma_load_4d(sa, &ta, 0, i0, kg, 0, fb);
-        tma_load_4d(sa + OZ_A_STAGE, &tb, 0, j0, kg, 0, fb);
+        tma_load_4d(sa, &ta, 0, i0 / OZ_RG, kg, 0, fb);
+        tma_load_4d(sa + OZ_A_STAGE, &tb, 0, j0 / OZ_RG, kg, 0, fb);
         issued = q + 1;
       }
       // the last loads issued must land before the CTA exits
@@ -422,9 +430,14 @@ int slice_map(CUtensorMap* map, const void* base, int64_t R, int64_t Kg, int box
   EncodeTiledFn fn = encode_fn();
   if (!fn) return HF_ERR_CUDA;
   if (((uintptr_t)base & 15) != 0) return HF_ERR_ARG;
-  const cuuint64_t dims[4] = {8, (cuuint64_t)R, (cuuint64_t)Kg, (cuuint64_t)OZ_S};
-  const cuuint64_t strides[3] = {16, (cuuint64_t)R * 16, (cuuint64_t)Kg * R * 16};
-  const cuuint32_t box[4] = {8, (cuuint32_t)box_rows, (cuuint32_t)(OZ_BK / 8), (cuuint32_t)OZ_S};
+  // [S][Kg][Rp][8] BF16 seen as (8 * 32, Rp / 32, Kg, S): the inner dimension is a group of
+  // 32 rows (512 contiguous bytes); the shared-memory image, [S][4][box_rows][8], is that
+  // of a box with an 8-element inner dimension
+  const int64_t Rp = oz_rows(R);
+  const cuuint64_t dims[4] = {(cuuint64_t)(8 * OZ_RG), (cuuint64_t)(Rp / OZ_RG), (cuuint64_t)Kg, (cuuint64_t)OZ_S};
+  const cuuint64_t strides[3] = {(cuuint64_t)OZ_RG * 16, (cuuint64_t)Rp * 16, (cuuint64_t)Kg * Rp * 16};
+  const cuuint32_t box[4] = {(cuuint32_t)(8 * OZ_RG), (cuuint32_t)(box_rows / OZ_RG), (cuuint32_t)(OZ_BK / 8),
+                             (cuuint32_t)OZ_S};
   const cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -451,7 +464,7 @@ unsigned slice_grid(int64_t items) {
 }  // namespace
 
 // Bytes of slice storage for an operand with R rows and K columns.
-size_t hf_oz_slice_bytes(int64_t R, int64_t K) { return (size_t)OZ_S * (size_t)((K + 7) / 8) * (size_t)R * 16; }
+size_t hf_oz_slice_bytes(int64_t R, int64_t K) { return (size_t)OZ_S * (size_t)((K + 7) / 8) * (size_t)oz_rows(R) * 16; }
 
 // Number of split-K chunks hf_oz_gram uses (sizes its partial-sum scratch).
 int64_t hf_oz_gram_chunks(int64_t L, int ma, int mb) {
@@ -482,10 +495,10 @@ int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const doub
   HF_LAUNCH(c, HF_PROF_GRAM, k_fill_int<<<(ne + 255) / 256, 256, 0, s>>>(ea, ne, -1060));
   const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, L / 1024), 512);
   HF_LAUNCH(c, HF_PROF_GRAM, k_oz_exp_cols<<<dim3(gx, (ma + 127) / 128), 128, 0, s>>>(A, L, ma, ea));
-  HF_LAUNCH(c, HF_PROF_GRAM, k_oz_slice<<<slice_grid((int64_t)ma * Kg), 256, 0, s>>>(A, ma, L, 1, ma, ea, SA, Kg));
+  HF_LAUNCH(c, HF_PROF_GRAM, k_oz_slice<<<slice_grid(oz_rows(ma) * Kg), 256, 0, s>>>(A, ma, L, 1, ma, ea, SA, Kg));
   if (!same) {
     HF_LAUNCH(c, HF_PROF_GRAM, k_oz_exp_cols<<<dim3(gx, (mb + 127) / 128), 128, 0, s>>>(B, L, mb, eb));
-    HF_LAUNCH(c, HF_PROF_GRAM, k_oz_slice<<<slice_grid((int64_t)mb * Kg), 256, 0, s>>>(B, mb, L, 1, mb, eb, SB, Kg));
+    HF_LAUNCH(c, HF_PROF_GRAM, k_oz_slice<<<slice_grid(oz_rows(mb) * Kg), 256, 0, s>>>(B, mb, L, 1, mb, eb, SB, Kg));
   }
   CUtensorMap ta, tb;
   if ((rc = slice_map(&ta, SA, ma, Kg, OZ_BI))) return rc;
@@ -522,8 +535,8 @@ int hf_oz_update(hf_ctx* c, int64_t L, int m, const double* A, const double* C, 
   int* eb = iscratch + L;                  // m column exponents of C
   HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_exp<<<(unsigned)L, 32, 0, s>>>(A, m, 1, (int)L, m, ea));
   HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_exp<<<m, 32, 0, s>>>(C, 1, m, m, m, eb));
-  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_slice<<<slice_grid(L * Kg), 256, 0, s>>>(A, L, m, m, 1, ea, SA, Kg));
-  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_slice<<<slice_grid((int64_t)m * Kg), 256, 0, s>>>(C, m, m, 1, m, eb, SB, Kg));
+  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_slice<<<slice_grid(oz_rows(L) * Kg), 256, 0, s>>>(A, L, m, m, 1, ea, SA, Kg));
+  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_slice<<<slice_grid(oz_rows(m) * Kg), 256, 0, s>>>(C, m, m, 1, m, eb, SB, Kg));
   CUtensorMap ta, tb;
   if ((rc = slice_map(&ta, SA, L, Kg, OZ_BI))) return rc;
   if ((rc = slice_map(&tb, SB, m, Kg, OZ_BJ))) return rc;
