@@ -275,9 +275,9 @@ def run_ours(args):
         "block_update": ("tensor", bf16_sus, "k_oz_mma (FP64 update P C emulated: 36 BF16 slice products)",
                          "MEASURED_PEAKS.json bf16_tflops_sustained"),
         # with M ~ 400 right-hand sides the sweeps do 2 M flops per factor entry read: FP32 ALU-bound
-        "trsv_fwd": ("alu", fp32_simt, "k_gemm_upd (+ fused diagonal solves) forward sweep, FP32",
+        "trsv_fwd": ("alu", fp32_simt, "k_sweep_df<1> (dataflow forward sweep of a tree level, FP32)",
                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "trsv_bwd": ("alu", fp32_simt, "k_gemm_upd (+ fused diagonal solves) backward sweep, FP32",
+        "trsv_bwd": ("alu", fp32_simt, "k_sweep_df<0> (dataflow backward sweep of a tree level, FP32)",
                      "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
         "spmm": ("hbm", hbm, "k_spmm (FP64 CSR x block)", "MEASURED_PEAKS.json hbm_gbs"),
     }
@@ -291,7 +291,8 @@ def run_ours(args):
         achieved = dom_flops / (dom_ms / 1e3) / 1e12 if dom_flops else None
         unit = "TFLOP/s"
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "traffic": measured_traffic(kname.split(" ")[0]),
             "kernel": kname, "peak_source": psrc, "launches_per_step": dom_n / prof_steps,
             "ms_per_step": dom_ms / prof_steps}
 
@@ -378,6 +379,33 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + dram__bytes_write.sum) from
+    a committed ncu summary under profiles/ that names the kernel, its source file and
+    that file's SHA-256 at capture time; None when there is none or the source changed
+    since (the counters then describe another kernel)."""
+    import glob
+    import hashlib
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.strip().startswith(("kernel:", "source:", "source_sha256:",
+                                                              "dram_bytes_per_launch:")):
+                    k, v = line.strip().split(":", 1)
+                    fields[k] = v.strip()
+        if fields.get("kernel") != kernel or "dram_bytes_per_launch" not in fields:
+            continue
+        try:
+            with open(os.path.join(ROOT, fields["source"]), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != fields.get("source_sha256"):
+                    return None
+            return float(fields["dram_bytes_per_launch"])
+        except (OSError, KeyError, ValueError):
+            return None
+    return None
 
 
 def main():
