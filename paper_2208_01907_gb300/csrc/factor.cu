@@ -372,6 +372,7 @@ constexpr int PCL_THREADS = 512;
 constexpr int PCL_RPT = 2;                    // rows per thread: Rcap <= PCL_RPT * PCL_THREADS
 constexpr int PCL_CMAX = 16;
 constexpr int PCL_SLOTS = PCL_CMAX + 2;       // candidates of C CTAs, row k, row nact-1
+constexpr int PCL_SWAPS = 256;                // listed row interchanges staged in shared memory
 
 template <typename T> struct PclLayout {
   // bytes of dynamic shared memory for Rcap rows and panel width nb
@@ -388,7 +389,7 @@ template <typename T>
 __global__ void __launch_bounds__(PCL_THREADS, 1)
 k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, T* __restrict__ arena,
            int32_t* __restrict__ rowid, T* __restrict__ Gall, int32_t* __restrict__ pos0all, int nb, double tau,
-           int C, int Rcap) {
+           int C, int Rcap, int4* __restrict__ swlist, int* __restrict__ swcount) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -396,6 +397,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   __shared__ int red_i[32], red_p[32];
   __shared__ T s_bk;
   __shared__ int s_bp, s_act, s_w;
+  __shared__ int s_swa[PCL_SWAPS], s_swb[PCL_SWAPS];
   const int rank = (int)cl.block_rank();
   const int t = t0 + (int)(blockIdx.x / (unsigned)C);
   const NodeDesc d = nd[t];
@@ -415,6 +417,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   int32_t* rid = rowid + d.row_off;
   int32_t* pos0 = pos0all + d.row_off;
   const int ps = nb + 1;
+  const int swbase = swcount[t];                       // read before the cluster barrier below
   // dynamic shared memory
   T* P = (T*)smem_raw;                         // Rcap x ps: panel rows
   T* dgl = P + (size_t)Rcap * ps;              // running candidate diagonal
@@ -472,6 +475,28 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       cl.map_shared_rank(pdg, r)[base] = dgl[l];
     }
   };
+  // The row interchanges of the columns of earlier panels, [0, k0), are not needed by this
+  // panel nor by any later step of the front's factorization: they are appended, in order
+  // and tagged with this panel's k0, to the front's interchange list, and the columns are
+  // put in their final row order once, after the front's last panel (k_swap_sigma,
+  // k_swap_apply), instead of two strided accesses per column and pivot here.
+  int4* gl = swlist + 2 * d.row_off;                   // 2 ld entries: <= ld pivots + ld postponements
+  const int gcap = 2 * (int)ld;
+  int nsw = 0, gsw = swbase;
+  auto defer_swap = [&](int a, int b) {               // uniform across the block
+    if (nsw == PCL_SWAPS) {
+      __syncthreads();
+      if (rank == 0)
+        for (int i = tid; i < nsw; i += nt)
+          if (gsw + i < gcap) gl[gsw + i] = make_int4(s_swa[i], s_swb[i], k0, 0);
+      __syncthreads();
+      gsw += nsw;
+      nsw = 0;
+    }
+    if (tid == 0) { s_swa[nsw] = a; s_swb[nsw] = b; }
+    ++nsw;
+  };
+
   // rows are owned by fixed threads: position p belongs to thread (p - p0) % nt, so the
   // column updates of one pivot and the argmax of the next touch only the thread's rows
   while (k < k0 + nb && k < nact) {
@@ -551,16 +576,14 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       const int b = nact - 1;
       if (q != b) {
         const int bsl = sb + PCL_CMAX + 1;
-        // rows q and b over the columns outside the computed panel: [0, k0) and [k, q), spread
-        // over the cluster (ordered before any later use by the next cluster barrier)
-        {
-          const int nL = k0, nM = q - k;
-          for (int e = rank * nt + tid; e < nL + nM; e += C * nt) {
-            const int j = e < nL ? e : k + (e - nL);
-            const int64_t x = q + (int64_t)j * ld, y = b + (int64_t)j * ld;
-            const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
-          }
+        // rows q and b over the trailing columns [k, q), spread over the cluster (ordered
+        // before any later use by the next cluster barrier); over [0, k0): deferred
+        for (int e = rank * nt + tid; e < q - k; e += C * nt) {
+          const int j = k + e;
+          const int64_t x = q + (int64_t)j * ld, y = b + (int64_t)j * ld;
+          const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
         }
+        defer_swap(q, b);
         if (owner(q) == rank) {
           const int l = q - p0;
           for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = prow[(size_t)bsl * nb + c];
@@ -614,8 +637,8 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       }
     }
     __syncthreads();
-    // 5. loads first: rows k and q over the earlier panels' columns [0, k0) (spread over the
-    // cluster; not read again in this panel) and the new column k of the own rows (swap fused)
+    // 5. loads first: the new column k of the own rows (swap fused); the interchange of rows
+    // k and q over the earlier panels' columns [0, k0) is listed for the end of the panel
     T v[PCL_RPT];
     int64_t wy[PCL_RPT];
     T wx[PCL_RPT];
@@ -637,11 +660,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
         }
       }
     }
-    if (q != k)
-      for (int j = rank * nt + tid; j < k0; j += C * nt) {
-        const int64_t x = k + (int64_t)j * ld, y = q + (int64_t)j * ld;
-        const T tmp = F[x]; F[x] = F[y]; F[y] = tmp;
-      }
+    if (q != k) defer_swap(k, q);                      // rows k and q over [0, k0)
     // d_k by every thread: the owner's operations on the winner's row
     const T dk = dot_sub_seq(pdiag[wsl], rq, wv, kk);
     // 6. c_i = A(i, k) - sum_c L(i, c) w_c; L(i, k) = c_i / d_k; diagonals and magnitudes
@@ -668,6 +687,11 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   }
   // write back: computed panel columns (lower part), diagonals of the unpivoted rows, row data
   __syncthreads();
+  if (rank == 0) {                                     // the rest of this panel's interchanges
+    for (int i = tid; i < nsw; i += nt)
+      if (gsw + i < gcap) gl[gsw + i] = make_int4(s_swa[i], s_swb[i], k0, 0);
+    if (tid == 0) swcount[t] = min(gcap, gsw + nsw);
+  }
   const int kdone = k - k0;
   for (int c = 0; c < kdone; ++c)
     for (int p = max(p0, k0 + c) + tid; p < p1; p += nt)
@@ -687,6 +711,91 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
     if (stopped) S->stopped = 1;
   }
   cl.sync();                               // no CTA leaves while its shared memory may be written
+}
+
+// ---------------------------------------------------------------------------
+// Final row order of the factor columns of the cluster-panel fronts.  The panel lists its
+// row interchanges (a, b) tagged with its first column k0 instead of applying them to the
+// columns [0, k0) of earlier panels.  A column c must receive, in list order, every
+// interchange tagged k0 > c: walking the list backwards one panel at a time, the map
+// sigma (new row pos takes old row sigma[pos]) of the interchanges after panel g is
+// sigma_g = s_g o sigma_{g+1}, s_g the panel's own composition (tabulated by applying its
+// interchanges, in order, to an identity array).  k_swap_sigma stores sigma_g per panel;
+// k_swap_apply gathers each column through shared memory (coalesced reads and writes).
+// ---------------------------------------------------------------------------
+constexpr size_t SW_SMEM = 200 * 1024;   // fronts of up to 25,600 rows
+// sig layout per front (stride sf): groups g = 0.. (last panel first), each sg ints:
+// [tag k0, sigma[0 .. f)]
+__global__ void __launch_bounds__(256) k_swap_sigma(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                    int t0, const int4* __restrict__ swlist,
+                                                    const int* __restrict__ swcount, int* __restrict__ sig, int64_t sf,
+                                                    int sg, int gcap, int* __restrict__ ngrp) {
+  extern __shared__ int sw_smem[];
+  const int t = t0 + blockIdx.x;
+  const int n = swcount[t];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (n <= 0) { if (tid == 0) ngrp[blockIdx.x] = 0; return; }
+  const NodeDesc d = nd[t];
+  const int f = st[t].f;
+  const int4* list = swlist + 2 * d.row_off;
+  int* sigma = sw_smem;            // f
+  int* img = sw_smem + f;          // f: composition of one panel's interchanges
+  int* out = sig + (int64_t)blockIdx.x * sf;
+  for (int p = tid; p < f; p += nt) { sigma[p] = p; img[p] = p; }
+  __syncthreads();
+  int g = 0;
+  int i = n - 1;
+  while (i >= 0 && g < gcap) {
+    const int tag = list[i].z;
+    int j = i;
+    while (j > 0 && list[j - 1].z == tag) --j;         // entries [j, i]: one panel, in order
+    if (tid == 0)
+      for (int e = j; e <= i; ++e) {
+        const int a = list[e].x, b = list[e].y;
+        const int x = img[a]; img[a] = img[b]; img[b] = x;
+      }
+    __syncthreads();
+    for (int p = tid; p < f; p += nt) sigma[p] = img[sigma[p]];
+    __syncthreads();
+    int* og = out + (int64_t)g * sg;
+    if (tid == 0) og[0] = tag;
+    for (int p = tid; p < f; p += nt) og[1 + p] = sigma[p];
+    if (tid == 0)
+      for (int e = j; e <= i; ++e) { img[list[e].x] = list[e].x; img[list[e].y] = list[e].y; }
+    __syncthreads();
+    ++g;
+    i = j - 1;
+  }
+  if (tid == 0) ngrp[blockIdx.x] = g;
+}
+
+// One column c of a front per block: the rows [c + 1, f) take their final order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_swap_apply(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                    int t0, T* __restrict__ arena, const int* __restrict__ sig,
+                                                    int64_t sf, int sg, const int* __restrict__ ngrp) {
+  extern __shared__ __align__(16) unsigned char sw_buf[];
+  const int ng = ngrp[blockIdx.y];
+  if (ng == 0) return;
+  const int t = t0 + blockIdx.y;
+  const int c = blockIdx.x;
+  const int k = st[t].k, f = st[t].f;
+  if (c >= k) return;
+  const int* base = sig + (int64_t)blockIdx.y * sf;
+  int m = 0;                                           // panels with tag > c (tags decrease with g)
+  while (m < ng && base[(int64_t)m * sg] > c) ++m;
+  if (m == 0) return;
+  const int* sigma = base + (int64_t)(m - 1) * sg + 1;
+  const NodeDesc d = nd[t];
+  T* col = arena + d.front_off + (int64_t)c * d.ld;
+  T* buf = (T*)sw_buf;
+  const int r0 = c + 1;
+  for (int p = r0 + threadIdx.x; p < f; p += blockDim.x) buf[p - r0] = col[p];
+  __syncthreads();
+  for (int p = r0 + threadIdx.x; p < f; p += blockDim.x) {
+    const int q = sigma[p];                            // in [c + 1, f): interchanges tagged > c
+    if (q != p && q >= r0 && q < f) col[p] = buf[q - r0];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1051,6 +1160,8 @@ int run_levels(hf_ctx* c) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCL_SMEM));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_swap_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_swap_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM));
     if (cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
       (void)cudaGetLastError();
     // largest cluster (<= 16) that can be resident with the full shared-memory panel
@@ -1129,6 +1240,8 @@ int run_levels(hf_ctx* c) {
     if (use_gl && smem > 220 * 1024) return HF_ERR_ARG;
     const int pthreads = maxld > 1024 ? 1024 : 256;
     const int tiles = (maxld + TB - 1) / TB;
+    int4* swl = (int4*)c->d_swlist.p;
+    int* swc = (int*)c->d_swcount.p;
     cudaLaunchConfig_t lc = {};
     cudaLaunchAttribute la[1];
     if (use_cl) {
@@ -1148,7 +1261,8 @@ int run_levels(hf_ctx* c) {
     for (int p = 0; p < npan; ++p) {
       if (use_cl)
         HF_LAUNCH(c, HF_PROF_PANEL, HF_CUDA_TRY(cudaLaunchKernelEx(&lc, k_panel_cl<T>, nd, st, t0, arena, rowid, gmag,
-                                                                   (int32_t*)c->d_pos0.p, nbl, c->tau, C, Rcap)));
+                                                                   (int32_t*)c->d_pos0.p, nbl, c->tau, C, Rcap,
+                                                                   swl, swc)));
       if (use_gl)
         HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag,
                                                                            (int32_t*)c->d_pos0.p, nbl, c->tau, cap));
@@ -1160,6 +1274,21 @@ int run_levels(hf_ctx* c) {
                                                        TT_THREADS, TT_SMEM, s>>>(nd, st, t0, (float*)arena, parts, flags));
       } else
         HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena));
+    }
+    if (use_cl) {
+      // the listed interchanges of this level's cluster-panel fronts, in their final order
+      if ((size_t)2 * maxld * sizeof(int) > SW_SMEM || (size_t)maxld * sizeof(T) > SW_SMEM) return HF_ERR_ARG;
+      const int gcap = npan + 1;
+      const int sg = maxld + 1;
+      const int64_t sf = (int64_t)gcap * sg;
+      int rc2;
+      if ((rc2 = hf_ensure(c->d_swsig, (size_t)cnt * sf * sizeof(int) + ((size_t)cnt + 1) * sizeof(int) + 64))) return rc2;
+      int* sig = (int*)c->d_swsig.p;
+      int* ngrp = sig + (size_t)cnt * sf;
+      HF_LAUNCH(c, HF_PROF_PANEL, k_swap_sigma<<<cnt, 256, (size_t)2 * maxld * sizeof(int), s>>>(
+                                      nd, st, t0, (const int4*)swl, swc, sig, sf, sg, gcap, ngrp));
+      HF_LAUNCH(c, HF_PROF_PANEL, k_swap_apply<T><<<dim3((unsigned)maxld, (unsigned)cnt), 256, (size_t)maxld * sizeof(T), s>>>(
+                                      nd, st, t0, arena, sig, sf, sg, ngrp));
     }
     if (level_times) {
       float ms = 0;
@@ -1258,6 +1387,10 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     if (!dbl && c->opts.trailing == 0 && (rc = hf_ensure(c->d_tparts, ((size_t)c->row_elems + TT_M) * 768 + 256))) return rc;
     if ((rc = hf_ensure(c->d_pos0, (size_t)c->row_elems * 4 + 64))) return rc;
     if ((rc = hf_ensure(c->d_invpos, (size_t)c->row_elems * 4 + 64))) return rc;
+    // listed row interchanges of the cluster panels: 2 ld entries per front, one count per front
+    if ((rc = hf_ensure(c->d_swlist, (size_t)c->row_elems * 2 * sizeof(int4) + 64))) return rc;
+    if ((rc = hf_ensure(c->d_swcount, ((size_t)c->n_nodes + 1) * sizeof(int) + 64))) return rc;
+    HF_CUDA_TRY(cudaMemsetAsync(c->d_swcount.p, 0, ((size_t)c->n_nodes + 1) * sizeof(int), s));
     HF_CUDA_TRY(cudaMemsetAsync(c->d_flags.p, 0, FLAG_COUNT * sizeof(int) + 64, s));
     HF_CUDA_TRY(cudaMemcpyAsync(c->d_rowid.p, c->d_rowid_static.p, c->rowid_static.size() * 4,
                                 cudaMemcpyDeviceToDevice, s));

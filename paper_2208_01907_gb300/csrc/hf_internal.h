@@ -87,6 +87,8 @@ struct hf_ctx {
   DevBuf d_gmag;                     // per front row: |K_ii| + accumulated |l|^2 |d| (null-pivot test)
   DevBuf d_pos0;                     // per front row: its position before pivoting
   DevBuf d_invpos;                   // inverse of d_pos0 (scratch)
+  DevBuf d_swlist, d_swcount;        // row interchanges listed by the cluster panel (per front)
+  DevBuf d_swsig;                    // per level: row maps of the listed interchanges (scratch)
   int front_prec = -1;               // precision the arena was sized for
   DevBuf d_flags;                    // int flags: [0] delay overflow, [1] numeric error
   DevBuf d_lam2pos;                  // L ints: position in Lambda_2 or -1
