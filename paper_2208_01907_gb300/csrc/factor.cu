@@ -553,19 +553,28 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       if (owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, T(0), kk);
     }
     if (C > 1) cl.sync(); else __syncthreads();                            // the only cluster barrier
-    // 3. the decision from the local slots (the same in every CTA): one thread, so that the
-    // two FP64 threshold tests do not occupy the FP64 pipe for the whole block
+    // 3. the decision from the local slots (the same in every CTA): the argmax by one warp,
+    // the two FP64 threshold tests by one thread (not on the FP64 pipe of the whole block)
     const int sb = buf * PCL_SLOTS;
-    if (tid == 0) {
+    if (tid < 32) {
+      // argmax over the C slots by the lanes (the order is strict: ids are unique)
       T gk = T(-2);
       int gi = 0x7fffffff, gw = -1;
-      for (int r = 0; r < C; ++r)
-        if (ppos[sb + r] >= 0 && better_t(pkey[sb + r], psid[sb + r], gk, gi)) { gk = pkey[sb + r]; gi = psid[sb + r]; gw = r; }
-      int a2 = 0;
-      if (!((double)gk >= tau * dref)) a2 = 1;                                   // ratio test (R2/R3)
-      else if (!((double)gk >= tau * (double)pG[sb + gw])) a2 = 2;              // null pivot (R3b)
-      s_act = a2;
-      s_w = gw;
+      if (tid < C && ppos[sb + tid] >= 0) { gk = pkey[sb + tid]; gi = psid[sb + tid]; gw = tid; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ok = __shfl_xor_sync(0xffffffffu, gk, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, gi, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, gw, o);
+        if (better_t(ok, oi, gk, gi)) { gk = ok; gi = oi; gw = ow; }
+      }
+      if (tid == 0) {
+        int a2 = 0;
+        if (!((double)gk >= tau * dref)) a2 = 1;                                 // ratio test (R2/R3)
+        else if (!((double)gk >= tau * (double)pG[sb + gw])) a2 = 2;            // null pivot (R3b)
+        s_act = a2;
+        s_w = gw;
+      }
     }
     __syncthreads();
     const int act = s_act, wsl = sb + s_w;
