@@ -850,19 +850,28 @@ __global__ void __launch_bounds__(256) k_chol_coop(int m, double* __restrict__ A
   }
 }
 
-// C = R^-1 R^-T Y (dropped directions give zero rows), m x ny row-major, blocked
-__global__ void __launch_bounds__(256) k_chol_solve_coop(int m, int ny, const double* __restrict__ R,
+// C = R^-1 R^-T Y (dropped directions give zero rows), m x ny row-major, blocked by CB
+// rows.  The right-hand sides are independent: block b solves the columns [b cpb, (b+1) cpb)
+// alone (block barriers only); per element the operations and their order are those of the
+// blocked substitution (diagonal block solved in registers, then the rows below (above)
+// updated by the CB-term dot product of the block).
+__global__ void __launch_bounds__(256) k_chol_solve_cols(int m, int ny, int cpb, const double* __restrict__ R,
                                                        const int* __restrict__ drop, const double* __restrict__ Y,
                                                        double* __restrict__ C) {
-  namespace cg = cooperative_groups;
-  cg::grid_group grid = cg::this_grid();
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gnt = gridDim.x * blockDim.x;
-  for (int64_t e = gtid; e < (int64_t)m * ny; e += gnt) C[e] = Y[e];
-  grid.sync();
+  const int c0 = blockIdx.x * cpb, c1 = min(ny, c0 + cpb);
+  const int nc = c1 - c0;
+  if (nc <= 0) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < m * nc; e += nt) {
+    const int64_t x = (int64_t)(e / nc) * ny + c0 + e % nc;
+    C[x] = Y[x];
+  }
+  __syncthreads();
   // forward: R^T z = y
   for (int jb = 0; jb < m; jb += CB) {
     const int je = min(m, jb + CB);
-    for (int c = gtid; c < ny; c += gnt) {
+    if (tid < nc) {
+      const int c = c0 + tid;
       double x[CB];
 #pragma unroll
       for (int u = 0; u < CB; ++u) {
@@ -876,20 +885,21 @@ __global__ void __launch_bounds__(256) k_chol_solve_coop(int m, int ny, const do
         }
       }
     }
-    grid.sync();
+    __syncthreads();
     const int nr = m - je;
-    for (int64_t e = gtid; e < (int64_t)nr * ny; e += gnt) {
-      const int i = je + (int)(e / ny), c = (int)(e % ny);
+    for (int e = tid; e < nr * nc; e += nt) {
+      const int i = je + e / nc, c = c0 + e % nc;
       double acc = 0.0;
       for (int k = jb; k < je; ++k) acc += R[k * m + i] * C[(int64_t)k * ny + c];
       C[(int64_t)i * ny + c] -= acc;
     }
-    grid.sync();
+    __syncthreads();
   }
   // backward: R x = z, blocks from the bottom
   for (int je = m; je > 0; je -= CB) {
     const int jb = max(0, je - CB);
-    for (int c = gtid; c < ny; c += gnt) {
+    if (tid < nc) {
+      const int c = c0 + tid;
       double x[CB];
 #pragma unroll
       for (int u = CB - 1; u >= 0; --u) {
@@ -904,14 +914,14 @@ __global__ void __launch_bounds__(256) k_chol_solve_coop(int m, int ny, const do
         }
       }
     }
-    grid.sync();
-    for (int64_t e = gtid; e < (int64_t)jb * ny; e += gnt) {
-      const int i = (int)(e / ny), c = (int)(e % ny);
+    __syncthreads();
+    for (int e = tid; e < jb * nc; e += nt) {
+      const int i = e / nc, c = c0 + e % nc;
       double acc = 0.0;
       for (int k = jb; k < je; ++k) acc += R[i * m + k] * C[(int64_t)k * ny + c];
       C[(int64_t)i * ny + c] -= acc;
     }
-    grid.sync();
+    __syncthreads();
   }
 }
 
@@ -2169,10 +2179,9 @@ static int coop_grid(hf_ctx* c) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int p1 = 0, p2 = 0;
+    int p1 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_chol_coop, 256, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_chol_solve_coop, 256, 0);
-    per = std::min(p1, p2);
+    per = p1;
     blocks = std::max(1, sms * std::min(per, 1));
   }
   (void)c;
@@ -2277,9 +2286,10 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   auto msolve = [&](int q, const double* Y, double* C) -> int {
     const double* Rq = Mstore + (size_t)q * mm;
     const int* dq = dropv + (size_t)q * dstride;
-    int mm_ = m, ny = m;
-    void* args[] = {&mm_, &ny, (void*)&Rq, (void*)&dq, (void*)&Y, (void*)&C};
-    HF_LAUNCH(c, HF_PROF_VECTOR, HF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_chol_solve_coop, cgrid, 256, args, 0, s)));
+    // one block per few right-hand sides: about one block per SM
+    const int cpb = std::max(1, (m + cgrid - 1) / cgrid);
+    const unsigned nbk = (unsigned)((m + cpb - 1) / cpb);
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_chol_solve_cols<<<nbk, 256, 0, s>>>(m, m, cpb, Rq, dq, Y, C));
     return HF_OK;
   };
   for (int n = 0; n < maxit; ++n) {
