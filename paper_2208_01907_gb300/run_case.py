@@ -4,7 +4,8 @@
 
 builds the 3D Stokes-like system of the benchmark at n^3 nodes, runs `factorize`
 (twice with --warm, so that the delayed-row capacity has settled), then `schur` and
-`solve` as requested by --phase, and prints one line.  Nothing is timed here; the
+`solve` as requested by --phase, and prints one line.  --phase gram / update runs one
+block-GCR product (hf_gram_fp64 / hf_update_fp64) on seeded L x m operands instead.  Nothing is timed here; the
 point is a fixed, short sequence of launches for a kernel profiler.
 """
 import argparse
@@ -21,7 +22,8 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=32)
-    ap.add_argument("--phase", choices=["factorize", "schur", "solve"], default="schur")
+    ap.add_argument("--phase", choices=["factorize", "schur", "solve", "gram", "update"], default="schur")
+    ap.add_argument("--m", type=int, default=388, help="columns of the gram / update operands")
     ap.add_argument("--warm", action="store_true", help="factorize twice before the measured phases")
     ap.add_argument("--fp64-gemm", type=int, default=0)
     args = ap.parse_args()
@@ -29,6 +31,26 @@ def main():
     import paper_2208_01907_gb300 as hf
     from workloads import stokes3d, consistent_rhs
 
+    if args.phase in ("gram", "update"):
+        # one product of the block GCR at the workload's shape (L of the n^3 Stokes-like
+        # system, m columns), seeded operands, through the public entry points
+        from workloads import diffusion2d
+        s = stokes3d(args.n, seed=2)
+        small = diffusion2d(12, 12, n_islands=0, seed=3)
+        H = hf.HybridFactor(small.L, small.rowptr, small.col, small.coords, fp64_gemm=args.fp64_gemm)
+        g = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(s.L, args.m, device="cuda", dtype=torch.float64, generator=g)
+        B = torch.randn(s.L, args.m, device="cuda", dtype=torch.float64, generator=g)
+        if args.phase == "gram":
+            G = torch.zeros(args.m, args.m, device="cuda", dtype=torch.float64)
+            H.gram_fp64(A, B, G, 1.0)
+        else:
+            C = torch.randn(args.m, args.m, device="cuda", dtype=torch.float64, generator=g)
+            Y = torch.zeros_like(A)
+            H.update_fp64(A, C, Y, B, -1.0)
+        torch.cuda.synchronize()
+        print(f"run_case {args.phase} L={s.L} m={args.m}")
+        return
     s = stokes3d(args.n, seed=2)
     H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, fp64_gemm=args.fp64_gemm)
     vals = torch.tensor(s.val, device="cuda", dtype=torch.float64)
