@@ -232,6 +232,7 @@ struct OzMma {
   const double* init;         // update mode: out = (init ? init : out) + alpha * AB
   double alpha;
   int partial;                // 1: out is a [chunks][Mi][Nj] partial buffer
+  int upper;                  // 1 (A^T A): only tiles meeting the upper triangle j >= i are needed
   int* err;
 };
 
@@ -245,6 +246,7 @@ k_oz_mma(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtenso
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j0 = blockIdx.x * OZ_BJ, i0 = blockIdx.y * OZ_BI;
+  if (p.upper && j0 + OZ_BJ - 1 < i0) return;        // tile strictly below the diagonal: not read
   const int64_t s_beg = (int64_t)blockIdx.z * p.chunk_steps;
   const int64_t n = max((int64_t)0, min(p.nsteps, s_beg + p.chunk_steps) - s_beg);
 
@@ -397,13 +399,10 @@ __global__ void k_oz_reduce(int Mi, int Nj, int nch, const double* __restrict__ 
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= Mi * Nj) return;
   int i = e / Nj, j = e % Nj;
+  // A^T A: only the upper triangle was computed; the lower one mirrors it (exactly symmetric)
+  const int a = (sym && i > j) ? j : i, b = (sym && i > j) ? i : j;
   double s = 0.0;
-  for (int c = 0; c < nch; ++c) s += part[((int64_t)c * Mi + i) * Nj + j];
-  if (sym) {   // A^T A: average the two triangles so the result is exactly symmetric
-    double s2 = 0.0;
-    for (int c = 0; c < nch; ++c) s2 += part[((int64_t)c * Mi + j) * Nj + i];
-    s = 0.5 * (s + s2);
-  }
+  for (int c = 0; c < nch; ++c) s += part[((int64_t)c * Mi + a) * Nj + b];
   G[e] = scale * s;
 }
 
@@ -511,6 +510,7 @@ int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const doub
   a.Mi = ma; a.Nj = mb; a.nsteps = nsteps; a.chunk_steps = chunk_steps;
   a.ea = ea; a.eb = eb;
   a.out = scratch; a.soi = 0; a.soj = 0; a.init = nullptr; a.alpha = 1.0; a.partial = 1; a.err = err;
+  a.upper = same ? 1 : 0;
   dim3 grid((mb + OZ_BJ - 1) / OZ_BJ, (ma + OZ_BI - 1) / OZ_BI, (unsigned)nch);
   HF_LAUNCH(c, HF_PROF_GRAM, k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, a));
   HF_LAUNCH(c, HF_PROF_GRAM, k_oz_reduce<<<(ma * mb + 255) / 256, 256, 0, s>>>(ma, mb, (int)nch, scratch, G, scale,
@@ -546,6 +546,7 @@ int hf_oz_update(hf_ctx* c, int64_t L, int m, const double* A, const double* C, 
   a.Mi = (int)L; a.Nj = m; a.nsteps = nsteps; a.chunk_steps = nsteps;
   a.ea = ea; a.eb = eb;
   a.out = Y; a.soi = m; a.soj = 1; a.init = Yinit; a.alpha = sgn; a.partial = 0; a.err = err;
+  a.upper = 0;
   dim3 grid((m + OZ_BJ - 1) / OZ_BJ, (unsigned)((L + OZ_BI - 1) / OZ_BI), 1);
   HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, a));
   HF_CUDA_TRY(cudaGetLastError());
