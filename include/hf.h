@@ -155,7 +155,9 @@ int hf_factorize(hf_ctx* ctx, const double* vals, double tau);
  * for the other forms S22 is taken from the factor.  Then S22 is factorized in FP64
  * by LDL^T with complete symmetric pivoting (Bunch-Parlett, 1x1 / 2x2 blocks), which puts
  * the null pivots last, and its kernel dimension is detected.
- * Errors: HF_ERR_STATE, HF_ERR_NOT_CONVERGED (results still usable), HF_ERR_CUDA, HF_ERR_OOM.
+ * Errors: HF_ERR_STATE, HF_ERR_NOT_CONVERGED (results still usable), HF_ERR_CUDA, HF_ERR_OOM,
+ * HF_ERR_TIMEOUT (a bounded wait of a tensor-core product or of a triangular sweep gave
+ * up: the results are not valid; a sweep timeout persists until the next hf_factorize).
  */
 int hf_schur(hf_ctx* ctx);
 
@@ -166,7 +168,8 @@ int hf_schur(hf_ctx* ctx);
  *   nrhs     number of right-hand sides (>= 1)
  *   b, ldb   device, column-major L x nrhs, leading dimension ldb >= L
  *   x, ldx   device, column-major L x nrhs output, ldx >= L (may not alias b)
- * Errors: HF_ERR_STATE, HF_ERR_ARG, HF_ERR_NOT_CONVERGED, HF_ERR_CUDA, HF_ERR_OOM.
+ * Errors: HF_ERR_STATE, HF_ERR_ARG, HF_ERR_NOT_CONVERGED, HF_ERR_CUDA, HF_ERR_OOM,
+ * HF_ERR_TIMEOUT (as for hf_schur).
  */
 int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int64_t ldx);
 
@@ -177,7 +180,11 @@ int hf_solve(hf_ctx* ctx, int nrhs, const double* b, int64_t ldb, double* x, int
  *   m     number of vectors (>= 1)
  *   R, W  device, row-major L x m (the m entries of an unknown contiguous); rows of
  *         Lambda_2 are ignored in R and set to zero in W.  W may not alias R.
- * Errors: HF_ERR_STATE (before hf_factorize), HF_ERR_ARG, HF_ERR_CUDA, HF_ERR_OOM.
+ * The FP32 forms run each tree level of the forward and backward substitution as one
+ * launch whose blocks wait (bounded) for the diagonal blocks they read; a wait that gives
+ * up is reported as HF_ERR_TIMEOUT (sticky until the next hf_factorize).
+ * Errors: HF_ERR_STATE (before hf_factorize), HF_ERR_ARG, HF_ERR_CUDA, HF_ERR_OOM,
+ * HF_ERR_TIMEOUT.
  */
 int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
 
@@ -209,7 +216,9 @@ int hf_update_fp64(hf_ctx* ctx, int64_t L, int m, const double* A, const double*
  * vectors and the precision-cast copies) lives in one file-scope device array of
  * 64 MiB that every GPU loading the library holds until the process exits.
  *  - Limits: rejects with HF_ERR_ARG any call whose scratch exceeds 64 MiB, i.e.
- *    (4 or 8) * m * (front rows of all fronts) + (12 or 8) * L * m bytes, rounded.
+ *    (4 or 8) * m4 * (front rows of all fronts) + (12 or 8) * L * m bytes, m4 = m rounded
+ *    up to a multiple of 4, plus 8 bytes per (64-row diagonal block, 64-column tile) for
+ *    the sweeps' tickets and flags, rounded.
  *  - The first call on a device looks up the array's device address (with that device
  *    current); make that first call before any stream capture.  Call with the device of
  *    the hf_factorize that built the context current.
@@ -220,7 +229,7 @@ int hf_update_fp64(hf_ctx* ctx, int64_t L, int m, const double* A, const double*
  *  - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.  Profiling
  *    events are not recorded for this call.
  * Errors: HF_ERR_ARG (bad argument or scratch above the limit), HF_ERR_STATE (before
- * hf_factorize), HF_ERR_CUDA.
+ * hf_factorize), HF_ERR_CUDA, HF_ERR_TIMEOUT (as for hf_precond).
  */
 int hf_precond_noalloc(hf_ctx* ctx, int m, const double* R, double* W);
 
