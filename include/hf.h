@@ -201,6 +201,24 @@ int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
  * Errors: HF_ERR_ARG (sizes), HF_ERR_OOM, HF_ERR_CUDA, HF_ERR_TIMEOUT (a bounded
  * tensor-core wait gave up; the output is not valid).
  */
+/*
+ * The iterations on K11 X = B compared in the paper (Sec. 3.3-3.5, Fig. 2), each with the
+ * lower-precision factor Q of hf_factorize as preconditioner, on the scaled unknowns:
+ *   method 0  block GCR on all m columns at once (Alg. 5; what hf_schur uses)
+ *   method 1  GCR one column at a time (Alg. 4)
+ *   method 2  iterative refinement (Alg. 3: x0 = Q^-1 b, then x += Q^-1 (b - K11 x))
+ *   m        number of columns (>= 1)
+ *   B, X     device, row-major L x m (the m entries of an unknown contiguous); the rows of
+ *            Lambda_2 must be zero in B and are zero in X.  X is overwritten.
+ *   maxit    iterations at most (>= 1); stop when max_k |r_k| / |b_k| <= opts.gcr_tol
+ *   hist     host, maxit + 1 doubles or NULL: hist[n] = max_k |r_k| / |b_k| after n
+ *            iterations (hist[0]: after x0 = Q^-1 b); entries past *iters are untouched
+ *   iters    host, iterations done (or NULL)
+ * Errors: HF_ERR_STATE (before hf_factorize), HF_ERR_ARG, HF_ERR_NOT_CONVERGED (X and
+ * hist still valid), HF_ERR_CUDA, HF_ERR_OOM, HF_ERR_TIMEOUT.
+ */
+int hf_k11_iterate(hf_ctx* ctx, int method, int m, const double* B, double* X, int maxit, double* hist, int* iters);
+
 int hf_gram_fp64(hf_ctx* ctx, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale);
 int hf_update_fp64(hf_ctx* ctx, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
                    double sgn);

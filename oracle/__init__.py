@@ -15,6 +15,8 @@ Parity status per function (what pins it is listed in tests/test_oracle_*.py):
   threshold_factorize     pinned (Eq. 1 reconstruction, tiny hand cases, tau limits)
   precond_apply           pinned (exact inverse of the recorded factor)
   block_gcr               pinned (invariants of Sec. 3.4-3.5, direct solve)
+  gcr_single              pinned (Krylov minimal residual with Q = I, equals block_gcr on one column)
+  iterative_refinement    pinned (closed form r_n = (I - A Q^-1)^n r_0 of Sec. 3.3)
   schur_direct            pinned (dense brute-force inverse, Eq. 2)
   bunch_kaufman           pinned (reconstruction, scipy/LAPACK sytrf comparison)
   kernel_dimension        pinned (dense SVD rank on small systems)

@@ -17,6 +17,7 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W);
 int hf_precond_noalloc_impl(hf_ctx* c, int m, const double* R, double* W);
 int hf_gram_fp64_impl(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale);
+int hf_k11_iterate_impl(hf_ctx* c, int method, int m, const double* B, double* X, int maxit, double* hist, int* iters);
 int hf_update_fp64_impl(hf_ctx* c, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
                         double sgn);
 int hf_kernel_basis_impl(hf_ctx* c, double* basis, int64_t ldb);
@@ -244,6 +245,11 @@ int hf_values_adjoint(hf_ctx* c, int nrhs, const double* x, int64_t ldx, const d
                       double* grad_vals) {
   if (!c) return HF_ERR_ARG;
   return hf_values_adjoint_impl(c, nrhs, x, ldx, lam, ldl, grad_vals);
+}
+
+int hf_k11_iterate(hf_ctx* c, int method, int m, const double* B, double* X, int maxit, double* hist, int* iters) {
+  if (!c) return HF_ERR_ARG;
+  return hf_k11_iterate_impl(c, method, m, B, X, maxit, hist, iters);
 }
 
 int hf_gram_fp64(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale) {

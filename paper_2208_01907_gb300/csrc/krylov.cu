@@ -2188,7 +2188,8 @@ static int coop_grid(hf_ctx* c) {
   return blocks;
 }
 
-static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, double* relres) {
+static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, double* relres,
+                     std::vector<double>* hist_out = nullptr) {
   cudaStream_t s = hf_stream(c);
   const int64_t L = c->L;
   const int maxit = std::max(1, c->opts.gcr_maxit);
@@ -2276,6 +2277,12 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   if ((rc = precond(c, m, B, X, tmp))) return rc;
   spmm(c, m, X, Z);
   HF_LAUNCH(c, HF_PROF_VECTOR, k_sub<<<nb, 256, 0, s>>>((int64_t)blk, B, Z, R));
+  if (hist_out) {                                   // max_k |r0_k| / |b_k| of the start
+    if ((rc = colnorms(R, hnorm))) return rc;
+    double r0 = 0;
+    for (int i = 0; i < m; ++i) r0 = std::max(r0, hnorm[i] / bnorm[i]);
+    hist_out->assign(1, r0);
+  }
   if ((rc = ensure_hist(0))) return rc;
   if ((rc = precond(c, m, R, Pm(0), tmp))) return rc;
   spmm(c, m, Pm(0), Qm(0));
@@ -2319,6 +2326,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
                    res, above, m > 1 ? rr[1] : 0.0, m > 2 ? rr[2] : 0.0);
     }
     hist_res.push_back(res);
+    if (hist_out) hist_out->push_back(res);
     if (!(res > c->opts.gcr_tol)) { conv = true; break; }
     if (n + 1 >= maxit) break;
     // stagnation: less than a 2x reduction over three iterations
@@ -2653,6 +2661,116 @@ int hf_update_fp64_impl(hf_ctx* c, int64_t L, int m, const double* A, const doub
     HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_block_axpy<<<nblk(L * m, 256), 256, use_smem ? mm * 8 : 0, s>>>(L, m, A, C, Y, Yinit, sgn, use_smem));
   }
   return products_status(c);
+}
+
+__global__ void k_addto(int64_t n, const double* __restrict__ W, double* __restrict__ X) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) X[e] += W[e];
+}
+
+// max_k |A_k| / bnorm_k over the m columns of a row-major L x m block (device reduction)
+static int max_col_ratio(hf_ctx* c, int m, const double* A, const std::vector<double>& bnorm, double* out,
+                         std::vector<double>* norms = nullptr) {
+  cudaStream_t s = hf_stream(c);
+  const int64_t L = c->L;
+  const int ncs = (int)std::max<int64_t>(1, std::min<int64_t>(L / 1024, 152));
+  int rc;
+  if ((rc = hf_ensure(c->d_small, std::max(((size_t)ncs + 1) * m * 8 + 64, (size_t)(1 << 20))))) return rc;
+  double* part = (double*)c->d_small.p;
+  double* sq = part + (size_t)ncs * m;
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_partial<<<dim3(ncs, (m + 127) / 128), 128, 0, s>>>(L, m, A, part));
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_reduce<<<(m + 127) / 128, 128, 0, s>>>(m, ncs, part, sq));
+  std::vector<double> g(m);
+  HF_CUDA_TRY(cudaMemcpyAsync(g.data(), sq, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  double r = 0;
+  for (int i = 0; i < m; ++i) {
+    const double v = std::sqrt(std::max(0.0, g[i]));
+    if (norms) (*norms)[i] = v;
+    r = std::max(r, bnorm.empty() ? v : v / bnorm[i]);
+  }
+  *out = r;
+  return HF_OK;
+}
+
+// The three iterations on K11 X = B that the paper compares (Sec. 3.3-3.5, Fig. 2), each
+// preconditioned by the lower-precision factor Q: block GCR on all columns (Alg. 5),
+// GCR one column at a time (Alg. 4: block GCR with one column), and iterative
+// refinement (Alg. 3: x0 = Q^-1 b, then x += Q^-1 (b - K11 x)).  hist[n] = max over the
+// columns of |r_n| / |b| after n steps (for Alg. 4 the worst column at each step).
+int hf_k11_iterate_impl(hf_ctx* c, int method, int m, const double* B, double* X, int maxit, double* hist,
+                        int* iters) {
+  if (!c->factored) return HF_ERR_STATE;
+  if (m < 1 || !B || !X || maxit < 1 || method < 0 || method > 2) return HF_ERR_ARG;
+  cudaStream_t s = hf_stream(c);
+  const int64_t L = c->L;
+  const size_t blk = (size_t)L * m;
+  std::vector<double> h;
+  int it = 0, rc = HF_OK;
+  if (method == 0) {
+    const int save = c->opts.gcr_maxit;
+    c->opts.gcr_maxit = maxit;
+    double rr = 0;
+    rc = block_gcr(c, m, B, X, &it, &rr, &h);
+    c->opts.gcr_maxit = save;
+  } else if (method == 1) {
+    int r2;
+    if ((r2 = hf_ensure(c->d_solve, (size_t)L * 2 * 8 + 256))) return r2;
+    double* bj = (double*)c->d_solve.p;
+    double* xj = bj + L;
+    const int save = c->opts.gcr_maxit;
+    c->opts.gcr_maxit = maxit;
+    std::vector<std::vector<double>> hs(m);
+    for (int j = 0; j < m && (rc == HF_OK || rc == HF_ERR_NOT_CONVERGED); ++j) {
+      HF_CUDA_TRY(cudaMemcpy2DAsync(bj, 8, B + j, (size_t)m * 8, 8, L, cudaMemcpyDeviceToDevice, s));
+      int itj = 0;
+      double rr = 0;
+      const int rj = block_gcr(c, 1, bj, xj, &itj, &rr, &hs[j]);
+      if (rj != HF_OK && rj != HF_ERR_NOT_CONVERGED) { rc = rj; break; }
+      if (rj == HF_ERR_NOT_CONVERGED) rc = rj;
+      HF_CUDA_TRY(cudaMemcpy2DAsync(X + j, (size_t)m * 8, xj, 8, 8, L, cudaMemcpyDeviceToDevice, s));
+      it = std::max(it, itj);
+    }
+    c->opts.gcr_maxit = save;
+    size_t len = 0;
+    for (const auto& v : hs) len = std::max(len, v.size());
+    h.assign(len, 0.0);
+    for (size_t k = 0; k < len; ++k)
+      for (const auto& v : hs)
+        if (!v.empty()) h[k] = std::max(h[k], v[std::min(k, v.size() - 1)]);
+  } else {
+    // iterative refinement, Alg. 3
+    int r2;
+    const size_t tmp_doubles = (blk * 3 + 1) / 2 + blk;
+    if ((r2 = hf_ensure(c->d_solve, (blk * 2 + tmp_doubles) * 8 + 1024))) return r2;
+    double* R = (double*)c->d_solve.p;
+    double* W = R + blk;
+    double* tmp = W + blk;
+    std::vector<double> bnorm(m), none;
+    double dummy = 0;
+    if ((r2 = max_col_ratio(c, m, B, none, &dummy, &bnorm))) return r2;
+    for (auto& v : bnorm) if (v == 0) v = 1.0;
+    if ((r2 = precond(c, m, B, X, tmp))) return r2;                      // steps 1-2
+    const unsigned nb = nblk((int64_t)blk, 256);
+    rc = HF_ERR_NOT_CONVERGED;
+    for (int n = 0;; ++n) {
+      spmm(c, m, X, W);                                                   // step 3 / 4d
+      HF_LAUNCH(c, HF_PROF_VECTOR, k_sub<<<nb, 256, 0, s>>>((int64_t)blk, B, W, R));
+      double res = 0;
+      if ((r2 = max_col_ratio(c, m, R, bnorm, &res))) return r2;
+      h.push_back(res);
+      it = n;
+      if (!(res > c->opts.gcr_tol)) { rc = HF_OK; break; }
+      if (n == maxit) break;
+      if ((r2 = precond(c, m, R, W, tmp))) return r2;                     // 4a-4b
+      HF_LAUNCH(c, HF_PROF_VECTOR, k_addto<<<nb, 256, 0, s>>>((int64_t)blk, W, X));   // 4c
+    }
+  }
+  HF_CUDA_TRY(cudaGetLastError());
+  HF_CUDA_TRY(cudaStreamSynchronize(s));
+  if (hist) for (size_t k = 0; k < h.size() && k <= (size_t)maxit; ++k) hist[k] = h[k];
+  if (iters) *iters = it;
+  return rc;
 }
 
 int hf_precond_impl(hf_ctx* c, int m, const double* R, double* W) {

@@ -25,7 +25,7 @@ EXPORTED = (
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
     "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc",
     "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis",
-    "hf_gram_fp64", "hf_update_fp64", "hf_free",
+    "hf_gram_fp64", "hf_update_fp64", "hf_k11_iterate", "hf_free",
 )
 HF_NPROF = 13
 
@@ -99,6 +99,7 @@ def lib():
     L.hf_free.restype = None
     L.hf_get_kernel_basis.argtypes = [vp, vp, i64]
     L.hf_gram_fp64.argtypes = [vp, i64, i32, i32, vp, vp, vp, dbl]
+    L.hf_k11_iterate.argtypes = [vp, i32, i32, vp, vp, i32, vp, vp]
     L.hf_update_fp64.argtypes = [vp, i64, i32, vp, vp, vp, vp, dbl]
     pp = C.POINTER(C.c_void_p)
     L.hf_factorize_batched.argtypes = [pp, i32, pp, dbl, vp]
@@ -207,6 +208,17 @@ class HybridFactor:
         """Same as precond(), with all scratch in the library's fixed device array (no allocation)."""
         m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
         _check(lib().hf_precond_noalloc(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond_noalloc")
+
+    def k11_iterate(self, method, B_dev, X_dev, maxit=40):
+        """K11 X = B by block GCR (method 0, Alg. 5), GCR per column (1, Alg. 4) or
+        iterative refinement (2, Alg. 3); returns (rc, iterations, residual history)."""
+        m = 1 if B_dev.dim() == 1 else B_dev.shape[1]
+        hist = np.zeros(maxit + 1)
+        it = C.c_int(0)
+        rc = lib().hf_k11_iterate(self._h, int(method), m, _ptr(B_dev), _ptr(X_dev), int(maxit), _ptr(hist),
+                                  C.byref(it))
+        _check(rc, "hf_k11_iterate", allow=(HF_ERR_NOT_CONVERGED,))
+        return rc, it.value, hist[:it.value + 1].copy()
 
     def gram_fp64(self, A_dev, B_dev, G_dev, scale=1.0):
         """G = scale * A^T B (Alg. 5's Gram products) on row-major L x ma / L x mb float64 CUDA tensors."""

@@ -5,7 +5,9 @@
 builds the 3D Stokes-like system of the benchmark at n^3 nodes, runs `factorize`
 (twice with --warm, so that the delayed-row capacity has settled), then `schur` and
 `solve` as requested by --phase, and prints one line.  --phase gram / update runs one
-block-GCR product (hf_gram_fp64 / hf_update_fp64) on seeded L x m operands instead.  Nothing is timed here; the
+block-GCR product (hf_gram_fp64 / hf_update_fp64) on seeded L x m operands instead;
+--phase iterate compares iterative refinement, GCR per column and block GCR on K11
+X = B (hf_k11_iterate, seeded B with --cols columns) after the factorization.  Nothing is timed here; the
 point is a fixed, short sequence of launches for a kernel profiler.
 """
 import argparse
@@ -22,7 +24,8 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=32)
-    ap.add_argument("--phase", choices=["factorize", "schur", "solve", "gram", "update"], default="schur")
+    ap.add_argument("--phase", choices=["factorize", "schur", "solve", "gram", "update", "iterate"], default="schur")
+    ap.add_argument("--cols", type=int, default=16, help="right-hand sides of --phase iterate")
     ap.add_argument("--m", type=int, default=388, help="columns of the gram / update operands")
     ap.add_argument("--warm", action="store_true", help="factorize twice before the measured phases")
     ap.add_argument("--fp64-gemm", type=int, default=0)
@@ -57,6 +60,24 @@ def main():
     if args.warm:
         H.factorize(vals, 1e-2)
     H.factorize(vals, 1e-2)
+    if args.phase == "iterate":
+        # Alg. 3 / Alg. 4 / Alg. 5 on K11 X = B (seeded B, Lambda_2 rows zero), Fig. 2 style
+        _, lam2 = H.split()
+        g = torch.Generator(device="cuda").manual_seed(7)
+        B = torch.randn(s.L, args.cols, device="cuda", dtype=torch.float64, generator=g)
+        B[torch.as_tensor(lam2, device="cuda", dtype=torch.long)] = 0
+        for method, name in ((2, "IR (Alg. 3)"), (1, "GCR per column (Alg. 4)"), (0, "block GCR (Alg. 5)")):
+            X = torch.zeros_like(B)
+            H.k11_iterate(method, B, X, maxit=40)                  # warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc, it, hist = H.k11_iterate(method, B, X, maxit=40)
+            e1.record()
+            torch.cuda.synchronize()
+            print(f"{name:26s} cols={args.cols} rc={rc} iterations={it} time={e0.elapsed_time(e1):.1f} ms "
+                  f"history={' '.join(f'{v:.2e}' for v in hist)}", flush=True)
+        return
     if args.phase in ("schur", "solve"):
         H.schur()
     if args.phase == "solve":

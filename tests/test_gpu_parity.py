@@ -396,3 +396,40 @@ def test_dataflow_sweeps_match_blocked(name, m, monkeypatch):
     assert np.abs(wd[lam2]).max(initial=0.0) == 0.0
     err = np.linalg.norm(wd - wb, axis=0) / np.maximum(np.linalg.norm(wb, axis=0), 1e-300)
     assert err.max() <= 1e-3                         # a missing block would be O(1)
+
+
+def test_k11_iterations_alg3_alg4_alg5(case):
+    """hf_k11_iterate: iterative refinement (Alg. 3), GCR per column (Alg. 4) and block GCR
+    (Alg. 5) with the FP32 factor as Q, on K11 X = B with a known solution.  All three reach
+    the solution; GCR minimises the residual over a Krylov space that holds IR's iterate and
+    block GCR over one that holds GCR's (Sec. 3.4-3.5), so step by step neither is above the
+    previous one; IR follows the oracle's Alg. 3 with the oracle's factor."""
+    s, H, K, fac = case["s"], case["out"]["H"], case["K"], case["fac"]
+    _, lam2 = H.split()
+    A = O.k11_operator(K, lam2)
+    rng = np.random.default_rng(11)
+    Xt = rng.standard_normal((s.L, 3))
+    Xt[lam2] = 0
+    B = A(Xt)
+    Bt = torch.tensor(B, device="cuda")
+    res = {}
+    for method in (0, 1, 2):
+        X = torch.zeros_like(Bt)
+        rc, it, hist = H.k11_iterate(method, Bt, X, maxit=40)
+        res[method] = (rc, it, hist, X.cpu().numpy())
+    for method, (rc, it, hist, X) in res.items():
+        assert rc == 0, (method, hist)
+        assert np.abs(X[lam2]).max(initial=0.0) == 0.0
+        true_res = np.linalg.norm(A(X) - B, axis=0) / np.linalg.norm(B, axis=0)
+        assert true_res.max() <= 1e-12, (method, true_res)
+    h0, h1, h2 = res[0][2], res[1][2], res[2][2]
+    for k in range(1, min(len(h1), len(h2))):
+        if h2[k] > 1e-12:
+            assert h1[k] <= h2[k] * (1 + 1e-3), (k, h1[k], h2[k])
+    for k in range(1, min(len(h0), len(h1))):
+        if h1[k] > 1e-12:
+            assert h0[k] <= h1[k] * (1 + 1e-3), (k, h0[k], h1[k])
+    _, ho = O.iterative_refinement(A, lambda R: O.precond_apply(fac, R), B, tol=1e-14, maxit=40)
+    steps = lambda h: next((k for k, v in enumerate(h) if v <= 1e-10), len(h))
+    assert abs(steps(h2) - steps(ho)) <= 1
+    assert abs(np.log10(h2[0] / ho[0])) <= 1.0                    # Q^-1 b starts: FP32 factors agree

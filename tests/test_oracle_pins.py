@@ -252,6 +252,52 @@ def test_block_gcr_single_rhs_equals_alg4():
     np.testing.assert_allclose(xb[:, 0], xs, rtol=1e-10, atol=1e-12 * np.abs(xs).max())
 
 
+def test_iterative_refinement_residuals_follow_the_closed_form():
+    # Sec. 3.3: with a fixed linear Q^-1, r_n = (I - A Q^-1)^n r_0 and the iterate lies in
+    # x_0 + span{Q^-1 r_0, (Q^-1 A) Q^-1 r_0, ...}; here Q^-1 is an inexact inverse (Jacobi)
+    rng = np.random.default_rng(7)
+    n = 25
+    Am = _rand_spd(n, rng, 20.0)
+    Qm = np.diag(1.0 / np.diag(Am))
+    A = lambda V: Am @ V
+    Qinv = lambda V: Qm @ V
+    B = rng.standard_normal((n, 2))
+    X, hist = O.iterative_refinement(A, Qinv, B, tol=0.0, maxit=6)
+    r0 = B - Am @ (Qm @ B)
+    Tm = np.eye(n) - Am @ Qm
+    for k in range(7):
+        rk = np.linalg.matrix_power(Tm, k) @ r0
+        want = np.max(np.linalg.norm(rk, axis=0) / np.linalg.norm(B, axis=0))
+        assert abs(hist[k] - want) <= 1e-12 * max(want, 1e-300) + 1e-15
+    # the iterate: x_6 = x_0 + sum_{j<6} (Q^-1 (I - A Q^-1)^j) r_0
+    xs = Qm @ B + sum(Qm @ np.linalg.matrix_power(Tm, j) @ r0 for j in range(6))
+    np.testing.assert_allclose(X, xs, rtol=1e-12, atol=1e-14)
+
+
+def test_iterative_refinement_exact_preconditioner_and_gcr_not_worse():
+    # exact Q: x_0 is the solution; inexact Q: GCR's residual (minimal over the same Krylov
+    # space, Sec. 3.4) is never above IR's at the same step
+    s, q, K, fac = _cfg1_small()
+    A = O.k11_operator(K, fac.lambda2)
+    Qi = lambda R: O.precond_apply(fac, R)
+    lam1 = np.setdiff1d(np.arange(s.L), fac.lambda2)
+    K11 = K.toarray()[np.ix_(lam1, lam1)]
+
+    def exact(R):
+        out = np.zeros_like(R)
+        out[lam1] = np.linalg.solve(K11, R[lam1])
+        return out
+    b = np.zeros(s.L)
+    b[lam1] = np.random.default_rng(4).standard_normal(len(lam1))
+    _, he = O.iterative_refinement(A, exact, b[:, None], tol=0.0, maxit=1)
+    assert he[0] < 1e-10
+    _, hi = O.iterative_refinement(A, Qi, b[:, None], tol=0.0, maxit=4)
+    _, hg, _, _ = O.gcr_single(A, Qi, b, tol=0.0, maxit=4)
+    for k in range(1, min(len(hi), len(hg))):
+        if hi[k] > 1e-13:                                       # above the FP64 floor
+            assert hg[k] <= hi[k] * (1 + 1e-6)
+
+
 def test_block_gcr_exact_preconditioner_converges_at_x0():
     s, q, K, fac = _cfg1_small()
     A = O.k11_operator(K, fac.lambda2)
