@@ -315,7 +315,7 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
     # plain FP64 GPU form (Table 1 "double"): factor in FP64, S22 from the factor
-    fp64 = None
+    fp64 = fp32 = None
     if not args.no_fp64:
         H64 = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, precision=hf.HF_PREC_FP64)
         H64.factorize(vals, 1e-2)
@@ -337,6 +337,24 @@ def run_ours(args):
                 "M": H64.info()["M"], "kernel_dim": H64.info()["kernel_dim"]}
         fp64["speedup_mixed_vs_fp64"] = fp64["factor_schur_ms"] / fs_ms
         H64.free()
+        # FP32-only form (Table 1 "single"): factor and S22 in FP32, no iteration; its
+        # backward error shows why the hybrid form iterates in FP64
+        H32 = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, precision=hf.HF_PREC_FP32)
+        H32.factorize(vals, 1e-2)
+        H32.schur()
+        torch.cuda.synchronize()
+        a.record()
+        H32.factorize(vals, 1e-2)
+        H32.schur()
+        c_.record()
+        torch.cuda.synchronize()
+        x32 = torch.zeros_like(bt)
+        H32.solve(bt, x32)
+        xx = x32.cpu().numpy().T
+        rr = Kb @ xx - b
+        be32 = float(np.abs(rr).max() / (abs(Kb).sum(axis=1).max() * np.abs(xx).max() + np.abs(b).max()))
+        fp32 = {"factor_schur_ms": a.elapsed_time(c_), "backward_error": be32, "gate_1e-12": bool(be32 <= 1e-12)}
+        H32.free()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -370,6 +388,7 @@ def run_ours(args):
             "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": s.nnz * 8,
                     "d2h_bytes_per_step": M * M * 8},
             "fp64_form": fp64,
+            "fp32_form": fp32,
             "gpu_launches": launches,
             "kernel_ms": {k: round(v[0] / prof_steps, 3) for k, v in prof.items()},
             "kernel_work": {k: {"gflop": round(v[2] / prof_steps / 1e9, 3), "gbytes": round(v[3] / prof_steps / 1e9, 3)}
