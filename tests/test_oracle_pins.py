@@ -125,6 +125,27 @@ def test_hand_case_tie_break_and_first_pivot_reference():
     assert fac2.node_pivots[0].tolist() == [] and fac2.lambda2.tolist() == [0, 1]
 
 
+def test_hand_case_ratio_to_previous_pivot():
+    # R3: each pivot is measured against the previous pivot of its set, not against 1 or
+    # the first pivot.  diag(1, 0.05, 0.004, 3e-5), tau = 1e-2: ratios 0.05, 0.08, 0.0075,
+    # so 0.004 is accepted although it is below tau * 1, and 3e-5 is postponed.
+    K = sp.csr_matrix(np.diag([1.0, 0.05, 0.004, 3e-5]))
+    fac = O.threshold_factorize(K, [np.array([0, 1, 2, 3])], tau=1e-2, n_enlarge=0)
+    assert fac.node_pivots[0].tolist() == [0, 1, 2]
+    assert fac.node_postponed[0].tolist() == [3]
+    # R2 on the refactorization of Lambda_0: its first pivot is compared with 1 again
+    assert fac.lam0_pivots.tolist() == [] and fac.lambda2.tolist() == [3]
+    # the reference restarts at 1 in every set: the second set's 0.004 fails against 1,
+    # although it is within tau of the previous set's last pivot 0.05 ...
+    fac2 = O.threshold_factorize(sp.csr_matrix(np.diag([1.0, 0.05, 0.004])),
+                                 [np.array([0, 1]), np.array([2])], tau=1e-2, n_enlarge=0)
+    assert fac2.node_pivots[1].tolist() == [] and fac2.lambda2.tolist() == [2]
+    # ... and passes against 1 when tau allows it, whatever the previous set ended with
+    fac3 = O.threshold_factorize(sp.csr_matrix(np.diag([1.0, 1e-3, 0.5])),
+                                 [np.array([0, 1]), np.array([2])], tau=1e-2, n_enlarge=0)
+    assert fac3.node_pivots[0].tolist() == [0] and fac3.node_pivots[1].tolist() == [2]
+
+
 def test_pivot_sequence_matches_brute_force_schur():
     # At every step the chosen pivot is the max |diag| of the exact Schur complement,
     # formed here from scratch with a dense inverse, and d equals that diagonal entry.
@@ -431,6 +452,38 @@ def test_hybrid_solve_singular_consistent():
     assert O.backward_error(Kb, x, b) < 1e-14
 
 
+def test_residual_measures_closed_form():
+    # |r|_2/|b|_2 and the normwise backward error |r|_inf / (|K|_inf |x|_inf + |b|_inf) on a
+    # 2x2 case worked by hand: K = [[2, -1], [-1, 3]], x = [1, 0], b = [2, -0.996]:
+    # r = K x - b = [0, -0.004], |K|_inf = 4, |x|_inf = 1, |b|_inf = 2.
+    Kb = sp.csr_matrix(np.array([[2.0, -1.0], [-1.0, 3.0]]))
+    x = np.array([[1.0], [0.0]])
+    b = np.array([[2.0], [-0.996]])
+    assert abs(O.relative_residual(Kb, x, b) - 0.004 / math.hypot(2.0, 0.996)) < 1e-15
+    assert abs(O.backward_error(Kb, x, b) - 0.004 / (4.0 * 1.0 + 2.0)) < 1e-16
+    # scaling x and b together leaves the measure unchanged
+    assert abs(O.backward_error(Kb, 10 * x, 10 * b) - O.backward_error(Kb, x, b)) < 1e-16
+    # max over columns
+    X2 = np.hstack([x, x])
+    B2 = np.hstack([b, np.array([[2.0], [-1.0]])])
+    assert O.backward_error(Kb, X2, B2) == O.backward_error(Kb, x, b)
+
+
+def test_s22_noise_estimates_the_schur_error():
+    # Perturb X12 by D on Lambda_1: S22 changes by exactly -K21 D, and the estimate
+    # factor * |K21 Q^-1 (K12 - K11 X12)|_max reads it through Q^-1 K11 ~ I (Sec. 3.3).
+    s, q, K, fac = _cfg1_small()
+    lam1 = np.setdiff1d(np.arange(s.L), fac.lambda2)
+    X12 = O.x12_direct(K, fac.lambda2)
+    assert O.s22_noise(K, fac, X12, factor=1.0) < 1e-12
+    D = np.zeros_like(X12)
+    D[lam1] = np.random.default_rng(8).standard_normal((len(lam1), fac.M)) * 1e-6
+    dS = O.schur_direct(K, fac.lambda2, X12 + D) - O.schur_direct(K, fac.lambda2, X12)
+    est = O.s22_noise(K, fac, X12 + D, factor=1.0)
+    assert abs(est - np.abs(dS).max()) <= 1e-2 * np.abs(dS).max()
+    assert abs(O.s22_noise(K, fac, X12 + D) - 100.0 * est) <= 1e-12 * est
+
+
 # --------------------------------------------------------------------------- adjoint
 def test_adjoint_gradient_matches_central_differences():
     n = 6
@@ -485,6 +538,48 @@ def test_bunch_parlett_reconstruction_inertia_and_bound():
         assert np.abs(Lf).max() <= 1.0 / (1.0 - alpha) + 1e-9   # complete-pivoting growth bound on L
         if n > 3:
             assert any(z == 2 for _, z, _ in blocks)
+
+
+def test_bunch_parlett_choice_matches_brute_force():
+    # R11 complete pivoting, checked step by step on Schur complements formed from scratch:
+    # a 1x1 pivot is the largest |diagonal| of the remaining block and is at least alpha
+    # times its largest off-diagonal; a 2x2 pivot holds that largest off-diagonal entry.
+    rng = np.random.default_rng(23)
+    alpha = (1 + math.sqrt(17)) / 8
+    seen = set()
+    for trial in range(8):
+        n = 9
+        A = _rand_sym(n, rng)
+        A[np.arange(n), np.arange(n)] *= rng.choice([1e-3, 1.0, 3.0])
+        perm, Lf, blocks = O.bunch_parlett(A)
+        Ap = A[np.ix_(perm, perm)]
+        for s0, z, B in blocks:
+            S = Ap[s0:, s0:] - (Ap[s0:, :s0] @ np.linalg.solve(Ap[:s0, :s0], Ap[:s0, s0:]) if s0 else 0)
+            mu0 = np.abs(np.diag(S)).max()
+            off = np.abs(S - np.diag(np.diag(S)))
+            mu1 = off.max()
+            np.testing.assert_allclose(B, S[:z, :z], rtol=1e-9, atol=1e-12)
+            if z == 1:
+                assert abs(B[0, 0]) >= mu0 * (1 - 1e-12) and mu0 >= alpha * mu1 * (1 - 1e-12)
+            else:
+                assert mu0 < alpha * mu1 * (1 + 1e-12) and abs(B[1, 0]) >= mu1 * (1 - 1e-12)
+            seen.add(z)
+    assert seen == {1, 2}
+
+
+def test_pivot_magnitudes_of_2x2_blocks():
+    # a 2x2 pivot counts by the magnitudes of its eigenvalues, not its diagonal:
+    # [[0, 1], [1, 0]] (+) [0] has a one-dimensional kernel, and the block itself is regular
+    A = np.zeros((3, 3))
+    A[0, 1] = A[1, 0] = 1.0
+    perm, Lf, blocks = O.bunch_parlett(A)
+    mags, owners = O.pivot_magnitudes(blocks)
+    assert sorted(z for _, z, _ in blocks) == [1, 2]
+    np.testing.assert_allclose(np.sort(mags), [0.0, 1.0, 1.0])
+    assert O.kernel_dimension(mags) == 1
+    B = np.array([[2.0, 5.0], [5.0, -1.0]])
+    m2, _ = O.pivot_magnitudes([(0, 2, B)])
+    np.testing.assert_allclose(np.sort(m2), np.sort(np.abs(np.linalg.eigvalsh(B))))
 
 
 def test_bunch_parlett_is_rank_revealing():
