@@ -403,23 +403,42 @@ def run_ours(args):
 def measured_traffic(kernel):
     """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + dram__bytes_write.sum) from
     a committed ncu summary under profiles/ that names the kernel, its source file and
-    that file's SHA-256 at capture time; None when there is none or the source changed
-    since (the counters then describe another kernel)."""
+    the SHA-256 of that source at capture time; None when there is none or the source
+    changed since (the counters then describe another kernel).
+
+    The hash covers the whole file, or with `source_until: <line>` the part of the file
+    before that line (the kernel, its helpers and its launches, when host code that
+    cannot reach the kernel follows); `headers: a, b` with `headers_sha256` adds the
+    concatenated headers the kernel is compiled with."""
     import glob
     import hashlib
+    keys = ("kernel:", "source:", "source_until:", "source_sha256:", "headers:", "headers_sha256:",
+            "dram_bytes_per_launch:")
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         fields = {}
         with open(path) as f:
             for line in f:
-                if ":" in line and line.strip().startswith(("kernel:", "source:", "source_sha256:",
-                                                              "dram_bytes_per_launch:")):
+                if line.strip().startswith(keys):
                     k, v = line.strip().split(":", 1)
                     fields[k] = v.strip()
         if fields.get("kernel") != kernel or "dram_bytes_per_launch" not in fields:
             continue
         try:
             with open(os.path.join(ROOT, fields["source"]), "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest() != fields.get("source_sha256"):
+                src = f.read()
+            if "source_until" in fields:
+                at = src.find(fields["source_until"].encode())
+                if at < 0:
+                    return None
+                src = src[:at]
+            if hashlib.sha256(src).hexdigest() != fields.get("source_sha256"):
+                return None
+            if "headers" in fields:
+                h = hashlib.sha256()
+                for name in fields["headers"].split(","):
+                    with open(os.path.join(ROOT, name.strip()), "rb") as f:
+                        h.update(f.read())
+                if h.hexdigest() != fields.get("headers_sha256"):
                     return None
             return float(fields["dram_bytes_per_launch"])
         except (OSError, KeyError, ValueError):
