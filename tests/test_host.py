@@ -104,3 +104,33 @@ def test_pattern_validation():
     with pytest.raises(hf.HFError) as e:
         hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, tau=-1.0)
     assert e.value.code == 1
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    # no CPU fallback: with libhf.so absent the first call into the library raises
+    import paper_2208_01907_gb300.hf as binding
+    s = diffusion2d(6, 6, n_islands=0)
+    A = s.to_scipy()
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "libhf.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.HybridFactor(A.shape[0], A.indptr, A.indices, s.coords)
+
+
+def test_product_path_never_reaches_the_oracle():
+    # the package neither imports the oracle nor names it in code; importing it leaves
+    # the oracle unloaded (checked in a fresh interpreter)
+    import subprocess
+    import sys
+    pkg = os.path.join(ROOT, "paper_2208_01907_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                text = open(os.path.join(dirpath, name)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), name
+                assert "oracle/" not in text and "import_module(\"oracle" not in text, name
+    code = ("import sys, paper_2208_01907_gb300, paper_2208_01907_gb300.shard; "
+            "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
+    subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
