@@ -42,6 +42,11 @@ the design notes):
       1x1 or 2x2 blocks, alpha = (1+sqrt 17)/8: the largest entries of the
       whole remaining block go first, so null pivots come last (rank
       revealing, as the kernel detection needs).
+  R15 An unsymmetric S22 (the LDU form with U != L^T, e.g. the saddle point
+      [A B^T; -B delta D] of Sec. 4.2) is factorized by Gaussian elimination
+      with complete pivoting, the unsymmetric counterpart of R11: the entry of
+      largest magnitude of the whole remaining block goes first, so null
+      pivots come last; the kernel rule R10 reads |u_kk|.
   R13 The enlargement moves the last n = 4 entries of the elimination order
       into hat-Lambda_0.  These are the last entries of tilde-Lambda_0 when it
       holds at least n of them; when tilde-Lambda_0 is shorter (every
@@ -64,6 +69,7 @@ __all__ = [
     "schur_direct", "x12_direct", "bunch_kaufman", "bunch_parlett", "bk_reconstruct", "pivot_magnitudes",
     "kernel_dimension", "bk_solve", "hybrid_solve", "relative_residual", "backward_error",
     "run_hybrid", "s22_noise", "adjoint_gradient", "diffusion_objective",
+    "lu_complete", "lu_reconstruct", "lu_pseudo_solve",
 ]
 
 
@@ -160,7 +166,8 @@ class FactorResult:
     lambda1_order: np.ndarray         # Pi_1: elimination order of Lambda_1
     lambda2: np.ndarray               # Lambda_2, sorted
     d: dict = field(default_factory=dict)       # pivot value (float32) per eliminated index
-    lcol: dict = field(default_factory=dict)    # index -> (rows, float32 values) of L
+    lcol: dict = field(default_factory=dict)    # index -> (rows, float32 values) of L (column)
+    urow: dict = field(default_factory=dict)    # index -> (rows, float32 values) of U (row); = lcol if K = K^T
     violations: list = field(default_factory=list)
 
     @property
@@ -175,19 +182,23 @@ class FactorResult:
 def _eliminate(S, G, remaining, q, fac):
     """One rank-1 Schur update with weight 1/d on the remaining indices (Sec. 2.1).
 
-    G accumulates, per index, |K_ii| plus the magnitudes |l_i|^2 |d| of the
+    The LDU form: the pivot's column (below) and row (right) enter the update
+    separately, S' = S - col d^-1 row, with l = col / d and u = row / d; for a
+    symmetric S the two are the same numbers and this is LDL^T.
+    G accumulates, per index, |K_ii| plus the magnitudes |l_i u_i d| of the
     updates its diagonal received (used by the null-pivot test R3b).
     """
     d = S[q, q]
     remaining[q] = False
-    row = S[q]
-    rows = np.flatnonzero((row != 0) & remaining)
-    col = row[rows].copy()
+    rows = np.flatnonzero(((S[:, q] != 0) | (S[q] != 0)) & remaining)
+    col = S[rows, q].copy()
+    row = S[q, rows].copy()
     if rows.size:
-        S[np.ix_(rows, rows)] -= np.outer(col, col) / d
-        G[rows] += np.abs(col * (col / d))
+        S[np.ix_(rows, rows)] -= np.outer(col, row) / d
+        G[rows] += np.abs(col * (row / d))
     fac.d[int(q)] = d
     fac.lcol[int(q)] = (rows, col / d)
+    fac.urow[int(q)] = (rows, row / d)
     return d
 
 
@@ -304,7 +315,7 @@ def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: in
 # Sec. 3.1-3.2: the lower-precision solve Q^-1 used as preconditioner
 # ---------------------------------------------------------------------------
 def precond_apply(fac: FactorResult, R: np.ndarray) -> np.ndarray:
-    """e = Q^-1 r: cast r to float32, solve L D L^T e = r with the float32 factor of K11, cast back.
+    """e = Q^-1 r: cast r to float32, solve L D U e = r with the float32 factor of K11, cast back.
 
     The factor of K11 in the order Pi_1 is the recorded factor restricted to
     Lambda_1 rows and columns (Eq. 1 with the leading block).  Rows of
@@ -323,10 +334,10 @@ def precond_apply(fac: FactorResult, R: np.ndarray) -> np.ndarray:
         y[rows[keep]] -= np.outer(l[keep], y[p])
     for p in order:                                   # diagonal
         y[p] /= fac.d[int(p)]
-    for p in order[::-1]:                             # backward, L^T
-        rows, l = fac.lcol[int(p)]
+    for p in order[::-1]:                             # backward, unit upper triangular U
+        rows, u = fac.urow[int(p)]
         keep = in1[rows]
-        y[p] -= l[keep] @ y[rows[keep]]
+        y[p] -= u[keep] @ y[rows[keep]]
     return y.astype(np.float64).reshape(R.shape)
 
 
@@ -664,6 +675,61 @@ def bk_solve(perm, Lf, blocks, y, kdim):
     return x
 
 
+def lu_complete(A):
+    """Gaussian elimination with complete pivoting, A[prow][:, pcol] = Lf U (R15).
+
+    Each step takes the entry of largest magnitude of the remaining block (ties:
+    smallest column, then smallest row) and moves it to the diagonal by one row and
+    one column interchange.  A remaining block that is exactly zero ends the
+    elimination (its pivots are zero).
+    Returns (prow, pcol, Lf, U): row i of the factor is row prow[i] of A and
+    column j is column pcol[j] of A; Lf is unit lower and U upper triangular.
+    """
+    A = np.array(A, dtype=np.float64, copy=True)
+    n = A.shape[0]
+    prow, pcol = np.arange(n), np.arange(n)
+    Lf = np.eye(n)
+    for k in range(n):
+        j, i = divmod(int(np.argmax(np.abs(A[k:, k:]).T)), n - k)   # column by column
+        i, j = i + k, j + k
+        A[[k, i], :] = A[[i, k], :]
+        Lf[[k, i], :k] = Lf[[i, k], :k]
+        prow[[k, i]] = prow[[i, k]]
+        A[:, [k, j]] = A[:, [j, k]]
+        pcol[[k, j]] = pcol[[j, k]]
+        d = A[k, k]
+        if d == 0.0:
+            break
+        l = A[k + 1:, k] / d
+        A[k + 1:, k + 1:] -= np.outer(l, A[k, k + 1:])
+        A[k + 1:, k] = 0.0
+        Lf[k + 1:, k] = l
+    return prow, pcol, Lf, np.triu(A)
+
+
+def lu_reconstruct(prow, pcol, Lf, U):
+    """A from the factors of lu_complete."""
+    A = np.empty_like(U)
+    A[np.ix_(prow, pcol)] = Lf @ U
+    return A
+
+
+def lu_pseudo_solve(prow, pcol, Lf, U, y, kdim):
+    """x with A x = y on the image, the kdim smallest |u_kk| treated as zero (kernel pivots)."""
+    n = len(prow)
+    y = np.asarray(y, dtype=np.float64).reshape(n, -1)
+    z = np.linalg.solve(Lf, y[prow])
+    zero = set(np.argsort(np.abs(np.diag(U)))[:kdim].tolist()) if kdim else set()
+    w = np.zeros_like(z)
+    for k in range(n - 1, -1, -1):
+        if k in zero or U[k, k] == 0.0:
+            continue
+        w[k] = (z[k] - U[k, k + 1:] @ w[k + 1:]) / U[k, k]
+    x = np.empty_like(w)
+    x[pcol] = w
+    return x
+
+
 # ---------------------------------------------------------------------------
 # Alg. 2: forward / backward substitution of the hybrid factorization
 # ---------------------------------------------------------------------------
@@ -674,7 +740,12 @@ def hybrid_solve(K: sp.csr_matrix, lambda2, X12, bk, kdim, b):
     x = np.zeros_like(b)
     y1 = spla.splu(K11).solve(b[lam1]) if len(lam1) else np.zeros((0, b.shape[1]))
     y2 = b[lambda2] - K21 @ y1
-    x2 = bk_solve(*bk, y2, kdim) if len(lambda2) else y2
+    if not len(lambda2):
+        x2 = y2
+    elif len(bk) == 4:                            # lu_complete factors of an unsymmetric S22
+        x2 = lu_pseudo_solve(*bk, y2, kdim)
+    else:
+        x2 = bk_solve(*bk, y2, kdim)
     x[lam1] = y1 - X12[lam1] @ x2
     x[lambda2] = x2
     return x
@@ -700,7 +771,11 @@ def backward_error(Kbar: sp.csr_matrix, x, b):
 
 def run_hybrid(Kbar: sp.csr_matrix, nodes, tau, n_enlarge=4, replay=None, kernel_eps=1e-10,
                gap_min=1e4, use_gcr=False, gcr_tol=1e-14, gcr_maxit=50, dtype=np.float32):
-    """Alg. 1 end to end: scale, threshold factorization, X12, S22, Bunch-Parlett, kernel dim."""
+    """Alg. 1 end to end: scale, threshold factorization, X12, S22, its dense factor, kernel dim.
+
+    S22 is factorized by Bunch-Parlett (R11) when K-bar is symmetric and by LU with
+    complete pivoting (R15) otherwise.
+    """
     q, K = scale_matrix(Kbar)
     fac = threshold_factorize(K, nodes, tau, n_enlarge, replay, dtype=dtype)
     if use_gcr and fac.M:
@@ -713,9 +788,17 @@ def run_hybrid(Kbar: sp.csr_matrix, nodes, tau, n_enlarge=4, replay=None, kernel
         X12, hist = x12_direct(K, fac.lambda2), None
     S22 = schur_direct(K, fac.lambda2, X12)
     noise = s22_noise(K, fac, X12) if (use_gcr and fac.M) else 0.0
-    bk = bunch_parlett(S22) if fac.M else (np.zeros(0, int), np.zeros((0, 0)), [])
+    symmetric = abs(Kbar - Kbar.T).max() == 0          # exact test on the user's matrix
+    if not fac.M:
+        bk, mags = (np.zeros(0, int), np.zeros((0, 0)), []), np.zeros(0)
+    elif symmetric:
+        bk = bunch_parlett(S22)
+        mags = pivot_magnitudes(bk[2])[0]
+    else:
+        bk = lu_complete(S22)
+        mags = np.abs(np.diag(bk[3]))
     ref = float(np.abs(K.diagonal()[fac.lambda2]).max()) if fac.M else 0.0
-    kdim = kernel_dimension(pivot_magnitudes(bk[2])[0], kernel_eps, gap_min, ref, noise) if fac.M else 0
+    kdim = kernel_dimension(mags, kernel_eps, gap_min, ref, noise) if fac.M else 0
     return dict(q=q, K=K, fac=fac, X12=X12, S22=S22, bk=bk, kdim=kdim, gcr_hist=hist, noise=noise)
 
 

@@ -72,6 +72,13 @@ PINS = {
     "residual_measures": pins.test_residual_measures_closed_form,
     "s22_noise": pins.test_s22_noise_estimates_the_schur_error,
     "adjoint_fd": pins.test_adjoint_gradient_matches_central_differences,
+    "ldu_eq1": pins.test_ldu_reconstructs_eq1_unsymmetric,
+    "ldu_brute_force": pins.test_ldu_pivots_match_brute_force_unsymmetric_schur,
+    "sign_form": pins.test_sign_form_factorizes_like_the_symmetric_matrix,
+    "lu_choice": pins.test_lu_complete_reconstruction_and_pivot_choice,
+    "lu_rank": pins.test_lu_complete_is_rank_revealing_and_pseudo_solves,
+    "precond_unsym": pins.test_unsymmetric_precond_and_gcr,
+    "solve_unsym": pins.test_unsymmetric_hybrid_solve,
 }
 
 # (id, text in the oracle, planted replacement, occurrence, pins that must fail)
@@ -87,12 +94,12 @@ MUTANTS = [
      "inupper[adj.indices[adj.indptr[v]:adj.indptr[v + 1]]].all()", 0, ["nd_separators", "nd_fig1"]),
     ("nd_root_first", "for lev in range(m, 0, -1)", "for lev in range(1, m + 1)", 0, ["nd_fig1"]),
     # Sec. 2.1 elimination
-    ("elim_sign", "S[np.ix_(rows, rows)] -= np.outer(col, col) / d",
-     "S[np.ix_(rows, rows)] += np.outer(col, col) / d", 0, ["brute_force_schur", "eq1"]),
+    ("elim_sign", "S[np.ix_(rows, rows)] -= np.outer(col, row) / d",
+     "S[np.ix_(rows, rows)] += np.outer(col, row) / d", 0, ["brute_force_schur", "eq1"]),
     ("elim_l_unscaled", "fac.lcol[int(q)] = (rows, col / d)", "fac.lcol[int(q)] = (rows, col)", 0,
      ["eq1", "precond"]),
-    ("null_test_not_accumulated", "G[rows] += np.abs(col * (col / d))",
-     "G[rows] = np.abs(col * (col / d))", 0, ["null_pivot"]),
+    ("null_test_not_accumulated", "G[rows] += np.abs(col * (row / d))",
+     "G[rows] = np.abs(col * (row / d))", 0, ["null_pivot"]),
     # Sec. 2.2 pivoting and postponing
     ("ratio_against_one", "if not (dg[t] >= tau * d_ref):", "if not (dg[t] >= tau):", 0,
      ["hand_ratio_previous"]),
@@ -108,7 +115,7 @@ MUTANTS = [
     ("enlarge_moves_first", "fac.moved = order[len(order) - nmove:]", "fac.moved = order[:nmove]", 0,
      ["hand_postponing"]),
     # Sec. 3.1-3.2 preconditioner
-    ("precond_bwd_sign", "y[p] -= l[keep] @ y[rows[keep]]", "y[p] += l[keep] @ y[rows[keep]]", 0,
+    ("precond_bwd_sign", "y[p] -= u[keep] @ y[rows[keep]]", "y[p] += u[keep] @ y[rows[keep]]", 0,
      ["precond"]),
     ("precond_diag_mul", "y[p] /= fac.d[int(p)]", "y[p] *= fac.d[int(p)]", 0, ["precond"]),
     ("precond_bwd_order", "for p in order[::-1]:", "for p in order:", 0, ["precond"]),
@@ -153,6 +160,20 @@ MUTANTS = [
     ("backward_error_no_b", "(nK * np.abs(x[:, j]).max() + np.abs(b[:, j]).max())",
      "(nK * np.abs(x[:, j]).max())", 0, ["residual_measures"]),
     ("noise_without_precond", "W = precond_apply(fac, R)", "W = R", 0, ["s22_noise"]),
+    # LDU form (U != L^T) and the unsymmetric S22 (R15)
+    ("elim_row_as_column", "row = S[q, rows].copy()", "row = S[rows, q].copy()", 0,
+     ["ldu_eq1", "ldu_brute_force"]),
+    ("elim_u_unscaled", "fac.urow[int(q)] = (rows, row / d)", "fac.urow[int(q)] = (rows, row)", 0,
+     ["ldu_eq1", "precond_unsym"]),
+    ("precond_bwd_uses_l", "rows, u = fac.urow[int(p)]", "rows, u = fac.lcol[int(p)]", 0, ["precond_unsym"]),
+    ("lu_column_not_swapped", "A[:, [k, j]] = A[:, [j, k]]", "pass", 0, ["lu_choice"]),
+    ("lu_partial_pivoting", "j, i = divmod(int(np.argmax(np.abs(A[k:, k:]).T)), n - k)",
+     "j, i = 0, int(np.argmax(np.abs(A[k:, k])))", 0, ["lu_choice"]),
+    ("lu_update_uses_column", "A[k + 1:, k + 1:] -= np.outer(l, A[k, k + 1:])",
+     "A[k + 1:, k + 1:] -= np.outer(l, A[k + 1:, k])", 0, ["lu_choice"]),
+    ("lu_solve_row_perm", "    x[pcol] = w\n", "    x[prow] = w\n", 0, ["lu_rank"]),
+    ("s22_dispatch_inverted", "    elif symmetric:\n", "    elif not symmetric:\n", 0,
+     ["sign_form", "solve_unsym"]),
     # adjoint
     ("adjoint_swapped_derivative", "db = 2 * kb * ka * ka / s", "db = 2 * ka * kb * kb / s", 0, ["adjoint_fd"]),
     ("adjoint_dirichlet_half", "g[:, 0] -= 2 * k[:, 0] * X[:, 0] * Lm[:, 0]",

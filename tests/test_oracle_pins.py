@@ -15,7 +15,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 import oracle as O
-from workloads import diffusion2d, stokes3d, elasticity3d, darcy2d, consistent_rhs
+from workloads import diffusion2d, stokes3d, stokes3d_ldu, elasticity3d, darcy2d, consistent_rhs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -594,3 +594,167 @@ def test_bunch_parlett_is_rank_revealing():
         assert (order_mags[r:] < 1e-12).all() and (order_mags[:r] > 1e-4).all()   # null pivots last
         assert O.kernel_dimension(mags) == n - r
         # Bunch-Kaufman (partial pivoting) does not promise this ordering
+
+
+# --------------------------------------------------------------------------- LDU form (U != L^T)
+def _rand_unsym(n, rng):
+    return rng.standard_normal((n, n)) * 0.3 + np.diag(rng.uniform(0.5, 3.0, n) * rng.choice([-1, 1], n))
+
+
+def _convection_diffusion(n, seed=0, peclet=0.4):
+    # diffusion with islands plus a skew-symmetric part on the same pattern: K-bar != K-bar^T
+    s = diffusion2d(n, n, n_islands=1, island=3, contrast=1e4, dirichlet_x=True, seed=seed)
+    K = s.to_scipy().tocsr()
+    U = sp.triu(K, 1).tocoo()
+    rng = np.random.default_rng(seed)
+    w = peclet * np.abs(U.data) * rng.uniform(0.5, 1.0, U.nnz)
+    N = sp.coo_matrix((np.concatenate([w, -w]), (np.concatenate([U.row, U.col]), np.concatenate([U.col, U.row]))),
+                      shape=K.shape)
+    return s, (K + N).tocsr()
+
+
+def test_ldu_reconstructs_eq1_unsymmetric():
+    # Eq. (1) in its LDU form: Pi^T K Pi = L D U with unit L (columns) and unit U (rows)
+    rng = np.random.default_rng(31)
+    for _ in range(4):
+        n = 11
+        A = _rand_unsym(n, rng)
+        fac = O.threshold_factorize(sp.csr_matrix(A), [np.arange(n)], tau=1e-6, n_enlarge=0)
+        elim = fac.node_pivots[0].astype(int)
+        pos = {int(g): i for i, g in enumerate(elim)}
+        m = len(elim)
+        Lm, Um, D = np.eye(m), np.eye(m), np.zeros(m)
+        for g in elim:
+            j = pos[int(g)]
+            D[j] = fac.d[int(g)]
+            for r, v in zip(*fac.lcol[int(g)]):
+                if int(r) in pos:
+                    Lm[pos[int(r)], j] = v
+            for r, v in zip(*fac.urow[int(g)]):
+                if int(r) in pos:
+                    Um[j, pos[int(r)]] = v
+        Ad = A[np.ix_(elim, elim)]
+        assert np.abs(np.tril(Lm, -1)).max() > 0 and np.abs(Lm - Um.T).max() > 1e-3   # really unsymmetric
+        assert np.abs(Lm @ np.diag(D) @ Um - Ad).max() / np.abs(Ad).max() < 1e-5
+
+
+def test_ldu_pivots_match_brute_force_unsymmetric_schur():
+    rng = np.random.default_rng(32)
+    for _ in range(6):
+        n = 8
+        A = _rand_unsym(n, rng)
+        fac = O.threshold_factorize(sp.csr_matrix(A), [np.arange(n)], tau=1e-6, n_enlarge=0)
+        elim = []
+        for q in fac.node_pivots[0]:
+            rest = [i for i in range(n) if i not in elim]
+            S = A[np.ix_(rest, rest)]
+            if elim:
+                S = S - A[np.ix_(rest, elim)] @ np.linalg.solve(A[np.ix_(elim, elim)], A[np.ix_(elim, rest)])
+            assert rest[int(np.argmax(np.abs(np.diag(S))))] == q
+            np.testing.assert_allclose(fac.d[int(q)], S[rest.index(q), rest.index(q)], rtol=2e-5)
+            elim.append(int(q))
+
+
+def test_sign_form_factorizes_like_the_symmetric_matrix():
+    # K-bar = J S (J = diag(I, -I), S symmetric): every Schur complement of Q K-bar Q is J times
+    # that of Q S Q, so the pivots, the split and X12 are those of S, d and l change sign with
+    # J, u does not, S22 = J2 S22(S), and K-bar x = b is S x = J b (Sec. 2.1 rank-1 update).
+    s = stokes3d_ldu(4, delta=0.01)
+    S = stokes3d(4, delta=0.01)
+    J = s.meta["row_sign"].astype(np.float64)
+    Ku, Ks = s.to_scipy(), S.to_scipy()
+    assert abs(Ku - Ku.T).max() > 0 and abs(Ks - Ks.T).max() == 0
+    qu, K1 = O.scale_matrix(Ku)
+    qs, K2 = O.scale_matrix(Ks)
+    np.testing.assert_array_equal(qu, qs)
+    sets, order = O.nested_dissection(K2, S.coords, 3)
+    nodes = [sets[l] for l in order]
+    fu = O.threshold_factorize(K1, nodes, tau=1e-2)
+    fs = O.threshold_factorize(K2, nodes, tau=1e-2)
+    for a, b in zip(fu.node_pivots, fs.node_pivots):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(fu.lambda2, fs.lambda2)
+    for g in fs.d:
+        assert fu.d[g] == J[g] * fs.d[g]
+        ru, lu = fu.lcol[g]
+        rs, ls = fs.lcol[g]
+        np.testing.assert_array_equal(ru, rs)
+        np.testing.assert_array_equal(lu, (J[rs] * J[g] * ls).astype(ls.dtype))
+        np.testing.assert_array_equal(fu.urow[g][1], fs.urow[g][1])
+    ru_ = O.run_hybrid(Ku, nodes, 1e-2)
+    rs_ = O.run_hybrid(Ks, nodes, 1e-2)
+    lam2 = fs.lambda2
+    np.testing.assert_allclose(ru_["S22"], J[lam2][:, None] * rs_["S22"], atol=1e-11 * np.abs(rs_["S22"]).max())
+    assert len(ru_["bk"]) == 4 and len(rs_["bk"]) == 3 and ru_["kdim"] == rs_["kdim"] == 3
+
+
+def test_lu_complete_reconstruction_and_pivot_choice():
+    rng = np.random.default_rng(33)
+    for n in (1, 2, 5, 9, 16):
+        A = rng.standard_normal((n, n))
+        prow, pcol, Lf, U = O.lu_complete(A)
+        np.testing.assert_allclose(O.lu_reconstruct(prow, pcol, Lf, U), A, atol=1e-12 * np.abs(A).max())
+        assert np.abs(Lf).max() <= 1.0 + 1e-12                        # complete pivoting: |l| <= 1
+        Ap = A[np.ix_(prow, pcol)]
+        for k in range(n):                                             # brute-force Schur complements
+            Sk = Ap[k:, k:] - (Ap[k:, :k] @ np.linalg.solve(Ap[:k, :k], Ap[:k, k:]) if k else 0)
+            assert abs(U[k, k]) >= np.abs(Sk).max() * (1 - 1e-10)
+            np.testing.assert_allclose(U[k, k:], Sk[0], rtol=1e-9, atol=1e-12 * np.abs(A).max())
+
+
+def test_lu_complete_is_rank_revealing_and_pseudo_solves():
+    rng = np.random.default_rng(34)
+    for n, r in ((8, 5), (12, 9), (20, 17)):
+        X, Y = rng.standard_normal((n, r)), rng.standard_normal((r, n))
+        A = X @ Y
+        prow, pcol, Lf, U = O.lu_complete(A)
+        mags = np.abs(np.diag(U))
+        assert (mags[r:] < 1e-10 * mags[0]).all() and (mags[:r] > 1e-6 * mags[0]).all()
+        assert O.kernel_dimension(mags) == n - r
+        y = A @ rng.standard_normal((n, 2))                            # consistent
+        x = O.lu_pseudo_solve(prow, pcol, Lf, U, y, n - r)
+        np.testing.assert_allclose(A @ x, y, atol=1e-9 * np.abs(y).max())
+    A = rng.standard_normal((9, 9))
+    y = rng.standard_normal((9, 3))
+    np.testing.assert_allclose(O.lu_pseudo_solve(*O.lu_complete(A), y, 0), np.linalg.solve(A, y), rtol=1e-9, atol=1e-10)
+
+
+def test_unsymmetric_precond_and_gcr():
+    s, Kb = _convection_diffusion(14, seed=3)
+    q, K = O.scale_matrix(Kb)
+    sets, order = O.nested_dissection(K, s.coords, 3)
+    fac = O.threshold_factorize(K, [sets[l] for l in order], tau=1e-2, n_enlarge=4)
+    A = O.k11_operator(K, fac.lambda2)
+    X = np.random.default_rng(1).standard_normal((s.L, 3))
+    X[fac.lambda2] = 0
+    Y = O.precond_apply(fac, A(X))
+    assert np.linalg.norm(Y - X) / np.linalg.norm(X) < 1e-3            # Q^-1 K11 ~ I with U != L^T
+    lam1 = np.setdiff1d(np.arange(s.L), fac.lambda2)
+    B = np.zeros((s.L, fac.M))
+    B[lam1] = K.toarray()[np.ix_(lam1, fac.lambda2)]
+    Xg, hist, _, _ = O.block_gcr(A, lambda R: O.precond_apply(fac, R), B, tol=1e-15, maxit=20)
+    Xd = O.x12_direct(K, fac.lambda2)
+    assert np.abs(Xg - Xd).max() / np.abs(Xd).max() < 1e-12
+
+
+def test_unsymmetric_hybrid_solve():
+    # nonsingular convection-diffusion: the exact solution; the singular Stokes LDU form of
+    # Sec. 4.2 with a consistent right-hand side: backward error at FP64 rounding, kernel 3
+    s, Kb = _convection_diffusion(12, seed=4)
+    q, K = O.scale_matrix(Kb)
+    sets, order = O.nested_dissection(K, s.coords, 3)
+    res = O.run_hybrid(Kb, [sets[l] for l in order], 1e-2, use_gcr=True)
+    assert len(res["bk"]) == 4 and res["kdim"] == 0
+    b = np.random.default_rng(0).standard_normal((s.L, 2))
+    x = q[:, None] * O.hybrid_solve(res["K"], res["fac"].lambda2, res["X12"], res["bk"], res["kdim"], q[:, None] * b)
+    xr = np.linalg.solve(Kb.toarray(), b)
+    assert np.abs(x - xr).max() / np.abs(xr).max() < 1e-9
+    t = stokes3d_ldu(4, delta=0.01)
+    Kt = t.to_scipy()
+    qt, K2 = O.scale_matrix(Kt)
+    sets, order = O.nested_dissection(K2, t.coords, 3)
+    res = O.run_hybrid(Kt, [sets[l] for l in order], 1e-2, use_gcr=True)
+    assert res["kdim"] == 3
+    b = consistent_rhs(t, 5, nrhs=2)
+    x = qt[:, None] * O.hybrid_solve(res["K"], res["fac"].lambda2, res["X12"], res["bk"], res["kdim"], qt[:, None] * b)
+    assert O.backward_error(Kt, x, b) < 1e-14

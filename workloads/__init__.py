@@ -9,6 +9,8 @@ from .gen import (  # noqa: F401
     CsrSystem,
     diffusion2d,
     stokes3d,
+    stokes3d_ldu,
+    row_sign_form,
     elasticity3d,
     darcy2d,
     batched_systems,

@@ -140,14 +140,16 @@ def diffusion2d(nx=48, ny=48, n_islands=6, island=4, contrast=1e8, seed=1, gap=2
 # --------------------------------------------------------------------------
 # 3D Stokes-like saddle point (Q1 velocity nodes, P0 cell pressures)
 # --------------------------------------------------------------------------
-def stokes3d(n=32, seed=2, mu_log10=(-3.0, 3.0), p_scale=None, name=None) -> CsrSystem:
-    """[A B^T; B 0] on an n^3 node grid, h = 1/(n-1).
+def stokes3d(n=32, seed=2, mu_log10=(-3.0, 3.0), p_scale=None, name=None, delta=0.0) -> CsrSystem:
+    """[A B^T; B -delta D] on an n^3 node grid, h = 1/(n-1).
 
     A: 7-point nodal Laplacian for each of the 3 velocity components; the
     weight of an edge is h times the mean viscosity of the (up to 4) cells that
     share it; natural boundary.  B: Q1-P0 divergence, the integral of
     d(phi_node)/dx_d over a cell, +-h^2/4 for its 8 corners, times ``p_scale``.
-    Viscosity is 10^U(mu_log10) per cell.  The pressure block is zero.
+    Viscosity is 10^U(mu_log10) per cell.  The pressure block is zero, or with
+    ``delta`` > 0 the stabilisation -delta D: D is the face-neighbour graph
+    Laplacian of the cells times p_scale^2 h^3 (the order of B A^-1 B^T).
 
     ``p_scale`` nondimensionalises the pressure unknowns.  The default
     h^(-3/2) makes the pressure Schur complement B A^-1 B^T of the same order
@@ -199,6 +201,15 @@ def stokes3d(n=32, seed=2, mu_log10=(-3.0, 3.0), p_scale=None, name=None) -> Csr
                     v = np.full(pc.shape, q if dd == 1 else -q)
                     rows += [pc, 3 * nd + d]; cols += [3 * nd + d, pc]; vals += [v, v]
     L = nv + nc ** 3
+    if delta:
+        w = delta * p_scale * p_scale * h ** 3
+        pdiag = np.zeros(nc ** 3)
+        for ax in range(3):
+            a = np.take(cell, np.arange(nc - 1), axis=ax).ravel()
+            b = np.take(cell, np.arange(1, nc), axis=ax).ravel()
+            rows += [nv + a, nv + b]; cols += [nv + b, nv + a]; vals += [np.full(a.shape, w)] * 2
+            np.add.at(pdiag, a, -w); np.add.at(pdiag, b, -w)
+        rows.append(nv + np.arange(nc ** 3)); cols.append(nv + np.arange(nc ** 3)); vals.append(pdiag)
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(L, L))
     g = np.arange(n) * h
     Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
@@ -210,7 +221,37 @@ def stokes3d(n=32, seed=2, mu_log10=(-3.0, 3.0), p_scale=None, name=None) -> Csr
     kern = np.zeros((L, 3))
     for d in range(3):
         kern[d:nv:3, d] = 1.0 / math.sqrt(n ** 3)
-    return _finish(name or f"stokes3d_{n}", A, coords, kern, n=n, h=h, p_scale=p_scale)
+    return _finish(name or f"stokes3d_{n}", A, coords, kern, n=n, h=h, p_scale=p_scale, delta=delta,
+                   n_velocity=nv)
+
+
+def row_sign_form(system: CsrSystem, sign: np.ndarray, name: str | None = None) -> CsrSystem:
+    """The matrix J K-bar, J = diag(sign), sign_i in {+1, -1}: every row i scaled by sign_i.
+
+    For the saddle point [A B^T; B -delta D] and J = diag(I, -I) this is the
+    unsymmetric form [A B^T; -B delta D] of Sec. 4.2.  Same pattern and kernel;
+    the signs are kept in meta["row_sign"] (int8).
+    """
+    sign = np.asarray(sign)
+    assert sign.shape == (system.L,) and np.all(np.abs(sign) == 1)
+    rows = np.repeat(np.arange(system.L), np.diff(system.rowptr))
+    return CsrSystem(
+        name=name or f"{system.name}_signed",
+        rowptr=system.rowptr.copy(),
+        col=system.col.copy(),
+        val=system.val * sign[rows],
+        coords=system.coords.copy(),
+        kernel=None if system.kernel is None else system.kernel.copy(),
+        meta={**system.meta, "row_sign": sign.astype(np.int8)},
+    )
+
+
+def stokes3d_ldu(n=8, seed=2, delta=0.01, **kw) -> CsrSystem:
+    """[A B^T; -B delta D]: the unsymmetric Stokes form of Sec. 4.2 (velocity rows +1, pressure rows -1)."""
+    s = stokes3d(n, seed=seed, delta=delta, **kw)
+    sign = np.ones(s.L, dtype=np.int8)
+    sign[s.meta["n_velocity"]:] = -1
+    return row_sign_form(s, sign, name=f"stokes3d_ldu_{n}")
 
 
 # --------------------------------------------------------------------------
