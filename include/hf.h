@@ -150,6 +150,24 @@ int hf_analyze(int64_t L, const int64_t* rowptr, const int32_t* col, const doubl
 int hf_factorize(hf_ctx* ctx, const double* vals, double tau);
 
 /*
+ * LDU form with row signs (Sec. 2.1 writes the rank-1 update with the pivot's column
+ * and row separately; the Stokes matrix [A B^T; -B delta D] of Sec. 4.2 is unsymmetric).
+ * Declares Kbar = J S with J = diag(sign) and S symmetric, as for [A B^T; -B delta D]
+ * = diag(I, -I) [A B^T; B -delta D].  Every Schur complement of J S is J times that of
+ * S, so the pivots, postponed sets, Lambda_2, X12 and the solution of Kbar x = b are
+ * those of S with the right-hand side J b.  The next hf_factorize therefore factorizes
+ * K = J Q Kbar Q (= Q S Q) and hf_solve scales b by J Q; the getters (factor, X12, S22,
+ * its LDL^T, Q^-1) describe that K, whose S22 is J_2 times the Schur complement of
+ * Q Kbar Q.  The kernel basis is that of Kbar.
+ *   sign  host, L entries, each +1 or -1, copied before the call returns; NULL clears
+ *         the signs (Kbar symmetric again).
+ * The values given to hf_factorize must make J Kbar symmetric; the library does not
+ * check it.  Invalidates an earlier factorization (hf_factorize must run again).
+ * Errors: HF_ERR_ARG (null ctx, an entry other than +1 / -1), HF_ERR_CUDA, HF_ERR_OOM.
+ */
+int hf_set_row_signs(hf_ctx* ctx, const int8_t* sign);
+
+/*
  * Schur generation, Alg. 1 steps 2-5: for HF_PREC_MIXED, X12 = K11^-1 K12 by block GCR
  * (Sec. 3.5) in FP64 preconditioned by the FP32 factor, S22 = K22 - K21 X12 in FP64;
  * for the other forms S22 is taken from the factor.  Then S22 is factorized in FP64

@@ -17,6 +17,9 @@ from .hf import HybridFactor
 class HybridSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, H: HybridFactor, vals: torch.Tensor, b: torch.Tensor, tau: float = 1e-2):
+        if H.has_row_signs:
+            # K-bar = J S is not symmetric: its transposed solve is J S^-1, not another hf_solve
+            raise NotImplementedError("HybridSolve needs a symmetric K-bar (no row signs)")
         vals_c = vals.detach().contiguous()
         H.factorize(vals_c, tau)
         H.schur()

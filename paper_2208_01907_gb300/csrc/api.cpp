@@ -226,6 +226,25 @@ int hf_factorize(hf_ctx* c, const double* vals, double tau) {
   return hf_factorize_impl(c, vals, tau);
 }
 
+int hf_set_row_signs(hf_ctx* c, const int8_t* sign) {
+  if (!c) return HF_ERR_ARG;
+  if (sign)
+    for (int64_t i = 0; i < c->L; ++i)
+      if (sign[i] != 1 && sign[i] != -1) return HF_ERR_ARG;   // state unchanged
+  c->factored = false;
+  c->schured = false;
+  c->has_rsign = false;
+  if (!sign) return HF_OK;
+  int rc;
+  if ((rc = hf_ensure(c->d_rsign, (size_t)c->L + 16))) return rc;
+  cudaStream_t s = (cudaStream_t)c->opts.cuda_stream;
+  cudaError_t e = cudaMemcpyAsync(c->d_rsign.p, sign, (size_t)c->L, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the caller may free its array on return
+  if (e != cudaSuccess) return hf_cuda_error(e);
+  c->has_rsign = true;
+  return HF_OK;
+}
+
 int hf_schur(hf_ctx* c) {
   if (!c) return HF_ERR_ARG;
   return hf_schur_impl(c);
@@ -500,7 +519,7 @@ void hf_free(hf_ctx* c) {
                     &c->d_s22, &c->d_bk_lf, &c->d_bk_perm, &c->d_bk_blk, &c->d_bk_dval, &c->d_bk_null,
                     &c->d_work, &c->d_small, &c->d_ozslice, &c->d_gsmall, &c->d_k12, &c->d_solve, &c->d_gmag,
                     &c->d_pos0, &c->d_invpos, &c->d_ozint, &c->d_tparts, &c->d_bpart, &c->d_swlist,
-                    &c->d_swcount, &c->d_swplan, &c->d_swsig};
+                    &c->d_swcount, &c->d_swplan, &c->d_swsig, &c->d_rsign, &c->d_qrow};
   for (DevBuf* b : bufs) hf_release(*b);
   for (DevBuf& b : c->d_hist) hf_release(b);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

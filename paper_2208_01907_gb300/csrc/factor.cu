@@ -27,23 +27,29 @@ constexpr int TB = 64;            // trailing-update tile
 constexpr int TK = 16;            // trailing-update k chunk
 
 // ---------------------------------------------------------------------------
-// Sec. 2: Q_ii = 1/sqrt(|Kbar_ii|) (1 if zero) and K = Q Kbar Q
+// Sec. 2: Q_ii = 1/sqrt(|Kbar_ii|) (1 if zero) and K = Q Kbar Q.
+// With row signs J (the LDU form Kbar = J S, S symmetric, Sec. 4.2) the rows are
+// scaled by J Q instead: K = J Q Kbar Q = Q S Q, the symmetric matrix whose Schur
+// complements are J times those of Q Kbar Q (same pivots and split, Sec. 2.1).
 // ---------------------------------------------------------------------------
 __global__ void k_scale_diag(int64_t L, const int64_t* __restrict__ diagpos, const double* __restrict__ vals,
-                             double* __restrict__ q) {
+                             double* __restrict__ q, const int8_t* __restrict__ rsign, double* __restrict__ qrow) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L) return;
   double d = vals[diagpos[i]];
-  q[i] = (d != 0.0) ? 1.0 / sqrt(fabs(d)) : 1.0;
+  const double qi = (d != 0.0) ? 1.0 / sqrt(fabs(d)) : 1.0;
+  q[i] = qi;
+  if (rsign) qrow[i] = rsign[i] < 0 ? -qi : qi;
 }
 
+// qrow: the row scale (Q, or J Q with row signs); q: the column scale Q
 __global__ void k_scale_vals(int64_t L, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ vals, const double* __restrict__ q,
-                             double* __restrict__ kval, int* __restrict__ flags) {
+                             const double* __restrict__ vals, const double* __restrict__ qrow,
+                             const double* __restrict__ q, double* __restrict__ kval, int* __restrict__ flags) {
   int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (row >= L) return;
-  double qi = q[row];
+  double qi = qrow[row];
   bool bad = false;
   for (int64_t e = rowptr[row] + lane; e < rowptr[row + 1]; e += 32) {
     double v = vals[e];
@@ -1367,6 +1373,7 @@ static int upload_analysis(hf_ctx* c) {
   if ((rc = hf_ensure(c->d_cbmap, c->rowid_static.size() * 4 + 16))) return rc;
   if ((rc = hf_ensure(c->d_flags, FLAG_COUNT * sizeof(int) + 64))) return rc;
   if ((rc = hf_ensure(c->d_q, c->L * 8))) return rc;
+  if ((rc = hf_ensure(c->d_qrow, c->L * 8))) return rc;
   if ((rc = hf_ensure(c->d_kval, c->nnz * 8))) return rc;
   if ((rc = hf_ensure(c->d_lam2pos, c->L * 4))) return rc;
   if ((rc = hf_ensure(c->d_lam2, c->L * 4 + 16))) return rc;
@@ -1404,9 +1411,12 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     HF_CUDA_TRY(cudaMemcpyAsync(c->d_rowid.p, c->d_rowid_static.p, c->rowid_static.size() * 4,
                                 cudaMemcpyDeviceToDevice, s));
     const int64_t L = c->L;
-    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_diag<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_diagpos.p, vals, (double*)c->d_q.p));
+    const int8_t* rsign = c->has_rsign ? (const int8_t*)c->d_rsign.p : nullptr;
+    const double* qrow = (const double*)(c->has_rsign ? c->d_qrow.p : c->d_q.p);
+    HF_LAUNCH(c, HF_PROF_SCALE, k_scale_diag<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_diagpos.p, vals, (double*)c->d_q.p,
+                                                                                      rsign, (double*)c->d_qrow.p));
     HF_LAUNCH(c, HF_PROF_SCALE, k_scale_vals<<<(unsigned)((L * 32 + 255) / 256), 256, 0, s>>>(L, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
-                                                          vals, (const double*)c->d_q.p, (double*)c->d_kval.p,
+                                                          vals, qrow, (const double*)c->d_q.p, (double*)c->d_kval.p,
                                                           (int*)c->d_flags.p));
     HF_CUDA_TRY(cudaGetLastError());
     rc = dbl ? run_levels<double>(c) : run_levels<float>(c);

@@ -81,6 +81,8 @@ struct hf_ctx {
   DevBuf d_rowptr, d_col, d_diagpos, d_nodes, d_state, d_rowid, d_rowid_static, d_smap, d_asm;
   DevBuf d_cbmap;                    // per front: parent row of each contribution row (ld entries)
   DevBuf d_q, d_kval;                // scaling diag(Q) and scaled K values (FP64)
+  DevBuf d_rsign, d_qrow;            // row signs J (int8, L) and the row scale J Q (FP64, L)
+  bool has_rsign = false;            // K = J Q Kbar Q is factorized (the LDU form Kbar = J S)
   DevBuf d_front;                    // front arena (float or double)
   DevBuf d_bpart;                    // per-block partial maxima of the cooperative S22 LDL^T
   DevBuf d_tparts;                   // BF16 parts of the current panel (tensor-core trailing update)

@@ -2552,7 +2552,9 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
   double* y2 = scratch + blk;
   double* x2 = y2 + (size_t)M * m;
   double* zt = x2 + (size_t)M * m;  // work vectors of the S22 solve when they do not fit in shared memory
-  HF_LAUNCH(c, HF_PROF_SCALE, k_scale_in<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, b, ldb, (const double*)c->d_q.p, bi));
+  // right-hand sides enter as J Q b (Q b without row signs): K x = J Q b with xbar = Q x
+  const double* qrow = (const double*)(c->has_rsign ? c->d_qrow.p : c->d_q.p);
+  HF_LAUNCH(c, HF_PROF_SCALE, k_scale_in<<<nblk((int64_t)blk, 256), 256, 0, s>>>(L, m, b, ldb, qrow, bi));
   int grc = HF_OK;
   auto s22_solve = [&]() {
     if (M == 0) return;

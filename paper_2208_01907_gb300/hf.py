@@ -25,7 +25,7 @@ EXPORTED = (
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
     "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc",
     "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis",
-    "hf_gram_fp64", "hf_update_fp64", "hf_k11_iterate", "hf_free",
+    "hf_gram_fp64", "hf_update_fp64", "hf_k11_iterate", "hf_set_row_signs", "hf_free",
 )
 HF_NPROF = 13
 
@@ -77,6 +77,7 @@ def lib():
     L.hf_error_string.restype = C.c_char_p
     L.hf_analyze.argtypes = [i64, vp, vp, vp, i32, C.POINTER(hf_opts), C.POINTER(vp)]
     L.hf_factorize.argtypes = [vp, vp, dbl]
+    L.hf_set_row_signs.argtypes = [vp, vp]
     L.hf_schur.argtypes = [vp]
     L.hf_solve.argtypes = [vp, i32, vp, i64, vp, i64]
     L.hf_get_split.argtypes = [vp, vp, vp, C.POINTER(hf_info)]
@@ -168,6 +169,21 @@ class HybridFactor:
         """vals_dev: torch float64 CUDA tensor with the CSR values of K-bar."""
         t = self.opts.tau if tau is None else tau
         _check(lib().hf_factorize(self._h, _ptr(vals_dev), float(t)), "hf_factorize")
+
+    def set_row_signs(self, sign):
+        """sign: host array of L entries in {+1, -1} (Kbar = diag(sign) S, S symmetric), or None."""
+        if sign is None:
+            self._rsign = None
+            _check(lib().hf_set_row_signs(self._h, None), "hf_set_row_signs")
+            return
+        self._rsign = np.ascontiguousarray(sign, dtype=np.int8)
+        if self._rsign.shape != (self.L,):
+            raise ValueError(f"row signs: expected {self.L} entries, got shape {self._rsign.shape}")
+        _check(lib().hf_set_row_signs(self._h, _ptr(self._rsign)), "hf_set_row_signs")
+
+    @property
+    def has_row_signs(self):
+        return getattr(self, "_rsign", None) is not None
 
     def schur(self):
         return _check(lib().hf_schur(self._h), "hf_schur", allow=(HF_ERR_NOT_CONVERGED,))

@@ -433,3 +433,76 @@ def test_k11_iterations_alg3_alg4_alg5(case):
     steps = lambda h: next((k for k, v in enumerate(h) if v <= 1e-10), len(h))
     assert abs(steps(h2) - steps(ho)) <= 1
     assert abs(np.log10(h2[0] / ho[0])) <= 1.0                    # Q^-1 b starts: FP32 factors agree
+
+
+def test_ldu_row_sign_form_matches_unsymmetric_oracle():
+    # The Stokes matrix of Sec. 4.2, [A B^T; -B delta D], is unsymmetric.  With its row signs
+    # declared the library factorizes J Q K-bar Q; the oracle takes the LDU route on K-bar
+    # itself (column and row of each pivot separately, LU with complete pivoting on S22).
+    import paper_2208_01907_gb300 as hf
+    from workloads import stokes3d_ldu
+
+    s = stokes3d_ldu(8, delta=0.0)                           # [A B^T; -B 0]: pressure rows reach Lambda_2
+    sign = s.meta["row_sign"]
+    J = sign.astype(np.float64)
+    Kb = s.to_scipy()
+    assert abs(Kb - Kb.T).max() > 0
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, nd_leaf=128)
+    H.set_row_signs(sign)
+    vals = torch.tensor(s.val, device="cuda", dtype=torch.float64)
+    H.factorize(vals, 1e-2)
+    H.schur()
+    info = H.info()
+    assert info["kernel_dim"] == 3 and info["gcr_relres"] <= 1e-13
+    q, K, fac, moved = replay(s, H, 1e-2)
+    assert fac.violations == []
+    order, lam2 = H.split()
+    assert lam2.tolist() == fac.lambda2.tolist()
+    assert order[:fac.N].tolist() == fac.lambda1_order.tolist()
+    assert (J[lam2] < 0).any() and (J[lam2] > 0).any()
+    X12 = H.x12(torch).cpu().numpy()
+    Xref = O.x12_direct(K, fac.lambda2)
+    assert np.abs(X12 - Xref).max() <= X12_TOL * max(np.abs(Xref).max(), 1.0)
+    S22 = H.s22(torch).cpu().numpy()
+    Sref = O.schur_direct(K, fac.lambda2)                    # unsymmetric
+    assert abs(Sref - Sref.T).max() > 1e-3 * np.abs(Sref).max()
+    assert rel_fro(J[lam2][:, None] * S22, Sref) <= S22_TOL
+    # Alg. 2 on K-bar: backward error, and the oracle's LDU solution modulo the kernel
+    b = consistent_rhs(s, 3, 2)
+    bt = torch.tensor(np.ascontiguousarray(b.T), device="cuda")
+    xt = torch.zeros_like(bt)
+    H.solve(bt, xt)
+    x = xt.cpu().numpy().T
+    assert O.backward_error(Kb, x, b) <= BWD_TOL
+    lu = O.lu_complete(Sref)
+    kd = O.kernel_dimension(np.abs(np.diag(lu[3])), ref=float(np.abs(K.diagonal()[fac.lambda2]).max()))
+    assert kd == 3
+    xo = q[:, None] * O.hybrid_solve(K, fac.lambda2, Xref, lu, kd, q[:, None] * b)
+    sv = np.linalg.svd(Kb.toarray(), compute_uv=False)
+    kappa = sv[0] / sv[-4]
+    diff = project_out(x - xo, s.kernel)
+    assert np.linalg.norm(diff) <= max(1e-8, 1e3 * 1.1e-16 * kappa) * np.linalg.norm(project_out(xo, s.kernel))
+    # the symmetric matrix J K-bar without signs: the same numbers bit for bit (sign flips are exact)
+    S = stokes3d(8, seed=2)
+    np.testing.assert_array_equal(S.val, J[np.repeat(np.arange(s.L), np.diff(s.rowptr))] * s.val)
+    H2 = hf.HybridFactor(S.L, S.rowptr, S.col, S.coords, nd_leaf=128)
+    H2.factorize(torch.tensor(S.val, device="cuda", dtype=torch.float64), 1e-2)
+    H2.schur()
+    assert H2.split()[1].tolist() == lam2.tolist()
+    np.testing.assert_array_equal(H2.x12(torch).cpu().numpy(), X12)
+    np.testing.assert_array_equal(H2.s22(torch).cpu().numpy(), S22)
+    x2 = torch.zeros_like(bt)
+    H2.solve(torch.tensor(np.ascontiguousarray((J[:, None] * b).T), device="cuda"), x2)
+    np.testing.assert_array_equal(x2.cpu().numpy().T, x)
+    # invalid signs leave the context as it was; valid ones ask for a new factorization
+    with pytest.raises(hf.HFError):
+        H.set_row_signs(np.zeros(s.L, dtype=np.int8))
+    H.solve(bt, xt)
+    H.set_row_signs(sign)
+    with pytest.raises(hf.HFError):
+        H.schur()
+    with pytest.raises(NotImplementedError):
+        from paper_2208_01907_gb300.autograd import hybrid_solve
+        hybrid_solve(H, vals, torch.tensor(b[:, 0], device="cuda"))
+    H.free()
+    H2.free()
