@@ -408,8 +408,9 @@ def measured_traffic(kernel):
 
     The hash covers the whole file, or with `source_until: <line>` the part of the file
     before that line (the kernel, its helpers and its launches, when host code that
-    cannot reach the kernel follows); `headers: a, b` with `headers_sha256` adds the
-    concatenated headers the kernel is compiled with."""
+    cannot reach the kernel follows); `headers: a, b@line` with `headers_sha256` adds the
+    concatenated headers the kernel is compiled with, `@line` cutting one before that
+    line (where only host-side declarations follow)."""
     import glob
     import hashlib
     keys = ("kernel:", "source:", "source_until:", "source_sha256:", "headers:", "headers_sha256:",
@@ -435,9 +436,16 @@ def measured_traffic(kernel):
                 return None
             if "headers" in fields:
                 h = hashlib.sha256()
-                for name in fields["headers"].split(","):
-                    with open(os.path.join(ROOT, name.strip()), "rb") as f:
-                        h.update(f.read())
+                for entry in fields["headers"].split(","):
+                    name, _, until = entry.strip().partition("@")
+                    with open(os.path.join(ROOT, name), "rb") as f:
+                        text = f.read()
+                    if until:
+                        at = text.find(until.encode())
+                        if at < 0:
+                            return None
+                        text = text[:at]
+                    h.update(text)
                 if h.hexdigest() != fields.get("headers_sha256"):
                     return None
             return float(fields["dram_bytes_per_launch"])
