@@ -14,8 +14,10 @@
  *
  * Conventions for every entry point:
  *   - Indices are 0-based.  Matrices are square, structurally symmetric and
- *     numerically symmetric (the LDL^T form of Sec. 4.1).  CSR rows are sorted
- *     by column and every row stores its diagonal entry (it may be 0).
+ *     numerically symmetric (the LDL^T form of Sec. 4.1), or J times a symmetric
+ *     matrix with the row signs J declared by hf_set_row_signs (the unsymmetric
+ *     LDU form [A B^T; -B delta D] of Sec. 4.2).  CSR rows are sorted by column
+ *     and every row stores its diagonal entry (it may be 0).
  *   - "device" pointers are CUDA global-memory addresses on the current device;
  *     "host" pointers are ordinary process memory.  The caller owns every
  *     buffer it passes; the library never frees or retains caller pointers
@@ -219,6 +221,10 @@ int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
  * Errors: HF_ERR_ARG (sizes), HF_ERR_OOM, HF_ERR_CUDA, HF_ERR_TIMEOUT (a bounded
  * tensor-core wait gave up; the output is not valid).
  */
+int hf_gram_fp64(hf_ctx* ctx, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale);
+int hf_update_fp64(hf_ctx* ctx, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
+                   double sgn);
+
 /*
  * The iterations on K11 X = B compared in the paper (Sec. 3.3-3.5, Fig. 2), each with the
  * lower-precision factor Q of hf_factorize as preconditioner, on the scaled unknowns:
@@ -236,10 +242,6 @@ int hf_precond(hf_ctx* ctx, int m, const double* R, double* W);
  * hist still valid), HF_ERR_CUDA, HF_ERR_OOM, HF_ERR_TIMEOUT.
  */
 int hf_k11_iterate(hf_ctx* ctx, int method, int m, const double* B, double* X, int maxit, double* hist, int* iters);
-
-int hf_gram_fp64(hf_ctx* ctx, int64_t L, int ma, int mb, const double* A, const double* B, double* G, double scale);
-int hf_update_fp64(hf_ctx* ctx, int64_t L, int m, const double* A, const double* C, double* Y, const double* Yinit,
-                   double sgn);
 
 /*
  * hf_precond without any device allocation (the paper has no counterpart; this is a
@@ -271,8 +273,8 @@ int hf_precond_noalloc(hf_ctx* ctx, int m, const double* R, double* W);
 
 /*
  * Adjoint of the solve with respect to the matrix values.  For x = Kbar^-1 b and an
- * objective J(x), with lam = Kbar^-T dJ/dx (Kbar is symmetric, so lam comes from
- * hf_solve with the same factor), dJ/dKbar_ij = -sum_r lam_i^r x_j^r for every stored
+ * objective J(x), with lam = Kbar^-T dJ/dx (for a symmetric Kbar, i.e. without row
+ * signs, lam comes from hf_solve with the same factor), dJ/dKbar_ij = -sum_r lam_i^r x_j^r for every stored
  * entry (i, j).  Writes that gradient in CSR order (the order given to hf_analyze).
  *   nrhs       number of columns of x and lam (>= 1)
  *   x, ldx     device, column-major L x nrhs, ldx >= L
