@@ -391,13 +391,27 @@ def run_ours(args):
             "fp32_form": fp32,
             "gpu_launches": launches,
             "kernel_ms": {k: round(v[0] / prof_steps, 3) for k, v in prof.items()},
-            "kernel_work": {k: {"gflop": round(v[2] / prof_steps / 1e9, 3), "gbytes": round(v[3] / prof_steps / 1e9, 3)}
-                            for k, v in prof.items() if v[2] or v[3]},
+            "kernel_work": kernel_work(prof, prof_steps),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def kernel_work(prof, steps):
+    """Per kernel class: algorithmic GFLOP and GB per step and the rates they give over the
+    class's measured time.  prof maps a class to (ms, launches, flops, bytes) summed over
+    `steps` steps; classes with no counted work are left out."""
+    out = {}
+    for k, v in prof.items():
+        ms, flops, nbytes = v[0], v[2], v[3]
+        if not (flops or nbytes):
+            continue
+        out[k] = {"gflop": round(flops / steps / 1e9, 3), "gbytes": round(nbytes / steps / 1e9, 3),
+                  "tflop_s": round(flops / ms * 1e-9, 3) if ms > 0 else None,
+                  "gb_s": round(nbytes / ms * 1e-6, 1) if ms > 0 else None}
+    return out
 
 
 def measured_traffic(kernel):

@@ -134,3 +134,15 @@ def test_product_path_never_reaches_the_oracle():
     code = ("import sys, paper_2208_01907_gb300, paper_2208_01907_gb300.shard; "
             "assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
     subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
+
+
+def test_bench_kernel_work_rates():
+    # per-class rates of the bench line: GFLOP and GB per step, TFLOP/s and GB/s over the class's time
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = {"trsv_fwd": (180.0, 477, 1.8e12, 15.0e9), "scale": (0.2, 3, 0.0, 0.0), "gram": (0.0, 9, 1e9, 2e9)}
+    w = bench.kernel_work(prof, 3)
+    assert set(w) == {"trsv_fwd", "gram"}
+    assert w["trsv_fwd"] == {"gflop": 600.0, "gbytes": 5.0, "tflop_s": 10.0, "gb_s": 83.3}
+    assert w["gram"]["tflop_s"] is None and w["gram"]["gb_s"] is None
