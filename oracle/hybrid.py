@@ -179,20 +179,24 @@ class FactorResult:
         return len(self.lambda2)
 
 
-def _eliminate(S, G, remaining, q, fac):
+def _eliminate(S, G, remaining, q, fac, symmetric):
     """One rank-1 Schur update with weight 1/d on the remaining indices (Sec. 2.1).
 
     The LDU form: the pivot's column (below) and row (right) enter the update
-    separately, S' = S - col d^-1 row, with l = col / d and u = row / d; for a
-    symmetric S the two are the same numbers and this is LDL^T.
+    separately, S' = S - col d^-1 row, with l = col / d and u = row / d.  For a
+    symmetric S the column is the row (LDL^T) and only the row is read.
     G accumulates, per index, |K_ii| plus the magnitudes |l_i u_i d| of the
     updates its diagonal received (used by the null-pivot test R3b).
     """
     d = S[q, q]
     remaining[q] = False
-    rows = np.flatnonzero(((S[:, q] != 0) | (S[q] != 0)) & remaining)
-    col = S[rows, q].copy()
-    row = S[q, rows].copy()
+    if symmetric:
+        rows = np.flatnonzero((S[q] != 0) & remaining)
+        col = row = S[q, rows].copy()
+    else:
+        rows = np.flatnonzero(((S[:, q] != 0) | (S[q] != 0)) & remaining)
+        col = S[rows, q].copy()
+        row = S[q, rows].copy()
     if rows.size:
         S[np.ix_(rows, rows)] -= np.outer(col, row) / d
         G[rows] += np.abs(col * (row / d))
@@ -202,7 +206,8 @@ def _eliminate(S, G, remaining, q, fac):
     return d
 
 
-def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_test=True, tag=""):
+def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_test=True, tag="",
+                symmetric=False):
     """Symmetric max-|diag| pivoting with threshold postponing on one index set (Sec. 2.1-2.2).
 
     Each step takes the candidate of largest |diag| (R5 ties).  If it fails the
@@ -257,7 +262,7 @@ def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_t
             if null_test and dg[t] < tau * float(G[q]) * (1 - slack):
                 fac.violations.append(f"{tag}: step {step} pivot {q} fails the null test")
         q = cand.pop(t)
-        d = _eliminate(S, G, remaining, q, fac)
+        d = _eliminate(S, G, remaining, q, fac, symmetric)
         d_ref = abs(float(d))
         chosen.append(q)
         step += 1
@@ -285,20 +290,25 @@ def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: in
     """
     L = K.shape[0]
     S = K.toarray().astype(dtype)                  # current Schur complement
+    # symmetric up to the rounding of the scaling, (q_i k_ij) q_j vs (q_j k_ji) q_i: LDL^T
+    Ks = sp.csr_matrix(K)
+    symmetric = (abs(Ks - Ks.T) > 1e-14 * abs(Ks)).nnz == 0
     G = np.abs(np.diag(S)).copy()                  # R3b magnitude of the terms in each diagonal
     remaining = np.ones(L, dtype=bool)
     fac = FactorResult([], [], None, None, None, None, None)
     fac.node_skipped = []
     for t, lam in enumerate(nodes):
         rp = None if replay is None else (replay["node_pivots"][t], replay["node_skipped"][t])
-        ch, pp, sk = _factor_set(S, G, remaining, lam, tau, fac, rp, slack, null_test, tag=f"node{t}")
+        ch, pp, sk = _factor_set(S, G, remaining, lam, tau, fac, rp, slack, null_test, tag=f"node{t}",
+                                 symmetric=symmetric)
         fac.node_pivots.append(ch)
         fac.node_postponed.append(pp)
         fac.node_skipped.append(sk)
     lam0 = np.concatenate(fac.node_postponed) if fac.node_postponed else np.zeros(0, np.int64)
     fac.lam0 = np.sort(lam0)
     rp = None if replay is None else (replay["lam0_pivots"], replay["lam0_skipped"])
-    ch0, hat0, sk0 = _factor_set(S, G, remaining, fac.lam0, tau, fac, rp, slack, null_test, tag="lambda0")
+    ch0, hat0, sk0 = _factor_set(S, G, remaining, fac.lam0, tau, fac, rp, slack, null_test, tag="lambda0",
+                                 symmetric=symmetric)
     fac.lam0_pivots = ch0
     fac.lam0_skipped = sk0
     # R13: move the last n entries of the elimination order into hat-Lambda_0.  They are

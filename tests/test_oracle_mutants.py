@@ -161,7 +161,7 @@ MUTANTS = [
      "(nK * np.abs(x[:, j]).max())", 0, ["residual_measures"]),
     ("noise_without_precond", "W = precond_apply(fac, R)", "W = R", 0, ["s22_noise"]),
     # LDU form (U != L^T) and the unsymmetric S22 (R15)
-    ("elim_row_as_column", "row = S[q, rows].copy()", "row = S[rows, q].copy()", 0,
+    ("elim_row_as_column", "row = S[q, rows].copy()", "row = S[rows, q].copy()", 1,
      ["ldu_eq1", "ldu_brute_force"]),
     ("elim_u_unscaled", "fac.urow[int(q)] = (rows, row / d)", "fac.urow[int(q)] = (rows, row)", 0,
      ["ldu_eq1", "precond_unsym"]),
