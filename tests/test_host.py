@@ -146,3 +146,44 @@ def test_bench_kernel_work_rates():
     assert set(w) == {"trsv_fwd", "gram"}
     assert w["trsv_fwd"] == {"gflop": 600.0, "gbytes": 5.0, "tflop_s": 10.0, "gb_s": 83.3}
     assert w["gram"]["tflop_s"] is None and w["gram"]["gb_s"] is None
+
+
+def test_analysis_edge_cases():
+    # empty and malformed inputs are refused on the host; the smallest systems analyse
+    import ctypes as C
+    hf = _hf()
+    L = hf.lib()
+    o = hf.default_opts()
+    h = C.c_void_p()
+    rp = np.array([0], dtype=np.int64)
+    cl = np.zeros(1, dtype=np.int32)
+    assert L.hf_analyze(0, rp.ctypes.data, cl.ctypes.data, None, 0, C.byref(o), C.byref(h)) == 1   # L = 0
+    s = diffusion2d(4, 4, n_islands=0)
+    with pytest.raises(hf.HFError) as e:                       # coordinates of dimension 4
+        hf.HybridFactor(s.L, s.rowptr, s.col, np.zeros((s.L, 4)))
+    assert e.value.code == 1
+    col = s.col.copy()
+    col[-1] = s.L                                              # column out of range
+    with pytest.raises(hf.HFError) as e:
+        hf.HybridFactor(s.L, s.rowptr, col, s.coords)
+    assert e.value.code == 3
+    rp = s.rowptr.copy()
+    rp[0] = 1                                                  # row pointers not starting at 0
+    with pytest.raises(hf.HFError) as e:
+        hf.HybridFactor(s.L, rp, s.col, s.coords)
+    assert e.value.code == 3
+    import scipy.sparse as sp
+    A = s.to_scipy().tolil()
+    A.setdiag(0)
+    A = A.tocsr()
+    A.eliminate_zeros()                                        # rows without a stored diagonal
+    with pytest.raises(hf.HFError) as e:
+        hf.HybridFactor(s.L, A.indptr.astype(np.int64), A.indices.astype(np.int32), s.coords)
+    assert e.value.code == 3
+    # one unknown, and two disconnected unknowns without coordinates: one tree each way
+    for n, rp, cl in ((1, [0, 1], [0]), (2, [0, 1, 2], [0, 1])):
+        H = hf.HybridFactor(n, np.array(rp), np.array(cl))
+        parent, sets = H.tree()
+        assert sorted(np.concatenate(sets).tolist()) == list(range(n))
+        assert sum(1 for p in parent if p < 0) == 1
+        H.free()
