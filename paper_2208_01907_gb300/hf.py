@@ -127,6 +127,23 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def _dev(t, name, numel, rows=None, cols=None):
+    """Pointer of a device operand after checking what the C ABI cannot: a contiguous
+    float64 CUDA tensor with at least `numel` entries (and `rows` rows / `cols` columns
+    when it is 2-D).  The library reads and writes exactly that many entries."""
+    if not hasattr(t, "data_ptr") or not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name}: expected a CUDA tensor, got {type(t).__name__}")
+    if str(t.dtype) != "torch.float64":
+        raise TypeError(f"{name}: expected float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: holds {t.numel()} entries, the call needs {numel}")
+    if t.dim() == 2 and ((rows is not None and t.shape[0] != rows) or (cols is not None and t.shape[1] != cols)):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} does not match ({rows}, {cols})")
+    return C.c_void_p(t.data_ptr())
+
+
 def default_opts(**kw) -> hf_opts:
     o = hf_opts()
     _check(lib().hf_default_opts(C.byref(o)), "hf_default_opts")
@@ -168,7 +185,8 @@ class HybridFactor:
     def factorize(self, vals_dev, tau=None):
         """vals_dev: torch float64 CUDA tensor with the CSR values of K-bar."""
         t = self.opts.tau if tau is None else tau
-        _check(lib().hf_factorize(self._h, _ptr(vals_dev), float(t)), "hf_factorize")
+        v = _dev(vals_dev, "vals", self._col.shape[0])
+        _check(lib().hf_factorize(self._h, v, float(t)), "hf_factorize")
 
     def set_row_signs(self, sign):
         """sign: host array of L entries in {+1, -1} (Kbar = diag(sign) S, S symmetric), or None."""
@@ -191,7 +209,11 @@ class HybridFactor:
     def solve(self, b_dev, x_dev):
         """b_dev, x_dev: torch float64 CUDA tensors, column-major L x nrhs (shape (nrhs, L) contiguous)."""
         nrhs = 1 if b_dev.dim() == 1 else b_dev.shape[0]
-        return _check(lib().hf_solve(self._h, nrhs, _ptr(b_dev), self.L, _ptr(x_dev), self.L),
+        b = _dev(b_dev, "b", self.L * nrhs, cols=self.L)
+        x = _dev(x_dev, "x", self.L * nrhs, cols=self.L)
+        if b.value == x.value:
+            raise ValueError("x may not alias b")
+        return _check(lib().hf_solve(self._h, nrhs, b, self.L, x, self.L),
                       "hf_solve", allow=(HF_ERR_NOT_CONVERGED,))
 
     def kernel_basis(self, torch):
@@ -205,7 +227,8 @@ class HybridFactor:
     def precond(self, R_dev, W_dev):
         """W = Q^-1 R (Sec. 3.2) on row-major L x m torch float64 CUDA tensors (scaled unknowns)."""
         m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
-        _check(lib().hf_precond(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond")
+        R, W = _dev(R_dev, "R", self.L * m, rows=self.L), _dev(W_dev, "W", self.L * m, rows=self.L)
+        _check(lib().hf_precond(self._h, m, R, W), "hf_precond")
 
     def profile(self, enable=True):
         _check(lib().hf_profile(self._h, 1 if enable else 0), "hf_profile")
@@ -223,16 +246,17 @@ class HybridFactor:
     def precond_noalloc(self, R_dev, W_dev):
         """Same as precond(), with all scratch in the library's fixed device array (no allocation)."""
         m = 1 if R_dev.dim() == 1 else R_dev.shape[1]
-        _check(lib().hf_precond_noalloc(self._h, m, _ptr(R_dev), _ptr(W_dev)), "hf_precond_noalloc")
+        R, W = _dev(R_dev, "R", self.L * m, rows=self.L), _dev(W_dev, "W", self.L * m, rows=self.L)
+        _check(lib().hf_precond_noalloc(self._h, m, R, W), "hf_precond_noalloc")
 
     def k11_iterate(self, method, B_dev, X_dev, maxit=40):
         """K11 X = B by block GCR (method 0, Alg. 5), GCR per column (1, Alg. 4) or
         iterative refinement (2, Alg. 3); returns (rc, iterations, residual history)."""
         m = 1 if B_dev.dim() == 1 else B_dev.shape[1]
-        hist = np.zeros(maxit + 1)
+        B, X = _dev(B_dev, "B", self.L * m, rows=self.L), _dev(X_dev, "X", self.L * m, rows=self.L)
+        hist = np.zeros(max(int(maxit), 0) + 1)
         it = C.c_int(0)
-        rc = lib().hf_k11_iterate(self._h, int(method), m, _ptr(B_dev), _ptr(X_dev), int(maxit), _ptr(hist),
-                                  C.byref(it))
+        rc = lib().hf_k11_iterate(self._h, int(method), m, B, X, int(maxit), _ptr(hist), C.byref(it))
         _check(rc, "hf_k11_iterate", allow=(HF_ERR_NOT_CONVERGED,))
         return rc, it.value, hist[:it.value + 1].copy()
 
@@ -240,21 +264,25 @@ class HybridFactor:
         """G = scale * A^T B (Alg. 5's Gram products) on row-major L x ma / L x mb float64 CUDA tensors."""
         L, ma = A_dev.shape
         mb = B_dev.shape[1]
-        _check(lib().hf_gram_fp64(self._h, L, ma, mb, _ptr(A_dev), _ptr(B_dev), _ptr(G_dev), float(scale)),
-               "hf_gram_fp64")
+        A, B = _dev(A_dev, "A", L * ma, rows=L), _dev(B_dev, "B", L * mb, rows=L)
+        G = _dev(G_dev, "G", ma * mb)
+        _check(lib().hf_gram_fp64(self._h, L, ma, mb, A, B, G, float(scale)), "hf_gram_fp64")
 
     def update_fp64(self, A_dev, C_dev, Y_dev, Yinit_dev=None, sgn=1.0):
         """Y = (Yinit or Y) + sgn * A C (Alg. 5's block updates), row-major float64 CUDA tensors."""
         L, m = A_dev.shape
-        yi = _ptr(Yinit_dev) if Yinit_dev is not None else None
-        _check(lib().hf_update_fp64(self._h, L, m, _ptr(A_dev), _ptr(C_dev), _ptr(Y_dev), yi, float(sgn)),
-               "hf_update_fp64")
+        A, Cm = _dev(A_dev, "A", L * m, rows=L), _dev(C_dev, "C", m * m)
+        Y = _dev(Y_dev, "Y", L * m, rows=L)
+        yi = _dev(Yinit_dev, "Yinit", L * m, rows=L) if Yinit_dev is not None else None
+        _check(lib().hf_update_fp64(self._h, L, m, A, Cm, Y, yi, float(sgn)), "hf_update_fp64")
 
     def values_adjoint(self, x_dev, lam_dev, grad_dev):
         """grad[e] = -sum_r lam[row_e, r] x[col_e, r] (tensors (nrhs, L) contiguous = column-major L x nrhs)."""
         nrhs = 1 if x_dev.dim() == 1 else x_dev.shape[0]
-        _check(lib().hf_values_adjoint(self._h, nrhs, _ptr(x_dev), self.L, _ptr(lam_dev), self.L, _ptr(grad_dev)),
-               "hf_values_adjoint")
+        x = _dev(x_dev, "x", self.L * nrhs, cols=self.L)
+        lam = _dev(lam_dev, "lam", self.L * nrhs, cols=self.L)
+        g = _dev(grad_dev, "grad", self._col.shape[0])
+        _check(lib().hf_values_adjoint(self._h, nrhs, x, self.L, lam, self.L, g), "hf_values_adjoint")
 
     # -- getters -----------------------------------------------------------
     def info(self) -> dict:
@@ -281,7 +309,7 @@ class HybridFactor:
         nn = self.info()["n_nodes"]
         ptr = np.zeros(nn + 2, np.int64)
         piv = np.zeros(self.L, np.int32)
-        moved = np.zeros(64, np.int32)
+        moved = np.zeros(max(64, int(self.opts.n_enlarge)), np.int32)
         nm = C.c_int32()
         _check(lib().hf_get_pivots(self._h, _ptr(ptr), _ptr(piv), _ptr(moved), C.byref(nm)), "hf_get_pivots")
         per = [piv[ptr[t]:ptr[t + 1]].astype(np.int64) for t in range(nn + 1)]
@@ -356,9 +384,11 @@ def _batched_check(rc, st, where, allow=()):
 def factorize_batched(factors, vals_list, tau=1e-2):
     """hf_factorize on every (HybridFactor, CUDA values) pair, run concurrently."""
     n = len(factors)
+    if len(vals_list) != n:
+        raise ValueError("one values tensor per system")
+    vp = [_dev(v, f"vals[{i}]", f._col.shape[0]).value for i, (f, v) in enumerate(zip(factors, vals_list))]
     st = np.zeros(n, np.int32)
-    rc = lib().hf_factorize_batched(_ptrs([f._h.value for f in factors]), n,
-                                    _ptrs([v.data_ptr() for v in vals_list]), float(tau), _ptr(st))
+    rc = lib().hf_factorize_batched(_ptrs([f._h.value for f in factors]), n, _ptrs(vp), float(tau), _ptr(st))
     return _batched_check(rc, st, "hf_factorize_batched")
 
 
@@ -372,8 +402,12 @@ def schur_batched(factors):
 def solve_batched(factors, bs, xs):
     """bs[i], xs[i]: CUDA float64 tensors of shape (nrhs, L_i), the same nrhs for all."""
     n = len(factors)
+    if len(bs) != n or len(xs) != n:
+        raise ValueError("one right-hand side and one solution tensor per system")
     nrhs = 1 if bs[0].dim() == 1 else bs[0].shape[0]
+    bp = [_dev(b, f"bs[{i}]", f.L * nrhs, cols=f.L).value for i, (f, b) in enumerate(zip(factors, bs))]
+    xp = [_dev(x, f"xs[{i}]", f.L * nrhs, cols=f.L).value for i, (f, x) in enumerate(zip(factors, xs))]
     st = np.zeros(n, np.int32)
-    rc = lib().hf_solve_batched(_ptrs([f._h.value for f in factors]), n, nrhs, _ptrs([b.data_ptr() for b in bs]),
-                                None, _ptrs([x.data_ptr() for x in xs]), None, _ptr(st))
+    rc = lib().hf_solve_batched(_ptrs([f._h.value for f in factors]), n, nrhs, _ptrs(bp), None, _ptrs(xp), None,
+                                _ptr(st))
     return _batched_check(rc, st, "hf_solve_batched", allow=(HF_ERR_NOT_CONVERGED,))

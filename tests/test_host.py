@@ -187,3 +187,58 @@ def test_analysis_edge_cases():
         assert sorted(np.concatenate(sets).tolist()) == list(range(n))
         assert sum(1 for p in parent if p < 0) == 1
         H.free()
+
+
+class _FakeCuda:
+    """Stands in for a CUDA tensor in argument checks that must fail before any library call."""
+
+    def __init__(self, shape, dtype="torch.float64", contiguous=True, ptr=1 << 20):
+        self.shape, self.dtype, self._c, self._p, self.is_cuda = tuple(shape), dtype, contiguous, ptr, True
+
+    def data_ptr(self):
+        return self._p
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        return int(np.prod(self.shape))
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_binding_checks_device_operands():
+    # the C ABI cannot see a device buffer's size or type: the binding refuses what would make
+    # the library read or write past a tensor, before calling it
+    import torch
+    hf = _hf()
+    s = diffusion2d(6, 6, n_islands=0)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    nnz = s.col.shape[0]
+    with pytest.raises(TypeError, match="CUDA"):
+        H.factorize(torch.zeros(nnz, dtype=torch.float64))             # host tensor
+    with pytest.raises(TypeError, match="float64"):
+        H.factorize(_FakeCuda((nnz,), dtype="torch.float32"))
+    with pytest.raises(ValueError, match="contiguous"):
+        H.factorize(_FakeCuda((nnz,), contiguous=False))
+    with pytest.raises(ValueError, match="entries"):
+        H.factorize(_FakeCuda((nnz - 1,)))
+    b = _FakeCuda((2, s.L))
+    with pytest.raises(ValueError, match="shape"):
+        H.solve(_FakeCuda((2, s.L + 1)), b)
+    with pytest.raises(ValueError, match="alias"):
+        H.solve(b, b)
+    with pytest.raises(ValueError, match="entries|shape"):
+        H.precond(_FakeCuda((3, s.L)), _FakeCuda((3, s.L)))            # transposed layout
+    with pytest.raises(ValueError, match="shape"):
+        H.k11_iterate(0, _FakeCuda((s.L + 1, 2)), _FakeCuda((s.L + 1, 2)))
+    with pytest.raises(ValueError, match="entries"):
+        H.gram_fp64(_FakeCuda((s.L, 4)), _FakeCuda((s.L, 5)), _FakeCuda((19,)))
+    with pytest.raises(ValueError, match="entries"):
+        H.values_adjoint(_FakeCuda((s.L,)), _FakeCuda((s.L,)), _FakeCuda((nnz - 1,)))
+    with pytest.raises(ValueError, match="row signs"):
+        H.set_row_signs(np.ones(s.L - 1, dtype=np.int8))
+    with pytest.raises(ValueError, match="per system"):
+        hf.factorize_batched([H, H], [_FakeCuda((nnz,))])
+    H.free()
