@@ -79,6 +79,8 @@ PINS = {
     "lu_rank": pins.test_lu_complete_is_rank_revealing_and_pseudo_solves,
     "precond_unsym": pins.test_unsymmetric_precond_and_gcr,
     "solve_unsym": pins.test_unsymmetric_hybrid_solve,
+    "kernel_rule": pins.test_kernel_dimension_rule_hand_cases,
+    "tau_limits": pins.test_tau_limits,
 }
 
 # (id, text in the oracle, planted replacement, occurrence, pins that must fail)
@@ -174,6 +176,29 @@ MUTANTS = [
     ("lu_solve_row_perm", "    x[pcol] = w\n", "    x[prow] = w\n", 0, ["lu_rank"]),
     ("s22_dispatch_inverted", "    elif symmetric:\n", "    elif not symmetric:\n", 0,
      ["sign_form", "solve_unsym"]),
+    # more: pattern, masks, measures, rule constants, forward solves
+    ("pattern_row_for_col", "pairs = set(zip(owner[C.row].tolist(), owner[C.col].tolist()))",
+     "pairs = set(zip(owner[C.row].tolist(), owner[C.row].tolist()))", 0, ["nd_fig1"]),
+    ("k11_rows_not_masked", "    in1[lambda2] = False\n    D1 = sp.diags", "    D1 = sp.diags", 0, ["gcr_block"]),
+    ("kernel_noise_dropped", "thr = max(kernel_eps * scale, noise)", "thr = kernel_eps * scale", 0, ["kernel_rule"]),
+    ("kernel_ref_dropped", "scale = max(s[0], ref)", "scale = s[0]", 0, ["kernel_rule"]),
+    ("backward_error_one_norm", "nK = float(abs(Kbar).sum(axis=1).max())", "nK = float(abs(Kbar).sum(axis=0).max())", 0,
+     ["residual_measures"]),
+    ("precond_fwd_sign", "y[rows[keep]] -= np.outer(l[keep], y[p])", "y[rows[keep]] += np.outer(l[keep], y[p])", 0,
+     ["precond"]),
+    ("enlarge_one_short", "nmove = min(n_enlarge, len(order))", "nmove = min(n_enlarge - 1, len(order))", 0,
+     ["hand_postponing", "tau_limits"]),
+    ("lam0_first_node_only", "lam0 = np.concatenate(fac.node_postponed) if", "lam0 = np.concatenate(fac.node_postponed[:1]) if",
+     0, ["tau_limits"]),
+    ("bk_sigma_test", "if akk * sigma >= alpha * lam * lam:", "if akk * sigma >= alpha * lam:", 0, ["bk_reconstruct"]),
+    ("gcr_x_with_q", "x = x + alpha * p[n]", "x = x + alpha * q[n]", 0, ["gcr_alg4"]),
+    ("scale_no_abs", "q[nz] = 1.0 / np.sqrt(np.abs(d[nz]))", "q[nz] = 1.0 / np.sqrt(d[nz])", 0, ["scaling_closed_form"]),
+    ("solve_x2_unsolved", "    x[lambda2] = x2\n", "    x[lambda2] = y2\n", 0, ["solve_nonsingular"]),
+    ("lu_zero_largest", "zero = set(np.argsort(np.abs(np.diag(U)))[:kdim].tolist())",
+     "zero = set(np.argsort(np.abs(np.diag(U)))[::-1][:kdim].tolist())", 0, ["lu_rank"]),
+    ("pivot_mags_signed", "mags.append(abs(B[0, 0])); owners.append((b, 0))", "mags.append(B[0, 0]); owners.append((b, 0))",
+     0, ["bp_rank"]),
+    ("adjoint_sign", "            g[:, :-1] -= da * prod", "            g[:, :-1] += da * prod", 0, ["adjoint_fd"]),
     # adjoint
     ("adjoint_swapped_derivative", "db = 2 * kb * ka * ka / s", "db = 2 * ka * kb * kb / s", 0, ["adjoint_fd"]),
     ("adjoint_dirichlet_half", "g[:, 0] -= 2 * k[:, 0] * X[:, 0] * Lm[:, 0]",

@@ -429,6 +429,21 @@ def test_kernel_dimension_matches_svd(maker, expect):
 
 
 # --------------------------------------------------------------------------- Alg. 2 solve
+def test_kernel_dimension_rule_hand_cases():
+    # R10 on hand-made pivot magnitudes: the tail after the largest gap >= gap_min whose
+    # tail lies at or below max(kernel_eps * scale, noise), scale = max(max pivot, ref)
+    assert O.kernel_dimension([1.0, 0.5, 1e-13, 1e-14]) == 2                 # gap 5e12
+    assert O.kernel_dimension([1.0, 9e-11, 1e-22]) == 1                      # the larger of two gaps wins
+    assert O.kernel_dimension([1.0, 0.5, 1e-8, 1e-9]) == 0                   # nothing below 1e-10
+    assert O.kernel_dimension([1.0, 0.5, 1e-8, 1e-9], noise=1e-7) == 2       # the S22 error estimate
+    assert O.kernel_dimension([1.0, 0.5, 1e-8, 1e-9], noise=1e-7, gap_min=1e9) == 0
+    assert O.kernel_dimension([1e-12, 1e-13], ref=1.0) == 2                  # all null against the unit diagonal
+    assert O.kernel_dimension([1e-12, 1e-13]) == 0                           # relative to themselves: no gap
+    assert O.kernel_dimension([1e-12, 1e-25]) == 1
+    assert O.kernel_dimension([0.0, 0.0]) == 2 and O.kernel_dimension([]) == 0
+    assert O.kernel_dimension([3.0, 2.0, 1.0]) == 0
+
+
 def test_hybrid_solve_exact_on_nonsingular():
     s = diffusion2d(12, 12, n_islands=1, island=3, contrast=1e6, dirichlet_x=True, seed=2)
     Kb = s.to_scipy()
@@ -454,18 +469,19 @@ def test_hybrid_solve_singular_consistent():
 
 def test_residual_measures_closed_form():
     # |r|_2/|b|_2 and the normwise backward error |r|_inf / (|K|_inf |x|_inf + |b|_inf) on a
-    # 2x2 case worked by hand: K = [[2, -1], [-1, 3]], x = [1, 0], b = [2, -0.996]:
-    # r = K x - b = [0, -0.004], |K|_inf = 4, |x|_inf = 1, |b|_inf = 2.
-    Kb = sp.csr_matrix(np.array([[2.0, -1.0], [-1.0, 3.0]]))
+    # 2x2 case worked by hand: K = [[2, -1], [0.5, 3]], x = [1, 0], b = [2, 0.496]:
+    # r = K x - b = [0, 0.004], |K|_inf = max row sum 3.5 (the column sums are 2.5 and 4),
+    # |x|_inf = 1, |b|_inf = 2.
+    Kb = sp.csr_matrix(np.array([[2.0, -1.0], [0.5, 3.0]]))
     x = np.array([[1.0], [0.0]])
-    b = np.array([[2.0], [-0.996]])
-    assert abs(O.relative_residual(Kb, x, b) - 0.004 / math.hypot(2.0, 0.996)) < 1e-15
-    assert abs(O.backward_error(Kb, x, b) - 0.004 / (4.0 * 1.0 + 2.0)) < 1e-16
+    b = np.array([[2.0], [0.496]])
+    assert abs(O.relative_residual(Kb, x, b) - 0.004 / math.hypot(2.0, 0.496)) < 1e-15
+    assert abs(O.backward_error(Kb, x, b) - 0.004 / (3.5 * 1.0 + 2.0)) < 1e-16
     # scaling x and b together leaves the measure unchanged
     assert abs(O.backward_error(Kb, 10 * x, 10 * b) - O.backward_error(Kb, x, b)) < 1e-16
     # max over columns
     X2 = np.hstack([x, x])
-    B2 = np.hstack([b, np.array([[2.0], [-1.0]])])
+    B2 = np.hstack([b, np.array([[2.0], [0.5]])])
     assert O.backward_error(Kb, X2, B2) == O.backward_error(Kb, x, b)
 
 
