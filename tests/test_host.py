@@ -242,3 +242,46 @@ def test_binding_checks_device_operands():
     with pytest.raises(ValueError, match="per system"):
         hf.factorize_batched([H, H], [_FakeCuda((nnz,))])
     H.free()
+
+
+@pytest.mark.parametrize("maker", [lambda: stokes3d(32, seed=2),                         # the benchmark workload
+                                   lambda: elasticity3d(40, seed=3)],                     # elasticity 40^3
+                         ids=["stokes32", "elasticity40"])
+def test_host_analysis_full_size(maker):
+    # Sec. 2.2 at the full sizes: the sets partition the unknowns and every coupling of K
+    # joins a node to itself or to one of its ancestors (each set separates its subtrees)
+    hf = _hf()
+    s = maker()
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    parent, sets = H.tree()
+    info = H.info()
+    nn = len(sets)
+    assert nn == info["n_nodes"] == 2 ** info["levels"] - 1
+    owner = np.full(s.L, -1)
+    for t, v in enumerate(sets):
+        assert (owner[v] == -1).all()
+        owner[v] = t
+    assert (owner >= 0).all()
+    children = [[] for _ in range(nn)]
+    roots = [t for t in range(nn) if parent[t] < 0]
+    for t, p in enumerate(parent):
+        if p >= 0:
+            children[p].append(t)
+    assert len(roots) == 1
+    tin, tout, clock, stack = np.zeros(nn, np.int64), np.zeros(nn, np.int64), 0, [(roots[0], 0)]
+    while stack:                                               # Euler tour of the tree
+        t, state = stack.pop()
+        if state == 0:
+            tin[t] = clock
+            clock += 1
+            stack.append((t, 1))
+            stack.extend((c, 0) for c in children[t])
+        else:
+            tout[t] = clock
+    rows = np.repeat(np.arange(s.L), np.diff(s.rowptr))
+    a, b = owner[rows], owner[s.col]
+    anc = ((tin[a] <= tin[b]) & (tin[b] < tout[a])) | ((tin[b] <= tin[a]) & (tin[a] < tout[b]))
+    assert anc.all()
+    leaves = [t for t in range(nn) if not children[t]]
+    assert max(len(sets[t]) for t in leaves) <= 2 * H.opts.nd_leaf
+    H.free()
