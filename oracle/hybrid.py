@@ -276,6 +276,18 @@ def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_t
     return np.array(chosen, dtype=np.int64), postponed, np.array(skipped, dtype=np.int64)
 
 
+def _symmetric(K) -> bool:
+    """K = K^T up to rounding: max |K - K^T| <= 1e-14 max |K|.
+
+    An assembled or scaled matrix can differ from its transpose in the last bits
+    (element sums taken in another order, (q_i k_ij) q_j against (q_j k_ji) q_i); for
+    the method it is symmetric (LDL^T, Bunch-Parlett).  The row-sign form
+    [A B^T; -B delta D] differs by 2|B| and takes the LDU route (R15).
+    """
+    K = sp.csr_matrix(K)
+    return bool(abs(K - K.T).max() <= 1e-14 * abs(K).max())
+
+
 def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: int = 4,
                         replay: dict | None = None, slack: float = 1e-4, dtype=np.float32,
                         null_test: bool = True) -> FactorResult:
@@ -290,9 +302,7 @@ def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: in
     """
     L = K.shape[0]
     S = K.toarray().astype(dtype)                  # current Schur complement
-    # symmetric up to the rounding of the scaling, (q_i k_ij) q_j vs (q_j k_ji) q_i: LDL^T
-    Ks = sp.csr_matrix(K)
-    symmetric = (abs(Ks - Ks.T) > 1e-14 * abs(Ks)).nnz == 0
+    symmetric = _symmetric(K)
     G = np.abs(np.diag(S)).copy()                  # R3b magnitude of the terms in each diagonal
     remaining = np.ones(L, dtype=bool)
     fac = FactorResult([], [], None, None, None, None, None)
@@ -798,7 +808,7 @@ def run_hybrid(Kbar: sp.csr_matrix, nodes, tau, n_enlarge=4, replay=None, kernel
         X12, hist = x12_direct(K, fac.lambda2), None
     S22 = schur_direct(K, fac.lambda2, X12)
     noise = s22_noise(K, fac, X12) if (use_gcr and fac.M) else 0.0
-    symmetric = abs(Kbar - Kbar.T).max() == 0          # exact test on the user's matrix
+    symmetric = _symmetric(Kbar)
     if not fac.M:
         bk, mags = (np.zeros(0, int), np.zeros((0, 0)), []), np.zeros(0)
     elif symmetric:
