@@ -285,3 +285,23 @@ def test_host_analysis_full_size(maker):
     leaves = [t for t in range(nn) if not children[t]]
     assert max(len(sets[t]) for t in leaves) <= 2 * H.opts.nd_leaf
     H.free()
+
+
+def test_device_entries_fail_cleanly_without_a_gpu():
+    # on a machine without a GPU the host-only analysis works and every call that needs the
+    # device returns an error code (no crash, no CPU fallback)
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    hf = _hf()
+    s = diffusion2d(6, 6, n_islands=0)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    with pytest.raises(hf.HFError) as e:
+        H.set_row_signs(np.ones(s.L, dtype=np.int8))
+    assert e.value.code in (7, 8)                               # HF_ERR_CUDA / HF_ERR_OOM
+    for call in (H.schur, H.split, H.pivots):
+        with pytest.raises(hf.HFError) as e:
+            call()
+        assert e.value.code == 2                                # HF_ERR_STATE: nothing factorized
+    assert H.info()["L"] == s.L
+    H.free()
