@@ -420,15 +420,15 @@ def measured_traffic(kernel):
     the SHA-256 of that source at capture time; None when there is none or the source
     changed since (the counters then describe another kernel).
 
-    The hash covers the whole file, or with `source_until: <line>` the part of the file
-    before that line (the kernel, its helpers and its launches, when host code that
+    The hash covers the whole file, or with `source_from: <line>` / `source_until: <line>`
+    the part of the file from the first line and before the second (the kernel, its helpers and its launches, when host code that
     cannot reach the kernel follows); `headers: a, b@line` with `headers_sha256` adds the
     concatenated headers the kernel is compiled with, `@line` cutting one before that
     line (where only host-side declarations follow)."""
     import glob
     import hashlib
-    keys = ("kernel:", "source:", "source_until:", "source_sha256:", "headers:", "headers_sha256:",
-            "dram_bytes_per_launch:")
+    keys = ("kernel:", "source:", "source_from:", "source_until:", "source_sha256:", "headers:",
+            "headers_sha256:", "dram_bytes_per_launch:")
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         fields = {}
         with open(path) as f:
@@ -441,6 +441,11 @@ def measured_traffic(kernel):
         try:
             with open(os.path.join(ROOT, fields["source"]), "rb") as f:
                 src = f.read()
+            if "source_from" in fields:
+                at = src.find(fields["source_from"].encode())
+                if at < 0:
+                    return None
+                src = src[at:]
             if "source_until" in fields:
                 at = src.find(fields["source_until"].encode())
                 if at < 0:
