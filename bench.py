@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the hybrid factorization (Alg. 1) on GB300.
 
-Workload: the 3D Stokes-like saddle point, 32^3 velocity nodes plus cell
-pressures (L = 128,095), per-cell viscosity 10^U(-3,3), zero pressure block,
-tau = 1e-2, seeded synthetic values.  One step = one pass of the whole path:
-hf_factorize (scaling, FP32 factorization with postponing, Lambda_0 stage) +
-hf_schur (block GCR for X12, S22, dense LDL^T) + hf_solve (Alg. 2, one rhs).
-The metric is the factor + Schur time; the plain FP64 GPU form (S22 from an
-FP64 factorization) is timed beside it.
+Workload (default): 3D Q1 linear elasticity on a 40^3 node grid (L = 192,000, 3 dofs
+per node), Young's modulus 1 with 8 seeded 4^3-element inclusions of modulus 1e6,
+nu = 0.3, traction free (6 rigid-body modes), tau = 1e-2, the postponing rule of
+Sec. 2.2 (ratio test alone), seeded synthetic values.  One step = one pass of the
+whole path: hf_factorize (scaling, FP32 factorization with postponing, Lambda_0
+stage) + hf_schur (block GCR for X12, S22, dense LDL^T) + hf_solve (Alg. 2, one rhs).
+The metric is the factor + Schur time; the plain FP64 GPU form (S22 from an FP64
+factorization) and the FP32-only form are timed beside it over the same steps, and
+the thresholds tau = 1e-1 and 1e-4 are reported too.  --workload stokes32 runs the
+3D Stokes-like saddle point (32^3 nodes, L = 128,095) with the null-pivot test.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: one independent system per rank (the path does not shard).
@@ -29,8 +32,19 @@ if ROOT not in sys.path:
 
 METRIC = "hybrid_factor_schur_time"
 UNIT = "ms"
-CONFIG_NAME = "stokes3d_32^3_mu1e-3..1e3_tau1e-2"
-SAMPLE_N = 10          # oracle sample: the same generator at 10^3 nodes
+# workload -> (generator call, tau, null-pivot test, name).  The Stokes-like saddle point
+# needs the null-pivot test at tau = 1e-2: with the ratio test alone FP32 noise pivots of
+# its singular zero block pass the test at 32^3 and stay in K11.
+WORKLOADS = {
+    "elasticity40": ("elasticity3d(40, seed=3)", 1e-2, 0, "elasticity3d_40^3_E1e6_incl8_tau1e-2"),
+    "stokes32": ("stokes3d(32, seed=2)", 1e-2, 1, "stokes3d_32^3_mu1e-3..1e3_tau1e-2_nulltest"),
+}
+# oracle samples of the same generator (and rule): fit sizes, and the reference arm's step
+SAMPLES = {
+    "elasticity40": {"fit": (10, 12, 14), "step": 10,
+                     "make": lambda n: f"elasticity3d({n}, seed=3, n_incl={n // 3}, incl={2 if n < 14 else 3})"},
+    "stokes32": {"fit": (8, 10, 12), "step": 10, "make": lambda n: f"stokes3d({n}, seed=2)"},
+}
 
 
 def _args():
@@ -39,8 +53,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=32, help="nodes per axis of the Stokes-like grid")
+    ap.add_argument("--workload", default="elasticity40", choices=sorted(WORKLOADS))
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other thresholds and forms")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-print", action="store_true")
     return ap.parse_args()
@@ -103,21 +118,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- CPU oracle leg
-def _oracle_sample_time(n, threads=1):
-    """Time the CPU oracle (Alg. 1 with block GCR) on the n^3 Stokes-like sample, in a child process."""
+def _oracle_sample_time(workload, n, threads=1):
+    """Time the CPU oracle (Alg. 1 with block GCR) on the n^3 sample of the workload's
+    generator, in a child process with `threads` BLAS threads."""
+    _, tau, null_test, _ = WORKLOADS[workload]
+    make = SAMPLES[workload]["make"](n)
     code = f"""
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 import oracle as O
-from workloads import stokes3d
-s = stokes3d({n}, seed=2)
+from workloads import stokes3d, elasticity3d
+s = {make}
 Kb = s.to_scipy()
 q, K = O.scale_matrix(Kb)
 m = max(1, int(np.ceil(np.log2(s.L / 512))) + 1)
 sets, order = O.nested_dissection(K, s.coords, m)
 t = time.perf_counter()
-r = O.run_hybrid(Kb, [sets[l] for l in order], 1e-2, use_gcr=True)
+r = O.run_hybrid(Kb, [sets[l] for l in order], {tau!r}, use_gcr=True, null_test={bool(null_test)!r})
 el = time.perf_counter() - t
 print(json.dumps(dict(seconds=el, L=s.L, M=int(r['fac'].M), kdim=int(r['kdim']))))
 """
@@ -130,44 +148,211 @@ print(json.dumps(dict(seconds=el, L=s.L, M=int(r['fac'].M), kdim=int(r['kdim']))
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def _extrapolate(seconds, L_sample, L_full):
-    # 3D nested dissection: work grows as L^2 (George 1973, the ordering of Sec. 2.2)
-    return seconds * (L_full / L_sample) ** 2
+def fit_exponent(samples):
+    """Least-squares slope p of log(seconds) against log(L) over the oracle samples
+    [(L, seconds), ...]: the oracle's time grows as L^p over the sampled range."""
+    xs = [math.log(L) for L, _ in samples]
+    ys = [math.log(t) for _, t in samples]
+    mx, my = sum(xs) / len(xs), sum(ys) / len(ys)
+    sxx = sum((x - mx) ** 2 for x in xs)
+    return sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sxx if sxx > 0 else 2.0
+
+
+def extrapolate(seconds, L_sample, L_full, p):
+    return seconds * (L_full / L_sample) ** p
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def full_size_L(workload):
+    return {"elasticity40": 3 * 40 ** 3, "stokes32": 3 * 32 ** 3 + 31 ** 3}[workload]
 
 
 def run_reference(args):
+    """The CPU oracle as it stands, on the host cores: the warm-up steps time it on the
+    three fit sizes (the exponent of its growth), the timed steps on the step sample; the
+    value is the step sample's mean time carried to the full workload by that exponent."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from workloads import stokes3d
-    L_full = stokes3d(args.n, seed=2).L if args.n <= 12 else 3 * args.n ** 3 + (args.n - 1) ** 3
+    wl = args.workload
+    smp = SAMPLES[wl]
+    fit = []
+    for i in range(max(args.warmup, len(smp["fit"]))):
+        n = smp["fit"][i] if i < len(smp["fit"]) else smp["step"]
+        r = _oracle_sample_time(wl, n)
+        if i < len(smp["fit"]):
+            fit.append((r["L"], r["seconds"]))
+    p = fit_exponent(fit)
     times = []
-    for i in range(args.warmup + args.steps):
-        r = _oracle_sample_time(SAMPLE_N)
-        if i >= args.warmup:
-            times.append(r["seconds"])
+    for _ in range(args.steps):
+        r = _oracle_sample_time(wl, smp["step"])
+        times.append(r["seconds"])
     t = sum(times) / len(times)
-    val = _extrapolate(t, r["L"], L_full) * 1e3
+    L_full = full_size_L(wl)
+    val = extrapolate(t, r["L"], L_full, p) * 1e3
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": val, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": CONFIG_NAME, "L": L_full},
+        "config": {"workload": WORKLOADS[wl][3], "L": L_full},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"stokes3d {SAMPLE_N}^3 (L={r['L']}), {t:.2f} s per run, "
-                                   f"extrapolated by (L/L_sample)^2"},
+                         "sample": f"{smp['make'](smp['step'])} (L={r['L']}): {t:.2f} s per run on 1 core "
+                                   f"({args.steps} runs), carried to L={L_full} by L^{p:.2f}, the exponent "
+                                   f"fitted to the oracle's times at n = {smp['fit']} "
+                                   f"({', '.join(f'L={a}: {b:.2f} s' for a, b in fit)})",
+                         "measured": {"L": r["L"], "seconds_per_run": t, "fit": fit, "exponent": p},
+                         "cpu": cpu_model()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def cpu_baseline_leg(workload):
+    """The oracle timed on the host: one core on the three fit sizes (the growth exponent)
+    and once with every core on the middle size; carried to the full workload."""
+    smp = SAMPLES[workload]
+    fit = [(r["L"], r["seconds"]) for r in (_oracle_sample_time(workload, n) for n in smp["fit"])]
+    p = fit_exponent(fit)
+    L_full = full_size_L(workload)
+    L_big, t_big = fit[-1]
+    ncores = os.cpu_count() or 1
+    mid = _oracle_sample_time(workload, smp["fit"][1], threads=ncores)
+    return {"value": extrapolate(t_big, L_big, L_full, p) * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle on {', '.join(smp['make'](n) for n in smp['fit'])} on 1 core "
+                      f"({', '.join(f'L={a}: {b:.2f} s' for a, b in fit)}); value = the largest sample "
+                      f"carried to L={L_full} by the fitted L^{p:.2f}",
+            "measured": {"fit": fit, "exponent": p,
+                         "all_cores": {"cores": ncores, "L": mid["L"], "seconds": mid["seconds"],
+                                       "value_ms": extrapolate(mid["seconds"], mid["L"], L_full, p) * 1e3}},
+            "cpu": cpu_model()}
+
+
 # ---------------------------------------------------------------------------- GPU arm
+def make_system(workload):
+    from workloads import stokes3d, elasticity3d
+    return eval(WORKLOADS[workload][0], {"__builtins__": {}, "stokes3d": stokes3d, "elasticity3d": elasticity3d})
+
+
+def backward_error(Kb, x, b):
+    import numpy as np
+    r = Kb @ x - b
+    return float(np.abs(r).max() / (abs(Kb).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max()))
+
+
+def time_steps(H, vals, tau, bt, xt, steps, warmup, solve=True):
+    """W untimed then K timed steps of factorize + schur (+ solve); per-step device times
+    (CUDA events on the current stream, which is the library's stream) of each phase."""
+    import torch
+    for _ in range(warmup):
+        H.factorize(vals, tau)
+        H.schur()
+        if solve:
+            H.solve(bt, xt)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for e in evs:
+        e[0].record()
+        H.factorize(vals, tau)
+        e[1].record()
+        H.schur()
+        e[2].record()
+        if solve:
+            H.solve(bt, xt)
+        e[3].record()
+    torch.cuda.synchronize()
+    fac = [e[0].elapsed_time(e[1]) for e in evs]
+    sch = [e[1].elapsed_time(e[2]) for e in evs]
+    sol = [e[2].elapsed_time(e[3]) for e in evs]
+    tot = evs[0][0].elapsed_time(evs[-1][3])
+    return fac, sch, sol, tot
+
+
+def form_line(hf, s, vals, bt, b, tau, steps, warmup, **opts):
+    """Another form or threshold on the same system, timed over the given steps."""
+    import torch
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, **opts)
+    xt = torch.zeros_like(bt)
+    fac, sch, _, _ = time_steps(H, vals, tau, bt, xt, steps, warmup, solve=False)
+    H.solve(bt, xt)
+    torch.cuda.synchronize()
+    info = H.info()
+    be = backward_error(s.to_scipy(), xt.cpu().numpy().T, b)
+    out = {"factor_schur_ms": (sum(fac) + sum(sch)) / steps, "steps": steps, "warmup": warmup,
+           "M": info["M"], "kernel_dim": info["kernel_dim"], "gcr_iters": info["gcr_iters"],
+           "backward_error": be, "gate_1e-12": bool(be <= 1e-12)}
+    H.free()
+    torch.cuda.empty_cache()
+    return out
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        src = "of measured (MEASURED_PEAKS.json)"
+    except Exception:
+        p, src = {}, "of fallback (profiling recipe)"
+    return {"hbm": p.get("hbm_gbs", 6800.0), "bf16": p.get("bf16_tflops_sustained", 1700.0),
+            "fp32_simt": 152 * 128 * 2 * 2.07e9 / 1e12, "src": src}
+
+
+def kernel_rooflines(prof, steps, trailing_tc):
+    """Per kernel: its device time per step, the algorithmic work the library counted for
+    exactly those launches, and the fraction of the roof that binds it.  Each profile class
+    is one kernel (the glue launches around them have classes of their own); the two block
+    GCR products are one kernel, k_oz_mma, and are merged."""
+    pk = peaks()
+    simt = ("alu", pk["fp32_simt"], "TFLOP/s", "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz")
+    hbm = ("hbm", pk["hbm"], "GB/s", "hbm_gbs " + pk["src"])
+    bf16 = ("tensor", pk["bf16"], "TFLOP/s", "bf16_tflops_sustained " + pk["src"])
+    table = {
+        "panel": ("k_panel_cl", "pivoted left-looking panel in cluster shared memory (latency chain)", simt, 1.0),
+        "trailing": ("k_trailing_tc" if trailing_tc else "k_trailing",
+                     "trailing Schur update" + (" (exact 3 x BF16 split of FP32, 6 products on tcgen05; "
+                                                "levels of fronts < 256 rows on the FP32 SIMT kernel)"
+                                                if trailing_tc else " (FP32 SIMT)"),
+                     bf16 if trailing_tc else simt, 6.0 if trailing_tc else 1.0),
+        "trsv_fwd": ("k_sweep_df<1>", "dataflow forward sweep of a tree level (FP32 factor streamed)", hbm, 1.0),
+        "trsv_bwd": ("k_sweep_df<0>", "dataflow backward sweep of a tree level (FP32 factor streamed)", hbm, 1.0),
+        "spmm": ("k_spmm", "FP64 CSR x block", hbm, 1.0),
+        "oz": ("k_oz_mma", "FP64-accurate Grams and block updates: 36 BF16 slice products", bf16, 36.0),
+    }
+    merged = dict(prof)
+    g, u = prof.get("gram", (0, 0, 0, 0)), prof.get("block_update", (0, 0, 0, 0))
+    merged["oz"] = tuple(a + b for a, b in zip(g, u))
+    out = {}
+    for cls, (kname, what, (bound, peak, unit, psrc), mult) in table.items():
+        ms, n, flops, nbytes = merged.get(cls, (0.0, 0, 0.0, 0.0))
+        if ms <= 0 or n == 0:
+            continue
+        if bound == "hbm":
+            achieved = nbytes / (ms / 1e3) / 1e9
+        else:
+            achieved = mult * flops / (ms / 1e3) / 1e12
+        out[kname] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                      "traffic": measured_traffic(kname), "kernel": kname, "what": what, "peak_source": psrc,
+                      "ms_per_step": ms / steps, "launches_per_step": n / steps,
+                      "algorithmic_per_launch": (nbytes if bound == "hbm" else mult * flops) / n,
+                      "algorithmic_unit": "bytes" if bound == "hbm" else "flops"}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import paper_2208_01907_gb300 as hf
-    import scipy.sparse as sp
-    from workloads import stokes3d, consistent_rhs
+    from workloads import consistent_rhs
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -184,58 +369,34 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    s = stokes3d(args.n, seed=2)
-    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    wl = args.workload
+    _, tau, null_test, cfg_name = WORKLOADS[wl]
+    s = make_system(wl)
+    Kb = s.to_scipy()
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, null_test=null_test)
     vals = torch.tensor(s.val, device=dev, dtype=torch.float64)
     b = consistent_rhs(s, 11, 1, "solution")
     bt = torch.tensor(np.ascontiguousarray(b.T), device=dev)
     xt = torch.zeros_like(bt)
-
-    def step(ev=None):
-        if ev:
-            ev[0].record()
-        H.factorize(vals, 1e-2)
-        if ev:
-            ev[1].record()
-        H.schur()
-        if ev:
-            ev[2].record()
-        H.solve(bt, xt)
-        if ev:
-            ev[3].record()
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    info = H.info()
-    H.profile(False)                    # counters reset; launches are counted, no events
+    warm = max(3, args.warmup)
+    time_steps(H, vals, tau, bt, xt, 1, warm - 1)          # warm-up (delay capacities settle)
+    H.profile(False)                                       # counters reset; launches counted, no events
+    H.get_profile()
     clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for k in range(args.steps):
-        step(evs[k])
-    t1.record()
-    torch.cuda.synchronize()
+    fac, sch, sol, total_ms = time_steps(H, vals, tau, bt, xt, args.steps, 0)
     barrier()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
     launches = sum(v[1] for v in H.get_profile().values())        # launches in the timed steps
-    # per-class device times from one more step with the library's event profiling on
-    # (kept out of the timed steps: two event records per launch slow the host enqueue)
+    # per-kernel device times from more steps with the library's event profiling on (kept out
+    # of the timed steps: two event records per launch slow the host enqueue)
+    prof_steps = min(3, args.steps)
     H.profile(True)
-    step()
-    torch.cuda.synchronize()
+    time_steps(H, vals, tau, bt, xt, prof_steps, 0)
     prof = H.get_profile()
     H.profile(False)
-    prof_steps = 1
-    fac = [e[0].elapsed_time(e[1]) for e in evs]
-    sch = [e[1].elapsed_time(e[2]) for e in evs]
-    sol = [e[2].elapsed_time(e[3]) for e in evs]
     fs_ms = (sum(fac) + sum(sch)) / args.steps
     step_ms = total_ms / args.steps
     if dist is not None:
@@ -243,155 +404,94 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         fs_ms, step_ms = float(tt[0]), float(tt[1])
     info = H.info()
-
-    # accuracy gate of the timed configuration
     x = xt.cpu().numpy().T
-    Kb = s.to_scipy()
-    r = Kb @ x - b
-    bwd = float(np.abs(r).max() / (abs(Kb).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max()))
-    relres = float(np.linalg.norm(r) / np.linalg.norm(b))
+    bwd = backward_error(Kb, x, b)
+    relres = float(np.linalg.norm(Kb @ x - b) / np.linalg.norm(b))
 
-    # roofline of the dominant kernel class (device time from the events of the timed region,
-    # algorithmic work counted by the library for exactly those launches)
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_n, dom_flops, dom_bytes = prof[dom]
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    fp32_simt = 152 * 128 * 2 * 2.07e9 / 1e12          # derived: SMs x FP32 lanes x FMA x max clock
-    fp64_peak = 1.25                                    # nominal GB300 FP64 (profiling recipe table)
-    bf16_sus = peaks.get("bf16_tflops_sustained", 1700.0)
-    kinds = {
-        "panel": ("alu", fp32_simt, "k_panel_cl (pivoted left-looking panel, cluster/DSMEM resident)",
-                  "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "trailing": ("alu", fp32_simt, "k_trailing (FP32 SIMT rank-nb Schur update)",
-                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "gram": ("tensor", bf16_sus, "k_oz_mma (FP64 Gram Q^T Z emulated: 36 BF16 slice products)",
-                 "MEASURED_PEAKS.json bf16_tflops_sustained"),
-        "block_update": ("tensor", bf16_sus, "k_oz_mma (FP64 update P C emulated: 36 BF16 slice products)",
-                         "MEASURED_PEAKS.json bf16_tflops_sustained"),
-        # with M ~ 400 right-hand sides the sweeps do 2 M flops per factor entry read: FP32 ALU-bound
-        "trsv_fwd": ("alu", fp32_simt, "k_sweep_df<1> (dataflow forward sweep of a tree level, FP32)",
-                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "trsv_bwd": ("alu", fp32_simt, "k_sweep_df<0> (dataflow backward sweep of a tree level, FP32)",
-                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"),
-        "spmm": ("hbm", hbm, "k_spmm (FP64 CSR x block)", "MEASURED_PEAKS.json hbm_gbs"),
-    }
-    bound, peak, kname, psrc = kinds.get(dom, ("alu", None, dom, None))
-    if dom in ("gram", "block_update") and not info.get("fp64_native", False):
-        dom_flops = 36.0 * dom_flops      # tensor work: 36 slice products per FP64 multiply-add
-    if bound == "hbm":
-        achieved = dom_bytes / (dom_ms / 1e3) / 1e9
-        unit = "GB/s"
-    else:
-        achieved = dom_flops / (dom_ms / 1e3) / 1e12 if dom_flops else None
-        unit = "TFLOP/s"
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if (achieved and peak) else None,
-            "traffic": measured_traffic(kname.split(" ")[0]),
-            "kernel": kname, "peak_source": psrc, "launches_per_step": dom_n / prof_steps,
-            "ms_per_step": dom_ms / prof_steps}
+    trailing_tc = H.opts.trailing == 0
+    roofs = kernel_rooflines(prof, prof_steps, trailing_tc)
+    dom = max(roofs.values(), key=lambda r: r["ms_per_step"]) if roofs else None
 
     # end to end through the C ABI with host buffers: H2D of the values, D2H of S22
     hv = torch.tensor(s.val, dtype=torch.float64).pin_memory()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     dvals = torch.empty_like(vals)
     M = info["M"]
     hs22 = torch.empty((max(M, 1), max(M, 1)), dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         dvals.copy_(hv, non_blocking=True)
-        H.factorize(dvals, 1e-2)
+        H.factorize(dvals, tau)
         H.schur()
         hs22[:M, :M].copy_(H.s22(torch), non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    H.free()
+    torch.cuda.empty_cache()
 
-    # plain FP64 GPU form (Table 1 "double"): factor in FP64, S22 from the factor
-    fp64 = fp32 = None
+    # the forms of Table 1 beside the hybrid one, over the same warm-up and timed steps:
+    # plain FP64 (factor in FP64, S22 from the factor) and FP32 only ("single")
+    forms = {}
     if not args.no_fp64:
-        H64 = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, precision=hf.HF_PREC_FP64)
-        H64.factorize(vals, 1e-2)
-        H64.schur()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        c_ = torch.cuda.Event(enable_timing=True)
-        a.record()
-        H64.factorize(vals, 1e-2)
-        H64.schur()
-        c_.record()
-        torch.cuda.synchronize()
-        x64 = torch.zeros_like(bt)
-        H64.solve(bt, x64)
-        xx = x64.cpu().numpy().T
-        rr = Kb @ xx - b
-        fp64 = {"factor_schur_ms": a.elapsed_time(c_),
-                "backward_error": float(np.abs(rr).max() / (abs(Kb).sum(axis=1).max() * np.abs(xx).max() + np.abs(b).max())),
-                "M": H64.info()["M"], "kernel_dim": H64.info()["kernel_dim"]}
-        fp64["speedup_mixed_vs_fp64"] = fp64["factor_schur_ms"] / fs_ms
-        H64.free()
-        # FP32-only form (Table 1 "single"): factor and S22 in FP32, no iteration; its
-        # backward error shows why the hybrid form iterates in FP64
-        H32 = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, precision=hf.HF_PREC_FP32)
-        H32.factorize(vals, 1e-2)
-        H32.schur()
-        torch.cuda.synchronize()
-        a.record()
-        H32.factorize(vals, 1e-2)
-        H32.schur()
-        c_.record()
-        torch.cuda.synchronize()
-        x32 = torch.zeros_like(bt)
-        H32.solve(bt, x32)
-        xx = x32.cpu().numpy().T
-        rr = Kb @ xx - b
-        be32 = float(np.abs(rr).max() / (abs(Kb).sum(axis=1).max() * np.abs(xx).max() + np.abs(b).max()))
-        fp32 = {"factor_schur_ms": a.elapsed_time(c_), "backward_error": be32, "gate_1e-12": bool(be32 <= 1e-12)}
-        H32.free()
+        forms["fp64_form"] = form_line(hf, s, vals, bt, b, tau, args.steps, warm, precision=hf.HF_PREC_FP64,
+                                       null_test=null_test)
+        forms["fp64_form"]["speedup_mixed_vs_fp64"] = forms["fp64_form"]["factor_schur_ms"] / fs_ms
+        forms["fp32_form"] = form_line(hf, s, vals, bt, b, tau, args.steps, warm, precision=hf.HF_PREC_FP32,
+                                       null_test=null_test)
+    extra = {}
+    if not args.no_extra:
+        ks, kw = min(args.steps, 5), 3
+        other = 1 if trailing_tc else 0
+        extra[f"trailing={'simt' if other else 'tensor_cores'}"] = form_line(
+            hf, s, vals, bt, b, tau, ks, kw, null_test=null_test, trailing=other)
+        for t2 in (1e-1, 1e-4):
+            extra[f"tau={t2:g}"] = form_line(hf, s, vals, bt, b, t2, ks, kw, null_test=null_test)
+        if not null_test:
+            extra["tau=1e-4_nulltest"] = form_line(hf, s, vals, bt, b, 1e-4, ks, kw, null_test=1)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
-            rs = _oracle_sample_time(12)
-            cpu_ms = _extrapolate(rs["seconds"], rs["L"], s.L) * 1e3
-            cpu = {"value": cpu_ms, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"stokes3d 12^3 (L={rs['L']}) factor+Schur by the CPU oracle in "
-                             f"{rs['seconds']:.1f} s on 1 core, extrapolated by (L/L_sample)^2"}
+            cpu = cpu_baseline_leg(wl)
         except Exception as e:  # noqa: BLE001
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
 
     if rank == 0:
-        factor_bytes = info["nnz_factor"] * 4
+        roof = None
+        if dom is not None:
+            roof = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+            roof.update({k: dom[k] for k in ("kernel", "what", "peak_source", "ms_per_step", "launches_per_step",
+                                             "algorithmic_per_launch", "algorithmic_unit")})
         line = {
             "metric": METRIC, "value": fs_ms, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": False,
+            "warmup": warm, "ms_per_step": step_ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": CONFIG_NAME, "L": s.L, "nnz": s.nnz, "M": info["M"],
-                       "n_lambda0": info["n_lambda0"], "kernel_dim": info["kernel_dim"],
+            "config": {"workload": cfg_name, "L": s.L, "nnz": s.nnz, "tau": tau,
+                       "postponing": "ratio test + null-pivot test" if null_test else "ratio test (Sec. 2.2)",
+                       "M": info["M"], "n_lambda0": info["n_lambda0"], "kernel_dim": info["kernel_dim"],
                        "gcr_iters": info["gcr_iters"], "levels": info["levels"],
                        "l2": "working set (factor arena %.1f GB) larger than L2" % (info["front_bytes"] / 1e9),
                        "parallelism": f"replicas x{world}"},
             "phases_ms": {"factorize": sum(fac) / args.steps, "schur": sum(sch) / args.steps,
                           "solve": sum(sol) / args.steps},
-            "factor_GBps": factor_bytes / (sum(fac) / args.steps / 1e3) / 1e9,
             "systems_per_s": world * 1e3 / step_ms,
             "rel_residual": relres, "backward_error": bwd, "gate_1e-12": bwd <= 1e-12,
             "roofline": roof,
+            "kernels": {k: {kk: (round(v, 4) if isinstance(v, float) else v) for kk, v in r.items()
+                            if kk in ("ms_per_step", "achieved", "unit", "frac", "bound")}
+                        for k, r in roofs.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": s.nnz * 8,
                     "d2h_bytes_per_step": M * M * 8},
-            "fp64_form": fp64,
-            "fp32_form": fp32,
+            **forms,
+            "other_forms": extra,
             "gpu_launches": launches,
             "kernel_ms": {k: round(v[0] / prof_steps, 3) for k, v in prof.items()},
             "kernel_work": kernel_work(prof, prof_steps),
+            "paths": {k: info[k] for k in ("panel_cluster", "panel_global", "sweep_blocks", "ldlt_kernel")},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -79,10 +79,20 @@ typedef struct {
   int    fp64_gemm;      /* FP64 Grams and block updates of block GCR: 0 = emulated on the BF16
                             tensor cores with exact slice products (FP64 accuracy), 1 = FP64
                             units; default 0 */
-  int    trailing;       /* trailing updates of the FP32 factor: 0 = tensor cores with the exact
-                            3 x BF16 split of FP32 (six products, FP32 accumulate per product
-                            order), 1 = FP32 SIMT; default 1 (faster here: the rank-64 update
-                            is memory-bound); the FP64 form always uses FP64 SIMT */
+  int    trailing;       /* trailing updates of the FP32 factor: 0 = tensor cores for the tree
+                            levels whose largest front has >= 256 rows (exact 3 x BF16 split of
+                            FP32, six products, FP32 accumulation in TMEM; FP32 SIMT for the
+                            smaller levels), 1 = FP32 SIMT everywhere; default 0; the FP64 form
+                            always uses FP64 SIMT */
+  int    null_test;      /* 0 = postpone on the ratio test of Sec. 2.2 alone (the paper's rule);
+                            1 = also postpone a candidate on its own when its diagonal is below
+                            tau times the magnitude of the terms it was formed from (|K_ii| plus
+                            the accumulated |l_ik|^2 |d_k|), a cancellation test that is not in the
+                            paper; default 0 */
+  int    spin_limit;     /* polls of a bounded device wait of the triangular sweeps (a block waiting
+                            for a diagonal block another block solves) before the wait gives up and
+                            the call returns HF_ERR_TIMEOUT; 0 = the built-in limit (2^22 polls with
+                            sleeps, seconds); default 0 */
 } hf_opts;
 
 typedef struct {
@@ -106,17 +116,38 @@ typedef struct {
                              sum over panels of 2 x width x (lower-triangle entries updated) */
   int64_t solve_factor_entries; /* factor entries one forward (or backward) sweep of the K11
                              solve reads */
+  /* which code paths the last calls took (for tests and profiles): */
+  int32_t panel_cluster;  /* largest thread-block cluster of the pivoted panel (CTAs per front) */
+  int32_t panel_global;   /* tree levels whose largest front ran the global-memory panel */
+  int32_t sweep_blocks;   /* largest number of 64-row diagonal blocks of one front in the sweeps */
+  int32_t ldlt_kernel;    /* S22 LDL^T of the last hf_schur: 0 none (M = 0), 1 one cluster with S22
+                             in distributed shared memory, 2 cooperative grid, 3 one block */
 } hf_info;
 
 /* Kernel classes of the profile (hf_get_profile). */
 enum {
   HF_PROF_SCALE = 0, HF_PROF_ASSEMBLE, HF_PROF_PANEL, HF_PROF_TRAILING, HF_PROF_LAMBDA,
   HF_PROF_TRSV_FWD, HF_PROF_TRSV_BWD, HF_PROF_SPMM, HF_PROF_GRAM, HF_PROF_BLOCK_UPDATE,
-  HF_PROF_SCHUR, HF_PROF_DENSE_LDLT, HF_PROF_VECTOR, HF_NPROF
+  HF_PROF_SCHUR, HF_PROF_DENSE_LDLT, HF_PROF_VECTOR,
+  /* the launches around the classes above, kept apart so that each class above is one kernel:
+     panel_swap = the row interchanges applied after a level's panels, sweep_io = gathers and
+     scatters of the solve vectors around each sweep level, tc_prep = operand preparation of
+     the tensor-core products (exponents, slices and split-K reductions of the emulated FP64
+     products; the BF16 split of the panel for the tensor-core trailing update) */
+  HF_PROF_PANEL_SWAP, HF_PROF_SWEEP_IO, HF_PROF_TC_PREP, HF_NPROF
 };
 
 /* Fill *opts with the defaults listed above.  Returns HF_ERR_ARG if opts is NULL. */
 int hf_default_opts(hf_opts* opts);
+
+/*
+ * Changes opts.spin_limit of an existing context (the other options are fixed at
+ * hf_analyze).  limit >= 0; 0 restores the built-in limit.  Takes effect at the next call
+ * that runs a triangular sweep.  A wait that gave up voids the solves of the current
+ * factor (HF_ERR_TIMEOUT from every later solve) until the next hf_factorize.
+ * Errors: HF_ERR_ARG (null ctx, negative limit).
+ */
+int hf_set_spin_limit(hf_ctx* ctx, int limit);
 
 /* Human-readable name of an HF_* code (static string). */
 const char* hf_error_string(int code);
@@ -261,9 +292,11 @@ int hf_k11_iterate(hf_ctx* ctx, int method, int m, const double* B, double* X, i
  *    current); make that first call before any stream capture.  Call with the device of
  *    the hf_factorize that built the context current.
  *  - Every call on a device shares the array and leaves its contents behind; the solve
- *    initialises everything it reads, so no clearing is needed.  Calls whose work can
- *    overlap on the GPU (other streams, other threads, other contexts) race on the
- *    array: serialise them.
+ *    writes every value it reads before reading it and clears the sweeps' tickets and
+ *    flags (cudaMemsetAsync) before each sweep.  Two calls whose GPU work overlapped
+ *    would race on the array.  Within one process the entry point prevents that: it
+ *    holds a library lock from its start until it has synchronised its stream, so
+ *    concurrent host callers run one after another.
  *  - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.  Profiling
  *    events are not recorded for this call.
  * Errors: HF_ERR_ARG (bad argument or scratch above the limit), HF_ERR_STATE (before

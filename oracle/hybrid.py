@@ -23,13 +23,12 @@ the design notes):
       and Q_{n+1} likewise (Sec. 3.5).
   R8  Block GCR starts as Alg. 4 (X0 = Q^-1 B) and stops when every column
       satisfies |r_k| / |b_k| <= tol.
-  R3b Null-pivot test: a candidate whose current diagonal is below tau times
-      the magnitude of the terms it was formed from (|K_ii| plus the
-      accumulated |l_ik|^2 |d_k| of earlier eliminations) has lost its
-      digits to cancellation; the lower precision cannot resolve it, so it is
+  R3b Optional null-pivot test, not in the paper and off by default
+      (null_test=False): Sec. 2.2 postpones on the ratio test alone.  When
+      asked for, a candidate whose current diagonal is below tau times the
+      magnitude of the terms it was formed from (|K_ii| plus the accumulated
+      |l_ik|^2 |d_k| of earlier eliminations) counts as cancelled: it is
       postponed on its own (skipped) and the elimination of the set goes on.
-      Without it, float32 noise pivots of a singular K pass the ratio test
-      and the kernel never reaches S22 (Sec. 3 requires it there).
   R14 The GPU path forms q_{n+1} = A p_{n+1} by a product with A instead of the
       recurrence q_{n+1} = z_{n+1} + sum beta q_m (Sec. 3.4 keeps the
       recurrence to save one SpMV for a single rhs; with M rhs the recurrence
@@ -206,20 +205,24 @@ def _eliminate(S, G, remaining, q, fac, symmetric):
     return d
 
 
-def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_test=True, tag="",
+def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_test=False, tag="",
                 symmetric=False):
     """Symmetric max-|diag| pivoting with threshold postponing on one index set (Sec. 2.1-2.2).
 
     Each step takes the candidate of largest |diag| (R5 ties).  If it fails the
-    ratio test (R2/R3) the rest of the set is postponed (stop); if it passes but
-    fails the null-pivot test (R3b) only that candidate is postponed (skip).
+    ratio test (R2/R3) the rest of the set is postponed (stop).  With the
+    optional null-pivot test (R3b, null_test=True) a candidate that passes the
+    ratio test but fails that test is postponed alone (skip).
     Returns (chosen, postponed, skipped).
 
     Replay mode: ``replay = (accepted sequence, set of skipped indices)`` chosen
     by another implementation.  The oracle follows it: it skips the listed
     candidates when they come up as the maximum and accepts the listed pivots
-    in order, recording any step that this rule would not admit (within a
-    relative slack for the other implementation's rounding).
+    in order, recording any step that this rule would not admit.  The decisions
+    are taken in the lower precision (Alg. 1 step 1), so a comparison counts as
+    admissible within the rounding of the values compared: a relative slack, plus
+    slack times the magnitude G of the terms each diagonal was formed from (the
+    size of its rounding error when cancellation has made it small).
     """
     cand = list(np.asarray(cand, dtype=np.int64))
     chosen, skipped = [], []
@@ -246,7 +249,8 @@ def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_t
                 skipped.append(cand.pop(best))
                 continue
             if step >= len(seq):
-                if dg[best] >= tau * d_ref * (1 + slack) and not (null_test and dg[best] < tau * float(G[bq])):
+                if dg[best] >= tau * d_ref * (1 + slack) + slack * float(G[bq]) and \
+                        not (null_test and dg[best] < tau * float(G[bq])):
                     fac.violations.append(f"{tag}: replay stopped at step {step} but oracle ratio "
                                           f"{dg[best] / d_ref:.6g} >= tau")
                 break
@@ -255,9 +259,9 @@ def _factor_set(S, G, remaining, cand, tau, fac, replay=None, slack=1e-4, null_t
                 fac.violations.append(f"{tag}: replay pivot {q} is not a candidate")
                 break
             t = cand.index(q)
-            if dg[t] < (1 - slack) * dg[best]:
+            if dg[t] < (1 - slack) * dg[best] - slack * (float(G[q]) + float(G[bq])):
                 fac.violations.append(f"{tag}: step {step} pivot {q} |d|={dg[t]:.8g} < max {dg[best]:.8g}")
-            if dg[t] < tau * d_ref * (1 - slack):
+            if dg[t] < tau * d_ref * (1 - slack) - slack * float(G[q]):
                 fac.violations.append(f"{tag}: step {step} pivot {q} fails the ratio test")
             if null_test and dg[t] < tau * float(G[q]) * (1 - slack):
                 fac.violations.append(f"{tag}: step {step} pivot {q} fails the null test")
@@ -290,7 +294,7 @@ def _symmetric(K) -> bool:
 
 def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: int = 4,
                         replay: dict | None = None, slack: float = 1e-4, dtype=np.float32,
-                        null_test: bool = True) -> FactorResult:
+                        null_test: bool = False) -> FactorResult:
     """Alg. 1 step 1: factor along the tree, postpone, refactor Lambda_0, enlarge.
 
     ``nodes``: index arrays Lambda_l in elimination order (children before parents).
@@ -299,6 +303,7 @@ def threshold_factorize(K: sp.csr_matrix, nodes: list, tau: float, n_enlarge: in
     ``replay``: optional {"node_pivots": [...], "node_skipped": [...],
     "lam0_pivots": [...], "lam0_skipped": [...]} chosen by another implementation;
     the oracle follows it and records any choice that this rule would not admit.
+    ``null_test``: add the optional null-pivot test R3b to the ratio test of Sec. 2.2.
     """
     L = K.shape[0]
     S = K.toarray().astype(dtype)                  # current Schur complement
@@ -790,14 +795,15 @@ def backward_error(Kbar: sp.csr_matrix, x, b):
 
 
 def run_hybrid(Kbar: sp.csr_matrix, nodes, tau, n_enlarge=4, replay=None, kernel_eps=1e-10,
-               gap_min=1e4, use_gcr=False, gcr_tol=1e-14, gcr_maxit=50, dtype=np.float32):
+               gap_min=1e4, use_gcr=False, gcr_tol=1e-14, gcr_maxit=50, dtype=np.float32,
+               null_test=False):
     """Alg. 1 end to end: scale, threshold factorization, X12, S22, its dense factor, kernel dim.
 
     S22 is factorized by Bunch-Parlett (R11) when K-bar is symmetric and by LU with
     complete pivoting (R15) otherwise.
     """
     q, K = scale_matrix(Kbar)
-    fac = threshold_factorize(K, nodes, tau, n_enlarge, replay, dtype=dtype)
+    fac = threshold_factorize(K, nodes, tau, n_enlarge, replay, dtype=dtype, null_test=null_test)
     if use_gcr and fac.M:
         lam1, _, K12, _, _ = _blocks(K, fac.lambda2)
         B = np.zeros((K.shape[0], fac.M))

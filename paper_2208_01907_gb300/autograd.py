@@ -6,6 +6,12 @@ pattern of ``H``), forms the Schur complement (Alg. 1) and returns x = K-bar^-1 
 kept by the context (K-bar is symmetric), dJ/db = lam, and dJ/dvals comes from
 hf_values_adjoint (dJ/dK-bar_ij = -lam_i x_j).  Only the context (factor, X12,
 S22 factors) and x are kept for the backward pass.
+
+The context holds one factorization at a time.  The forward pass records the
+context's factorization generation; a backward pass that finds the context
+factorized again since then (another hybrid_solve on the same HybridFactor in
+the same graph, or a deferred backward) raises instead of using the wrong factor.
+Give each live graph node its own HybridFactor.
 """
 from __future__ import annotations
 
@@ -27,6 +33,7 @@ class HybridSolve(torch.autograd.Function):
         x = torch.zeros_like(bt)
         H.solve(bt, x)
         ctx.H = H
+        ctx.generation = H.generation
         ctx.b_shape = b.shape
         ctx.save_for_backward(x)
         return x.reshape(b.shape)
@@ -35,6 +42,10 @@ class HybridSolve(torch.autograd.Function):
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
         H = ctx.H
+        if H.generation != ctx.generation:
+            raise RuntimeError("HybridSolve.backward: the HybridFactor was factorized again after this "
+                               "forward pass (its factor no longer matches x); use one HybridFactor per "
+                               "live hybrid_solve")
         g = gx.detach().reshape(-1, H.L).contiguous()
         lam = torch.zeros_like(g)
         H.solve(g, lam)                                      # K-bar^T = K-bar: the same factor

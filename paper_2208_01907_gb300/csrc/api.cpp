@@ -171,7 +171,8 @@ int hf_get_profile(hf_ctx* c, double* ms, int64_t* launches, double* flops, doub
 const char* hf_profile_name(int cls) {
   static const char* names[HF_NPROF] = {"scale", "assemble", "panel", "trailing", "lambda0",
                                         "trsv_fwd", "trsv_bwd", "spmm", "gram", "block_update",
-                                        "schur", "dense_ldlt", "vector"};
+                                        "schur", "dense_ldlt", "vector", "panel_swap", "sweep_io",
+                                        "tc_prep"};
   return (cls >= 0 && cls < HF_NPROF) ? names[cls] : "unknown";
 }
 
@@ -191,7 +192,15 @@ int hf_default_opts(hf_opts* o) {
   o->panel = 64;
   o->cuda_stream = nullptr;
   o->fp64_gemm = 0;
-  o->trailing = 1;
+  o->trailing = 0;
+  o->null_test = 0;
+  o->spin_limit = 0;
+  return HF_OK;
+}
+
+int hf_set_spin_limit(hf_ctx* c, int limit) {
+  if (!c || limit < 0) return HF_ERR_ARG;
+  c->opts.spin_limit = limit;
   return HF_OK;
 }
 
@@ -214,7 +223,8 @@ int hf_analyze(int64_t L, const int64_t* rowptr, const int32_t* col, const doubl
                const hf_opts* opts, hf_ctx** out) {
   if (opts) {
     if (!(opts->tau > 0) || opts->n_enlarge < 0 || opts->gcr_maxit < 1 || opts->nd_leaf < 1 ||
-        opts->panel < 1 || opts->delay_cap < 0 || opts->nd_levels < 0 || opts->nd_levels > 24)
+        opts->panel < 1 || opts->delay_cap < 0 || opts->nd_levels < 0 || opts->nd_levels > 24 ||
+        opts->spin_limit < 0 || opts->null_test < 0 || opts->null_test > 1)
       return HF_ERR_ARG;
     if (opts->precision < HF_PREC_MIXED || opts->precision > HF_PREC_FP32) return HF_ERR_ARG;
   }
@@ -320,10 +330,14 @@ int hf_get_info(hf_ctx* c, hf_info* info) {
         tf += (k1 - k0) * n * (n + 1);
       }
       se += (int64_t)(f * ks - ks * (ks + 1) / 2);
+      info->sweep_blocks = std::max(info->sweep_blocks, (int32_t)((c->state_host[t].ksolve + 63) / 64));
     }
     info->trailing_flops = tf;
     info->solve_factor_entries = se;
   }
+  info->panel_cluster = c->path_cluster;
+  info->panel_global = c->path_global;
+  info->ldlt_kernel = c->path_ldlt;
   info->front_bytes = c->d_front.p ? (int64_t)c->d_front.bytes : 0;
   info->delay_retries = c->delay_retries;
   info->precision = c->prec;

@@ -215,7 +215,7 @@ __device__ __forceinline__ void sym_swap(T* F, int64_t ld, int f, int a, int b, 
 template <typename T>
 __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0,
                         T* __restrict__ arena, int32_t* __restrict__ rowid, T* __restrict__ Gall,
-                        int32_t* __restrict__ pos0all, int nb, double tau, int cap) {
+                        int32_t* __restrict__ pos0all, int nb, double tau, double tau_null, int cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red_k[32];
   __shared__ int red_i[32], red_p[32];
@@ -269,11 +269,11 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
     if (tid == 0) {
       for (int wv = 1; wv < (nt + 31) / 32; ++wv)
         if (better_t(red_k[wv], red_i[wv], bk, bi)) { bk = red_k[wv]; bi = red_i[wv]; bp = red_p[wv]; }
-      // ratio test |d_{i+1} / d_i| < tau stops the set (R2/R3; NaN fails it);
-      // the null-pivot test |d| < tau * G postpones this candidate alone (R3b)
+      // ratio test |d_{i+1} / d_i| < tau stops the set (R2/R3; NaN fails it); the
+      // optional null-pivot test |d| < tau * G postpones this candidate alone (R3b)
       int act = 0;
       if (!((double)bk >= tau * dref)) act = 1;
-      else if (!((double)bk >= tau * (double)G[bp])) act = 2;
+      else if (!((double)bk >= tau_null * (double)G[bp])) act = 2;
       s_act = act;
       s_q = bp;
     }
@@ -351,7 +351,7 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
 // One cluster barrier per pivot.  Before it, every CTA pushes into every CTA's
 // (double-buffered) slots: its best candidate (key, id, G, diagonal, panel row),
 // and the owners of positions k and nact-1 push those rows.  After it, every CTA
-// takes the same decision (R2, R3, R3b, R5) from its local slots, forms
+// takes the same decision (R2, R3, the optional R3b, R5) from its local slots, forms
 // w_c = d_c L(q, c), computes d_k itself (same operations, same order as the
 // owner would) and processes its own rows: the symmetric swap k <-> q is fused into
 // the load of the new column k, then L(i, k), the diagonals and the magnitudes.
@@ -395,7 +395,7 @@ template <typename T>
 __global__ void __launch_bounds__(PCL_THREADS, 1)
 k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, T* __restrict__ arena,
            int32_t* __restrict__ rowid, T* __restrict__ Gall, int32_t* __restrict__ pos0all, int nb, double tau,
-           int C, int Rcap, int4* __restrict__ swlist, int* __restrict__ swcount) {
+           double tau_null, int C, int Rcap, int4* __restrict__ swlist, int* __restrict__ swcount) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -577,7 +577,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       if (tid == 0) {
         int a2 = 0;
         if (!((double)gk >= tau * dref)) a2 = 1;                                 // ratio test (R2/R3)
-        else if (!((double)gk >= tau * (double)pG[sb + gw])) a2 = 2;            // null pivot (R3b)
+        else if (!((double)gk >= tau_null * (double)pG[sb + gw])) a2 = 2;       // null pivot (R3b)
         s_act = a2;
         s_w = gw;
       }
@@ -880,21 +880,52 @@ __global__ void __launch_bounds__(256) k_trailing(const NodeDesc* __restrict__ n
 }
 
 // ---------------------------------------------------------------------------
-// The same trailing update on the tensor cores (the precision form of the FP32 factor):
-// each FP32 operand is split exactly into three BF16 parts, x = x0 + x1 + x2 with
+// The same trailing update on the tensor cores (the precision form of the FP32 factor).
+// Each FP32 operand is split exactly into three BF16 parts, x = x0 + x1 + x2 with
 // x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1) (24 significant bits), and
-// the six products of total order <= 2 accumulate in three FP32 TMEM accumulators, one
-// per order.  The dropped products are below 2^-24 of |W| |D| |W|^T,
-// the rounding level of the FP32 SIMT update.  One 128 x 64 tile of the lower trailing
-// block per CTA of 128 threads; K = the panel width (<= 64) in one shared-memory stage.
+// the six products of total order <= 2 accumulate in FP32 in TMEM: the order-0 product
+// x0 y0 in one accumulator, the five of orders 1 and 2 (at most 2^-8 of it) in a second,
+// the two added in registers, so the tensor core's FP32 accumulation never adds terms of
+// very different magnitude.  The dropped products are below 2^-24 of |W| |D| |W|^T, the
+// rounding level of the FP32 SIMT update.
+//
+// One persistent CTA per SM takes the 128 x 128 tiles of the lower trailing blocks of
+// all fronts of the level in a fixed order (tile u, u + grid, ...).  Warp roles:
+//   warp 0  one thread issues the bulk copies of a tile's pre-split operands into one of
+//           two shared-memory stages (the parts are laid out so that a tile's rows of one
+//           part and k-group are one contiguous block)
+//   warp 1  allocates TMEM (two accumulator pairs of 2 x 128 columns) and one thread
+//           issues the 24 MMAs of a tile (M = N = 128, K = 16, kind::f16)
+//   warps 2-9  the epilogue: TMEM -> registers, C -= acc0 + acc1 on the lower triangle
+//           (two warps per TMEM lane quarter, 64 columns each)
+// so the copies of tile u+1 and the epilogue of tile u-1 overlap the MMAs of tile u.
+// Every mbarrier wait is bounded; a wait that gives up sets the error flag and an abort
+// word that ends every role, each role waits (bounded) for its own work in flight, and
+// the TMEM is freed before the CTA returns.
 // ---------------------------------------------------------------------------
-constexpr int TT_M = 128, TT_N = 64, TT_K = 64, TT_THREADS = 128;
-constexpr int TT_A = 3 * TT_M * TT_K * 2;          // 48 KB: three BF16 parts of W rows
-constexpr int TT_B = 3 * TT_N * TT_K * 2;          // 24 KB: three BF16 parts of (W D) rows
-constexpr int TT_SMEM = TT_A + TT_B + 128;
-constexpr uint32_t TT_IDESC = tc::bf16_idesc(TT_M, TT_N);
-constexpr int TT_COLS = 256;                        // TMEM columns: three accumulators of TT_N
+constexpr int TT_M = 128, TT_K = 64;                 // tile rows; k = the panel's columns
+constexpr int TT_EPI = 8;                           // epilogue warps: two per TMEM lane quarter
+constexpr int TT_THREADS = 64 + 32 * TT_EPI;
+constexpr int TT_PART = TT_M * TT_K * 2;            // 16 KB: one BF16 part of 128 rows x 64 k
+constexpr int TT_MAXF = 4096;                       // fronts per level the tile map holds
+constexpr int TT_COLS = 512;                        // TMEM columns allocated (all of them)
+constexpr int TT_SPIN = 1 << 22;
+constexpr int TT_MIN_ROWS = 256;                    // levels with smaller fronts keep the SIMT update
 
+// Tile shape and accumulation of one form of the kernel: TN columns per tile; the order-0
+// products x0 y0 of the tile's k range are summed by the tensor core in KS accumulators
+// (k-steps of 16 split evenly over them), the order-1 and order-2 products in one more;
+// the KS + 1 partial sums are added in registers.  NBUF accumulator sets fit the TMEM.
+template <int TN, int KS> struct TtCfg {
+  static constexpr int B_PART = TN * TT_K * 2;
+  static constexpr int STAGE = 3 * TT_PART + 3 * B_PART;
+  static constexpr int ACOLS = (KS + 1) * TN;                  // TMEM columns of one accumulator set
+  static constexpr int NBUF = 2 * ACOLS <= TT_COLS ? 2 : 1;
+  static constexpr int SMEM = 2 * STAGE + (TT_MAXF + 1) * 4 + 1024;
+  static constexpr int R = TT_M / TN;                          // column blocks per row block
+  static constexpr uint32_t IDESC = tc::bf16_idesc(TT_M, TN);
+  static_assert(ACOLS <= TT_COLS && TT_K / 16 % KS == 0 && TT_M % TN == 0, "tile form");
+};
 __device__ __forceinline__ void split3(float x, uint32_t& h0, uint32_t& h1, uint32_t& h2) {
   const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
   const float r1 = x - __bfloat162float(b0);
@@ -911,8 +942,9 @@ __device__ __forceinline__ void split3(float x, uint32_t& h0, uint32_t& h1, uint
 // (16 bytes per row and k-group; row = front position), i.e. already in the K-major
 // core-matrix layout of a tile, so that a tile of consecutive rows is one contiguous
 // block per part and k-group.
-__global__ void k_trailing_split(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
-                                 const float* __restrict__ arena, uint4* __restrict__ parts) {
+__global__ void __launch_bounds__(256) k_trailing_split(const NodeDesc* __restrict__ nd,
+                                                         const NodeState* __restrict__ st, int t0,
+                                                         const float* __restrict__ arena, uint4* __restrict__ parts) {
   const int t = t0 + blockIdx.y;
   const int k0 = st[t].kp0, k1 = st[t].k, f = st[t].f;
   if (k1 <= k0) return;
@@ -920,16 +952,23 @@ __global__ void k_trailing_split(const NodeDesc* __restrict__ nd, const NodeStat
   const float* F = arena + d.front_off;
   const int64_t ld = d.ld;
   const int K = min(k1 - k0, TT_K);
+  __shared__ float dk[TT_K];
+  if (threadIdx.x < TT_K) dk[threadIdx.x] = threadIdx.x < K ? F[(k0 + threadIdx.x) * (ld + 1)] : 0.f;
+  __syncthreads();
   uint4* P = parts + d.row_off * 48;                           // 6 parts x 8 k-groups per row
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (f - k1) * 8; e += gridDim.x * blockDim.x) {
-    const int r = k1 + e / 8, kg = e % 8;                      // 8 threads per row
+  // a warp takes 32 consecutive rows of one k-group: the column reads and the 16-byte part
+  // writes of a warp are contiguous
+  const int kg = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rb = k1 + blockIdx.x * 32; rb < f; rb += gridDim.x * 32) {
+    const int r = rb + lane;
+    if (r >= f) continue;
     float w[8], b[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = kg * 8 + q;
       const float x = k < K ? F[r + (int64_t)(k0 + k) * ld] : 0.f;
       w[q] = x;
-      b[q] = k < K ? x * F[(k0 + k) + (int64_t)(k0 + k) * ld] : 0.f;
+      b[q] = x * dk[k];
     }
     uint32_t p[6][4];
 #pragma unroll
@@ -953,91 +992,228 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(TT_THREADS) k_trailing_tc(const NodeDesc* __restrict__ nd,
-                                                          const NodeState* __restrict__ st, int t0,
-                                                          float* __restrict__ arena, const uint4* __restrict__ parts,
-                                                          int* __restrict__ flags) {
-  const int t = t0 + blockIdx.z;
-  const int k0 = st[t].kp0, k1 = st[t].k, f = st[t].f;
-  if (k1 <= k0) return;
-  const int i0 = k1 + blockIdx.x * TT_M, j0 = k1 + blockIdx.y * TT_N;
-  if (i0 >= f || j0 >= f || j0 > i0 + TT_M - 1) return;       // outside the front or strictly upper
-  const NodeDesc d = nd[t];
-  float* F = arena + d.front_off;
-  const int64_t ld = d.ld;
-  const uint4* P = parts + d.row_off * 48;
-  extern __shared__ __align__(128) unsigned char tt_raw[];
-  unsigned char* sA = (unsigned char*)(((uintptr_t)tt_raw + 127) & ~(uintptr_t)127);
-  unsigned char* sB = sA + TT_A;
+// tile u of the level -> (front slot, row block bi, column block bj < R (bi + 1)): fronts by
+// the prefix of their tile counts, then the lower tile index within the front (row block bi
+// of 128 rows holds the R (bi + 1) column blocks of TT_M / R columns that reach its last row)
+struct TtTile { int slot, bi, bj; };
+__device__ __forceinline__ TtTile tt_tile(const int* pre, int cnt, int u, int R) {
+  int lo = 0, hi = cnt - 1;                           // last slot with pre[slot] <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  const int v = u - pre[lo];
+  int bi = (int)((sqrtf(8.f * (float)v / (float)R + 1.f) - 1.f) * 0.5f);
+  while (R * (bi + 1) * (bi + 2) / 2 <= v) ++bi;
+  while (bi > 0 && R * bi * (bi + 1) / 2 > v) --bi;
+  return {lo, bi, v - R * bi * (bi + 1) / 2};
+}
+
+// bounded wait on an mbarrier phase; false when it gave up (abort word set) or another
+// role already gave up
+__device__ __forceinline__ bool tt_wait(uint32_t bar, uint32_t par, volatile int* abort_w, int* flags) {
+  for (int it = 0; it < TT_SPIN; ++it) {
+    if (tc::mbar_try(bar, par)) return true;
+    if (*abort_w) return false;
+  }
+  *abort_w = 1;
+  atomicExch(flags + FLAG_TC_TIMEOUT, 1);
+  return false;
+}
+
+// the same wait for the clean-up of an aborted CTA: ignores the abort word
+__device__ __forceinline__ void tt_drain(uint32_t bar, uint32_t par) {
+  for (int it = 0; it < TT_SPIN; ++it)
+    if (tc::mbar_try(bar, par)) return;
+}
+
+__device__ __forceinline__ void tt_bar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::smem_u32(b)), "r"(count));
+}
+
+template <int TN, int KS>
+__global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* __restrict__ nd,
+                                                             const NodeState* __restrict__ st, int t0, int cnt,
+                                                             float* __restrict__ arena,
+                                                             const uint4* __restrict__ parts,
+                                                             int* __restrict__ flags) {
+  using Cfg = TtCfg<TN, KS>;
+  constexpr int NB = Cfg::NBUF;
+  constexpr int CW = TN / 2;                                   // columns per epilogue warp
+  extern __shared__ __align__(1024) unsigned char tt_raw[];
+  unsigned char* stages = (unsigned char*)(((uintptr_t)tt_raw + 1023) & ~(uintptr_t)1023);
+  int* pre = (int*)(stages + 2 * Cfg::STAGE);                // cnt + 1 tile prefix counts
   __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_tfull[2], bar_tempty[2];
+  __shared__ int seg[TT_THREADS + 1];
+  __shared__ int abort_s;
+  volatile int* abort_w = &abort_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) {
+
+  // tiles of every front of the level: n = f - k1 trailing rows, nt = ceil(n / 128) row
+  // blocks, R nt (nt + 1) / 2 lower tiles; prefix over the fronts (segments of threads)
+  const int per = (cnt + TT_THREADS - 1) / TT_THREADS;
+  const int a0 = min(cnt, tid * per), a1 = min(cnt, a0 + per);
+  int sum = 0;
+  for (int i = a0; i < a1; ++i) {
+    const int k0 = st[t0 + i].kp0, k1 = st[t0 + i].k, f = st[t0 + i].f;
+    const int n = k1 > k0 ? f - k1 : 0;
+    const int nt = (n + TT_M - 1) / TT_M;
+    pre[i] = Cfg::R * nt * (nt + 1) / 2;
+    sum += pre[i];
+  }
+  seg[tid] = sum;
+  if (tid == 0) {
+    abort_s = 0;
+    for (int s = 0; s < 2; ++s) {
+      tt_bar_init(&bar_full[s], 1);
+      tt_bar_init(&bar_empty[s], 1);
+      tt_bar_init(&bar_tfull[s], 1);
+      tt_bar_init(&bar_tempty[s], TT_EPI);                   // one arrival per epilogue warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc::smem_u32(&tslot)), "r"(TT_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  __syncthreads();
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::smem_u32(&bar_ld)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(tc::smem_u32(&bar_mma)), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;");
+    int acc = 0;
+    for (int w = 0; w < TT_THREADS; ++w) { const int v = seg[w]; seg[w] = acc; acc += v; }
+    seg[TT_THREADS] = acc;
   }
   __syncthreads();
-  // bulk copies of the pre-split parts: A = parts 0..2 of rows [i0, i0+128), B = parts 3..5 of
-  // rows [j0, j0+64), each k-group one contiguous block (rows past f are masked in the epilogue)
-  if (tid == 0) {
-    const uint32_t bl = tc::smem_u32(&bar_ld);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bl), "r"(TT_A + TT_B) : "memory");
-    for (int part = 0; part < 3; ++part)
-      for (int kg = 0; kg < 8; ++kg) {
-        bulk_g2s(tc::smem_u32(sA + part * (TT_M * TT_K * 2) + kg * (TT_M * 16)), P + (int64_t)(part * 8 + kg) * ld + i0,
-                 TT_M * 16, bl);
-        bulk_g2s(tc::smem_u32(sB + part * (TT_N * TT_K * 2) + kg * (TT_N * 16)),
-                 P + (int64_t)((part + 3) * 8 + kg) * ld + j0, TT_N * 16, bl);
-      }
+  {
+    int acc = seg[tid];
+    for (int i = a0; i < a1; ++i) { const int v = pre[i]; pre[i] = acc; acc += v; }
+    if (tid == 0) pre[cnt] = seg[TT_THREADS];
   }
-  bool ok = false;
-  for (int it = 0; it < (1 << 22) && !ok; ++it) ok = tc::mbar_try(tc::smem_u32(&bar_ld), 0u);
   asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
   const uint32_t tmem = tslot;
-  if (tid == 0 && ok) {
-    // one accumulator per order of the products (x0y0 | x0y1 + x1y0 | x0y2 + x1y1 + x2y0),
-    // added in registers afterwards: the tensor core's FP32 accumulation then never adds
-    // terms of very different magnitude
-    const int ps[6] = {0, 1, 0, 2, 1, 0}, qs[6] = {0, 0, 1, 0, 1, 2}, os[6] = {0, 1, 1, 2, 2, 2};
-    for (int ks = 0; ks < TT_K / 16; ++ks)
-      for (int u = 0; u < 6; ++u) {
-        const uint64_t ad = tc::smem_desc(tc::smem_u32(sA + ps[u] * (TT_M * TT_K * 2) + ks * (2 * TT_M * 16)), 16 * TT_M, 128);
-        const uint64_t bd = tc::smem_desc(tc::smem_u32(sB + qs[u] * (TT_N * TT_K * 2) + ks * (2 * TT_N * 16)), 16 * TT_N, 128);
-        const bool first = ks == 0 && (u == 0 || u == 1 || u == 3);
-        tc::mma_bf16(tmem + (uint32_t)(os[u] * TT_N), ad, bd, TT_IDESC, first ? 0u : 1u);
-      }
-    tc::mma_commit(tc::smem_u32(&bar_mma));
-  }
-  bool done = false;
-  if (ok)
-    for (int it = 0; it < (1 << 22) && !done; ++it) done = tc::mbar_try(tc::smem_u32(&bar_mma), 0u);
-  if (!done && lane == 0) atomicExch(flags + FLAG_TC_TIMEOUT, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (done) {
-    const int i = i0 + warp * 32 + lane;
+  const int total = pre[cnt];
+  const int G = (int)gridDim.x;
+  const int ntile = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: bulk copies of the pre-split parts of tile it into stage it % 2
+    int issued = 0;
+    for (int it = 0; it < ntile; ++it) {
+      const int s = it & 1;
+      if (it >= 2 && !tt_wait(tc::smem_u32(&bar_empty[s]), ((it >> 1) + 1) & 1, abort_w, flags)) break;
+      const TtTile tl = tt_tile(pre, cnt, (int)blockIdx.x + it * G, Cfg::R);
+      const int t = t0 + tl.slot;
+      const int k1 = st[t].k;
+      const int64_t ld = nd[t].ld;
+      const uint4* P = parts + nd[t].row_off * 48;
+      const int i0 = k1 + tl.bi * TT_M, j0 = k1 + tl.bj * TN;
+      const uint32_t bf = tc::smem_u32(&bar_full[s]);
+      const uint32_t sa = tc::smem_u32(stages + s * Cfg::STAGE);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bf), "r"(Cfg::STAGE) : "memory");
+      for (int part = 0; part < 3; ++part)
+        for (int kg = 0; kg < 8; ++kg) {
+          bulk_g2s(sa + part * TT_PART + kg * (TT_M * 16), P + (int64_t)(part * 8 + kg) * ld + i0, TT_M * 16, bf);
+          bulk_g2s(sa + 3 * TT_PART + part * Cfg::B_PART + kg * (TN * 16),
+                   P + (int64_t)((part + 3) * 8 + kg) * ld + j0, TN * 16, bf);
+        }
+      issued = it + 1;
+    }
+    if (*abort_w)                                            // own copies still in flight
+      for (int it = max(0, issued - 2); it < issued; ++it) tt_drain(tc::smem_u32(&bar_full[it & 1]), (it >> 1) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: 6 products x 4 k-steps into accumulator set it % NB
+    const int ps[6] = {0, 0, 1, 0, 1, 2}, qs[6] = {0, 1, 0, 2, 1, 0};
+    int done_it = 0;
+    for (int it = 0; it < ntile; ++it) {
+      const int s = it & 1, ab = NB == 2 ? (it & 1) : 0, use = it / NB;
+      if (!tt_wait(tc::smem_u32(&bar_full[s]), (it >> 1) & 1, abort_w, flags)) break;
+      if (use >= 1 && !tt_wait(tc::smem_u32(&bar_tempty[ab]), (use - 1) & 1, abort_w, flags)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sa = tc::smem_u32(stages + s * Cfg::STAGE), sb = sa + 3 * TT_PART;
+      const uint32_t acc = tmem + (uint32_t)(ab * Cfg::ACOLS);
 #pragma unroll 1
-    for (int c0 = 0; c0 < TT_N; c0 += 32) {
-      uint32_t r0[32], r1[32], r2[32];
-      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      tc::tmem_ld32(tl, r0);
-      tc::tmem_ld32(tl + TT_N, r1);
-      tc::tmem_ld32(tl + 2 * TT_N, r2);
+      for (int ks = 0; ks < TT_K / 16; ++ks) {
+        const int a0c = ks / (TT_K / 16 / KS);                  // which order-0 accumulator
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = j0 + c0 + q;
-        const float v = __uint_as_float(r0[q]) + (__uint_as_float(r1[q]) + __uint_as_float(r2[q]));
-        if (i < f && j < f && i >= j) F[i + (int64_t)j * ld] -= v;
+        for (int u = 0; u < 6; ++u) {
+          const uint64_t ad = tc::smem_desc(sa + ps[u] * TT_PART + ks * (2 * TT_M * 16), 16 * TT_M, 128);
+          const uint64_t bd = tc::smem_desc(sb + qs[u] * Cfg::B_PART + ks * (2 * TN * 16), 16 * TN, 128);
+          const bool first = u == 0 ? (ks % (TT_K / 16 / KS) == 0) : (ks == 0 && u == 1);
+          tc::mma_bf16(acc + (uint32_t)((u == 0 ? a0c : KS) * TN), ad, bd, Cfg::IDESC, first ? 0u : 1u);
+        }
+      }
+      tc::mma_commit(tc::smem_u32(&bar_empty[s]));          // stage s may be refilled
+      tc::mma_commit(tc::smem_u32(&bar_tfull[ab]));         // accumulator set ab is complete
+      done_it = it + 1;
+    }
+    if (done_it > 0) {                                        // own MMAs done before the TMEM is freed
+      const int last = done_it - 1;
+      tt_drain(tc::smem_u32(&bar_tfull[NB == 2 ? (last & 1) : 0]), (last / NB) & 1);
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: rows i0 + 32 q4 + lane, columns j0 + CW h .. + CW of the tile,
+    // C -= (acc0_0 + .. + acc0_KS-1) + acc1 on the lower triangle
+    const int q4 = warp & 3;                                  // the TMEM lane quarter this warp may read
+    const int h = (warp - 2) >> 2;                            // which half of the tile's columns
+    for (int it = 0; it < ntile; ++it) {
+      const int ab = NB == 2 ? (it & 1) : 0, use = it / NB;
+      const TtTile tl = tt_tile(pre, cnt, (int)blockIdx.x + it * G, Cfg::R);
+      const int t = t0 + tl.slot;
+      const int k1 = st[t].k, f = st[t].f;
+      const int64_t ld = nd[t].ld;
+      float* F = arena + nd[t].front_off;
+      const int i0 = k1 + tl.bi * TT_M, j0 = k1 + tl.bj * TN + h * CW;
+      const int i = i0 + q4 * 32 + lane;
+      // columns q <= qmax of this row are in the lower triangle of the front
+      const int qmax = i < f ? min(i, f - 1) - j0 : -1;
+      float cv[CW];                                           // C loaded while the MMAs run
+      {
+        const float* pc = F + i + (int64_t)j0 * ld;
+#pragma unroll
+        for (int q = 0; q < CW; ++q) {
+          cv[q] = q <= qmax ? *pc : 0.f;
+          pc += ld;
+        }
+      }
+      int ok = 1;
+      if (lane == 0) ok = tt_wait(tc::smem_u32(&bar_tfull[ab]), use & 1, abort_w, flags) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * Cfg::ACOLS + h * CW);
+      float* pw = F + i + (int64_t)j0 * ld;
+#pragma unroll
+      for (int ch = 0; ch < CW / 16; ++ch) {
+        const int c0 = ch * 16;
+        float v[16];
+        uint32_t r[16];
+        tc::tmem_ld16(ta + (uint32_t)c0, r);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+#pragma unroll
+        for (int a = 1; a <= KS; ++a) {                       // the other order-0 sums, then acc1
+          tc::tmem_ld16(ta + (uint32_t)(a * TN + c0), r);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) v[q] += __uint_as_float(r[q]);
+        }
+        if (ch == CW / 16 - 1) {                              // this warp's part read: release it
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&bar_tempty[ab])) : "memory");
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          if (c0 + q <= qmax) *pw = cv[c0 + q] - v[q];
+          pw += ld;
+        }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TT_COLS));
@@ -1170,11 +1346,23 @@ int run_levels(hf_ctx* c) {
   static bool attr_set[2] = {false, false};
   static int max_cluster[2] = {0, 0};
   static std::mutex attr_mu;                 // contexts may be driven from several host threads
-  std::lock_guard<std::mutex> attr_lock(attr_mu);
+  static int num_sms = 0;
+  int cmax = 0;
+  {
+  std::lock_guard<std::mutex> attr_lock(attr_mu);   // the one-time set-up only, not the launches
+  if (!num_sms) {
+    int dev = 0;
+    HF_CUDA_TRY(cudaGetDevice(&dev));
+    HF_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    num_sms = std::max(1, num_sms);
+  }
   if (!attr_set[sizeof(T) == 8]) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCL_SMEM));
-    HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TT_SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtCfg<128, 1>::SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtCfg<128, 2>::SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtCfg<64, 2>::SMEM));
+    HF_CUDA_TRY(cudaFuncSetAttribute(k_trailing_tc<64, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtCfg<64, 4>::SMEM));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_swap_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM));
     HF_CUDA_TRY(cudaFuncSetAttribute(k_swap_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM));
     if (cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -1198,15 +1386,35 @@ int run_levels(hf_ctx* c) {
     }
     attr_set[sizeof(T) == 8] = true;
   }
-  const int cmax = max_cluster[sizeof(T) == 8];
+  cmax = max_cluster[sizeof(T) == 8];
+  }
+  // the optional null-pivot test (R3b) compares |d| with tau_null * G; 0 switches it off
+  // (|d| >= 0 always holds; a NaN pivot already fails the ratio test)
+  const double tau_null = c->opts.null_test ? c->tau : 0.0;
   // trailing updates of the FP32 factor on the tensor cores (3 x BF16 split) when selected
   const bool use_tc = sizeof(T) == 4 && c->opts.trailing == 0;
+  // HF_TC_MIN_ROWS=n: smallest largest-front order of a level that takes the tensor cores
+  // (default TT_MIN_ROWS; 0 = every level; diagnostic)
+  const char* tmr = std::getenv("HF_TC_MIN_ROWS");
+  const int tc_min_rows = tmr ? std::max(0, std::atoi(tmr)) : TT_MIN_ROWS;
+  // HF_TC_FORM=n: tile form of the tensor-core update (0: 128 x 128 tiles, order-0 products in
+  // one accumulator; 1: 128 x 128, two; 2: 128 x 64, two; 3: 128 x 64, one per k-step of 16,
+  // the default: the fewer products one tensor-core FP32 sum takes, the closer the update is
+  // to the FP32 SIMT one; diagnostic)
+  const char* tfm = std::getenv("HF_TC_FORM");
+  const int tc_form = tfm ? std::atoi(tfm) : 3;
   // HF_LEVEL_TIMES=1: time the panel and trailing launches of every level (diagnostic)
   const char* lt = std::getenv("HF_LEVEL_TIMES");
   const bool level_times = lt && lt[0] == '1';
   // HF_PANEL_KERNEL=global: one CTA per front with the panel in global memory (for comparison)
   const char* pk = std::getenv("HF_PANEL_KERNEL");
   const bool panel_global = pk && pk[0] == 'g';
+  // HF_PANEL_ROWS=n: at most n rows per CTA of the cluster panel, so that small fronts take
+  // the larger clusters of large ones (the same arithmetic spread over more CTAs; diagnostic)
+  const char* pr = std::getenv("HF_PANEL_ROWS");
+  const int rows_cap = pr ? std::max(1, std::atoi(pr)) : 0;
+  c->path_cluster = 0;
+  c->path_global = 0;
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
     int maxn = 0, maxld = 0;
@@ -1244,16 +1452,27 @@ int run_levels(hf_ctx* c) {
     const int nbc = sizeof(T) == 8 ? std::min(nb, 32) : nb;
     const size_t per_row = (size_t)(nbc + 1) * sizeof(T) + 3 * sizeof(T) + 3 * sizeof(int);
     const size_t fixed = PclLayout<T>::bytes(0, nbc);
-    const int Rcap = std::min((int)((PCL_SMEM - fixed) / per_row), PCL_RPT * PCL_THREADS);
+    int Rcap = std::min((int)((PCL_SMEM - fixed) / per_row), PCL_RPT * PCL_THREADS);
+    if (rows_cap > 0) Rcap = std::min(Rcap, rows_cap);
     const int C = std::max(1, std::min(cmax, (maxld + Rcap - 1) / Rcap));
     const bool use_cl = cmax > 0 && maxld > 0 && !panel_global;
     const int cap = use_cl ? C * Rcap : -1;
     const bool use_gl = !use_cl || maxld > cap;
+    if (use_cl) c->path_cluster = std::max(c->path_cluster, C);
+    if (use_gl) c->path_global++;
     const int nbl = use_cl ? nbc : nb;
     const int npan = (maxn + nbl - 1) / nbl;
     const size_t smem = (size_t)nbl * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
     if (use_gl && smem > 220 * 1024) return HF_ERR_ARG;
     const int pthreads = maxld > 1024 ? 1024 : 256;
+    // tensor-core trailing update for the levels of large fronts (a panel of <= 64 pivots,
+    // the tile map of <= TT_MAXF fronts): one persistent CTA per SM, at most one per tile
+    const bool tc_level = use_tc && nbl <= TT_K && cnt <= TT_MAXF && maxld >= tc_min_rows;
+    unsigned tc_grid = 1;
+    if (tc_level) {
+      const int64_t nt = (maxld + TT_M - 1) / TT_M;
+      tc_grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)cnt * 2 * nt * (nt + 1) / 2, num_sms));
+    }
     const int tiles = (maxld + TB - 1) / TB;
     int4* swl = (int4*)c->d_swlist.p;
     int* swc = (int*)c->d_swcount.p;
@@ -1276,17 +1495,26 @@ int run_levels(hf_ctx* c) {
     for (int p = 0; p < npan; ++p) {
       if (use_cl)
         HF_LAUNCH(c, HF_PROF_PANEL, HF_CUDA_TRY(cudaLaunchKernelEx(&lc, k_panel_cl<T>, nd, st, t0, arena, rowid, gmag,
-                                                                   (int32_t*)c->d_pos0.p, nbl, c->tau, C, Rcap,
+                                                                   (int32_t*)c->d_pos0.p, nbl, c->tau, tau_null, C, Rcap,
                                                                    swl, swc)));
       if (use_gl)
         HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag,
-                                                                           (int32_t*)c->d_pos0.p, nbl, c->tau, cap));
-      if (use_tc) {
+                                                                           (int32_t*)c->d_pos0.p, nbl, c->tau, tau_null, cap));
+      if (tc_level) {
         uint4* parts = (uint4*)c->d_tparts.p;
-        HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_split<<<dim3((unsigned)std::min(1024, (maxld * 8 + 255) / 256), cnt), 256, 0, s>>>(
+        HF_LAUNCH(c, HF_PROF_TC_PREP, k_trailing_split<<<dim3((unsigned)std::min(1024, (maxld + 31) / 32), cnt), 256, 0, s>>>(
                                            nd, st, t0, (const float*)arena, parts));
-        HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_tc<<<dim3((maxld + TT_M - 1) / TT_M, (maxld + TT_N - 1) / TT_N, cnt),
-                                                       TT_THREADS, TT_SMEM, s>>>(nd, st, t0, (float*)arena, parts, flags));
+        float* fa = (float*)arena;
+        switch (tc_form) {
+          case 1: HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_tc<128, 2><<<tc_grid, TT_THREADS, TtCfg<128, 2>::SMEM, s>>>(
+                                                     nd, st, t0, cnt, fa, parts, flags)); break;
+          case 2: HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_tc<64, 2><<<tc_grid, TT_THREADS, TtCfg<64, 2>::SMEM, s>>>(
+                                                     nd, st, t0, cnt, fa, parts, flags)); break;
+          case 3: HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_tc<64, 4><<<tc_grid, TT_THREADS, TtCfg<64, 4>::SMEM, s>>>(
+                                                     nd, st, t0, cnt, fa, parts, flags)); break;
+          default: HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing_tc<128, 1><<<tc_grid, TT_THREADS, TtCfg<128, 1>::SMEM, s>>>(
+                                                     nd, st, t0, cnt, fa, parts, flags)); break;
+        }
       } else
         HF_LAUNCH(c, HF_PROF_TRAILING, k_trailing<T><<<dim3(tiles, tiles, cnt), 256, 0, s>>>(nd, st, t0, arena));
     }
@@ -1300,9 +1528,9 @@ int run_levels(hf_ctx* c) {
       if ((rc2 = hf_ensure(c->d_swsig, (size_t)cnt * sf * sizeof(int) + ((size_t)cnt + 1) * sizeof(int) + 64))) return rc2;
       int* sig = (int*)c->d_swsig.p;
       int* ngrp = sig + (size_t)cnt * sf;
-      HF_LAUNCH(c, HF_PROF_PANEL, k_swap_sigma<<<cnt, 256, (size_t)2 * maxld * sizeof(int), s>>>(
+      HF_LAUNCH(c, HF_PROF_PANEL_SWAP, k_swap_sigma<<<cnt, 256, (size_t)2 * maxld * sizeof(int), s>>>(
                                       nd, st, t0, (const int4*)swl, swc, sig, sf, sg, gcap, ngrp));
-      HF_LAUNCH(c, HF_PROF_PANEL, k_swap_apply<T><<<dim3((unsigned)maxld, (unsigned)cnt), 256, (size_t)maxld * sizeof(T), s>>>(
+      HF_LAUNCH(c, HF_PROF_PANEL_SWAP, k_swap_apply<T><<<dim3((unsigned)maxld, (unsigned)cnt), 256, (size_t)maxld * sizeof(T), s>>>(
                                       nd, st, t0, arena, sig, sf, sg, ngrp));
     }
     if (level_times) {

@@ -132,6 +132,10 @@ struct hf_ctx {
   DevBuf d_k12;                      // K12 block (L x M), the right-hand sides of Alg. 1 step 3
   DevBuf d_ozint;                    // scaling exponents of the emulated FP64 products
   DevBuf d_solve;                    // hf_solve scratch
+  // ---- code paths of the last calls (hf_info) ----
+  int path_cluster = 0;              // largest panel cluster of the last factorization
+  int path_global = 0;               // levels that ran the global-memory panel
+  int path_ldlt = 0;                 // S22 LDL^T kernel of the last hf_schur (hf_info.ldlt_kernel)
 };
 
 // analyze.cpp

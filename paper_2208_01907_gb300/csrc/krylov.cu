@@ -388,11 +388,11 @@ __device__ __forceinline__ void df_st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 waits for *flag != 0 (bounded); false (uniform) on timeout or abort.
-__device__ __forceinline__ bool df_wait(const int* flag, int* abort_word, int* s_ok) {
+// Thread 0 waits for *flag != 0 (at most `spin` polls); false (uniform) on timeout or abort.
+__device__ __forceinline__ bool df_wait(const int* flag, int* abort_word, int* s_ok, int spin) {
   if (threadIdx.x == 0) {
     int ok = 0;
-    for (int it = 0; it < DF_SPIN; ++it) {
+    for (int it = 0; it < spin; ++it) {
       if (df_ld_acquire(flag)) { ok = 1; break; }
       if (*(volatile int*)abort_word) break;
       __nanosleep(it < 64 ? 32 : 256);
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
                                                    const float* __restrict__ arena, float* vec, int m, int vs, int gt,
                                                    const int2* __restrict__ items, int nitems,
                                                    const int* __restrict__ blockbase, int* flags, int* counter,
-                                                   int* abort_word) {
+                                                   int* abort_word, int spin) {
   constexpr int APT = DF_K * DF_R / DF_TH;       // 4-byte A copies per thread per chunk
   constexpr int BPT = DF_K * DF_C / 4 / DF_TH;   // 16-byte B copies per thread per chunk
   struct Gemm { float A[DF_ST][DF_K][DF_R + 4]; float B[DF_ST][DF_K][DF_C + 4]; };
@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     if (FWD) {
       const int bend = tri ? code : nblk;                 // blocks [0, bend) feed this item
       for (int b = 0; b < bend && ok;) {
-        ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok);
+        ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
         const int e = df_ready_run(fl, gt, b, bend, true, &s_e);
         gemm_range(b * DF_R, min(ks, e * DF_R));
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     } else {
       if (f > ks) gemm_range(ks, f);                      // solved rows of the ancestors
       for (int b = nblk - 1; b > code && ok;) {
-        ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok);
+        ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
         const int e = df_ready_run(fl, gt, b, code, false, &s_e);
         gemm_range((e + 1) * DF_R, min(ks, (b + 1) * DF_R));
@@ -1820,6 +1820,8 @@ static size_t sweep_half_ints(const hf_ctx* c, int m) {
 }
 static size_t sweep_sync_bytes(const hf_ctx* c, int m) { return 2 * sweep_half_ints(c, m) * sizeof(int); }
 static int* sweep_err(hf_ctx* c) { return (int*)c->d_flags.p + FLAG_COUNT + 11; }
+// polls of a dataflow wait before it gives up (hf_opts.spin_limit, 0 = built in)
+static int sweep_spin(const hf_ctx* c) { return c->opts.spin_limit > 0 ? c->opts.spin_limit : DF_SPIN; }
 
 // Synchronises the stream; HF_ERR_TIMEOUT once a wait of a dataflow sweep has given up
 // (the word stays set until the next factorization: the solves of this factor are void).
@@ -1984,20 +1986,20 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
     const LevelDims D = level_dims(c, lev);
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
-    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m, vs));
+    HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m, vs));
     if (D.maxcb > 0) {
       const unsigned cx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxcb * m / 1024), 512);
       for (int slot = 0; slot < 2; ++slot)
-        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m, vs));
+        HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m, vs));
     }
     if constexpr (DF) if (use_df) {
       const int ni = c->sw_fwd_cnt[lev];
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(true));
         HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_fwd_start[lev], ni,
-                                                                          bbase, flags, sync + lev, sweep_err(c)));
+                                                                          bbase, flags, sync + lev, sweep_err(c), sweep_spin(c)));
       }
-      HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
+      HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
       tm.end(lev, cnt, D.maxf, D.maxks);
       continue;
     }
@@ -2010,7 +2012,7 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
       if (rx > 0)
         HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_gemm_upd<TF, TV, 0, fused><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
-    HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
+    HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
     tm.end(lev, cnt, D.maxf, D.maxks);
   }
 }
@@ -2039,15 +2041,15 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
     if (D.maxks == 0) continue;
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
-    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m, vs));
+    HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_bwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Ytmp, Xout, m, vs));
     if constexpr (DF) if (use_df) {
       const int ni = c->sw_bwd_cnt[lev];
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(false));
         HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_bwd_start[lev], ni,
-                                                                           bbase, flags, sync + lev, sweep_err(c)));
+                                                                           bbase, flags, sync + lev, sweep_err(c), sweep_spin(c)));
       }
-      HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
+      HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
       tm.end(lev, cnt, D.maxf, D.maxks);
       continue;
     }
@@ -2061,7 +2063,7 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
       if ((int)rx > 0)
         HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_gemm_upd<TF, TV, 1, fused><<<dim3(rx, gt, cnt), SGTH, 0, s>>>(nd, st, t0, arena, vec, m, b));
     }
-    HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
+    HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
     tm.end(lev, cnt, D.maxf, D.maxks);
   }
 }
@@ -2380,6 +2382,7 @@ static int bk_factor(hf_ctx* c) {
   if ((rc = hf_ensure(c->d_bk_blk, (size_t)M * 4 + 64))) return rc;
   if ((rc = hf_ensure(c->d_bk_dval, (size_t)M * 16 + 64 + (size_t)M * 16))) return rc;
   if ((rc = hf_ensure(c->d_bk_null, (size_t)M * 4 + 64))) return rc;
+  c->path_ldlt = 0;
   if (M == 0) { c->kernel_dim = 0; return HF_OK; }
   double* A = (double*)c->d_bk_lf.p + (size_t)M * M;     // working copy after Lf
   HF_CUDA_TRY(cudaMemcpyAsync(A, c->d_s22.p, (size_t)M * M * 8, cudaMemcpyDeviceToDevice, s));
@@ -2412,6 +2415,7 @@ static int bk_factor(hf_ctx* c) {
   const int bpc_R = bpc_C > 0 ? (M + bpc_C - 1) / bpc_C : 0;
   const size_t bpc_bytes = ((size_t)bpc_R * M + 8 * (size_t)M) * 8 + 2 * BPC_CMAX * 4 * 8 + 64;
   if (bpc_C > 0 && bpc_R <= BPC_RMAX && bpc_bytes <= BPC_SMEM) {
+    c->path_ldlt = 1;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(bpc_C); lc.blockDim = dim3(BPC_THREADS); lc.dynamicSmemBytes = bpc_bytes; lc.stream = s;
     cudaLaunchAttribute la[1];
@@ -2426,6 +2430,7 @@ static int bk_factor(hf_ctx* c) {
                                                                     (const int64_t*)c->d_diagpos.p,
                                                                     (const double*)c->d_kval.p, c->s22_noise, kd, mags)));
   } else if (M <= BP_MAX_M) {
+    c->path_ldlt = 2;
     // over all SMs (cooperative); partial maxima of two steps in flight per block
     static std::mutex bp_mu;
     static int bp_blocks = 0;
@@ -2457,6 +2462,7 @@ static int bk_factor(hf_ctx* c) {
     HF_LAUNCH(c, HF_PROF_DENSE_LDLT, HF_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_bp_coop, bp_blocks, BP_THREADS,
                                                                              args, 3 * (size_t)M * 8, s)));
   } else {
+    c->path_ldlt = 3;
     HF_LAUNCH(c, HF_PROF_DENSE_LDLT, k_bunch_parlett<<<1, 512, 0, s>>>(M, A, (double*)c->d_bk_lf.p, (int*)c->d_bk_perm.p, (int*)c->d_bk_blk.p,
                                       (double*)c->d_bk_dval.p, (int*)c->d_bk_null.p, c->opts.kernel_eps,
                                       c->opts.kernel_gap, (const int32_t*)c->d_lam2.p, (const int64_t*)c->d_diagpos.p,

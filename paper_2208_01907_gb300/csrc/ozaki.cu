@@ -491,13 +491,13 @@ int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const doub
   int* ea = iscratch;
   int* eb = same ? ea : iscratch + ma;
   const int ne = same ? ma : ma + mb;
-  HF_LAUNCH(c, HF_PROF_GRAM, k_fill_int<<<(ne + 255) / 256, 256, 0, s>>>(ea, ne, -1060));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_fill_int<<<(ne + 255) / 256, 256, 0, s>>>(ea, ne, -1060));
   const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, L / 1024), 512);
-  HF_LAUNCH(c, HF_PROF_GRAM, k_oz_exp_cols<<<dim3(gx, (ma + 127) / 128), 128, 0, s>>>(A, L, ma, ea));
-  HF_LAUNCH(c, HF_PROF_GRAM, k_oz_slice<<<slice_grid(oz_rows(ma) * Kg), 256, 0, s>>>(A, ma, L, 1, ma, ea, SA, Kg));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_cols<<<dim3(gx, (ma + 127) / 128), 128, 0, s>>>(A, L, ma, ea));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(ma) * Kg), 256, 0, s>>>(A, ma, L, 1, ma, ea, SA, Kg));
   if (!same) {
-    HF_LAUNCH(c, HF_PROF_GRAM, k_oz_exp_cols<<<dim3(gx, (mb + 127) / 128), 128, 0, s>>>(B, L, mb, eb));
-    HF_LAUNCH(c, HF_PROF_GRAM, k_oz_slice<<<slice_grid(oz_rows(mb) * Kg), 256, 0, s>>>(B, mb, L, 1, mb, eb, SB, Kg));
+    HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_cols<<<dim3(gx, (mb + 127) / 128), 128, 0, s>>>(B, L, mb, eb));
+    HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(mb) * Kg), 256, 0, s>>>(B, mb, L, 1, mb, eb, SB, Kg));
   }
   CUtensorMap ta, tb;
   if ((rc = slice_map(&ta, SA, ma, Kg, OZ_BI))) return rc;
@@ -513,7 +513,7 @@ int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const doub
   a.upper = same ? 1 : 0;
   dim3 grid((mb + OZ_BJ - 1) / OZ_BJ, (ma + OZ_BI - 1) / OZ_BI, (unsigned)nch);
   HF_LAUNCH(c, HF_PROF_GRAM, k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, a));
-  HF_LAUNCH(c, HF_PROF_GRAM, k_oz_reduce<<<(ma * mb + 255) / 256, 256, 0, s>>>(ma, mb, (int)nch, scratch, G, scale,
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_reduce<<<(ma * mb + 255) / 256, 256, 0, s>>>(ma, mb, (int)nch, scratch, G, scale,
                                                                                same ? 1 : 0));
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
@@ -533,10 +533,10 @@ int hf_oz_update(hf_ctx* c, int64_t L, int m, const double* A, const double* C, 
   uint4* SB = (uint4*)((unsigned char*)slices + sa_bytes);
   int* ea = iscratch;                      // L row exponents of A
   int* eb = iscratch + L;                  // m column exponents of C
-  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_exp<<<(unsigned)L, 32, 0, s>>>(A, m, 1, (int)L, m, ea));
-  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_exp<<<m, 32, 0, s>>>(C, 1, m, m, m, eb));
-  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_slice<<<slice_grid(oz_rows(L) * Kg), 256, 0, s>>>(A, L, m, m, 1, ea, SA, Kg));
-  HF_LAUNCH(c, HF_PROF_BLOCK_UPDATE, k_oz_slice<<<slice_grid(oz_rows(m) * Kg), 256, 0, s>>>(C, m, m, 1, m, eb, SB, Kg));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp<<<(unsigned)L, 32, 0, s>>>(A, m, 1, (int)L, m, ea));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp<<<m, 32, 0, s>>>(C, 1, m, m, m, eb));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(L) * Kg), 256, 0, s>>>(A, L, m, m, 1, ea, SA, Kg));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(m) * Kg), 256, 0, s>>>(C, m, m, 1, m, eb, SB, Kg));
   CUtensorMap ta, tb;
   if ((rc = slice_map(&ta, SA, L, Kg, OZ_BI))) return rc;
   if ((rc = slice_map(&tb, SB, m, Kg, OZ_BJ))) return rc;

@@ -25,9 +25,9 @@ EXPORTED = (
     "hf_get_s22", "hf_get_s22_factor", "hf_get_pivot_events", "hf_precond", "hf_profile",
     "hf_get_profile", "hf_profile_name", "hf_values_adjoint", "hf_precond_noalloc",
     "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis",
-    "hf_gram_fp64", "hf_update_fp64", "hf_k11_iterate", "hf_set_row_signs", "hf_free",
+    "hf_gram_fp64", "hf_update_fp64", "hf_k11_iterate", "hf_set_row_signs", "hf_set_spin_limit", "hf_free",
 )
-HF_NPROF = 13
+HF_NPROF = 16
 
 
 class hf_opts(C.Structure):
@@ -36,7 +36,7 @@ class hf_opts(C.Structure):
         ("gcr_tol", C.c_double), ("gcr_maxit", C.c_int), ("kernel_eps", C.c_double),
         ("kernel_gap", C.c_double), ("nd_leaf", C.c_int), ("nd_levels", C.c_int),
         ("delay_cap", C.c_int), ("panel", C.c_int), ("cuda_stream", C.c_void_p),
-        ("fp64_gemm", C.c_int), ("trailing", C.c_int),
+        ("fp64_gemm", C.c_int), ("trailing", C.c_int), ("null_test", C.c_int), ("spin_limit", C.c_int),
     ]
 
 
@@ -48,6 +48,8 @@ class hf_info(C.Structure):
         ("gcr_relres", C.c_double), ("solve_relres", C.c_double), ("factor_flops", C.c_double),
         ("front_bytes", C.c_int64), ("delay_retries", C.c_int32), ("precision", C.c_int32),
         ("trailing_flops", C.c_double), ("solve_factor_entries", C.c_int64),
+        ("panel_cluster", C.c_int32), ("panel_global", C.c_int32), ("sweep_blocks", C.c_int32),
+        ("ldlt_kernel", C.c_int32),
     ]
 
     def as_dict(self):
@@ -78,6 +80,7 @@ def lib():
     L.hf_analyze.argtypes = [i64, vp, vp, vp, i32, C.POINTER(hf_opts), C.POINTER(vp)]
     L.hf_factorize.argtypes = [vp, vp, dbl]
     L.hf_set_row_signs.argtypes = [vp, vp]
+    L.hf_set_spin_limit.argtypes = [vp, i32]
     L.hf_schur.argtypes = [vp]
     L.hf_solve.argtypes = [vp, i32, vp, i64, vp, i64]
     L.hf_get_split.argtypes = [vp, vp, vp, C.POINTER(hf_info)]
@@ -168,6 +171,7 @@ class HybridFactor:
         _check(lib().hf_analyze(self.L, _ptr(self._rowptr), _ptr(self._col), _ptr(crd), dim,
                                 C.byref(self.opts), C.byref(h)), "hf_analyze")
         self._h = h
+        self.generation = 0      # bumped by every factorize(): which factor the context holds
 
     # -- lifecycle ---------------------------------------------------------
     def free(self):
@@ -186,7 +190,13 @@ class HybridFactor:
         """vals_dev: torch float64 CUDA tensor with the CSR values of K-bar."""
         t = self.opts.tau if tau is None else tau
         v = _dev(vals_dev, "vals", self._col.shape[0])
+        self.generation += 1
         _check(lib().hf_factorize(self._h, v, float(t)), "hf_factorize")
+
+    def set_spin_limit(self, limit):
+        """Polls of a bounded wait of the triangular sweeps before HF_ERR_TIMEOUT (0 = built in)."""
+        _check(lib().hf_set_spin_limit(self._h, int(limit)), "hf_set_spin_limit")
+        self.opts.spin_limit = int(limit)
 
     def set_row_signs(self, sign):
         """sign: host array of L entries in {+1, -1} (Kbar = diag(sign) S, S symmetric), or None."""

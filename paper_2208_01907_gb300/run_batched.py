@@ -37,8 +37,11 @@ def main():
     bs = [torch.tensor(np.ascontiguousarray(consistent_rhs(s, 100 + i, args.nrhs, "uniform").T), device="cuda")
           for i, s in enumerate(systems)]
     xs = [torch.zeros_like(b) for b in bs]
-    one = [hf.HybridFactor(s.L, s.rowptr, s.col, s.coords) for s in systems]
-    bat = [hf.HybridFactor(s.L, s.rowptr, s.col, s.coords) for s in systems]
+    # saddle-point systems (mixed Darcy) with the null-pivot test, the others with the ratio
+    # test of Sec. 2.2 alone
+    nt = [int(bool(s.meta.get("saddle_point"))) for s in systems]
+    one = [hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, null_test=n) for s, n in zip(systems, nt)]
+    bat = [hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, null_test=n) for s, n in zip(systems, nt)]
 
     def run_one():
         for H, v, b, x in zip(one, vals, bs, xs):

@@ -27,15 +27,18 @@ def run_gpu(system, tau=1e-2, nrhs=1, rhs_seed=3, rhs_mode="uniform", solve=True
     return out
 
 
-def replay(system, H, tau, n_enlarge=4, slack=1e-4, dtype=np.float32):
-    """Oracle factorization on the GPU's tree, following the GPU's pivot decisions."""
+def replay(system, H, tau, n_enlarge=4, slack=1e-4, dtype=np.float32, null_test=None):
+    """Oracle factorization on the GPU's tree, following the GPU's pivot decisions, under the
+    rule the context ran with (the ratio test of Sec. 2.2, plus R3b if H asked for it)."""
+    if null_test is None:
+        null_test = bool(H.opts.null_test)
     _, sets = H.tree()
     ev = H.pivot_events()
     _, _, moved = H.pivots()
     q, K = O.scale_matrix(system.to_scipy())
     rp = {"node_pivots": [e[0] for e in ev[:-1]], "node_skipped": [e[2] for e in ev[:-1]],
           "lam0_pivots": ev[-1][0], "lam0_skipped": ev[-1][2]}
-    fac = O.threshold_factorize(K, sets, tau, n_enlarge, replay=rp, slack=slack, dtype=dtype)
+    fac = O.threshold_factorize(K, sets, tau, n_enlarge, replay=rp, slack=slack, dtype=dtype, null_test=null_test)
     return q, K, fac, moved
 
 

@@ -71,3 +71,18 @@ def test_adjoint_matches_oracle_gradient(n):
     go = O.adjoint_gradient(n, n, theta, xo, lam)
     assert np.abs(x.detach().cpu().numpy() - xo).max() <= 1e-9 * np.abs(xo).max()
     assert np.linalg.norm(g.cpu().numpy() - go) <= 1e-9 * np.linalg.norm(go)
+
+
+def test_backward_refuses_a_refactorized_context():
+    """One HybridFactor holds one factorization: a second hybrid_solve on it before the
+    first one's backward makes that backward raise instead of using the wrong factor."""
+    s, theta, b, xs, dirs, st, H = _model(16)
+    th = torch.tensor(theta, device="cuda", requires_grad=True)
+    bt = torch.tensor(b, device="cuda")
+    xst = torch.tensor(xs, device="cuda")
+    J1, _ = _J(H, th, st, s, bt, xst)
+    J2, _ = _J(H, 1.5 * th, st, s, bt, xst)
+    with pytest.raises(RuntimeError, match="factorized again"):
+        torch.autograd.grad(J1, th, retain_graph=True)
+    (g2,) = torch.autograd.grad(J2, th)              # the latest forward still differentiates
+    assert torch.isfinite(g2).all()

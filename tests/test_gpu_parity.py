@@ -26,24 +26,37 @@ CASES = {
     "cfg1_diffusion48": (lambda: diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1), 1, {}),
     "stokes8": (lambda: stokes3d(8, seed=2), 3, {"nd_leaf": 128}),
     "elasticity6": (lambda: elasticity3d(6, n_incl=1, incl=2, seed=3), 6, {"nd_leaf": 64}),
-    "darcy16": (lambda: darcy2d(16, 16, seed=4, n_islands=2, island=3), 1, {"nd_leaf": 64}),
+    "darcy16": (lambda: darcy2d(16, 16, seed=4, n_islands=2, island=3), 1, {"nd_leaf": 64, "null_test": 1}),
     "dirichlet20": (lambda: diffusion2d(20, 20, n_islands=2, island=3, contrast=1e6, dirichlet_x=True, seed=6), 0,
                     {"panel": 16}),
 }
 
+# Every case under the paper's rule (the ratio test of Sec. 2.2 alone, the default) and
+# with the optional null-pivot test R3b.  The mixed Darcy saddle point runs with R3b only:
+# under the ratio test alone an FP32 noise pivot of its singular zero-block structure
+# stays in K11 (its GPU and oracle float32 factors then differ in the digits the noise
+# decides), which the null-pivot test postpones.
+RULES = {"ratio": 0, "ratio+null": 1}
+CASE_RULES = [(n, r) for n in sorted(CASES) for r in RULES
+              if "null_test" not in CASES[n][2] or RULES[r] == CASES[n][2]["null_test"]]
 
-@pytest.fixture(scope="module", params=sorted(CASES))
+
+@pytest.fixture(scope="module", params=CASE_RULES, ids=[f"{n}-{r}" for n, r in CASE_RULES])
 def case(request):
-    make, kdim, opts = CASES[request.param]
+    name, rule = request.param
+    make, kdim, opts = CASES[name]
     s = make()
+    opts = {**opts, "null_test": RULES[rule]}
     out = run_gpu(s, tau=1e-2, **opts)
     q, K, fac, moved = replay(s, out["H"], 1e-2)
-    return dict(name=request.param, s=s, kdim=kdim, out=out, q=q, K=K, fac=fac, moved=moved)
+    return dict(name=name, rule=rule, s=s, kdim=kdim, out=out, q=q, K=K, fac=fac, moved=moved)
 
 
 def test_split_replay_bit_exact(case):
     fac, H = case["fac"], case["out"]["H"]
     assert fac.violations == []
+    if case["rule"] == "ratio":                      # the paper's rule postpones nothing on its own
+        assert all(len(e[2]) == 0 for e in H.pivot_events())
     order, lam2 = H.split()
     assert lam2.tolist() == fac.lambda2.tolist()
     assert order[:fac.N].tolist() == fac.lambda1_order.tolist()
@@ -161,11 +174,17 @@ def test_fp64_form_schur_and_solve():
     assert out["info"]["kernel_dim"] == 1
 
 
-@pytest.mark.parametrize("name", ["cfg1_diffusion48", "stokes8", "elasticity6", "darcy16"])
-def test_trailing_tensor_cores_match_fp32_simt(name):
+CASES["elasticity10"] = (lambda: elasticity3d(10, n_incl=3, incl=2, seed=3), 6, {})
+
+
+@pytest.mark.parametrize("name", ["cfg1_diffusion48", "stokes8", "elasticity6", "darcy16", "elasticity10"])
+def test_trailing_tensor_cores_match_fp32_simt(name, monkeypatch):
     """Precision form: the trailing updates on the tensor cores (exact 3 x BF16 split of
     FP32, six products, FP32 accumulate) against the FP32 SIMT updates: the same pivots,
-    pivots and factor entries within FP32 rounding, the same S22 to the GCR tolerance."""
+    pivots and factor entries within FP32 rounding, the same S22 to the GCR tolerance.
+    Every level takes the tensor cores here (HF_TC_MIN_ROWS=0), so fronts of every size,
+    ragged tiles and levels of hundreds of fronts go through the persistent tile map."""
+    monkeypatch.setenv("HF_TC_MIN_ROWS", "0")
     make, _, opts = CASES[name]
     s = make()
     tc_ = run_gpu(s, tau=1e-2, trailing=0, **opts)
@@ -321,10 +340,20 @@ def test_api_errors_without_state():
 
 # --------------------------------------------------------------------------- full-size configuration
 def test_full_size_stokes32_properties():
-    """The timed workload (3D Stokes-like, 32^3 nodes): properties that hold at any size."""
+    """The 3D Stokes-like workload at 32^3 nodes: properties that hold at any size.
+
+    With the ratio test of Sec. 2.2 alone at tau = 1e-2, FP32 noise pivots of the
+    singular saddle point pass the test at this size (they follow small pressure
+    pivots), K11 keeps part of the kernel, the block GCR cannot converge and the
+    solution misses the gate; the null-pivot test postpones them and the kernel reaches
+    S22.  Both are checked here."""
     import scipy.sparse as sp
     s = stokes3d(32, seed=2)
-    out = run_gpu(s, tau=1e-2, rhs_mode="solution")
+    lit = run_gpu(s, tau=1e-2, rhs_mode="solution", null_test=0)
+    assert lit["info"]["kernel_dim"] != 3 or lit["schur_rc"] != 0 or \
+        O.backward_error(s.to_scipy(), lit["x"], lit["b"]) > BWD_TOL
+    lit["H"].free()
+    out = run_gpu(s, tau=1e-2, rhs_mode="solution", null_test=1)
     H, info = out["H"], out["info"]
     assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
     assert info["kernel_dim"] == 3
@@ -447,7 +476,9 @@ def test_ldu_row_sign_form_matches_unsymmetric_oracle():
     J = sign.astype(np.float64)
     Kb = s.to_scipy()
     assert abs(Kb - Kb.T).max() > 0
-    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, nd_leaf=128)
+    # with the null-pivot test, coupled velocity and pressure rows reach Lambda_2 (S22 is then
+    # genuinely unsymmetric); the ratio test alone leaves only decoupled ones at this size
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, nd_leaf=128, null_test=1)
     H.set_row_signs(sign)
     vals = torch.tensor(s.val, device="cuda", dtype=torch.float64)
     H.factorize(vals, 1e-2)
@@ -485,7 +516,7 @@ def test_ldu_row_sign_form_matches_unsymmetric_oracle():
     # the symmetric matrix J K-bar without signs: the same numbers bit for bit (sign flips are exact)
     S = stokes3d(8, seed=2)
     np.testing.assert_array_equal(S.val, J[np.repeat(np.arange(s.L), np.diff(s.rowptr))] * s.val)
-    H2 = hf.HybridFactor(S.L, S.rowptr, S.col, S.coords, nd_leaf=128)
+    H2 = hf.HybridFactor(S.L, S.rowptr, S.col, S.coords, nd_leaf=128, null_test=1)
     H2.factorize(torch.tensor(S.val, device="cuda", dtype=torch.float64), 1e-2)
     H2.schur()
     assert H2.split()[1].tolist() == lam2.tolist()

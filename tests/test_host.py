@@ -34,7 +34,29 @@ def test_default_opts_and_error_strings():
     hf = _hf()
     o = hf.default_opts()
     assert o.tau == 1e-2 and o.n_enlarge == 4 and o.precision == hf.HF_PREC_MIXED
+    assert o.null_test == 0 and o.spin_limit == 0         # the ratio test of Sec. 2.2 alone
     assert hf.lib().hf_error_string(5) == b"block GCR did not converge"
+
+
+def test_binding_mirrors_the_header_structs_and_profile_classes():
+    # the ctypes structs and the profile class count follow include/hf.h field by field
+    import ctypes
+    hf = _hf()
+    header = open(os.path.join(ROOT, "include", "hf.h")).read()
+
+    def fields(struct):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + struct + ";", header).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        return [m.group(2) for m in re.finditer(r"(\w+\*?)\s+(\w+)\s*;", body)]
+
+    assert fields("hf_opts") == [f for f, _ in hf.hf.hf_opts._fields_]
+    assert fields("hf_info") == [f for f, _ in hf.hf.hf_info._fields_]
+    enum = re.search(r"HF_PROF_SCALE = 0,(.*?)HF_NPROF", header, re.S).group(1)
+    enum = re.sub(r"/\*.*?\*/", "", enum, flags=re.S)
+    assert hf.hf.HF_NPROF == 1 + len(re.findall(r"HF_PROF_\w+", enum))
+    names = [hf.lib().hf_profile_name(i).decode() for i in range(hf.hf.HF_NPROF)]
+    assert len(set(names)) == hf.hf.HF_NPROF and "unknown" not in names
+    assert hf.lib().hf_profile_name(hf.hf.HF_NPROF) == b"unknown"
 
 
 def test_host_analysis_reproduces_fig1():
@@ -305,3 +327,23 @@ def test_device_entries_fail_cleanly_without_a_gpu():
         assert e.value.code == 2                                # HF_ERR_STATE: nothing factorized
     assert H.info()["L"] == s.L
     H.free()
+
+
+def test_bench_fit_and_rooflines():
+    # the oracle's growth exponent is the least-squares slope in log-log; the per-kernel
+    # roofline divides the counted work of exactly the profiled launches by their time
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    pts = [(1000, 2.0), (2000, 2.0 * 2 ** 1.7), (4000, 2.0 * 4 ** 1.7)]
+    assert abs(bench.fit_exponent(pts) - 1.7) < 1e-12
+    assert abs(bench.extrapolate(2.0, 1000, 8000, 1.7) - 2.0 * 8 ** 1.7) < 1e-9
+    prof = {"trsv_fwd": (20.0, 40, 1e9, 34e9), "gram": (4.0, 2, 1e11, 1e9), "block_update": (6.0, 3, 2e11, 1e9),
+            "panel": (30.0, 60, 3e9, 1e9)}
+    r = bench.kernel_rooflines(prof, 2, trailing_tc=False)
+    assert r["k_sweep_df<1>"]["bound"] == "hbm"
+    assert abs(r["k_sweep_df<1>"]["achieved"] - 34e9 / 0.02 / 1e9) < 1e-6
+    oz = r["k_oz_mma"]
+    assert oz["ms_per_step"] == 5.0 and oz["launches_per_step"] == 2.5
+    assert abs(oz["achieved"] - 36 * 3e11 / 0.01 / 1e12) < 1e-6
+    assert r["k_panel_cl"]["bound"] == "alu" and r["k_panel_cl"]["ms_per_step"] == 15.0

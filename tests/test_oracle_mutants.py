@@ -105,6 +105,8 @@ MUTANTS = [
      ["eq1", "precond"]),
     ("null_test_not_accumulated", "G[rows] += np.abs(col * (row / d))",
      "G[rows] = np.abs(col * (row / d))", 0, ["null_pivot"]),
+    ("null_test_on_by_default", "null_test: bool = False) -> FactorResult:",
+     "null_test: bool = True) -> FactorResult:", 0, ["null_pivot"]),
     # Sec. 2.2 pivoting and postponing
     ("ratio_against_one", "if not (dg[t] >= tau * d_ref):", "if not (dg[t] >= tau):", 0,
      ["hand_ratio_previous"]),

@@ -526,16 +526,20 @@ def test_adjoint_gradient_matches_central_differences():
 # --------------------------------------------------------------------------- R3b null-pivot test
 def test_null_pivot_test_skips_cancelled_pivot():
     # index 2 keeps 1.5e-3 of a diagonal built from terms of size ~2: the ratio test to the
-    # previous pivot (0.5) passes at tau = 1e-3, the cancellation (null) test does not.
+    # previous pivot (0.5) passes at tau = 1e-3.  Sec. 2.2 postpones on that ratio alone, so
+    # by default all three are eliminated and only the enlargement (n = 1) moves index 2.
     a = np.sqrt(1 - 1.5e-3)
     K = sp.csr_matrix(np.array([[0.5, 0, 0], [0, 1.0, a], [0, a, 1.0]]))
-    fac = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-3, n_enlarge=1)
+    lit = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-3, n_enlarge=1)
+    assert lit.node_pivots[0].tolist() == [1, 0, 2]
+    assert lit.node_skipped[0].tolist() == [] and lit.lam0.tolist() == []
+    assert lit.lambda2.tolist() == [2]
+    # the optional cancellation (null) test R3b skips index 2 instead
+    fac = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-3, n_enlarge=1, null_test=True)
     assert fac.node_pivots[0].tolist() == [1, 0]
     assert fac.node_skipped[0].tolist() == [2]
     assert fac.lam0_skipped.tolist() == [2] and fac.lam0_pivots.tolist() == []
     assert fac.lambda2.tolist() == [0, 2]
-    off = O.threshold_factorize(K, [np.array([0, 1, 2])], tau=1e-3, n_enlarge=1, null_test=False)
-    assert off.node_pivots[0].tolist() == [1, 0, 2]
 
 
 # --------------------------------------------------------------------------- R11 Bunch-Parlett
@@ -774,3 +778,25 @@ def test_unsymmetric_hybrid_solve():
     b = consistent_rhs(t, 5, nrhs=2)
     x = qt[:, None] * O.hybrid_solve(res["K"], res["fac"].lambda2, res["X12"], res["bk"], res["kdim"], qt[:, None] * b)
     assert O.backward_error(Kt, x, b) < 1e-14
+
+
+# --------------------------------------------------------------------------- replay admissibility
+def test_replay_admits_the_rule_and_flags_other_choices():
+    # replaying the oracle's own decisions is admissible; a pivot order that takes a clearly
+    # smaller diagonal first, or an early stop, is reported; a near-tie inside the rounding
+    # of the compared values (relative slack) is admitted
+    K = sp.csr_matrix(np.diag([1.0, 0.5, 0.25, 0.2]))
+    nodes = [np.array([0, 1, 2, 3])]
+    own = O.threshold_factorize(K, nodes, tau=1e-2, n_enlarge=0)
+    rp = {"node_pivots": [own.node_pivots[0]], "node_skipped": [np.zeros(0, np.int64)],
+          "lam0_pivots": own.lam0_pivots, "lam0_skipped": np.zeros(0, np.int64)}
+    assert O.threshold_factorize(K, nodes, 1e-2, 0, replay=rp).violations == []
+    bad = dict(rp, node_pivots=[np.array([1, 0, 2, 3])])
+    v = O.threshold_factorize(K, nodes, 1e-2, 0, replay=bad).violations
+    assert any("< max" in m for m in v)
+    stop = dict(rp, node_pivots=[np.array([0, 1])], lam0_pivots=np.array([2, 3]))
+    assert any("stopped" in m for m in O.threshold_factorize(K, nodes, 1e-2, 0, replay=stop).violations)
+    Kt = sp.csr_matrix(np.diag([1.0, 1.0 - 2e-5, 0.5]))
+    tie = {"node_pivots": [np.array([1, 0, 2])], "node_skipped": [np.zeros(0, np.int64)],
+           "lam0_pivots": np.zeros(0, np.int64), "lam0_skipped": np.zeros(0, np.int64)}
+    assert O.threshold_factorize(Kt, [np.array([0, 1, 2])], 1e-2, 0, replay=tie).violations == []

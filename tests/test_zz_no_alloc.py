@@ -17,10 +17,16 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_precond_noalloc_matches_precond_on_two_calls():
+# both scratch layouts: the FP32 factor (FP32 sweep vectors and cast copies) and the FP64
+# factor of the plain double form (FP64 sweep vectors)
+FORMS = {"fp32_factor": 0, "fp64_factor": 1}
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_precond_noalloc_matches_precond_on_two_calls(form):
     import paper_2208_01907_gb300 as hf
     s = diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1)
-    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, precision=FORMS[form])
     H.factorize(torch.tensor(s.val, device="cuda"), 1e-2)
     rng = np.random.default_rng(7)
     for m in (3, 5):
@@ -34,12 +40,13 @@ def test_precond_noalloc_matches_precond_on_two_calls():
         assert np.linalg.norm(new - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
-def test_precond_noalloc_rejects_scratch_above_limit():
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_precond_noalloc_rejects_scratch_above_limit(form):
     import paper_2208_01907_gb300 as hf
     s = diffusion2d(48, 48, n_islands=6, island=4, contrast=1e8, seed=1)
-    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, precision=FORMS[form])
     H.factorize(torch.tensor(s.val, device="cuda"), 1e-2)
-    m = 2000                                   # (rows of all fronts + 3 L) * m * 4 B > 64 MiB
+    m = 2000                                   # (rows of all fronts + L) * m * (4 or 8) B > 64 MiB
     R = torch.zeros((s.L, m), dtype=torch.float64, device="cuda")
     W = torch.zeros_like(R)
     with pytest.raises(hf.HFError) as e:

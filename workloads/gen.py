@@ -29,7 +29,8 @@ class CsrSystem:
     val: np.ndarray             # float64, nnz
     coords: np.ndarray          # float64, L x dim (node / cell / face centres)
     kernel: np.ndarray | None   # float64, L x r basis of ker(K-bar) when known analytically
-    meta: dict = field(default_factory=dict)
+    meta: dict = field(default_factory=dict)   # generator parameters; "saddle_point": True marks
+                                               # a zero diagonal block ([A B^T; B 0] forms)
 
     @property
     def L(self) -> int:
@@ -222,7 +223,7 @@ def stokes3d(n=32, seed=2, mu_log10=(-3.0, 3.0), p_scale=None, name=None, delta=
     for d in range(3):
         kern[d:nv:3, d] = 1.0 / math.sqrt(n ** 3)
     return _finish(name or f"stokes3d_{n}", A, coords, kern, n=n, h=h, p_scale=p_scale, delta=delta,
-                   n_velocity=nv)
+                   n_velocity=nv, saddle_point=True)
 
 
 def row_sign_form(system: CsrSystem, sign: np.ndarray, name: str | None = None) -> CsrSystem:
@@ -386,7 +387,7 @@ def darcy2d(nx=32, ny=32, seed=4, n_islands=2, island=4, contrast=1e6, gap=2, na
     coords = np.concatenate([cfx, cfy, cc], axis=0)
     kern = np.zeros((L, 1))
     kern[nf:, 0] = 1.0 / math.sqrt(nx * ny)
-    return _finish(name or f"darcy2d_{nx}x{ny}", A, coords, kern, nx=nx, ny=ny)
+    return _finish(name or f"darcy2d_{nx}x{ny}", A, coords, kern, nx=nx, ny=ny, saddle_point=True)
 
 
 # --------------------------------------------------------------------------
