@@ -133,8 +133,9 @@ enum {
      panel_swap = the row interchanges applied after a level's panels, sweep_io = gathers and
      scatters of the solve vectors around each sweep level, tc_prep = operand preparation of
      the tensor-core products (exponents, slices and split-K reductions of the emulated FP64
-     products; the BF16 split of the panel for the tensor-core trailing update) */
-  HF_PROF_PANEL_SWAP, HF_PROF_SWEEP_IO, HF_PROF_TC_PREP, HF_NPROF
+     products; the BF16 split of the panel for the tensor-core trailing update),
+     diag_inverse = the inverses of the factor's 64 x 64 diagonal blocks for the sweeps */
+  HF_PROF_PANEL_SWAP, HF_PROF_SWEEP_IO, HF_PROF_TC_PREP, HF_PROF_DIAG_INV, HF_NPROF
 };
 
 /* Fill *opts with the defaults listed above.  Returns HF_ERR_ARG if opts is NULL. */

@@ -1695,6 +1695,7 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     }
     c->nnz_factor = nz;
     if ((rc = hf_sweep_plan(c))) return rc;
+    if ((rc = hf_diag_inverses(c))) return rc;
     c->front_prec = c->prec;
     c->factored = true;
     trailing_work(c, dbl ? 8 : 4);

@@ -98,6 +98,7 @@ struct hf_ctx {
   DevBuf d_vec;                      // per-front solve vectors (+ the sweep flags and tickets)
   size_t vec_cap = 0;
   DevBuf d_swplan;                   // dataflow sweeps: work items (forward, backward), block bases
+  DevBuf d_dinv;                     // dataflow sweeps: inverse of every 64 x 64 unit lower diagonal block
   std::vector<int> sw_fwd_start, sw_fwd_cnt, sw_bwd_start, sw_bwd_cnt;   // per level: item range
   int sw_blocks = 0;                 // 64-row diagonal blocks of all fronts
   // ---- split (host copy) ----
@@ -145,6 +146,7 @@ void hf_layout_fronts(hf_ctx* c);
 
 // krylov.cu: work-item lists of the dataflow sweeps, from the host front state
 int hf_sweep_plan(hf_ctx* c);   // capacities, ld, offsets (depends on opts.delay_cap)
+int hf_diag_inverses(hf_ctx* c);   // inverses of the diagonal blocks of the FP32 factor (after the plan)
 
 // Counts a kernel launch of class `cls` and, when profiling, brackets it with events.
 struct ProfScope {

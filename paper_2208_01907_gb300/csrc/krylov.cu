@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
                                                    const float* __restrict__ arena, float* vec, int m, int vs, int gt,
                                                    const int2* __restrict__ items, int nitems,
                                                    const int* __restrict__ blockbase, int* flags, int* counter,
-                                                   int* abort_word, int spin) {
+                                                   int* abort_word, int spin, const float* __restrict__ dinv) {
   constexpr int APT = DF_K * DF_R / DF_TH;       // 4-byte A copies per thread per chunk
   constexpr int BPT = DF_K * DF_C / 4 / DF_TH;   // 16-byte B copies per thread per chunk
   struct Gemm { float A[DF_ST][DF_K][DF_R + 4]; float B[DF_ST][DF_K][DF_C + 4]; };
@@ -480,10 +480,21 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     const int r0 = tri ? code * DF_R : ks + (-1 - code) * DF_R;
     const int nr = min(DF_R, (tri ? ks : f) - r0);
     int* fl = flags + (int64_t)blockbase[t] * gt + C;     // flag of block b: fl[b * gt]
-    if (tri) {                                           // diagonal block, staged early
-      for (int e = tid; e < TS * TS; e += DF_TH) {
-        const int r = e % TS, cc = e / TS;
-        Ls[r][cc] = (r < nr && cc < nr && r > cc) ? F[(r0 + r) + (int64_t)(r0 + cc) * ld] : 0.f;
+    // a triangle block stages the inverse of its unit lower diagonal block (made once per
+    // factorization by k_diag_inverse) and loads its own rows of v before it waits: neither
+    // is written by another item of the launch
+    float vpre[8][4];
+    if (tri) {
+      const float* Di = dinv + ((int64_t)blockbase[t] + code) * (TS * TS);
+      for (int e = tid; e < TS * TS; e += DF_TH) Ls[e / TS][e % TS] = Di[e];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = ty * 8 + i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + tx * 4 + j;
+          vpre[i][j] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * vs + c) : 0.f;
+        }
       }
     }
     // blocked summation: acc holds the products of at most DF_R consecutive k, then is
@@ -596,16 +607,39 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     for (int i = 0; i < 8; ++i) {
       const int r = ty * 8 + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int cc = tx * 4 + j, c = c0 + cc;
-        Vs[r][cc] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * vs + c) - tot[i][j] : 0.f;
-      }
+      for (int j = 0; j < 4; ++j) Vs[r][tx * 4 + j] = vpre[i][j] - tot[i][j];   // 0 outside the block
     }
     __syncthreads();
-    diag_solve<float, FWD, DF_C, DF_TH>(Ls, Vs, nr, tid);
-    for (int e = tid; e < nr * DF_C; e += DF_TH) {
-      const int r = e / DF_C, cc = e % DF_C;
-      if (c0 + cc < m) V[(int64_t)(r0 + r) * vs + c0 + cc] = Vs[r][cc];
+    // y = L_RR^-1 v (forward) or x = L_RR^-T v (backward) as one product with the staged
+    // inverse, in place of the row-by-row substitution: the triangle ends the chain of the
+    // front's blocks, and a product has no dependency from row to row
+    {
+      float o[8][4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[i][j] = 0.f;
+      const int qlo = FWD ? 0 : ty * 8, qhi = FWD ? min(nr, ty * 8 + 8) : nr;
+      for (int q = qlo; q < qhi; ++q) {
+        float a[8], b[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = FWD ? Ls[ty * 8 + i][q] : Ls[q][ty * 8 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Vs[q][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) o[i][j] += a[i] * b[j];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = ty * 8 + i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = c0 + tx * 4 + j;
+          if (r < nr && c < m) V[(int64_t)(r0 + r) * vs + c] = o[i][j];
+        }
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -613,6 +647,37 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
       df_st_release(fl + (int64_t)code * gt, 1);
     }
   }
+}
+
+// Inverse of the unit lower triangular 64 x 64 diagonal block of a triangle item (R of front
+// t, rows [64R, 64R + nr) of the solved columns), for the dataflow sweeps: column j of
+// L_RR^-1 by forward substitution on e_j (thread j), x_i = -sum_{j <= q < i} L_iq x_q in
+// ascending q, zero outside the nr x nr block; stored row-major at the block's index.
+__global__ void __launch_bounds__(TS) k_diag_inverse(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                                                     const float* __restrict__ arena, const int2* __restrict__ items,
+                                                     const int* __restrict__ blockbase, float* __restrict__ dinv) {
+  const int2 itm = items[blockIdx.x];
+  if (itm.y < 0) return;                               // contribution block
+  const int t = itm.x, R = itm.y, j = threadIdx.x;
+  const NodeDesc d = nd[t];
+  const int r0 = R * TS, nr = min(TS, st[t].ksolve - r0);
+  const float* F = arena + d.front_off;
+  const int64_t ld = d.ld;
+  __shared__ float Ls[TS][TS + 1];
+  __shared__ float Xs[TS][TS + 1];
+  for (int e = j; e < TS * TS; e += TS) {
+    const int r = e % TS, cc = e / TS;
+    Ls[r][cc] = (r < nr && cc < nr && r > cc) ? F[(r0 + r) + (int64_t)(r0 + cc) * ld] : 0.f;
+  }
+  __syncthreads();
+  for (int i = 0; i < TS; ++i) {
+    float v = i == j ? 1.f : 0.f;
+    for (int q = j; q < i; ++q) v -= Ls[i][q] * Xs[q][j];
+    Xs[i][j] = (i < nr && j < nr) ? v : 0.f;
+  }
+  __syncthreads();
+  float* D = dinv + ((int64_t)blockbase[t] + R) * (TS * TS);
+  for (int e = j; e < TS * TS; e += TS) D[e] = Xs[e / TS][e % TS];
 }
 
 // r (FP64) -> lower precision with Lambda_2 rows zeroed (the cast of Sec. 3.1)
@@ -1888,6 +1953,27 @@ static const int* sweep_bbase(const hf_ctx* c) {
   return (const int*)((const char*)c->d_swplan.p + pairs * 2 * sizeof(int32_t));
 }
 
+// The inverses of every diagonal block of the FP32 factor, for the dataflow sweeps (one CTA
+// per triangle item of the forward lists; called after hf_sweep_plan)
+int hf_diag_inverses(hf_ctx* c) {
+  if (c->prec == HF_PREC_FP64) return HF_OK;           // the FP64 factor uses the per-block sweeps
+  int rc;
+  if ((rc = hf_ensure(c->d_dinv, (size_t)std::max(1, c->sw_blocks) * TS * TS * sizeof(float) + 64))) return rc;
+  cudaStream_t s = hf_stream(c);
+  const int2* items = (const int2*)c->d_swplan.p;
+  for (int lev = 0; lev <= c->m; ++lev) {
+    const int ni = c->sw_fwd_cnt[lev];
+    if (ni > 0)
+      HF_LAUNCH(c, HF_PROF_DIAG_INV, k_diag_inverse<<<ni, TS, 0, s>>>((const NodeDesc*)c->d_nodes.p,
+                                                                   (const NodeState*)c->d_state.p,
+                                                                   (const float*)c->d_front.p,
+                                                                   items + c->sw_fwd_start[lev], sweep_bbase(c),
+                                                                   (float*)c->d_dinv.p));
+  }
+  HF_CUDA_TRY(cudaGetLastError());
+  return HF_OK;
+}
+
 // CTAs of a dataflow sweep launch: all resident at once is not required, only useful
 static int sweep_grid(bool fwd) {
   static std::mutex mu;
@@ -1997,7 +2083,8 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(true));
         HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_fwd_start[lev], ni,
-                                                                          bbase, flags, sync + lev, sweep_err(c), sweep_spin(c)));
+                                                                          bbase, flags, sync + lev, sweep_err(c), sweep_spin(c),
+                                                                          (const float*)c->d_dinv.p));
       }
       HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_store<TF, TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, arena, rowid, vec, Ytmp, m, vs));
       tm.end(lev, cnt, D.maxf, D.maxks);
@@ -2047,7 +2134,8 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(false));
         HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_bwd_start[lev], ni,
-                                                                           bbase, flags, sync + lev, sweep_err(c), sweep_spin(c)));
+                                                                           bbase, flags, sync + lev, sweep_err(c), sweep_spin(c),
+                                                                          (const float*)c->d_dinv.p));
       }
       HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_bwd_store<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Xout, m, vs));
       tm.end(lev, cnt, D.maxf, D.maxks);

@@ -2,7 +2,8 @@
 
     python -m paper_2208_01907_gb300.run_case --n 32 --phase schur
 
-builds the 3D Stokes-like system of the benchmark at n^3 nodes, runs `factorize`
+builds the 3D Stokes-like system (or with --workload elasticity the Q1 elasticity system
+of the benchmark) at n^3 nodes, runs `factorize`
 (twice with --warm, so that the delayed-row capacity has settled), then `schur` and
 `solve` as requested by --phase, and prints one line.  --phase gram / update runs one
 block-GCR product (hf_gram_fp64 / hf_update_fp64) on seeded L x m operands instead;
@@ -29,10 +30,12 @@ def main():
     ap.add_argument("--m", type=int, default=388, help="columns of the gram / update operands")
     ap.add_argument("--warm", action="store_true", help="factorize twice before the measured phases")
     ap.add_argument("--fp64-gemm", type=int, default=0)
+    ap.add_argument("--workload", choices=["stokes", "elasticity"], default="stokes",
+                    help="Stokes-like saddle point (null-pivot test) or Q1 elasticity (ratio test alone)")
     args = ap.parse_args()
     import torch
     import paper_2208_01907_gb300 as hf
-    from workloads import stokes3d, consistent_rhs
+    from workloads import stokes3d, elasticity3d, consistent_rhs
 
     if args.phase in ("gram", "update"):
         # one product of the block GCR at the workload's shape (L of the n^3 Stokes-like
@@ -54,8 +57,12 @@ def main():
         torch.cuda.synchronize()
         print(f"run_case {args.phase} L={s.L} m={args.m}")
         return
-    s = stokes3d(args.n, seed=2)
-    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, fp64_gemm=args.fp64_gemm)
+    if args.workload == "elasticity":
+        s = elasticity3d(args.n, seed=3, n_incl=min(8, args.n // 3), incl=4 if args.n >= 24 else 2)
+        H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, fp64_gemm=args.fp64_gemm)
+    else:
+        s = stokes3d(args.n, seed=2)
+        H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, fp64_gemm=args.fp64_gemm, null_test=1)
     vals = torch.tensor(s.val, device="cuda", dtype=torch.float64)
     if args.warm:
         H.factorize(vals, 1e-2)
