@@ -77,8 +77,10 @@ typedef struct {
   int    panel;          /* pivots per panel of the front factorization; default 64 */
   void*  cuda_stream;    /* cudaStream_t; NULL = default stream */
   int    fp64_gemm;      /* FP64 Grams and block updates of block GCR: 0 = emulated on the BF16
-                            tensor cores with exact slice products (FP64 accuracy), 1 = FP64
-                            units; default 0 */
+                            tensor cores with exact slice products (FP64 accuracy normwise, i.e.
+                            relative to the largest entries of each column; hf_schur and hf_solve
+                            run a block GCR that stagnates above gcr_tol again with the FP64
+                            units, counted in hf_info.gcr_restarts), 1 = FP64 units; default 0 */
   int    trailing;       /* trailing updates of the FP32 factor: 0 = tensor cores for the tree
                             levels whose largest front has >= 256 rows (exact 3 x BF16 split of
                             FP32, six products, FP32 accumulation in TMEM; FP32 SIMT for the
@@ -122,6 +124,9 @@ typedef struct {
   int32_t sweep_blocks;   /* largest number of 64-row diagonal blocks of one front in the sweeps */
   int32_t ldlt_kernel;    /* S22 LDL^T of the last hf_schur: 0 none (M = 0), 1 one cluster with S22
                              in distributed shared memory, 2 cooperative grid, 3 one block */
+  int32_t gcr_restarts;   /* block GCR runs since the last hf_schur began (its own and those of the
+                             hf_solve calls after it) that stagnated above gcr_tol with the
+                             emulated FP64 products and were run again with the native ones */
 } hf_info;
 
 /* Kernel classes of the profile (hf_get_profile). */

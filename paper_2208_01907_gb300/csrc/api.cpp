@@ -338,6 +338,7 @@ int hf_get_info(hf_ctx* c, hf_info* info) {
   info->panel_cluster = c->path_cluster;
   info->panel_global = c->path_global;
   info->ldlt_kernel = c->path_ldlt;
+  info->gcr_restarts = c->gcr_restarts;
   info->front_bytes = c->d_front.p ? (int64_t)c->d_front.bytes : 0;
   info->delay_retries = c->delay_retries;
   info->precision = c->prec;

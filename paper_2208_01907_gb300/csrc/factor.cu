@@ -374,6 +374,31 @@ __device__ __forceinline__ T dot_sub_seq(T acc, const T* __restrict__ a, const T
   return acc;
 }
 
+// smallest float >= x (for a float g, g >= x exactly when g >= ceil_float(x); NaN stays NaN)
+__device__ __forceinline__ float ceil_float(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+}
+
+// the ratio-test threshold in the factor's type: g >= x exactly when g >= thr_up<T>(x)
+template <typename T> __device__ __forceinline__ T thr_up(double x);
+template <> __device__ __forceinline__ float thr_up<float>(double x) { return ceil_float(x); }
+template <> __device__ __forceinline__ double thr_up<double>(double x) { return x; }
+
+// the data pushed with a candidate row into a slot of every CTA of the cluster
+template <typename T> struct __align__(16) PclMeta {
+  T key, G, diag, dg;                          // pivot key, term magnitude, diagonal entry, running diagonal
+  int sid, pos, rid, p0;                       // original index, front position, row id, position before pivoting
+};
+template <typename T>
+__device__ __forceinline__ void pcl_store_meta(PclMeta<T>* dst, const PclMeta<T>& m) {
+  const int4* src = reinterpret_cast<const int4*>(&m);
+  int4* d = reinterpret_cast<int4*>(dst);
+#pragma unroll
+  for (int u = 0; u < (int)(sizeof(PclMeta<T>) / 16); ++u) d[u] = src[u];
+}
+
 constexpr int PCL_THREADS = 512;
 constexpr int PCL_RPT = 2;                    // rows per thread: Rcap <= PCL_RPT * PCL_THREADS
 constexpr int PCL_CMAX = 16;
@@ -404,6 +429,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   __shared__ T s_bk;
   __shared__ int s_bp, s_act, s_w;
   __shared__ int s_swa[PCL_SWAPS], s_swb[PCL_SWAPS];
+  __shared__ T s_thr;                          // tau |previous pivot| rounded up to T
   const int rank = (int)cl.block_rank();
   const int t = t0 + (int)(blockIdx.x / (unsigned)C);
   const NodeDesc d = nd[t];
@@ -432,15 +458,9 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   T* wv = diagl + Rcap;                        // nb
   T* dpiv = wv + nb;                           // nb: pivots of this panel
   T* prow = dpiv + nb;                         // [2][SLOTS][nb] pushed panel rows
-  T* pG = prow + 2 * PCL_SLOTS * nb;           // [2][SLOTS]
-  T* pdiag = pG + 2 * PCL_SLOTS;
-  T* pdg = pdiag + 2 * PCL_SLOTS;
-  T* pkey = pdg + 2 * PCL_SLOTS;               // [2][SLOTS]
-  int* psid = (int*)(pkey + 2 * PCL_SLOTS);    // [2][SLOTS]
-  int* ppos = psid + 2 * PCL_SLOTS;
-  int* prid = ppos + 2 * PCL_SLOTS;
-  int* pp0 = prid + 2 * PCL_SLOTS;
-  int* sidl = pp0 + 2 * PCL_SLOTS;             // Rcap
+  // [2][SLOTS] pushed row data, one 16-byte aligned record per slot (stored with vector stores)
+  PclMeta<T>* pm = (PclMeta<T>*)(((uintptr_t)(prow + 2 * PCL_SLOTS * nb) + 15) & ~(uintptr_t)15);
+  int* sidl = (int*)(pm + 2 * PCL_SLOTS);      // Rcap
   int* ridl = sidl + Rcap;                     // Rcap
   int* pos0l = ridl + Rcap;                    // Rcap
   const int R = (f - k0 + C - 1) / C;
@@ -456,7 +476,8 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
     ridl[l] = rid[p];
     pos0l[l] = pos0[p];
   }
-  double dref = S->dref;
+  double dref = S->dref;                       // kept by the last thread
+  if (tid == nt - 1) s_thr = thr_up<T>(tau * dref);
   int k = k0;
   bool stopped = false;
   int it = 0;
@@ -470,15 +491,10 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       cl.map_shared_rank(prow, r)[(size_t)base * nb + c] = P[(size_t)l * ps + c];
     }
     if (tid < C) {
-      const int r = tid;
-      cl.map_shared_rank(pkey, r)[base] = key;
-      cl.map_shared_rank(psid, r)[base] = sidl[l];
-      cl.map_shared_rank(ppos, r)[base] = p;
-      cl.map_shared_rank(prid, r)[base] = ridl[l];
-      cl.map_shared_rank(pp0, r)[base] = pos0l[l];
-      cl.map_shared_rank(pG, r)[base] = Gl[l];
-      cl.map_shared_rank(pdiag, r)[base] = diagl[l];
-      cl.map_shared_rank(pdg, r)[base] = dgl[l];
+      PclMeta<T> mt;
+      mt.key = key; mt.G = Gl[l]; mt.diag = diagl[l]; mt.dg = dgl[l];
+      mt.sid = sidl[l]; mt.pos = p; mt.rid = ridl[l]; mt.p0 = pos0l[l];
+      pcl_store_meta(cl.map_shared_rank(pm, tid) + base, mt);
     }
   };
   // The row interchanges of the columns of earlier panels, [0, k0), are not needed by this
@@ -551,12 +567,13 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       if (pbest >= 0) {
         push_row(buf, rank, pbest, s_bk, kk);
       } else if (tid < C) {
-        cl.map_shared_rank(pkey, tid)[base] = T(-2);
-        cl.map_shared_rank(psid, tid)[base] = 0x7fffffff;
-        cl.map_shared_rank(ppos, tid)[base] = -1;
+        PclMeta<T> mt = {};
+        mt.key = T(-2); mt.sid = 0x7fffffff; mt.pos = -1;
+        pcl_store_meta(cl.map_shared_rank(pm, tid) + base, mt);
       }
       if (owner(k) == rank) push_row(buf, PCL_CMAX, k, T(0), kk);
-      if (owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, T(0), kk);
+      // row nact-1 is read only when a candidate is postponed alone (the null-pivot test)
+      if (tau_null > 0.0 && owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, T(0), kk);
     }
     if (C > 1) cl.sync(); else __syncthreads();                            // the only cluster barrier
     // 3. the decision from the local slots (the same in every CTA): the argmax by one warp,
@@ -566,7 +583,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       // argmax over the C slots by the lanes (the order is strict: ids are unique)
       T gk = T(-2);
       int gi = 0x7fffffff, gw = -1;
-      if (tid < C && ppos[sb + tid] >= 0) { gk = pkey[sb + tid]; gi = psid[sb + tid]; gw = tid; }
+      if (tid < C && pm[sb + tid].pos >= 0) { gk = pm[sb + tid].key; gi = pm[sb + tid].sid; gw = tid; }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ok = __shfl_xor_sync(0xffffffffu, gk, o);
@@ -576,15 +593,17 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       }
       if (tid == 0) {
         int a2 = 0;
-        if (!((double)gk >= tau * dref)) a2 = 1;                                 // ratio test (R2/R3)
-        else if (!((double)gk >= tau_null * (double)pG[sb + gw])) a2 = 2;       // null pivot (R3b)
+        // ratio test (R2/R3) against the threshold in the factor's type (exact: gk is a T,
+        // s_thr the smallest T >= tau |d_prev|); the null-pivot test (R3b) only when asked for
+        if (!(gk >= s_thr)) a2 = 1;
+        else if (tau_null > 0.0 && !((double)gk >= tau_null * (double)pm[sb + gw].G)) a2 = 2;
         s_act = a2;
         s_w = gw;
       }
     }
     __syncthreads();
     const int act = s_act, wsl = sb + s_w;
-    const int q = s_w >= 0 ? ppos[wsl] : -1;
+    const int q = s_w >= 0 ? pm[wsl].pos : -1;
     if (act == 1) { stopped = true; break; }
     if (act == 2) {
       // 4a. postpone the null candidate: swap q <-> b = nact-1 (both candidates)
@@ -603,16 +622,16 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
           const int l = q - p0;
           for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = prow[(size_t)bsl * nb + c];
           if (tid == 0) {
-            dgl[l] = pdg[bsl]; Gl[l] = pG[bsl]; diagl[l] = pdiag[bsl];
-            sidl[l] = psid[bsl]; ridl[l] = prid[bsl]; pos0l[l] = pp0[bsl];
+            dgl[l] = pm[bsl].dg; Gl[l] = pm[bsl].G; diagl[l] = pm[bsl].diag;
+            sidl[l] = pm[bsl].sid; ridl[l] = pm[bsl].rid; pos0l[l] = pm[bsl].p0;
           }
         }
         if (owner(b) == rank) {
           const int l = b - p0;
           for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = prow[(size_t)wsl * nb + c];
           if (tid == 0) {
-            dgl[l] = pdg[wsl]; Gl[l] = pG[wsl]; diagl[l] = pdiag[wsl];
-            sidl[l] = psid[wsl]; ridl[l] = prid[wsl]; pos0l[l] = pp0[wsl];
+            dgl[l] = pm[wsl].dg; Gl[l] = pm[wsl].G; diagl[l] = pm[wsl].diag;
+            sidl[l] = pm[wsl].sid; ridl[l] = pm[wsl].rid; pos0l[l] = pm[wsl].p0;
           }
         }
         // middle (j in (q, b): (j, q) <-> (b, j)) and lower (i > b: (i, q) <-> (i, b)) parts by row owners
@@ -640,15 +659,15 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       const int l = k - p0;
       for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rq[c];
       if (tid == 0) {
-        sidl[l] = psid[wsl]; ridl[l] = prid[wsl]; pos0l[l] = pp0[wsl]; Gl[l] = pG[wsl];
+        sidl[l] = pm[wsl].sid; ridl[l] = pm[wsl].rid; pos0l[l] = pm[wsl].p0; Gl[l] = pm[wsl].G;
       }
     }
     if (q != k && owner(q) == rank) {
       const int l = q - p0;
       for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rk[c];
       if (tid == 0) {
-        dgl[l] = pdg[ksl]; Gl[l] = pG[ksl]; diagl[l] = pdiag[ksl];
-        sidl[l] = psid[ksl]; ridl[l] = prid[ksl]; pos0l[l] = pp0[ksl];
+        dgl[l] = pm[ksl].dg; Gl[l] = pm[ksl].G; diagl[l] = pm[ksl].diag;
+        sidl[l] = pm[ksl].sid; ridl[l] = pm[ksl].rid; pos0l[l] = pm[ksl].p0;
       }
     }
     __syncthreads();
@@ -677,7 +696,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
     }
     if (q != k) defer_swap(k, q);                      // rows k and q over [0, k0)
     // d_k by every thread: the owner's operations on the winner's row
-    const T dk = dot_sub_seq(pdiag[wsl], rq, wv, kk);
+    const T dk = dot_sub_seq(pm[wsl].diag, rq, wv, kk);
     // 6. c_i = A(i, k) - sum_c L(i, c) w_c; L(i, k) = c_i / d_k; diagonals and magnitudes
 #pragma unroll
     for (int j = 0; j < PCL_RPT; ++j) {
@@ -696,7 +715,12 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       }
     }
     if (tid == 0) dpiv[kk] = dk;
-    if (tid == 0) dref = fabs((double)dk);     // used by the deciding thread only
+    // the next threshold, in FP64, by the last thread: it has the fewest rows of the CTA,
+    // so this latency stays off the pivot's critical path
+    if (tid == nt - 1) {
+      dref = fabs((double)dk);
+      s_thr = thr_up<T>(tau * dref);
+    }
     ++k;
     ++it;
   }
@@ -721,10 +745,10 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   if (rank == 0 && tid == 0) {
     S->kp0 = k0;
     S->k = k;
-    S->dref = dref;
     S->nact = nact;
     if (stopped) S->stopped = 1;
   }
+  if (rank == 0 && tid == nt - 1) S->dref = dref;
   cl.sync();                               // no CTA leaves while its shared memory may be written
 }
 

@@ -137,6 +137,7 @@ struct hf_ctx {
   int path_cluster = 0;              // largest panel cluster of the last factorization
   int path_global = 0;               // levels that ran the global-memory panel
   int path_ldlt = 0;                 // S22 LDL^T kernel of the last hf_schur (hf_info.ldlt_kernel)
+  int gcr_restarts = 0;              // block GCR runs restarted with native FP64 products (hf_info)
 };
 
 // analyze.cpp

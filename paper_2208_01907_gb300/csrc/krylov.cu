@@ -481,21 +481,10 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     const int nr = min(DF_R, (tri ? ks : f) - r0);
     int* fl = flags + (int64_t)blockbase[t] * gt + C;     // flag of block b: fl[b * gt]
     // a triangle block stages the inverse of its unit lower diagonal block (made once per
-    // factorization by k_diag_inverse) and loads its own rows of v before it waits: neither
-    // is written by another item of the launch
-    float vpre[8][4];
+    // factorization by k_diag_inverse) before it waits
     if (tri) {
       const float* Di = dinv + ((int64_t)blockbase[t] + code) * (TS * TS);
       for (int e = tid; e < TS * TS; e += DF_TH) Ls[e / TS][e % TS] = Di[e];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = ty * 8 + i;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = c0 + tx * 4 + j;
-          vpre[i][j] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * vs + c) : 0.f;
-        }
-      }
     }
     // blocked summation: acc holds the products of at most DF_R consecutive k, then is
     // added into tot (the error of a long FP32 dot product grows with its length; this
@@ -607,7 +596,10 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     for (int i = 0; i < 8; ++i) {
       const int r = ty * 8 + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Vs[r][tx * 4 + j] = vpre[i][j] - tot[i][j];   // 0 outside the block
+      for (int j = 0; j < 4; ++j) {
+        const int cc = tx * 4 + j, c = c0 + cc;
+        Vs[r][cc] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * vs + c) - tot[i][j] : 0.f;
+      }
     }
     __syncthreads();
     // y = L_RR^-1 v (forward) or x = L_RR^-T v (backward) as one product with the staged
@@ -2461,6 +2453,23 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
   return conv ? HF_OK : HF_ERR_NOT_CONVERGED;
 }
 
+// Block GCR as hf_schur and hf_solve run it: with the emulated FP64 products, whose error
+// is normwise (relative to the largest entries of each column), an iteration on vectors
+// whose entries span many orders of magnitude can stagnate above the tolerance; it is then
+// run again from the start with the native FP64 products (c->gcr_restarts counts these).
+static int block_gcr_robust(hf_ctx* c, int m, const double* B, double* X, int* iters, double* relres) {
+  int rc = block_gcr(c, m, B, X, iters, relres);
+  if (c->opts.fp64_gemm != 0 || (rc != HF_OK && rc != HF_ERR_NOT_CONVERGED) || !(*relres > c->opts.gcr_tol))
+    return rc;
+  const int it0 = *iters;
+  c->opts.fp64_gemm = 1;
+  rc = block_gcr(c, m, B, X, iters, relres);
+  c->opts.fp64_gemm = 0;
+  *iters += it0;
+  c->gcr_restarts++;
+  return rc;
+}
+
 static int bk_factor(hf_ctx* c) {
   cudaStream_t s = hf_stream(c);
   const int M = (int)c->M;
@@ -2587,7 +2596,8 @@ int hf_schur_impl(hf_ctx* c) {
       HF_LAUNCH(c, HF_PROF_SCHUR, k_extract_k12<<<M, 128, 0, s>>>(M, (const int64_t*)c->d_rowptr.p, (const int32_t*)c->d_col.p,
                                       (const double*)c->d_kval.p, (const int32_t*)c->d_lam2.p,
                                       (const int32_t*)c->d_lam2pos.p, B));
-      grc = block_gcr(c, M, B, X12, &c->gcr_iters, &c->gcr_relres);
+      c->gcr_restarts = 0;
+      grc = block_gcr_robust(c, M, B, X12, &c->gcr_iters, &c->gcr_relres);
       if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
       // error estimate of S22 for the kernel rule: E = K21 Q^-1 (K12 - K11 X12)
       {
@@ -2666,7 +2676,7 @@ int hf_solve_impl(hf_ctx* c, int nrhs, const double* b, int64_t ldb, double* x, 
     // Alg. 2: y1 by block GCR on K11, y2 = b2 - K21 y1, S22 x2 = y2, x1 = y1 - X12 x2
     HF_CUDA_TRY(cudaMemcpyAsync(y, bi, blk * 8, cudaMemcpyDeviceToDevice, s));
     if (M) HF_LAUNCH(c, HF_PROF_VECTOR, k_zero_lam2_rows<<<nblk((int64_t)M * m, 256), 256, 0, s>>>(M, m, (const int32_t*)c->d_lam2.p, y));
-    grc = block_gcr(c, m, y, y1, &c->solve_iters, &c->solve_relres);
+    grc = block_gcr_robust(c, m, y, y1, &c->solve_iters, &c->solve_relres);
     if (grc && grc != HF_ERR_NOT_CONVERGED) return grc;
     if (M) {
       HF_LAUNCH(c, HF_PROF_SCHUR, k_schur_rows<<<nblk((int64_t)M * 32, 256), 256, 0, s>>>(M, m, (const int64_t*)c->d_rowptr.p,

@@ -49,7 +49,7 @@ class hf_info(C.Structure):
         ("front_bytes", C.c_int64), ("delay_retries", C.c_int32), ("precision", C.c_int32),
         ("trailing_flops", C.c_double), ("solve_factor_entries", C.c_int64),
         ("panel_cluster", C.c_int32), ("panel_global", C.c_int32), ("sweep_blocks", C.c_int32),
-        ("ldlt_kernel", C.c_int32),
+        ("ldlt_kernel", C.c_int32), ("gcr_restarts", C.c_int32),
     ]
 
     def as_dict(self):

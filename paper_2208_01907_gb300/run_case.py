@@ -94,7 +94,9 @@ def main():
         H.solve(bt, xt)
     torch.cuda.synchronize()
     i = H.info()
-    print(f"run_case n={args.n} L={i['L']} M={i['M']} gcr_iters={i['gcr_iters']} kernel_dim={i['kernel_dim']}")
+    launches = {k: v[1] for k, v in H.get_profile().items() if v[1]}
+    print(f"run_case n={args.n} L={i['L']} M={i['M']} gcr_iters={i['gcr_iters']} kernel_dim={i['kernel_dim']} "
+          f"launches={launches}")
 
 
 if __name__ == "__main__":
