@@ -1120,12 +1120,15 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
   const int G = (int)gridDim.x;
   const int ntile = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
 
-  if (warp == 0 && lane == 0) {
-    // ---- producer: bulk copies of the pre-split parts of tile it into stage it % 2
+  if (warp == 0) {
+    // ---- producer: bulk copies of the pre-split parts of tile it into stage it % 2, the 48
+    // copies (3 parts x 8 k-groups for each operand) issued by the 32 lanes of the warp
     int issued = 0;
     for (int it = 0; it < ntile; ++it) {
       const int s = it & 1;
-      if (it >= 2 && !tt_wait(tc::smem_u32(&bar_empty[s]), ((it >> 1) + 1) & 1, abort_w, flags)) break;
+      int ok = 1;
+      if (it >= 2 && lane == 0) ok = tt_wait(tc::smem_u32(&bar_empty[s]), ((it >> 1) + 1) & 1, abort_w, flags) ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
       const TtTile tl = tt_tile(pre, cnt, (int)blockIdx.x + it * G, Cfg::R);
       const int t = t0 + tl.slot;
       const int k1 = st[t].k;
@@ -1134,16 +1137,20 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
       const int i0 = k1 + tl.bi * TT_M, j0 = k1 + tl.bj * TN;
       const uint32_t bf = tc::smem_u32(&bar_full[s]);
       const uint32_t sa = tc::smem_u32(stages + s * Cfg::STAGE);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bf), "r"(Cfg::STAGE) : "memory");
-      for (int part = 0; part < 3; ++part)
-        for (int kg = 0; kg < 8; ++kg) {
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bf), "r"(Cfg::STAGE) : "memory");
+      __syncwarp();
+      for (int e = lane; e < 48; e += 32) {
+        const int op = e / 24, part = (e % 24) / 8, kg = e % 8;
+        if (op == 0)
           bulk_g2s(sa + part * TT_PART + kg * (TT_M * 16), P + (int64_t)(part * 8 + kg) * ld + i0, TT_M * 16, bf);
+        else
           bulk_g2s(sa + 3 * TT_PART + part * Cfg::B_PART + kg * (TN * 16),
                    P + (int64_t)((part + 3) * 8 + kg) * ld + j0, TN * 16, bf);
-        }
+      }
       issued = it + 1;
     }
-    if (*abort_w)                                            // own copies still in flight
+    if (lane == 0 && *abort_w)                               // own copies still in flight
       for (int it = max(0, issued - 2); it < issued; ++it) tt_drain(tc::smem_u32(&bar_full[it & 1]), (it >> 1) & 1);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: 6 products x 4 k-steps into accumulator set it % NB
@@ -1180,25 +1187,43 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
     // C -= (acc0_0 + .. + acc0_KS-1) + acc1 on the lower triangle
     const int q4 = warp & 3;                                  // the TMEM lane quarter this warp may read
     const int h = (warp - 2) >> 2;                            // which half of the tile's columns
-    for (int it = 0; it < ntile; ++it) {
-      const int ab = NB == 2 ? (it & 1) : 0, use = it / NB;
+    // this thread's row of tile it: front, leading dimension, row i, first column j0, and
+    // qmax (columns q <= qmax are in the lower triangle of the front)
+    struct EpiRow { float* F; int64_t ld; int i, j0, qmax; };
+    auto row_of = [&](int it) {
       const TtTile tl = tt_tile(pre, cnt, (int)blockIdx.x + it * G, Cfg::R);
       const int t = t0 + tl.slot;
       const int k1 = st[t].k, f = st[t].f;
-      const int64_t ld = nd[t].ld;
-      float* F = arena + nd[t].front_off;
-      const int i0 = k1 + tl.bi * TT_M, j0 = k1 + tl.bj * TN + h * CW;
-      const int i = i0 + q4 * 32 + lane;
-      // columns q <= qmax of this row are in the lower triangle of the front
-      const int qmax = i < f ? min(i, f - 1) - j0 : -1;
-      float cv[CW];                                           // C loaded while the MMAs run
-      {
-        const float* pc = F + i + (int64_t)j0 * ld;
+      EpiRow e;
+      e.F = arena + nd[t].front_off;
+      e.ld = nd[t].ld;
+      e.i = k1 + tl.bi * TT_M + q4 * 32 + lane;
+      e.j0 = k1 + tl.bj * TN + h * CW;
+      e.qmax = e.i < f ? min(e.i, f - 1) - e.j0 : -1;
+      return e;
+    };
+    auto load_row = [&](const EpiRow& e, float* v) {
+      const float* pc = e.F + e.i + (int64_t)e.j0 * e.ld;
 #pragma unroll
-        for (int q = 0; q < CW; ++q) {
-          cv[q] = q <= qmax ? *pc : 0.f;
-          pc += ld;
-        }
+      for (int q = 0; q < CW; ++q) {
+        v[q] = q <= e.qmax ? *pc : 0.f;
+        pc += e.ld;
+      }
+    };
+    // C of a tile is loaded one tile ahead: while this tile's MMAs run and its accumulator
+    // is read and stored
+    float cv[CW], cvn[CW];
+    EpiRow cur = {};
+    if (ntile > 0) {
+      cur = row_of(0);
+      load_row(cur, cv);
+    }
+    for (int it = 0; it < ntile; ++it) {
+      const int ab = NB == 2 ? (it & 1) : 0, use = it / NB;
+      EpiRow nxt = cur;
+      if (it + 1 < ntile) {
+        nxt = row_of(it + 1);
+        load_row(nxt, cvn);
       }
       int ok = 1;
       if (lane == 0) ok = tt_wait(tc::smem_u32(&bar_tfull[ab]), use & 1, abort_w, flags) ? 1 : 0;
@@ -1206,7 +1231,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(ab * Cfg::ACOLS + h * CW);
-      float* pw = F + i + (int64_t)j0 * ld;
+      float* pw = cur.F + cur.i + (int64_t)cur.j0 * cur.ld;
 #pragma unroll
       for (int ch = 0; ch < CW / 16; ++ch) {
         const int c0 = ch * 16;
@@ -1229,10 +1254,13 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
         }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          if (c0 + q <= qmax) *pw = cv[c0 + q] - v[q];
-          pw += ld;
+          if (c0 + q <= cur.qmax) *pw = cv[c0 + q] - v[q];
+          pw += cur.ld;
         }
       }
+      cur = nxt;
+#pragma unroll
+      for (int q = 0; q < CW; ++q) cv[q] = cvn[q];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
