@@ -283,7 +283,12 @@ def form_line(hf, s, vals, bt, b, tau, steps, warmup, **opts):
     import torch
     H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, **opts)
     xt = torch.zeros_like(bt)
-    fac, sch, _, _ = time_steps(H, vals, tau, bt, xt, steps, warmup, solve=False)
+    try:
+        fac, sch, _, _ = time_steps(H, vals, tau, bt, xt, steps, warmup, solve=False)
+    except hf.HFError as e:                      # e.g. a threshold that postpones too much
+        H.free()
+        torch.cuda.empty_cache()
+        return {"error": str(e), "code": e.code}
     H.solve(bt, xt)
     torch.cuda.synchronize()
     info = H.info()
@@ -438,7 +443,8 @@ def run_ours(args):
     if not args.no_fp64:
         forms["fp64_form"] = form_line(hf, s, vals, bt, b, tau, args.steps, warm, precision=hf.HF_PREC_FP64,
                                        null_test=null_test)
-        forms["fp64_form"]["speedup_mixed_vs_fp64"] = forms["fp64_form"]["factor_schur_ms"] / fs_ms
+        if "factor_schur_ms" in forms["fp64_form"]:
+            forms["fp64_form"]["speedup_mixed_vs_fp64"] = forms["fp64_form"]["factor_schur_ms"] / fs_ms
         forms["fp32_form"] = form_line(hf, s, vals, bt, b, tau, args.steps, warm, precision=hf.HF_PREC_FP32,
                                        null_test=null_test)
     extra = {}

@@ -48,7 +48,10 @@ enum {
   HF_ERR_NOT_CONVERGED = 5,  /* block GCR hit gcr_maxit; results usable, see hf_info */
   HF_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
   HF_ERR_CUDA = 7,           /* a CUDA runtime call failed */
-  HF_ERR_OOM = 8             /* device memory allocation failed */
+  HF_ERR_OOM = 8,            /* device memory allocation failed */
+  HF_ERR_CAPACITY = 9        /* a front outgrew the panel kernels' shared memory: with
+                                the rows postponed into it, more than about 25,000 rows
+                                (FP32 factor); a smaller tau postpones fewer rows */
 };
 
 /* Precision forms (Table 1 columns). */
@@ -184,7 +187,7 @@ int hf_analyze(int64_t L, const int64_t* rowptr, const int32_t* col, const doubl
  *         hf_analyze.  Read during the call only.
  *   tau   threshold (> 0); overrides opts.tau for this and later calls.
  * On return the split (N, M, Lambda_2) is known on the host (one small D2H copy).
- * Errors: HF_ERR_ARG, HF_ERR_NUMERIC, HF_ERR_CUDA, HF_ERR_OOM.
+ * Errors: HF_ERR_ARG, HF_ERR_NUMERIC, HF_ERR_CUDA, HF_ERR_OOM, HF_ERR_CAPACITY.
  */
 int hf_factorize(hf_ctx* ctx, const double* vals, double tau);
 

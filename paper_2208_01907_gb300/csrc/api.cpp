@@ -215,6 +215,7 @@ const char* hf_error_string(int code) {
     case HF_ERR_TIMEOUT: return "device wait timed out";
     case HF_ERR_CUDA: return "CUDA error";
     case HF_ERR_OOM: return "device out of memory";
+    case HF_ERR_CAPACITY: return "front too large for the panel kernels (too many postponed rows)";
     default: return "unknown error";
   }
 }

@@ -426,8 +426,6 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red_k[32];
   __shared__ int red_i[32], red_p[32];
-  __shared__ T s_bk;
-  __shared__ int s_bp, s_act, s_w;
   __shared__ int s_swa[PCL_SWAPS], s_swb[PCL_SWAPS];
   __shared__ T s_thr;                          // tau |previous pivot| rounded up to T
   const int rank = (int)cl.block_rank();
@@ -437,7 +435,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
   const int f = S->f;
   const int k0 = S->k;
   int nact = S->nact;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   // the same decisions in every CTA of the cluster
   if (S->stopped || k0 >= nact || f - k0 > C * Rcap) {
     if (rank == 0 && tid == 0 && (S->stopped || k0 >= nact)) S->kp0 = k0;
@@ -543,13 +541,15 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       int op = __shfl_xor_sync(0xffffffffu, bp, o);
       if (better_t(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
     }
-    if ((tid & 31) == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; red_p[tid >> 5] = bp; }
+    if (lane == 0) { red_k[tid >> 5] = bk; red_i[tid >> 5] = bi; red_p[tid >> 5] = bp; }
     __syncthreads();
-    if (tid < 32) {
+    {
+      // every warp reduces the warps' candidates itself (the same result everywhere), so
+      // no second block barrier publishes it
       const int nw = (nt + 31) / 32;
-      bk = tid < nw ? red_k[tid] : T(-2);
-      bi = tid < nw ? red_i[tid] : 0x7fffffff;
-      bp = tid < nw ? red_p[tid] : -1;
+      bk = lane < nw ? red_k[lane] : T(-2);
+      bi = lane < nw ? red_i[lane] : 0x7fffffff;
+      bp = lane < nw ? red_p[lane] : -1;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         T ok = __shfl_xor_sync(0xffffffffu, bk, o);
@@ -557,15 +557,13 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
         int op = __shfl_xor_sync(0xffffffffu, bp, o);
         if (better_t(ok, oi, bk, bi)) { bk = ok; bi = oi; bp = op; }
       }
-      if (tid == 0) { s_bk = bk; s_bp = bp; }
     }
-    __syncthreads();
     // 2. pushes: own candidate, and rows k / nact-1 by their owners
     {
-      const int pbest = s_bp;
+      const int pbest = bp;
       const int base = buf * PCL_SLOTS + rank;
       if (pbest >= 0) {
-        push_row(buf, rank, pbest, s_bk, kk);
+        push_row(buf, rank, pbest, bk, kk);
       } else if (tid < C) {
         PclMeta<T> mt = {};
         mt.key = T(-2); mt.sid = 0x7fffffff; mt.pos = -1;
@@ -576,14 +574,15 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       if (tau_null > 0.0 && owner(nact - 1) == rank) push_row(buf, PCL_CMAX + 1, nact - 1, T(0), kk);
     }
     if (C > 1) cl.sync(); else __syncthreads();                            // the only cluster barrier
-    // 3. the decision from the local slots (the same in every CTA): the argmax by one warp,
-    // the two FP64 threshold tests by one thread (not on the FP64 pipe of the whole block)
+    // 3. the decision from the local slots, taken by every warp (the same in every warp and
+    // every CTA, so no block barrier publishes it): the argmax over the C slots by the lanes
+    // (the order is strict: ids are unique), the FP64 null-pivot test by lane 0
     const int sb = buf * PCL_SLOTS;
-    if (tid < 32) {
-      // argmax over the C slots by the lanes (the order is strict: ids are unique)
+    int act, wslot;
+    {
       T gk = T(-2);
       int gi = 0x7fffffff, gw = -1;
-      if (tid < C && pm[sb + tid].pos >= 0) { gk = pm[sb + tid].key; gi = pm[sb + tid].sid; gw = tid; }
+      if (lane < C && pm[sb + lane].pos >= 0) { gk = pm[sb + lane].key; gi = pm[sb + lane].sid; gw = lane; }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ok = __shfl_xor_sync(0xffffffffu, gk, o);
@@ -591,19 +590,19 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
         const int ow = __shfl_xor_sync(0xffffffffu, gw, o);
         if (better_t(ok, oi, gk, gi)) { gk = ok; gi = oi; gw = ow; }
       }
-      if (tid == 0) {
-        int a2 = 0;
-        // ratio test (R2/R3) against the threshold in the factor's type (exact: gk is a T,
-        // s_thr the smallest T >= tau |d_prev|); the null-pivot test (R3b) only when asked for
-        if (!(gk >= s_thr)) a2 = 1;
-        else if (tau_null > 0.0 && !((double)gk >= tau_null * (double)pm[sb + gw].G)) a2 = 2;
-        s_act = a2;
-        s_w = gw;
+      // ratio test (R2/R3) against the threshold in the factor's type (exact: gk is a T,
+      // s_thr the smallest T >= tau |d_prev|); the null-pivot test (R3b) only when asked for
+      int a2 = 0;
+      if (!(gk >= s_thr)) a2 = 1;
+      else if (tau_null > 0.0) {
+        if (lane == 0) a2 = ((double)gk >= tau_null * (double)pm[sb + gw].G) ? 0 : 2;
+        a2 = __shfl_sync(0xffffffffu, a2, 0);
       }
+      act = a2;
+      wslot = gw;
     }
-    __syncthreads();
-    const int act = s_act, wsl = sb + s_w;
-    const int q = s_w >= 0 ? pm[wsl].pos : -1;
+    const int wsl = sb + wslot;
+    const int q = wslot >= 0 ? pm[wsl].pos : -1;
     if (act == 1) { stopped = true; break; }
     if (act == 2) {
       // 4a. postpone the null candidate: swap q <-> b = nact-1 (both candidates)
@@ -650,29 +649,9 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       __syncthreads();
       continue;
     }
-    // 4b. pivot q -> position k: w from the winner's row, new contents of positions k and q
-    const T* rq = prow + (size_t)wsl * nb;
-    const int ksl = sb + PCL_CMAX;
-    const T* rk = prow + (size_t)ksl * nb;
-    for (int c = tid; c < kk; c += nt) wv[c] = dpiv[c] * rq[c];
-    if (owner(k) == rank) {
-      const int l = k - p0;
-      for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rq[c];
-      if (tid == 0) {
-        sidl[l] = pm[wsl].sid; ridl[l] = pm[wsl].rid; pos0l[l] = pm[wsl].p0; Gl[l] = pm[wsl].G;
-      }
-    }
-    if (q != k && owner(q) == rank) {
-      const int l = q - p0;
-      for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rk[c];
-      if (tid == 0) {
-        dgl[l] = pm[ksl].dg; Gl[l] = pm[ksl].G; diagl[l] = pm[ksl].diag;
-        sidl[l] = pm[ksl].sid; ridl[l] = pm[ksl].rid; pos0l[l] = pm[ksl].p0;
-      }
-    }
-    __syncthreads();
-    // 5. loads first: the new column k of the own rows (swap fused); the interchange of rows
-    // k and q over the earlier panels' columns [0, k0) is listed for the end of the panel
+    // 4. loads first, as soon as q is known: the new column k of the own rows (swap fused),
+    // in flight while the rows of positions k and q are exchanged below; the interchange of
+    // rows k and q over the earlier panels' columns [0, k0) is listed for the end of the panel
     T v[PCL_RPT];
     int64_t wy[PCL_RPT];
     T wx[PCL_RPT];
@@ -695,6 +674,27 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       }
     }
     if (q != k) defer_swap(k, q);                      // rows k and q over [0, k0)
+    // 5. pivot q -> position k: w from the winner's row, new contents of positions k and q
+    const T* rq = prow + (size_t)wsl * nb;
+    const int ksl = sb + PCL_CMAX;
+    const T* rk = prow + (size_t)ksl * nb;
+    for (int c = tid; c < kk; c += nt) wv[c] = dpiv[c] * rq[c];
+    if (owner(k) == rank) {
+      const int l = k - p0;
+      for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rq[c];
+      if (tid == 0) {
+        sidl[l] = pm[wsl].sid; ridl[l] = pm[wsl].rid; pos0l[l] = pm[wsl].p0; Gl[l] = pm[wsl].G;
+      }
+    }
+    if (q != k && owner(q) == rank) {
+      const int l = q - p0;
+      for (int c = tid; c < kk; c += nt) P[(size_t)l * ps + c] = rk[c];
+      if (tid == 0) {
+        dgl[l] = pm[ksl].dg; Gl[l] = pm[ksl].G; diagl[l] = pm[ksl].diag;
+        sidl[l] = pm[ksl].sid; ridl[l] = pm[ksl].rid; pos0l[l] = pm[ksl].p0;
+      }
+    }
+    __syncthreads();
     // d_k by every thread: the owner's operations on the winner's row
     const T dk = dot_sub_seq(pm[wsl].diag, rq, wv, kk);
     // 6. c_i = A(i, k) - sum_c L(i, c) w_c; L(i, k) = c_i / d_k; diagonals and magnitudes
@@ -702,10 +702,11 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
     for (int j = 0; j < PCL_RPT; ++j) {
       const int p = p0 + tid + j * nt;
       if (p > k && p < p1) {
-        if (wy[j] >= 0) F[wy[j]] = wx[j];
         const int l = p - p0;
         T* Pr = P + (size_t)l * ps;
-        const T acc = dot_sub_seq(v[j], Pr, wv, kk);
+        // the sum starts from zero, so that it runs while the column's load is in flight
+        const T acc = v[j] + dot_sub_seq(T(0), Pr, wv, kk);
+        if (wy[j] >= 0) F[wy[j]] = wx[j];
         const T lv = acc / dk;
         Pr[kk] = lv;
         if (p < nact) dgl[l] -= lv * acc;
@@ -1515,7 +1516,7 @@ int run_levels(hf_ctx* c) {
     const int nbl = use_cl ? nbc : nb;
     const int npan = (maxn + nbl - 1) / nbl;
     const size_t smem = (size_t)nbl * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
-    if (use_gl && smem > 220 * 1024) return HF_ERR_ARG;
+    if (use_gl && smem > 220 * 1024) return HF_ERR_CAPACITY;
     const int pthreads = maxld > 1024 ? 1024 : 256;
     // tensor-core trailing update for the levels of large fronts (a panel of <= 64 pivots,
     // the tile map of <= TT_MAXF fronts): one persistent CTA per SM, at most one per tile
@@ -1572,7 +1573,7 @@ int run_levels(hf_ctx* c) {
     }
     if (use_cl) {
       // the listed interchanges of this level's cluster-panel fronts, in their final order
-      if ((size_t)2 * maxld * sizeof(int) > SW_SMEM || (size_t)maxld * sizeof(T) > SW_SMEM) return HF_ERR_ARG;
+      if ((size_t)2 * maxld * sizeof(int) > SW_SMEM || (size_t)maxld * sizeof(T) > SW_SMEM) return HF_ERR_CAPACITY;
       const int gcap = npan + 1;
       const int sg = maxld + 1;
       const int64_t sf = (int64_t)gcap * sg;

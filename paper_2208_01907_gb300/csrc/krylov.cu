@@ -395,7 +395,7 @@ __device__ __forceinline__ bool df_wait(const int* flag, int* abort_word, int* s
     for (int it = 0; it < spin; ++it) {
       if (df_ld_acquire(flag)) { ok = 1; break; }
       if (*(volatile int*)abort_word) break;
-      __nanosleep(it < 64 ? 32 : 256);
+      __nanosleep(32);
     }
     if (!ok) atomicExch(abort_word, 1);
     *s_ok = ok;
@@ -560,7 +560,8 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
       for (int b = 0; b < bend && ok;) {
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
-        const int e = df_ready_run(fl, gt, b, bend, true, &s_e);
+        // the last block the item reads ends the run (no flags to look at)
+        const int e = b + 1 == bend ? bend : df_ready_run(fl, gt, b, bend, true, &s_e);
         gemm_range(b * DF_R, min(ks, e * DF_R));
         b = e;
       }
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
       for (int b = nblk - 1; b > code && ok;) {
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
-        const int e = df_ready_run(fl, gt, b, code, false, &s_e);
+        const int e = b - 1 == code ? code : df_ready_run(fl, gt, b, code, false, &s_e);
         gemm_range((e + 1) * DF_R, min(ks, (b + 1) * DF_R));
         b = e;
       }
@@ -633,11 +634,10 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
         }
       }
     }
+    // the block barrier orders every thread's stores before thread 0's release store
+    // (cumulative at gpu scope), which publishes the block to the acquiring readers
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      df_st_release(fl + (int64_t)code * gt, 1);
-    }
+    if (tid == 0) df_st_release(fl + (int64_t)code * gt, 1);
   }
 }
 

@@ -170,17 +170,48 @@ __global__ void k_oz_exp(const double* __restrict__ X, int64_t si, int64_t sk, i
   }
 }
 
-// column exponents of a row-major L x m block: per-block maxima, then atomicMax
-__global__ void k_oz_exp_cols(const double* __restrict__ A, int64_t L, int m, int* __restrict__ e) {
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;
-  if (j >= m) return;
+// Max-magnitude exponents of the n rows of a row-major n x K block: one warp per row,
+// eight rows per block at a time.
+__global__ void __launch_bounds__(256) k_oz_exp_rows(const double* __restrict__ X, int64_t n, int K, int* __restrict__ e) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[i * K + k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      int ex = -1060;
+      if (mx > 0) frexp(mx, &ex);
+      e[i] = ex;
+    }
+  }
+}
+
+// Column exponents of a row-major L x m block (e preset to -1060). The 256 threads of a
+// block cover a window of w = min(m, 256) columns on 256 / w rows at a time, so that
+// consecutive threads read consecutive entries; each block takes a contiguous range of
+// rows, reduces its maxima in shared memory and merges them into e by atomicMax.
+__global__ void __launch_bounds__(256) k_oz_exp_cols(const double* __restrict__ A, int64_t L, int m, int* __restrict__ e) {
+  __shared__ int sx[256];
+  const int w = min(m, 256), rpi = 256 / w;                 // window width, rows per step
+  const int tid = threadIdx.x, jr = tid / w, jc = tid % w;
   const int64_t rows = (L + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows, r1 = min(L, r0 + rows);
-  double mx = 0.0;
-  for (int64_t r = r0; r < r1; ++r) mx = fmax(mx, fabs(A[r * m + j]));
-  int ex = -1060;
-  if (mx > 0) frexp(mx, &ex);
-  atomicMax(&e[j], ex);
+  for (int c0 = 0; c0 < m; c0 += w) {
+    const int j = c0 + jc;
+    const bool act = jr < rpi && j < m;
+    double mx = 0.0;
+    if (act)
+      for (int64_t r = r0 + jr; r < r1; r += rpi) mx = fmax(mx, fabs(A[r * m + j]));
+    int ex = -1060;
+    if (mx > 0) frexp(mx, &ex);
+    if (tid < w) sx[tid] = -1060;
+    __syncthreads();
+    if (act) atomicMax(&sx[jc], ex);
+    __syncthreads();
+    if (tid < w && c0 + tid < m) atomicMax(&e[c0 + tid], sx[tid]);
+    __syncthreads();
+  }
 }
 
 __global__ void k_fill_int(int* __restrict__ p, int n, int v) {
@@ -492,11 +523,11 @@ int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const doub
   int* eb = same ? ea : iscratch + ma;
   const int ne = same ? ma : ma + mb;
   HF_LAUNCH(c, HF_PROF_TC_PREP, k_fill_int<<<(ne + 255) / 256, 256, 0, s>>>(ea, ne, -1060));
-  const unsigned gx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, L / 1024), 512);
-  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_cols<<<dim3(gx, (ma + 127) / 128), 128, 0, s>>>(A, L, ma, ea));
+  const unsigned gx = (unsigned)std::min<int64_t>((L + 255) / 256, 1216);
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_cols<<<gx, 256, 0, s>>>(A, L, ma, ea));
   HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(ma) * Kg), 256, 0, s>>>(A, ma, L, 1, ma, ea, SA, Kg));
   if (!same) {
-    HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_cols<<<dim3(gx, (mb + 127) / 128), 128, 0, s>>>(B, L, mb, eb));
+    HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_cols<<<gx, 256, 0, s>>>(B, L, mb, eb));
     HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(mb) * Kg), 256, 0, s>>>(B, mb, L, 1, mb, eb, SB, Kg));
   }
   CUtensorMap ta, tb;
@@ -533,7 +564,7 @@ int hf_oz_update(hf_ctx* c, int64_t L, int m, const double* A, const double* C, 
   uint4* SB = (uint4*)((unsigned char*)slices + sa_bytes);
   int* ea = iscratch;                      // L row exponents of A
   int* eb = iscratch + L;                  // m column exponents of C
-  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp<<<(unsigned)L, 32, 0, s>>>(A, m, 1, (int)L, m, ea));
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp_rows<<<(unsigned)std::min<int64_t>((L + 7) / 8, 4864), 256, 0, s>>>(A, L, m, ea));
   HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_exp<<<m, 32, 0, s>>>(C, 1, m, m, m, eb));
   HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(L) * Kg), 256, 0, s>>>(A, L, m, m, 1, ea, SA, Kg));
   HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_slice<<<slice_grid(oz_rows(m) * Kg), 256, 0, s>>>(C, m, m, 1, m, eb, SB, Kg));

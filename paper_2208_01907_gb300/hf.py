@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhf.so")
 
 HF_OK, HF_ERR_ARG, HF_ERR_STATE, HF_ERR_PATTERN, HF_ERR_NUMERIC = 0, 1, 2, 3, 4
-HF_ERR_NOT_CONVERGED, HF_ERR_TIMEOUT, HF_ERR_CUDA, HF_ERR_OOM = 5, 6, 7, 8
+HF_ERR_NOT_CONVERGED, HF_ERR_TIMEOUT, HF_ERR_CUDA, HF_ERR_OOM, HF_ERR_CAPACITY = 5, 6, 7, 8, 9
 HF_PREC_MIXED, HF_PREC_FP64, HF_PREC_FP32 = 0, 1, 2
 
 #: every symbol declared in include/hf.h

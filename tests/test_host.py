@@ -36,6 +36,14 @@ def test_default_opts_and_error_strings():
     assert o.tau == 1e-2 and o.n_enlarge == 4 and o.precision == hf.HF_PREC_MIXED
     assert o.null_test == 0 and o.spin_limit == 0         # the ratio test of Sec. 2.2 alone
     assert hf.lib().hf_error_string(5) == b"block GCR did not converge"
+    # every code of the header's enum has its own message, mirrored by the binding
+    header = open(os.path.join(ROOT, "include", "hf.h")).read()
+    codes = {n: int(v) for n, v in re.findall(r"(HF_(?:OK|ERR_\w+)) = (\d+)", header)}
+    assert sorted(codes.values()) == list(range(len(codes)))
+    msgs = [hf.lib().hf_error_string(v) for v in codes.values()]
+    assert len(set(msgs)) == len(codes) and b"unknown error" not in msgs
+    for n, v in codes.items():
+        assert getattr(hf.hf, n) == v, n
 
 
 def test_binding_mirrors_the_header_structs_and_profile_classes():
