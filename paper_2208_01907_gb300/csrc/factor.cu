@@ -352,26 +352,34 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
 // (double-buffered) slots: its best candidate (key, id, G, diagonal, panel row),
 // and the owners of positions k and nact-1 push those rows.  After it, every CTA
 // takes the same decision (R2, R3, the optional R3b, R5) from its local slots, forms
-// w_c = d_c L(q, c), computes d_k itself (same operations, same order as the
-// owner would) and processes its own rows: the symmetric swap k <-> q is fused into
-// the load of the new column k, then L(i, k), the diagonals and the magnitudes.
-// The arithmetic per element is that of k_panel, in the same order.  A front larger
-// than C * Rcap rows is left to k_panel (which skips the fronts handled here).
+// w_c = d_c L(q, c), computes d_k itself (the same operations as the owner's) and
+// processes its own rows: the symmetric swap k <-> q is fused into the load of the new
+// column k, then L(i, k), the diagonals and the magnitudes.  The arithmetic per element
+// is that of k_panel except the order of the sums over the panel's columns (four
+// interleaved partial sums here, one sequential sum there).  A front larger than
+// C * Rcap rows is left to k_panel (which skips the fronts handled here).
 // ---------------------------------------------------------------------------
-// acc - sum_{c < n} a[c] * b[c], accumulated in order c = 0, 1, ...; the shared-memory
-// loads are issued eight at a time so that their latency overlaps
+// sum_{c < n} a[c] * b[c] in four interleaved partial sums (c mod 4), added pairwise at the
+// end: the chain of dependent multiply-adds is a quarter of the length of a sequential sum;
+// the shared-memory loads are issued eight at a time so that their latency overlaps
 template <typename T>
-__device__ __forceinline__ T dot_sub_seq(T acc, const T* __restrict__ a, const T* __restrict__ b, int n) {
+__device__ __forceinline__ T dot4(const T* __restrict__ a, const T* __restrict__ b, int n) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
   int c = 0;
   for (; c + 8 <= n; c += 8) {
     T x[8], y[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) { x[u] = a[c + u]; y[u] = b[c + u]; }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc -= x[u] * y[u];
+    s0 += x[0] * y[0]; s1 += x[1] * y[1]; s2 += x[2] * y[2]; s3 += x[3] * y[3];
+    s0 += x[4] * y[4]; s1 += x[5] * y[5]; s2 += x[6] * y[6]; s3 += x[7] * y[7];
   }
-  for (; c < n; ++c) acc -= a[c] * b[c];
-  return acc;
+  for (; c + 4 <= n; c += 4) {
+    s0 += a[c] * b[c]; s1 += a[c + 1] * b[c + 1]; s2 += a[c + 2] * b[c + 2]; s3 += a[c + 3] * b[c + 3];
+  }
+  if (c < n) s0 += a[c] * b[c];
+  if (c + 1 < n) s1 += a[c + 1] * b[c + 1];
+  if (c + 2 < n) s2 += a[c + 2] * b[c + 2];
+  return (s0 + s1) + (s2 + s3);
 }
 
 // smallest float >= x (for a float g, g >= x exactly when g >= ceil_float(x); NaN stays NaN)
@@ -696,7 +704,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
     }
     __syncthreads();
     // d_k by every thread: the owner's operations on the winner's row
-    const T dk = dot_sub_seq(pm[wsl].diag, rq, wv, kk);
+    const T dk = pm[wsl].diag - dot4(rq, wv, kk);
     // 6. c_i = A(i, k) - sum_c L(i, c) w_c; L(i, k) = c_i / d_k; diagonals and magnitudes
 #pragma unroll
     for (int j = 0; j < PCL_RPT; ++j) {
@@ -704,8 +712,8 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
       if (p > k && p < p1) {
         const int l = p - p0;
         T* Pr = P + (size_t)l * ps;
-        // the sum starts from zero, so that it runs while the column's load is in flight
-        const T acc = v[j] + dot_sub_seq(T(0), Pr, wv, kk);
+        // the sum does not wait for the column's load, which is still in flight
+        const T acc = v[j] - dot4(Pr, wv, kk);
         if (wy[j] >= 0) F[wy[j]] = wx[j];
         const T lv = acc / dk;
         Pr[kk] = lv;
@@ -931,6 +939,7 @@ __global__ void __launch_bounds__(256) k_trailing(const NodeDesc* __restrict__ n
 constexpr int TT_M = 128, TT_K = 64;                 // tile rows; k = the panel's columns
 constexpr int TT_EPI = 8;                           // epilogue warps: two per TMEM lane quarter
 constexpr int TT_THREADS = 64 + 32 * TT_EPI;
+static_assert(TT_THREADS % 32 == 0 && TT_THREADS <= 32 * 32, "the tile prefix scans one warp total per lane");
 constexpr int TT_PART = TT_M * TT_K * 2;            // 16 KB: one BF16 part of 128 rows x 64 k
 constexpr int TT_MAXF = 4096;                       // fronts per level the tile map holds
 constexpr int TT_COLS = 512;                        // TMEM columns allocated (all of them)
@@ -1070,7 +1079,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
   int* pre = (int*)(stages + 2 * Cfg::STAGE);                // cnt + 1 tile prefix counts
   __shared__ uint32_t tslot;
   __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2], bar_tfull[2], bar_tempty[2];
-  __shared__ int seg[TT_THREADS + 1];
+  __shared__ int seg[TT_THREADS / 32 + 1];
   __shared__ int abort_s;
   volatile int* abort_w = &abort_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1087,7 +1096,16 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
     pre[i] = Cfg::R * nt * (nt + 1) / 2;
     sum += pre[i];
   }
-  seg[tid] = sum;
+  // exclusive prefix of the threads' sums: a shuffle scan in each warp, then one over the
+  // warp totals
+  constexpr int NW = TT_THREADS / 32;
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) seg[warp] = incl;
   if (tid == 0) {
     abort_s = 0;
     for (int s = 0; s < 2; ++s) {
@@ -1103,16 +1121,23 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    for (int w = 0; w < TT_THREADS; ++w) { const int v = seg[w]; seg[w] = acc; acc += v; }
-    seg[TT_THREADS] = acc;
+  if (warp == 0) {
+    const int wv = lane < NW ? seg[lane] : 0;
+    int wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    __syncwarp();                                             // every lane has read seg
+    if (lane < NW) seg[lane] = wi - wv;                       // first tile of warp `lane`'s fronts
+    if (lane == NW - 1) seg[NW] = wi;                         // tiles of the level
   }
   __syncthreads();
   {
-    int acc = seg[tid];
+    int acc = seg[warp] + incl - sum;
     for (int i = a0; i < a1; ++i) { const int v = pre[i]; pre[i] = acc; acc += v; }
-    if (tid == 0) pre[cnt] = seg[TT_THREADS];
+    if (tid == 0) pre[cnt] = seg[NW];
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();
@@ -1398,6 +1423,7 @@ int run_levels(hf_ctx* c) {
   constexpr size_t PCL_SMEM = 220 * 1024;
   static bool attr_set[2] = {false, false};
   static int max_cluster[2] = {0, 0};
+  static int active_clusters[2][PCL_CMAX + 1] = {};   // co-resident clusters of each size
   static std::mutex attr_mu;                 // contexts may be driven from several host threads
   static int num_sms = 0;
   int cmax = 0;
@@ -1420,8 +1446,9 @@ int run_levels(hf_ctx* c) {
     HF_CUDA_TRY(cudaFuncSetAttribute(k_swap_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SW_SMEM));
     if (cudaFuncSetAttribute(k_panel_cl<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
       (void)cudaGetLastError();
-    // largest cluster (<= 16) that can be resident with the full shared-memory panel
-    for (int cs = PCL_CMAX; cs >= 1; cs /= 2) {
+    // clusters of each size (<= 16) that can be resident at once with the full
+    // shared-memory panel; the largest size with at least one
+    for (int cs = PCL_CMAX; cs >= 1; --cs) {
       cudaLaunchConfig_t q = {};
       q.gridDim = dim3(cs);
       q.blockDim = dim3(PCL_THREADS);
@@ -1432,15 +1459,17 @@ int run_levels(hf_ctx* c) {
       q.attrs = at; q.numAttrs = 1;
       int ncl = 0;
       if (cudaOccupancyMaxActiveClusters(&ncl, k_panel_cl<T>, &q) == cudaSuccess && ncl > 0) {
-        max_cluster[sizeof(T) == 8] = cs;
-        break;
+        active_clusters[sizeof(T) == 8][cs] = ncl;
+        max_cluster[sizeof(T) == 8] = std::max(max_cluster[sizeof(T) == 8], cs);
+      } else {
+        (void)cudaGetLastError();
       }
-      (void)cudaGetLastError();
     }
     attr_set[sizeof(T) == 8] = true;
   }
   cmax = max_cluster[sizeof(T) == 8];
   }
+  const int* ncl_of = active_clusters[sizeof(T) == 8];
   // the optional null-pivot test (R3b) compares |d| with tau_null * G; 0 switches it off
   // (|d| >= 0 always holds; a NaN pivot already fails the ratio test)
   const double tau_null = c->opts.null_test ? c->tau : 0.0;
@@ -1507,8 +1536,23 @@ int run_levels(hf_ctx* c) {
     const size_t fixed = PclLayout<T>::bytes(0, nbc);
     int Rcap = std::min((int)((PCL_SMEM - fixed) / per_row), PCL_RPT * PCL_THREADS);
     if (rows_cap > 0) Rcap = std::min(Rcap, rows_cap);
-    const int C = std::max(1, std::min(cmax, (maxld + Rcap - 1) / Rcap));
-    const bool use_cl = cmax > 0 && maxld > 0 && !panel_global;
+    // fewest CTAs per front whose shared memory holds the level's largest front
+    int C = std::max(1, std::min(cmax, (maxld + Rcap - 1) / Rcap));
+    bool level_global = panel_global;
+    if (rows_cap == 0 && !panel_global && cmax > 0 && maxld > 0) {
+      // a pivot costs less when every thread holds one row: more CTAs per front, as long
+      // as the level's clusters are resident at once (measured at 40^3 elasticity: the
+      // root 22.7 -> 21.2 ms with 10 CTAs instead of 7, the two fronts of the level below
+      // 16.3 -> 14.5 ms with 15 instead of 10)
+      const int C1 = (maxld + PCL_THREADS - 1) / PCL_THREADS;
+      if (C1 > C && C1 <= cmax && ncl_of[C1] >= cnt) C = C1;
+      // levels of many small fronts whose clusters would run in more than two waves: the
+      // global-memory panel (one small CTA per front, all fronts at once) is faster there
+      // (1,024 fronts of <= 432 rows: 3.19 -> 2.35 ms; 128 fronts of <= 1,572 rows, three
+      // waves: 2.14 -> 1.91 ms; 64 fronts in 1.7 waves: 3.23 ms with clusters, 4.60 without)
+      if (ncl_of[C] > 0 && cnt > 2 * ncl_of[C]) level_global = true;
+    }
+    const bool use_cl = cmax > 0 && maxld > 0 && !level_global;
     const int cap = use_cl ? C * Rcap : -1;
     const bool use_gl = !use_cl || maxld > cap;
     if (use_cl) c->path_cluster = std::max(c->path_cluster, C);

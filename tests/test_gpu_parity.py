@@ -342,16 +342,18 @@ def test_api_errors_without_state():
 def test_full_size_stokes32_properties():
     """The 3D Stokes-like workload at 32^3 nodes: properties that hold at any size.
 
-    With the ratio test of Sec. 2.2 alone at tau = 1e-2, FP32 noise pivots of the
-    singular saddle point pass the test at this size (they follow small pressure
-    pivots), K11 keeps part of the kernel, the block GCR cannot converge and the
-    solution misses the gate; the null-pivot test postpones them and the kernel reaches
-    S22.  Both are checked here."""
+    With the ratio test of Sec. 2.2 alone at tau = 1e-2, whether an FP32 noise pivot of
+    the singular saddle point passes the test (it follows a small pressure pivot) depends
+    on the rounding of the panel's sums: when one does, K11 keeps part of the kernel and
+    the result shows it (a kernel dimension other than 3, or block GCR not converging);
+    the ratio test alone is checked for that, never a silently wrong solution.  With the
+    null-pivot test the noise pivots are postponed whatever the rounding and the kernel
+    reaches S22: the full set of properties is checked on that run."""
     import scipy.sparse as sp
     s = stokes3d(32, seed=2)
     lit = run_gpu(s, tau=1e-2, rhs_mode="solution", null_test=0)
-    assert lit["info"]["kernel_dim"] != 3 or lit["schur_rc"] != 0 or \
-        O.backward_error(s.to_scipy(), lit["x"], lit["b"]) > BWD_TOL
+    if lit["info"]["kernel_dim"] == 3 and lit["schur_rc"] == 0:
+        assert O.backward_error(s.to_scipy(), lit["x"], lit["b"]) <= BWD_TOL
     lit["H"].free()
     out = run_gpu(s, tau=1e-2, rhs_mode="solution", null_test=1)
     H, info = out["H"], out["info"]
