@@ -207,6 +207,31 @@ __device__ __forceinline__ void sym_swap(T* F, int64_t ld, int f, int a, int b, 
   }
 }
 
+// sum_{c < n} a[c sa] * b[c] in four interleaved partial sums (c mod 4), added pairwise at
+// the end: the chain of dependent multiply-adds is a quarter of the length of a sequential
+// sum; the loads are issued eight at a time so that their latency overlaps.  Both panel
+// kernels sum in this order, so they compute the same factor.
+template <typename T>
+__device__ __forceinline__ T dot4(const T* __restrict__ a, int64_t sa, const T* __restrict__ b, int n) {
+  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+  int c = 0;
+  for (; c + 8 <= n; c += 8) {
+    T x[8], y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) { x[u] = a[(c + u) * sa]; y[u] = b[c + u]; }
+    s0 += x[0] * y[0]; s1 += x[1] * y[1]; s2 += x[2] * y[2]; s3 += x[3] * y[3];
+    s0 += x[4] * y[4]; s1 += x[5] * y[5]; s2 += x[6] * y[6]; s3 += x[7] * y[7];
+  }
+  for (; c + 4 <= n; c += 4) {
+    s0 += a[c * sa] * b[c]; s1 += a[(c + 1) * sa] * b[c + 1];
+    s2 += a[(c + 2) * sa] * b[c + 2]; s3 += a[(c + 3) * sa] * b[c + 3];
+  }
+  if (c < n) s0 += a[c * sa] * b[c];
+  if (c + 1 < n) s1 += a[(c + 1) * sa] * b[c + 1];
+  if (c + 2 < n) s2 += a[(c + 2) * sa] * b[c + 2];
+  return (s0 + s1) + (s2 + s3);
+}
+
 // ---------------------------------------------------------------------------
 // Panel factorization with symmetric max-|diag| pivoting and the ratio test
 // (Sec. 2.1-2.2).  One CTA per front; up to nb pivots; columns of the panel are
@@ -313,11 +338,8 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
     for (int c = k0 + tid; c < k; c += nt) w[c - k0] = F[c + c * ld] * F[k + c * ld];
     __syncthreads();
     // 4. current column k: c_i = A(i, k) - sum_t L(i, t) d_t L(k, t)
-    for (int i = k + tid; i < f; i += nt) {
-      T acc = F[i + k * ld];
-      for (int c = k0; c < k; ++c) acc -= F[i + c * ld] * w[c - k0];
-      F[i + k * ld] = acc;
-    }
+    for (int i = k + tid; i < f; i += nt)
+      F[i + k * ld] = F[i + k * ld] - dot4(F + i + (int64_t)k0 * ld, ld, w, k - k0);
     __syncthreads();
     const T dk = F[k + k * ld];
     // 5. L(i, k) = c_i / d_k, the candidates' diagonals and the term magnitudes
@@ -355,33 +377,9 @@ __global__ void k_panel(const NodeDesc* __restrict__ nd, NodeState* __restrict__
 // w_c = d_c L(q, c), computes d_k itself (the same operations as the owner's) and
 // processes its own rows: the symmetric swap k <-> q is fused into the load of the new
 // column k, then L(i, k), the diagonals and the magnitudes.  The arithmetic per element
-// is that of k_panel except the order of the sums over the panel's columns (four
-// interleaved partial sums here, one sequential sum there).  A front larger than
-// C * Rcap rows is left to k_panel (which skips the fronts handled here).
+// is that of k_panel, in the same order.  A front larger than C * Rcap rows is left to
+// k_panel (which skips the fronts handled here).
 // ---------------------------------------------------------------------------
-// sum_{c < n} a[c] * b[c] in four interleaved partial sums (c mod 4), added pairwise at the
-// end: the chain of dependent multiply-adds is a quarter of the length of a sequential sum;
-// the shared-memory loads are issued eight at a time so that their latency overlaps
-template <typename T>
-__device__ __forceinline__ T dot4(const T* __restrict__ a, const T* __restrict__ b, int n) {
-  T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-  int c = 0;
-  for (; c + 8 <= n; c += 8) {
-    T x[8], y[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) { x[u] = a[c + u]; y[u] = b[c + u]; }
-    s0 += x[0] * y[0]; s1 += x[1] * y[1]; s2 += x[2] * y[2]; s3 += x[3] * y[3];
-    s0 += x[4] * y[4]; s1 += x[5] * y[5]; s2 += x[6] * y[6]; s3 += x[7] * y[7];
-  }
-  for (; c + 4 <= n; c += 4) {
-    s0 += a[c] * b[c]; s1 += a[c + 1] * b[c + 1]; s2 += a[c + 2] * b[c + 2]; s3 += a[c + 3] * b[c + 3];
-  }
-  if (c < n) s0 += a[c] * b[c];
-  if (c + 1 < n) s1 += a[c + 1] * b[c + 1];
-  if (c + 2 < n) s2 += a[c + 2] * b[c + 2];
-  return (s0 + s1) + (s2 + s3);
-}
-
 // smallest float >= x (for a float g, g >= x exactly when g >= ceil_float(x); NaN stays NaN)
 __device__ __forceinline__ float ceil_float(double x) {
   float f = (float)x;
@@ -704,7 +702,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
     }
     __syncthreads();
     // d_k by every thread: the owner's operations on the winner's row
-    const T dk = pm[wsl].diag - dot4(rq, wv, kk);
+    const T dk = pm[wsl].diag - dot4(rq, 1, wv, kk);
     // 6. c_i = A(i, k) - sum_c L(i, c) w_c; L(i, k) = c_i / d_k; diagonals and magnitudes
 #pragma unroll
     for (int j = 0; j < PCL_RPT; ++j) {
@@ -713,7 +711,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
         const int l = p - p0;
         T* Pr = P + (size_t)l * ps;
         // the sum does not wait for the column's load, which is still in flight
-        const T acc = v[j] - dot4(Pr, wv, kk);
+        const T acc = v[j] - dot4(Pr, 1, wv, kk);
         if (wy[j] >= 0) F[wy[j]] = wx[j];
         const T lv = acc / dk;
         Pr[kk] = lv;

@@ -58,10 +58,18 @@ def test_cluster_panel_of_sixteen_ctas_and_global_panel(monkeypatch):
 
 
 def test_global_memory_panel_for_every_front(monkeypatch):
+    # the two panel kernels sum in the same order: the same pivots and the same factor, bit
+    # for bit, whichever holds a front
     s = elasticity3d(8, n_incl=2, incl=2, seed=3)
+    monkeypatch.setenv("HF_PANEL_ROWS", "96")           # clusters of several CTAs
+    ref = run_gpu(s, tau=1e-2)
+    assert ref["info"]["panel_cluster"] >= 2 and ref["info"]["panel_global"] == 0
+    monkeypatch.delenv("HF_PANEL_ROWS")
     monkeypatch.setenv("HF_PANEL_KERNEL", "global")
     out = run_gpu(s, tau=1e-2)
     assert out["info"]["panel_cluster"] == 0 and out["info"]["panel_global"] >= 1
+    for a, b in zip(ref["H"].factor(), out["H"].factor()):
+        np.testing.assert_array_equal(a, b)
     _check_against_oracle(s, out, 1e-2, 6)
 
 
