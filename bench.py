@@ -323,6 +323,8 @@ def kernel_rooflines(prof, steps, trailing_tc):
     bf16 = ("tensor", pk["bf16"], "TFLOP/s", "bf16_tflops_sustained " + pk["src"])
     table = {
         "panel": ("k_panel_cl", "pivoted left-looking panel in cluster shared memory (latency chain)", simt, 1.0),
+        "panel_global": ("k_panel", "pivoted left-looking panel in global memory, one CTA per front (levels of "
+                                    "many small fronts)", simt, 1.0),
         "trailing": ("k_trailing_tc" if trailing_tc else "k_trailing",
                      "trailing Schur update" + (" (exact 3 x BF16 split of FP32, 6 products on tcgen05; "
                                                 "levels of fronts < 256 rows on the FP32 SIMT kernel)"

@@ -142,8 +142,10 @@ enum {
      scatters of the solve vectors around each sweep level, tc_prep = operand preparation of
      the tensor-core products (exponents, slices and split-K reductions of the emulated FP64
      products; the BF16 split of the panel for the tensor-core trailing update),
-     diag_inverse = the inverses of the factor's 64 x 64 diagonal blocks for the sweeps */
-  HF_PROF_PANEL_SWAP, HF_PROF_SWEEP_IO, HF_PROF_TC_PREP, HF_PROF_DIAG_INV, HF_NPROF
+     diag_inverse = the inverses of the factor's 64 x 64 diagonal blocks for the sweeps;
+     panel_global = the panels of the levels that take the global-memory panel kernel
+     (panel = the cluster panel) */
+  HF_PROF_PANEL_SWAP, HF_PROF_SWEEP_IO, HF_PROF_TC_PREP, HF_PROF_DIAG_INV, HF_PROF_PANEL_GLOBAL, HF_NPROF
 };
 
 /* Fill *opts with the defaults listed above.  Returns HF_ERR_ARG if opts is NULL. */

@@ -172,7 +172,7 @@ const char* hf_profile_name(int cls) {
   static const char* names[HF_NPROF] = {"scale", "assemble", "panel", "trailing", "lambda0",
                                         "trsv_fwd", "trsv_bwd", "spmm", "gram", "block_update",
                                         "schur", "dense_ldlt", "vector", "panel_swap", "sweep_io",
-                                        "tc_prep", "diag_inverse"};
+                                        "tc_prep", "diag_inverse", "panel_global"};
   return (cls >= 0 && cls < HF_NPROF) ? names[cls] : "unknown";
 }
 

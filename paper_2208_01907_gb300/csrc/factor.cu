@@ -1495,6 +1495,7 @@ int run_levels(hf_ctx* c) {
   const int rows_cap = pr ? std::max(1, std::atoi(pr)) : 0;
   c->path_cluster = 0;
   c->path_global = 0;
+  c->lev_panel_global.assign(c->m + 1, 0);
   for (int lev = c->m; lev >= 0; --lev) {
     const int t0 = c->level_start[lev], cnt = c->level_count[lev];
     int maxn = 0, maxld = 0;
@@ -1555,6 +1556,7 @@ int run_levels(hf_ctx* c) {
     const bool use_gl = !use_cl || maxld > cap;
     if (use_cl) c->path_cluster = std::max(c->path_cluster, C);
     if (use_gl) c->path_global++;
+    c->lev_panel_global[lev] = use_cl ? 0 : 1;       // fronts of a mixed level: counted as cluster
     const int nbl = use_cl ? nbc : nb;
     const int npan = (maxn + nbl - 1) / nbl;
     const size_t smem = (size_t)nbl * sizeof(T) + (size_t)maxn * (sizeof(T) + sizeof(int));
@@ -1593,7 +1595,7 @@ int run_levels(hf_ctx* c) {
                                                                    (int32_t*)c->d_pos0.p, nbl, c->tau, tau_null, C, Rcap,
                                                                    swl, swc)));
       if (use_gl)
-        HF_LAUNCH(c, HF_PROF_PANEL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag,
+        HF_LAUNCH(c, HF_PROF_PANEL_GLOBAL, k_panel<T><<<cnt, pthreads, smem, s>>>(nd, st, t0, arena, rowid, gmag,
                                                                            (int32_t*)c->d_pos0.p, nbl, c->tau, tau_null, cap));
       if (tc_level) {
         uint4* parts = (uint4*)c->d_tparts.p;
@@ -1659,16 +1661,21 @@ static void trailing_work(hf_ctx* c, size_t esz) {
   // panels: column k of a panel costs 2 (f - k) (k - k0) for the left-looking products plus
   // 3 (f - k) for the division, diagonal and magnitude updates; the panel block is read and
   // written once
-  double pf = 0, pb = 0;
-  for (const NodeState& S : c->state_host) {
+  // (to the class of the panel kernel that the front's level took)
+  for (size_t t = 0; t < c->state_host.size(); ++t) {
+    const NodeState& S = c->state_host[t];
+    const int lev = c->nodes[t].level;
+    const int cls = lev >= 0 && lev < (int)c->lev_panel_global.size() && c->lev_panel_global[lev]
+                        ? HF_PROF_PANEL_GLOBAL : HF_PROF_PANEL;
+    double pf = 0, pb = 0;
     for (double k = 0; k < S.k; k += 1) {
       const double kk = std::fmod(k, nb), rows = S.f - k;
       pf += 2.0 * rows * kk + 3.0 * rows;
       if (kk == 0) pb += 2.0 * rows * std::min(nb, (double)S.k - k) * esz;
     }
+    c->work_flops[cls] += pf;
+    c->work_bytes[cls] += pb;
   }
-  c->work_flops[HF_PROF_PANEL] += pf;
-  c->work_bytes[HF_PROF_PANEL] += pb;
 }
 
 }  // namespace

@@ -138,6 +138,7 @@ struct hf_ctx {
   int path_global = 0;               // levels that ran the global-memory panel
   int path_ldlt = 0;                 // S22 LDL^T kernel of the last hf_schur (hf_info.ldlt_kernel)
   int gcr_restarts = 0;              // block GCR runs restarted with native FP64 products (hf_info)
+  std::vector<char> lev_panel_global;  // per tree level: 1 when its panels took k_panel
 };
 
 // analyze.cpp

@@ -571,7 +571,9 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
         const int e = b - 1 == code ? code : df_ready_run(fl, gt, b, code, false, &s_e);
-        gemm_range((e + 1) * DF_R, min(ks, (b + 1) * DF_R));
+        // the run's blocks one by one from the top: the partial sums go into tot in
+        // descending block order whatever runs the blocks were published in (deterministic)
+        for (int bb = b; bb > e; --bb) gemm_range(bb * DF_R, min(ks, (bb + 1) * DF_R));
         b = e;
       }
     }

@@ -27,7 +27,7 @@ EXPORTED = (
     "hf_factorize_batched", "hf_schur_batched", "hf_solve_batched", "hf_get_kernel_basis",
     "hf_gram_fp64", "hf_update_fp64", "hf_k11_iterate", "hf_set_row_signs", "hf_set_spin_limit", "hf_free",
 )
-HF_NPROF = 17
+HF_NPROF = 18
 
 
 class hf_opts(C.Structure):
