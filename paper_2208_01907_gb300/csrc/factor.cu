@@ -717,7 +717,7 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
         Pr[kk] = lv;
         if (p < nact) dgl[l] -= lv * acc;
         Gl[l] += fabs(lv * acc);
-      } else if (p == k) {
+      } else if (p == k && p < p1) {                   // position k, if this CTA owns it
         P[(size_t)(k - p0) * ps + kk] = dk;
       }
     }
