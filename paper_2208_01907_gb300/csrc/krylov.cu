@@ -495,11 +495,14 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
 #pragma unroll
       for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; tot[i][j] = 0.f; }
     // acc += A(rows of the item, k in [k_lo, k_hi)) * V(k rows, tile columns); k_lo is a
-    // multiple of DF_R or the start of the ancestors' rows
-    auto gemm_range = [&](int k_lo, int k_hi) {
+    // multiple of DF_R or the start of the ancestors' rows.  The chunks of DF_K rows run
+    // upward, or downward with `down`; acc goes into tot at every boundary of DF_R rows, so
+    // tot sums the blocks in ascending (descending) order however the range was split
+    auto gemm_range = [&](int k_lo, int k_hi, bool down) {
       const int nch = (k_hi - k_lo + DF_K - 1) / DF_K;
+      auto kc_of = [&](int ch) { return k_lo + (down ? nch - 1 - ch : ch) * DF_K; };
       auto issue = [&](int ch) {
-        const int kc = k_lo + ch * DF_K, stg = ch % DF_ST;
+        const int kc = kc_of(ch), stg = ch % DF_ST;
 #pragma unroll
         for (int u = 0; u < APT; ++u) {
           const int e = tid + u * DF_TH;
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
         }
-        if (ch == nch - 1 || ((ch + 1) * DF_K) % DF_R == 0) {
+        if (ch == nch - 1 || (down ? (kc_of(ch) - k_lo) % DF_R == 0 : ((ch + 1) * DF_K) % DF_R == 0)) {
 #pragma unroll
           for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -562,18 +565,18 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
         if (!ok) break;
         // the last block the item reads ends the run (no flags to look at)
         const int e = b + 1 == bend ? bend : df_ready_run(fl, gt, b, bend, true, &s_e);
-        gemm_range(b * DF_R, min(ks, e * DF_R));
+        gemm_range(b * DF_R, min(ks, e * DF_R), false);
         b = e;
       }
     } else {
-      if (f > ks) gemm_range(ks, f);                      // solved rows of the ancestors
+      if (f > ks) gemm_range(ks, f, false);               // solved rows of the ancestors
       for (int b = nblk - 1; b > code && ok;) {
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
         const int e = b - 1 == code ? code : df_ready_run(fl, gt, b, code, false, &s_e);
-        // the run's blocks one by one from the top: the partial sums go into tot in
-        // descending block order whatever runs the blocks were published in (deterministic)
-        for (int bb = b; bb > e; --bb) gemm_range(bb * DF_R, min(ks, (bb + 1) * DF_R));
+        // the run downward: the partial sums go into tot in descending block order whatever
+        // runs the blocks were published in (deterministic)
+        gemm_range((e + 1) * DF_R, min(ks, (b + 1) * DF_R), true);
         b = e;
       }
     }
