@@ -1141,30 +1141,56 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
   __syncthreads();
   const uint32_t tmem = tslot;
   const int total = pre[cnt];
+  // a contiguous run of tiles per CTA: consecutive tiles of a row block share the A operand
+  // (the panel's rows i0..i0+127), which then stays in the stage instead of being copied again
   const int G = (int)gridDim.x;
-  const int ntile = total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
+  const int chunk = (total + G - 1) / G;
+  const int u0 = (int)blockIdx.x * chunk;
+  const int ntile = max(0, min(chunk, total - u0));
 
   if (warp == 0) {
     // ---- producer: bulk copies of the pre-split parts of tile it into stage it % 2, the 48
     // copies (3 parts x 8 k-groups for each operand) issued by the 32 lanes of the warp
     int issued = 0;
+    // where the parts of tile it come from: the front's parts, its leading dimension, the
+    // first rows of the A (i0) and B (j0) operands.  Found one tile ahead (the tile map's
+    // search and the front's fields are dependent loads), while the copies are in flight
+    struct TtSrc { const uint4* P; int64_t ld; int i0, j0, akey; };
+    int akey0 = -1, akey1 = -1;                                 // the A operand held by each stage
+    auto src_of = [&](int it) {
+      const TtTile tl = tt_tile(pre, cnt, u0 + it, Cfg::R);
+      const int t = t0 + tl.slot;
+      const int k1 = st[t].k;
+      TtSrc r;
+      r.akey = tl.slot * 65536 + tl.bi;
+      r.ld = nd[t].ld;
+      r.P = parts + nd[t].row_off * 48;
+      r.i0 = k1 + tl.bi * TT_M;
+      r.j0 = k1 + tl.bj * TN;
+      return r;
+    };
+    TtSrc nx = {};
+    if (ntile > 0) nx = src_of(0);
     for (int it = 0; it < ntile; ++it) {
       const int s = it & 1;
+      const TtSrc cu = nx;
       int ok = 1;
       if (it >= 2 && lane == 0) ok = tt_wait(tc::smem_u32(&bar_empty[s]), ((it >> 1) + 1) & 1, abort_w, flags) ? 1 : 0;
       if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      const TtTile tl = tt_tile(pre, cnt, (int)blockIdx.x + it * G, Cfg::R);
-      const int t = t0 + tl.slot;
-      const int k1 = st[t].k;
-      const int64_t ld = nd[t].ld;
-      const uint4* P = parts + nd[t].row_off * 48;
-      const int i0 = k1 + tl.bi * TT_M, j0 = k1 + tl.bj * TN;
+      const int64_t ld = cu.ld;
+      const uint4* P = cu.P;
+      const int i0 = cu.i0, j0 = cu.j0;
       const uint32_t bf = tc::smem_u32(&bar_full[s]);
       const uint32_t sa = tc::smem_u32(stages + s * Cfg::STAGE);
+      // the stage's A operand is that of the tile two before (the same stage): kept if it
+      // is this tile's too, only the B operand is copied
+      const bool copy_a = (s ? akey1 : akey0) != cu.akey;
+      if (s) akey1 = cu.akey; else akey0 = cu.akey;
       if (lane == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bf), "r"(Cfg::STAGE) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bf),
+                     "r"(copy_a ? Cfg::STAGE : 3 * Cfg::B_PART) : "memory");
       __syncwarp();
-      for (int e = lane; e < 48; e += 32) {
+      for (int e = lane + (copy_a ? 0 : 24); e < 48; e += 32) {
         const int op = e / 24, part = (e % 24) / 8, kg = e % 8;
         if (op == 0)
           bulk_g2s(sa + part * TT_PART + kg * (TT_M * 16), P + (int64_t)(part * 8 + kg) * ld + i0, TT_M * 16, bf);
@@ -1172,6 +1198,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
           bulk_g2s(sa + 3 * TT_PART + part * Cfg::B_PART + kg * (TN * 16),
                    P + (int64_t)((part + 3) * 8 + kg) * ld + j0, TN * 16, bf);
       }
+      if (it + 1 < ntile) nx = src_of(it + 1);
       issued = it + 1;
     }
     if (lane == 0 && *abort_w)                               // own copies still in flight
@@ -1215,7 +1242,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1) k_trailing_tc(const NodeDesc* _
     // qmax (columns q <= qmax are in the lower triangle of the front)
     struct EpiRow { float* F; int64_t ld; int i, j0, qmax; };
     auto row_of = [&](int it) {
-      const TtTile tl = tt_tile(pre, cnt, (int)blockIdx.x + it * G, Cfg::R);
+      const TtTile tl = tt_tile(pre, cnt, u0 + it, Cfg::R);
       const int t = t0 + tl.slot;
       const int k1 = st[t].k, f = st[t].f;
       EpiRow e;

@@ -561,6 +561,12 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     if (FWD) {
       const int bend = tri ? code : nblk;                 // blocks [0, bend) feed this item
       for (int b = 0; b < bend && ok;) {
+        {
+          // the factor block this item multiplies once block b is published, into L2 while
+          // it waits (columns 64b.. of rows r0..r0+nr: two 128-byte lines per column)
+          const int q = b * DF_R + (tid >> 1), rr = (tid & 1) * 32;
+          if (q < ks && rr < nr) asm volatile("prefetch.global.L2 [%0];" :: "l"(F + (r0 + rr) + (int64_t)q * ld));
+        }
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
         // the last block the item reads ends the run (no flags to look at)
@@ -571,6 +577,12 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     } else {
       if (f > ks) gemm_range(ks, f, false);               // solved rows of the ancestors
       for (int b = nblk - 1; b > code && ok;) {
+        {
+          // the factor block L(64b.., r0..)^T this item multiplies once block b is published
+          // (rows 64b.. of columns r0..r0+nr: two 128-byte lines per column)
+          const int rr = tid >> 1, q = b * DF_R + (tid & 1) * 32;
+          if (rr < nr && q < ks) asm volatile("prefetch.global.L2 [%0];" :: "l"(F + q + (int64_t)(r0 + rr) * ld));
+        }
         ok = df_wait(fl + (int64_t)b * gt, abort_word, &s_ok, spin);
         if (!ok) break;
         const int e = b - 1 == code ? code : df_ready_run(fl, gt, b, code, false, &s_e);
