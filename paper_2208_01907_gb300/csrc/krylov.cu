@@ -2449,13 +2449,17 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     if ((rc = ensure_hist(n + 1))) return rc;
     double* Pn = Pm(n + 1);
     double* Qn = Qm(n + 1);
+    // Q_{n+1} = K11 P_{n+1} (reading R14): by the recurrence of Sec. 3.4, Z + sum_q Q_q C_q,
+    // while its n+1 products of m x m blocks (on the tensor cores) cost less than one FP64
+    // SpMM, i.e. while (n+1) m <= 2 nnz / L; otherwise by the SpMM
+    const bool recur = (double)(n + 1) * m <= 2.0 * (double)c->nnz / (double)L;
     for (int q = 0; q <= n; ++q) {
       if ((rc = gram(c, L, m, m, Qm(q), Z, Gm, -1.0))) return rc;      // B_qn = -Q_q^T Z
       if ((rc = msolve(q, Gm, Cm))) return rc;
       if ((rc = block_update(Pm(q), Cm, Pn, q == 0 ? W : nullptr, 1.0))) return rc;
+      if (recur && (rc = block_update(Qm(q), Cm, Qn, q == 0 ? Z : nullptr, 1.0))) return rc;
     }
-    // Q_{n+1} = K11 P_{n+1}: one FP64 SpMM instead of the n+1 dense recurrence terms (reading R14)
-    spmm(c, m, Pn, Qn);
+    if (!recur) spmm(c, m, Pn, Qn);
     HF_CUDA_TRY(cudaGetLastError());
   }
   *iters = it;
