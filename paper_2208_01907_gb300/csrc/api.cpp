@@ -534,7 +534,7 @@ void hf_free(hf_ctx* c) {
                     &c->d_front, &c->d_flags, &c->d_lam2pos, &c->d_lam2, &c->d_vec, &c->d_x12,
                     &c->d_s22, &c->d_bk_lf, &c->d_bk_perm, &c->d_bk_blk, &c->d_bk_dval, &c->d_bk_null,
                     &c->d_work, &c->d_small, &c->d_ozslice, &c->d_gsmall, &c->d_k12, &c->d_solve, &c->d_gmag,
-                    &c->d_pos0, &c->d_invpos, &c->d_ozint, &c->d_tparts, &c->d_dinv, &c->d_bpart, &c->d_swlist,
+                    &c->d_pos0, &c->d_invpos, &c->d_ozint, &c->d_tparts, &c->d_dinv, &c->d_gmap, &c->d_bpart, &c->d_swlist,
                     &c->d_swcount, &c->d_swplan, &c->d_swsig, &c->d_rsign, &c->d_qrow};
   for (DevBuf* b : bufs) hf_release(*b);
   for (DevBuf& b : c->d_hist) hf_release(b);

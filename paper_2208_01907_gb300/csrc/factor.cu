@@ -1345,6 +1345,25 @@ __global__ void k_cbmap_post(const NodeDesc* __restrict__ nd, const NodeState* _
   }
 }
 
+// The contribution maps read the other way, for the gathers of the triangular sweeps:
+// gmap[slot][row of front p] = the contribution row a of p's child `slot` mapped to that row
+// (-1 where none), after the factorization's final maps and states.
+__global__ void k_gmap_build(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+                             const int32_t* __restrict__ cbmap, int32_t* __restrict__ gmap, int64_t rows) {
+  const int p = blockIdx.x;
+  const NodeDesc d = nd[p];
+  for (int slot = 0; slot < 2; ++slot) {
+    const int ch = slot == 0 ? d.child0 : d.child1;
+    if (ch < 0) continue;
+    const NodeDesc dc = nd[ch];
+    const int mc = st[ch].f - st[ch].k;
+    for (int a = threadIdx.x; a < mc; a += blockDim.x) {
+      const int tg = cbmap[dc.row_off + a];
+      if (tg >= 0) gmap[slot * rows + d.row_off + tg] = a;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Enlargement (Sec. 2.2, reading R13) and collection of Lambda_2
 // ---------------------------------------------------------------------------
@@ -1786,6 +1805,13 @@ int hf_factorize_impl(hf_ctx* c, const double* vals, double tau) {
     int64_t* counts = (int64_t*)((int*)c->d_flags.p + FLAG_COUNT);
     HF_LAUNCH(c, HF_PROF_LAMBDA, k_finalize<<<1, 256, 0, s>>>((const NodeDesc*)c->d_nodes.p, (NodeState*)c->d_state.p, c->n_nodes,
                                  c->opts.n_enlarge, (const int32_t*)c->d_rowid.p, (int32_t*)c->d_lam2.p, counts));
+    // the child contributions of every front row, read by the sweeps' gathers
+    if ((rc = hf_ensure(c->d_gmap, (size_t)c->row_elems * 2 * sizeof(int32_t) + 64))) return rc;
+    HF_CUDA_TRY(cudaMemsetAsync(c->d_gmap.p, 0xFF, (size_t)c->row_elems * 2 * sizeof(int32_t), s));
+    HF_LAUNCH(c, HF_PROF_LAMBDA, k_gmap_build<<<c->n_nodes + 1, 256, 0, s>>>((const NodeDesc*)c->d_nodes.p,
+                                                                            (const NodeState*)c->d_state.p,
+                                                                            (const int32_t*)c->d_cbmap.p,
+                                                                            (int32_t*)c->d_gmap.p, c->row_elems));
     HF_CUDA_TRY(cudaGetLastError());
     int hflags[FLAG_COUNT];
     int64_t hcounts[3];

@@ -99,6 +99,7 @@ struct hf_ctx {
   size_t vec_cap = 0;
   DevBuf d_swplan;                   // dataflow sweeps: work items (forward, backward), block bases
   DevBuf d_dinv;                     // dataflow sweeps: inverse of every 64 x 64 unit lower diagonal block
+  DevBuf d_gmap;                     // per front row and child slot: the child's contribution row mapped there, or -1
   std::vector<int> sw_fwd_start, sw_fwd_cnt, sw_bwd_start, sw_bwd_cnt;   // per level: item range
   int sw_blocks = 0;                 // 64-row diagonal blocks of all fronts
   // ---- split (host copy) ----

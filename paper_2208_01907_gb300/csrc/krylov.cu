@@ -35,38 +35,32 @@ constexpr int TS = 64;       // row tile / diagonal block of the triangular solv
 constexpr int TR = 64;       // right-hand-side tile
 constexpr int TKK = 16;      // k chunk of the GEMM updates
 
+// Start of a forward sweep level: row i of front t's vectors is its own right-hand side (or
+// 0), plus the contribution row of child 0 mapped to it, plus that of child 1, in that order
+// (one gather through the reverse maps gmap instead of a write and two scatter-adds)
 template <typename TV>
-__global__ void k_fwd_init(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
-                           const int32_t* __restrict__ rowid, TV* __restrict__ vec, const TV* __restrict__ B, int m,
-                           int vs) {
+__global__ void k_fwd_gather(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0,
+                             const int32_t* __restrict__ rowid, const int32_t* __restrict__ gmap, int64_t rows,
+                             TV* __restrict__ vec, const TV* __restrict__ B, int m, int vs) {
   const int t = t0 + blockIdx.y;
   const NodeDesc d = nd[t];
   const int f = st[t].f;
   const int nown = d.cand_all ? 0 : d.n;
   TV* V = vec + d.row_off * vs;
   const int32_t* rid = rowid + d.row_off;
+  const int32_t* g0 = gmap + d.row_off;
+  const int32_t* g1 = gmap + rows + d.row_off;
+  const TV* U0 = nullptr;
+  const TV* U1 = nullptr;
+  if (d.child0 >= 0) U0 = vec + (nd[d.child0].row_off + st[d.child0].k) * vs;
+  if (d.child1 >= 0) U1 = vec + (nd[d.child1].row_off + st[d.child1].k) * vs;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)f * m; e += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
-    V[(int64_t)i * vs + c] = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
-  }
-}
-
-template <typename TV>
-__global__ void k_fwd_child(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st, int t0, int slot,
-                            const int32_t* __restrict__ cbmap, TV* __restrict__ vec, int m, int vs) {
-  const int t = t0 + blockIdx.y;
-  const NodeDesc d = nd[t];
-  const int ch = slot == 0 ? d.child0 : d.child1;
-  if (ch < 0) return;
-  const NodeDesc dc = nd[ch];
-  const int kc = st[ch].k, mc = st[ch].f - kc;
-  const TV* U = vec + (dc.row_off + kc) * vs;
-  const int32_t* map = cbmap + dc.row_off;
-  TV* V = vec + d.row_off * vs;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)mc * m; e += (int64_t)gridDim.x * blockDim.x) {
-    int a = (int)(e / m), c = (int)(e - (int64_t)a * m);
-    int tg = map[a];
-    if (tg >= 0) V[(int64_t)tg * vs + c] += U[(int64_t)a * vs + c];
+    const int i = (int)(e / m), c = (int)(e - (int64_t)i * m);
+    TV v = (i < nown) ? B[(int64_t)rid[i] * m + c] : TV(0);
+    const int a0 = U0 ? g0[i] : -1, a1 = U1 ? g1[i] : -1;
+    if (a0 >= 0) v += U0[(int64_t)a0 * vs + c];
+    if (a1 >= 0) v += U1[(int64_t)a1 * vs + c];
+    V[(int64_t)i * vs + c] = v;
   }
 }
 
@@ -2081,12 +2075,10 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
     const LevelDims D = level_dims(c, lev);
     tm.begin();
     const unsigned ex = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxf * m / 1024), 512);
-    HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_init<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid, vec, Bin, m, vs));
-    if (D.maxcb > 0) {
-      const unsigned cx = (unsigned)std::min<int64_t>(std::max<int64_t>(1, (int64_t)D.maxcb * m / 1024), 512);
-      for (int slot = 0; slot < 2; ++slot)
-        HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_child<TV><<<dim3(cx, cnt), 256, 0, s>>>(nd, st, t0, slot, cbmap, vec, m, vs));
-    }
+    HF_LAUNCH(c, HF_PROF_SWEEP_IO, k_fwd_gather<TV><<<dim3(ex, cnt), 256, 0, s>>>(nd, st, t0, rowid,
+                                                                                (const int32_t*)c->d_gmap.p,
+                                                                                c->row_elems, vec, Bin, m, vs));
+    (void)cbmap;
     if constexpr (DF) if (use_df) {
       const int ni = c->sw_fwd_cnt[lev];
       if (ni > 0) {

@@ -278,6 +278,20 @@ def test_everything_postponed_grows_delay_capacity():
     assert O.backward_error(s.to_scipy(), out["x"], out["b"]) <= BWD_TOL
 
 
+def test_front_beyond_the_panel_kernels_reports_capacity():
+    """Every pivot postponed (tau = 2 fails every ratio test) on 28,900 unknowns: the Lambda_0
+    front holds them all, more rows than a panel kernel's shared memory can hold, and
+    hf_factorize says so (HF_ERR_CAPACITY) instead of running."""
+    import paper_2208_01907_gb300 as hf
+    s = diffusion2d(170, 170, n_islands=0, dirichlet_x=True)
+    H = hf.HybridFactor(s.L, s.rowptr, s.col, s.coords, delay_cap=32768)
+    with pytest.raises(hf.HFError) as e:
+        H.factorize(torch.tensor(s.val, device="cuda", dtype=torch.float64), 2.0)
+    assert e.value.code == hf.hf.HF_ERR_CAPACITY
+    H.free()
+    torch.cuda.empty_cache()
+
+
 def test_single_node_tree():
     s = diffusion2d(12, 10, n_islands=1, island=3, contrast=1e8, seed=5)
     out = run_gpu(s, tau=1e-2, nd_levels=1)
