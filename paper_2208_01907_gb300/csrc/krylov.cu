@@ -482,12 +482,21 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     }
     // blocked summation: acc holds the products of at most DF_R consecutive k, then is
     // added into tot (the error of a long FP32 dot product grows with its length; this
-    // keeps it at that of the per-block updates)
+    // keeps it at that of the per-block updates).  A triangle item starts tot at -v_R (its
+    // own rows of the right-hand side, which no other item of the launch writes), so that
+    // the load is made before the waits and not on the chain after the last one; the block
+    // then solves for -tot = v_R - (the blocks' products).
     float acc[8][4], tot[8][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+      const int r = ty * 8 + i;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { acc[i][j] = 0.f; tot[i][j] = 0.f; }
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + tx * 4 + j;
+        acc[i][j] = 0.f;
+        tot[i][j] = (tri && r < nr && c < m) ? -__ldcg(V + (int64_t)(r0 + r) * vs + c) : 0.f;
+      }
+    }
     // acc += A(rows of the item, k in [k_lo, k_hi)) * V(k rows, tile columns); k_lo is a
     // multiple of DF_R or the start of the ancestors' rows.  The chunks of DF_K rows run
     // upward, or downward with `down`; acc goes into tot at every boundary of DF_R rows, so
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int cc = tx * 4 + j, c = c0 + cc;
-        Vs[r][cc] = (r < nr && c < m) ? __ldcg(V + (int64_t)(r0 + r) * vs + c) - tot[i][j] : 0.f;
+        Vs[r][cc] = (r < nr && c < m) ? -tot[i][j] : 0.f;
       }
     }
     __syncthreads();
