@@ -625,28 +625,45 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     __syncthreads();
     // y = L_RR^-1 v (forward) or x = L_RR^-T v (backward) as one product with the staged
     // inverse, in place of the row-by-row substitution: the triangle ends the chain of the
-    // front's blocks, and a product has no dependency from row to row
+    // front's blocks, and a product has no dependency from row to row.  A thread's eight
+    // rows are four from the top (4ty..) and four from the bottom (60-4ty..), so that each
+    // warp does the same share of the triangle (row r takes q <= r forward, q >= r backward);
+    // the loop bounds are the warp's, and terms past a row's own bound multiply the stored
+    // zeros of the inverse.
     {
       float o[8][4];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) o[i][j] = 0.f;
-      const int qlo = FWD ? 0 : ty * 8, qhi = FWD ? min(nr, ty * 8 + 8) : nr;
-      for (int q = qlo; q < qhi; ++q) {
-        float a[8], b[4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = FWD ? Ls[ty * 8 + i][q] : Ls[q][ty * 8 + i];
+      const int w = tid >> 5;                            // rows 8w.. and 56-8w.. (ty = 2w, 2w+1)
+      auto term = [&](int q, bool top, bool bot) {
+        float b[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) b[j] = Vs[q][tx * 4 + j];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+          if (i < 4 ? !top : !bot) continue;
+          const int r = i < 4 ? ty * 4 + i : 60 - ty * 4 + (i - 4);
+          const float a = FWD ? Ls[r][q] : Ls[q][r];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) o[i][j] += a[i] * b[j];
+          for (int j = 0; j < 4; ++j) o[i][j] += a * b[j];
+        }
+      };
+      if (FWD) {
+        const int qa = min(nr, 8 * w + 8), qb = min(nr, TS - 8 * w);
+        int q = 0;
+        for (; q < qa; ++q) term(q, true, true);
+        for (; q < qb; ++q) term(q, false, true);
+      } else {
+        const int qa = min(nr, TS - 8 - 8 * w);
+        int q = 8 * w;
+        for (; q < qa; ++q) term(q, true, false);
+        for (; q < nr; ++q) term(q, true, true);
       }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int r = ty * 8 + i;
+        const int r = i < 4 ? ty * 4 + i : 60 - ty * 4 + (i - 4);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int c = c0 + tx * 4 + j;
