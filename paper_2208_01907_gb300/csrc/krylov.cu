@@ -430,7 +430,14 @@ __device__ __forceinline__ void df_cp16(void* dst, const void* src, bool pred) {
 __device__ __forceinline__ void df_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void df_wait_copies() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
-constexpr int DF_ST = 3;       // cp.async pipeline stages
+constexpr int DF_ST = 4;       // cp.async pipeline stages (three chunks in flight)
+// shared memory of a sweep CTA (dynamic: above the 48 KB of static shared memory): the GEMM
+// stages, which the block being solved reuses, then the staged diagonal-block inverse
+struct DfGemm { float A[DF_ST][DF_K][DF_R + 4]; float B[DF_ST][DF_K][DF_C + 4]; };
+constexpr size_t DF_UB = sizeof(DfGemm) > sizeof(float) * DF_R * (DF_C + 1) ? sizeof(DfGemm)
+                                                                              : sizeof(float) * DF_R * (DF_C + 1);
+constexpr size_t DF_SMEM = DF_UB + sizeof(float) * TS * (TS + 1);
+static_assert(DF_UB % 16 == 0, "the inverse follows the stages 16-byte aligned");
 
 // vs: row stride of the per-front vectors (m rounded up to 4, so that rows are 16-byte aligned)
 template <bool FWD>
@@ -441,14 +448,12 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
                                                    int* abort_word, int spin, const float* __restrict__ dinv) {
   constexpr int APT = DF_K * DF_R / DF_TH;       // 4-byte A copies per thread per chunk
   constexpr int BPT = DF_K * DF_C / 4 / DF_TH;   // 16-byte B copies per thread per chunk
-  struct Gemm { float A[DF_ST][DF_K][DF_R + 4]; float B[DF_ST][DF_K][DF_C + 4]; };
   constexpr int VS = DF_C + 1;
-  constexpr size_t UB = sizeof(Gemm) > sizeof(float) * DF_R * VS ? sizeof(Gemm) : sizeof(float) * DF_R * VS;
-  __shared__ __align__(16) unsigned char ubuf[UB];     // GEMM stages, then the block being solved
-  __shared__ float Ls[TS][TS + 1];
+  extern __shared__ __align__(16) unsigned char dsm[];  // DF_SMEM bytes
   __shared__ int s_ticket, s_ok, s_e;
-  Gemm& G = *reinterpret_cast<Gemm*>(ubuf);
-  float (*Vs)[VS] = reinterpret_cast<float (*)[VS]>(ubuf);
+  DfGemm& G = *reinterpret_cast<DfGemm*>(dsm);          // GEMM stages, then the block being solved
+  float (*Vs)[VS] = reinterpret_cast<float (*)[VS]>(dsm);
+  float (*Ls)[TS + 1] = reinterpret_cast<float (*)[TS + 1]>(dsm + DF_UB);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t total = (int64_t)nitems * gt;
@@ -2012,8 +2017,11 @@ static int sweep_grid(bool fwd) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sweep_df<false>, DF_TH, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sweep_df<true>, DF_TH, 0);
+    // errors show at the launch (cudaGetLastError after it)
+    cudaFuncSetAttribute(k_sweep_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DF_SMEM);
+    cudaFuncSetAttribute(k_sweep_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DF_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], k_sweep_df<false>, DF_TH, DF_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], k_sweep_df<true>, DF_TH, DF_SMEM);
     sms = std::max(sms, 1);
   }
   return sms * std::max(1, per[fwd ? 1 : 0]);
@@ -2109,7 +2117,7 @@ static void fwd_sweep(hf_ctx* c, int m, const TV* Bin, TV* Ytmp, TV* vec) {
       const int ni = c->sw_fwd_cnt[lev];
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(true));
-        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_fwd_start[lev], ni,
+        HF_LAUNCH(c, HF_PROF_TRSV_FWD, k_sweep_df<true><<<g, DF_TH, DF_SMEM, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_fwd_start[lev], ni,
                                                                           bbase, flags, sync + lev, sweep_err(c), sweep_spin(c),
                                                                           (const float*)c->d_dinv.p));
       }
@@ -2160,7 +2168,7 @@ static void bwd_sweep(hf_ctx* c, int m, const TV* Ytmp, TV* Xout, TV* vec) {
       const int ni = c->sw_bwd_cnt[lev];
       if (ni > 0) {
         const int g = (int)std::min<int64_t>((int64_t)ni * gt, sweep_grid(false));
-        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, 0, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_bwd_start[lev], ni,
+        HF_LAUNCH(c, HF_PROF_TRSV_BWD, k_sweep_df<false><<<g, DF_TH, DF_SMEM, s>>>(nd, st, arena, vec, m, vs, (int)gt, items + c->sw_bwd_start[lev], ni,
                                                                            bbase, flags, sync + lev, sweep_err(c), sweep_spin(c),
                                                                           (const float*)c->d_dinv.p));
       }
