@@ -487,10 +487,10 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
     }
     // blocked summation: acc holds the products of at most DF_R consecutive k, then is
     // added into tot (the error of a long FP32 dot product grows with its length; this
-    // keeps it at that of the per-block updates).  A triangle item starts tot at -v_R (its
-    // own rows of the right-hand side, which no other item of the launch writes), so that
-    // the load is made before the waits and not on the chain after the last one; the block
-    // then solves for -tot = v_R - (the blocks' products).
+    // keeps it at that of the per-block updates).  An item starts tot at -v (its own rows of
+    // the vectors, which no other item of the launch writes), so that the loads are made
+    // before the waits, all at once, and not after the last one: a triangle item then solves
+    // for -tot = v_R - (the blocks' products), a contribution item stores -tot.
     float acc[8][4], tot[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
       for (int j = 0; j < 4; ++j) {
         const int c = c0 + tx * 4 + j;
         acc[i][j] = 0.f;
-        tot[i][j] = (tri && r < nr && c < m) ? -__ldcg(V + (int64_t)(r0 + r) * vs + c) : 0.f;
+        tot[i][j] = (r < nr && c < m) ? -__ldcg(V + (int64_t)(r0 + r) * vs + c) : 0.f;
       }
     }
     // acc += A(rows of the item, k in [k_lo, k_hi)) * V(k rows, tile columns); k_lo is a
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
       }
     }
     if (!ok) return;                                      // uniform: s_ok after a barrier
-    if (!tri) {                                           // contribution rows: v -= tot
+    if (!tri) {                                           // contribution rows: v - the products
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = ty * 8 + i;
@@ -609,10 +609,7 @@ __global__ void __launch_bounds__(DF_TH, 4) k_sweep_df(const NodeDesc* __restric
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int c = c0 + tx * 4 + j;
-          if (c < m) {
-            float* p = V + (int64_t)(r0 + r) * vs + c;
-            *p = __ldcg(p) - tot[i][j];
-          }
+          if (c < m) V[(int64_t)(r0 + r) * vs + c] = -tot[i][j];
         }
       }
       __syncthreads();
