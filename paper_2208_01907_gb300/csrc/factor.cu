@@ -150,13 +150,30 @@ __global__ void k_extend_add(const NodeDesc* __restrict__ nd, const NodeState* _
   const T* CB = arena + dc.front_off + kc + (int64_t)kc * dc.ld;
   const int32_t* map = cbmap + dc.row_off;
   T* F = arena + d.front_off;
+  // four entries of a column per pass, all loads before the stores: the map is one to one,
+  // so the four targets are distinct and the loads need not wait for the stores before them
+  constexpr int U = 4;
   for (int a = blockIdx.x; a < m; a += gridDim.x) {
-    int ta = map[a];
-    for (int b = a + threadIdx.x; b < m; b += blockDim.x) {
-      int tb = map[b];
-      if (ta < 0 || tb < 0) continue;
-      int r = max(ta, tb), cc = min(ta, tb);
-      F[r + (int64_t)cc * d.ld] += CB[b + (int64_t)a * dc.ld];
+    const int ta = map[a];
+    if (ta < 0) continue;
+    const T* cba = CB + (int64_t)a * dc.ld;
+    for (int b0 = a + threadIdx.x; b0 < m; b0 += U * blockDim.x) {
+      T v[U], o[U];
+      int64_t pos[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int b = b0 + u * blockDim.x;
+        const int tb = b < m ? map[b] : -1;
+        pos[u] = -1;
+        if (tb >= 0) {
+          pos[u] = max(ta, tb) + (int64_t)min(ta, tb) * d.ld;
+          v[u] = cba[b];
+          o[u] = F[pos[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (pos[u] >= 0) F[pos[u]] = o[u] + v[u];
     }
   }
 }
