@@ -789,11 +789,15 @@ k_panel_cl(const NodeDesc* __restrict__ nd, NodeState* __restrict__ st, int t0, 
 constexpr size_t SW_SMEM = 200 * 1024;   // fronts of up to 25,600 rows
 // sig layout per front (stride sf): groups g = 0.. (last panel first), each sg ints:
 // [tag k0, sigma[0 .. f)]
-__global__ void __launch_bounds__(256) k_swap_sigma(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
+constexpr int SW_THREADS = 1024;
+constexpr int SW_WIN = 256;              // list entries staged in shared memory at a time
+__global__ void __launch_bounds__(SW_THREADS) k_swap_sigma(const NodeDesc* __restrict__ nd, const NodeState* __restrict__ st,
                                                     int t0, const int4* __restrict__ swlist,
                                                     const int* __restrict__ swcount, int* __restrict__ sig, int64_t sf,
                                                     int sg, int gcap, int* __restrict__ ngrp) {
   extern __shared__ int sw_smem[];
+  __shared__ int2 lst[SW_WIN];
+  __shared__ int s_cut;
   const int t = t0 + blockIdx.x;
   const int n = swcount[t];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -809,22 +813,50 @@ __global__ void __launch_bounds__(256) k_swap_sigma(const NodeDesc* __restrict__
   int g = 0;
   int i = n - 1;
   while (i >= 0 && g < gcap) {
+    // entries [j, i]: one panel (the run of entry i's tag), found a window at a time: the
+    // last entry before i with another tag ends the run
     const int tag = list[i].z;
     int j = i;
-    while (j > 0 && list[j - 1].z == tag) --j;         // entries [j, i]: one panel, in order
-    if (tid == 0)
-      for (int e = j; e <= i; ++e) {
-        const int a = list[e].x, b = list[e].y;
-        const int x = img[a]; img[a] = img[b]; img[b] = x;
+    for (;;) {
+      const int lo = max(0, j - SW_WIN);
+      if (tid == 0) s_cut = -1;
+      __syncthreads();
+      for (int e = lo + tid; e < j; e += nt)
+        if (list[e].z != tag) atomicMax(&s_cut, e);
+      __syncthreads();
+      const int cut = s_cut;
+      __syncthreads();
+      if (cut >= 0) { j = cut + 1; break; }
+      j = lo;
+      if (lo == 0) break;
+    }
+    // the panel's interchanges, in order, on img: staged into shared memory, applied by one
+    // thread (each may touch the rows of the ones before it)
+    for (int e0 = j; e0 <= i; e0 += SW_WIN) {
+      const int ne = min(SW_WIN, i - e0 + 1);
+      for (int e = tid; e < ne; e += nt) {
+        const int4 v = list[e0 + e];
+        lst[e] = make_int2(v.x, v.y);
       }
-    __syncthreads();
+      __syncthreads();
+      if (tid == 0)
+        for (int e = 0; e < ne; ++e) {
+          const int a = lst[e].x, b = lst[e].y;
+          const int x = img[a]; img[a] = img[b]; img[b] = x;
+        }
+      __syncthreads();
+    }
     for (int p = tid; p < f; p += nt) sigma[p] = img[sigma[p]];
     __syncthreads();
     int* og = out + (int64_t)g * sg;
     if (tid == 0) og[0] = tag;
     for (int p = tid; p < f; p += nt) og[1 + p] = sigma[p];
-    if (tid == 0)
-      for (int e = j; e <= i; ++e) { img[list[e].x] = list[e].x; img[list[e].y] = list[e].y; }
+    // img back to the identity on the rows the panel touched (same values from any thread)
+    for (int e = j + tid; e <= i; e += nt) {
+      const int4 v = list[e];
+      img[v.x] = v.x;
+      img[v.y] = v.y;
+    }
     __syncthreads();
     ++g;
     i = j - 1;
@@ -1688,7 +1720,7 @@ int run_levels(hf_ctx* c) {
       if ((rc2 = hf_ensure(c->d_swsig, (size_t)cnt * sf * sizeof(int) + ((size_t)cnt + 1) * sizeof(int) + 64))) return rc2;
       int* sig = (int*)c->d_swsig.p;
       int* ngrp = sig + (size_t)cnt * sf;
-      HF_LAUNCH(c, HF_PROF_PANEL_SWAP, k_swap_sigma<<<cnt, 256, (size_t)2 * maxld * sizeof(int), s>>>(
+      HF_LAUNCH(c, HF_PROF_PANEL_SWAP, k_swap_sigma<<<cnt, SW_THREADS, (size_t)2 * maxld * sizeof(int), s>>>(
                                       nd, st, t0, (const int4*)swl, swc, sig, sf, sg, gcap, ngrp));
       HF_LAUNCH(c, HF_PROF_PANEL_SWAP, k_swap_apply<T><<<dim3((unsigned)maxld, (unsigned)cnt), 256, (size_t)maxld * sizeof(T), s>>>(
                                       nd, st, t0, arena, sig, sf, sg, ngrp));
