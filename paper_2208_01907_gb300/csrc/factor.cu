@@ -877,8 +877,15 @@ __global__ void __launch_bounds__(256) k_swap_apply(const NodeDesc* __restrict__
   const int k = st[t].k, f = st[t].f;
   if (c >= k) return;
   const int* base = sig + (int64_t)blockIdx.y * sf;
-  int m = 0;                                           // panels with tag > c (tags decrease with g)
-  while (m < ng && base[(int64_t)m * sg] > c) ++m;
+  // m = the panels with tag > c; the tags decrease with g, so m is one past the last such g
+  // (all tags read at once, not one after another)
+  __shared__ int s_m;
+  if (threadIdx.x == 0) s_m = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < ng; g += blockDim.x)
+    if (base[(int64_t)g * sg] > c) atomicMax(&s_m, g + 1);
+  __syncthreads();
+  const int m = s_m;
   if (m == 0) return;
   const int* sigma = base + (int64_t)(m - 1) * sg + 1;
   const NodeDesc d = nd[t];
@@ -1605,7 +1612,7 @@ int run_levels(hf_ctx* c) {
     }
     HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_prep<<<(cnt + 127) / 128, 128, 0, s>>>(nd, st, t0, cnt, flags));
     if (has_children)
-      HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_maps<<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_smap.p, (int32_t*)c->d_cbmap.p));
+      HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_maps<<<cnt, 1024, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_smap.p, (int32_t*)c->d_cbmap.p));
     {
       int bx = std::min(std::max(1, maxld), 512);
       HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_front_zero<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, st, t0, arena));
@@ -1620,7 +1627,7 @@ int run_levels(hf_ctx* c) {
       for (int slot = 0; slot < 2; ++slot)
         HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_extend_add<T><<<dim3(bx, cnt), 128, 0, s>>>(nd, st, t0, slot, (const int32_t*)c->d_cbmap.p, arena));
     }
-    HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_g_assemble<T><<<cnt, 256, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_cbmap.p,
+    HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_g_assemble<T><<<cnt, 1024, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_cbmap.p,
                                         (const int64_t*)c->d_diagpos.p, (const double*)c->d_kval.p, gmag,
                                         (int32_t*)c->d_pos0.p));
     // panel in distributed shared memory for the fronts a cluster of <= cmax CTAs can hold;

@@ -826,14 +826,32 @@ __global__ void k_gram_partial(int64_t L, int ma, int mb, const double* __restri
 
 // Column sums of squares of a row-major L x m block: per row-chunk partials (pass 1),
 // then a fixed-order reduction (pass 2), so the result does not depend on scheduling.
-__global__ void k_colsq_partial(int64_t L, int m, const double* __restrict__ A, double* __restrict__ part) {
-  const int j = blockIdx.y * blockDim.x + threadIdx.x;
-  if (j >= m) return;
+// Column sums of squares of a row-major L x m block over one chunk of rows per block: the
+// CSQ_TH threads cover a window of w = min(m, CSQ_TH) columns on CSQ_TH / w rows at a time
+// (consecutive threads read consecutive entries, and many rows are in flight); the row
+// lanes' partial sums are added in lane order (deterministic).
+constexpr int CSQ_TH = 512;
+__global__ void __launch_bounds__(CSQ_TH) k_colsq_partial(int64_t L, int m, const double* __restrict__ A,
+                                                         double* __restrict__ part) {
+  __shared__ double sp[CSQ_TH];
+  const int w = min(m, CSQ_TH), rpi = CSQ_TH / w;
+  const int tid = threadIdx.x, jr = tid / w, jc = tid % w;
   const int64_t rows = (L + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows, r1 = min(L, r0 + rows);
-  double s = 0.0;
-  for (int64_t r = r0; r < r1; ++r) { const double v = A[r * m + j]; s += v * v; }
-  part[(int64_t)blockIdx.x * m + j] = s;
+  for (int c0 = 0; c0 < m; c0 += w) {
+    const int j = c0 + jc;
+    double s = 0.0;
+    if (jr < rpi && j < m)
+      for (int64_t r = r0 + jr; r < r1; r += rpi) { const double v = A[r * m + j]; s += v * v; }
+    sp[tid] = s;
+    __syncthreads();
+    if (tid < w && c0 + tid < m) {
+      double t = 0.0;
+      for (int q = 0; q < rpi; ++q) t += sp[q * w + tid];
+      part[(int64_t)blockIdx.x * m + c0 + tid] = t;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void k_colsq_reduce(int m, int nchunks, const double* __restrict__ part, double* __restrict__ out) {
@@ -2382,7 +2400,7 @@ static int block_gcr(hf_ctx* c, int m, const double* B, double* X, int* iters, d
     int r = hf_ensure(c->d_small, std::max((size_t)ncs * m * 8 + 64, (size_t)(1 << 20)));
     if (r) return r;
     double* part = (double*)c->d_small.p;
-    HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_partial<<<dim3(ncs, (m + 127) / 128), 128, 0, s>>>(L, m, A, part));
+    HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_partial<<<ncs, CSQ_TH, 0, s>>>(L, m, A, part));
     HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_reduce<<<(m + 127) / 128, 128, 0, s>>>(m, ncs, part, diag));
     HF_CUDA_TRY(cudaGetLastError());
     std::vector<double> g(m);
@@ -2828,7 +2846,7 @@ static int max_col_ratio(hf_ctx* c, int m, const double* A, const std::vector<do
   if ((rc = hf_ensure(c->d_small, std::max(((size_t)ncs + 1) * m * 8 + 64, (size_t)(1 << 20))))) return rc;
   double* part = (double*)c->d_small.p;
   double* sq = part + (size_t)ncs * m;
-  HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_partial<<<dim3(ncs, (m + 127) / 128), 128, 0, s>>>(L, m, A, part));
+  HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_partial<<<ncs, CSQ_TH, 0, s>>>(L, m, A, part));
   HF_LAUNCH(c, HF_PROF_VECTOR, k_colsq_reduce<<<(m + 127) / 128, 128, 0, s>>>(m, ncs, part, sq));
   std::vector<double> g(m);
   HF_CUDA_TRY(cudaMemcpyAsync(g.data(), sq, (size_t)m * 8, cudaMemcpyDeviceToHost, s));

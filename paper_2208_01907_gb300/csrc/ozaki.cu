@@ -170,19 +170,31 @@ __global__ void k_oz_exp(const double* __restrict__ X, int64_t si, int64_t sk, i
   }
 }
 
-// Max-magnitude exponents of the n rows of a row-major n x K block: one warp per row,
-// eight rows per block at a time.
+// Max-magnitude exponents of the n rows of a row-major n x K block: a warp takes four
+// consecutive rows at a time, their loads all issued before the four reductions.
 __global__ void __launch_bounds__(256) k_oz_exp_rows(const double* __restrict__ X, int64_t n, int K, int* __restrict__ e) {
+  constexpr int RPW = 4;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
-    double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[i * K + k]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) {
+  for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW; i0 < n; i0 += nw * RPW) {
+    double mx[RPW];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) mx[r] = 0.0;
+    for (int k = lane; k < K; k += 32)
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+        if (i0 + r < n) mx[r] = fmax(mx[r], fabs(X[(i0 + r) * K + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) mx[r] = fmax(mx[r], __shfl_xor_sync(0xffffffffu, mx[r], o));
+    double v = mx[0];
+#pragma unroll
+    for (int r = 1; r < RPW; ++r) if (lane == r) v = mx[r];
+    if (lane < RPW && i0 + lane < n) {
       int ex = -1060;
-      if (mx > 0) frexp(mx, &ex);
-      e[i] = ex;
+      if (v > 0) frexp(v, &ex);
+      e[i0 + lane] = ex;
     }
   }
 }
