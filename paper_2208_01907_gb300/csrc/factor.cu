@@ -1613,17 +1613,21 @@ int run_levels(hf_ctx* c) {
     HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_prep<<<(cnt + 127) / 128, 128, 0, s>>>(nd, st, t0, cnt, flags));
     if (has_children)
       HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_level_maps<<<cnt, 1024, 0, s>>>(nd, st, t0, rowid, (const int32_t*)c->d_smap.p, (int32_t*)c->d_cbmap.p));
+    // blocks per front: enough for the largest front, but about 4,864 in all for a level of
+    // many fronts (the kernels loop over columns or entries, so fewer blocks each do more;
+    // a level of 1,024 fronts with one block per column made 400k blocks of a few stores)
+    const int per_front = std::max(1, 4864 / cnt);
     {
-      int bx = std::min(std::max(1, maxld), 512);
+      int bx = std::min({std::max(1, maxld), 512, per_front});
       HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_front_zero<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, st, t0, arena));
     }
     if (maxasm > 0) {
-      int bx = (int)std::min<int64_t>((maxasm + 255) / 256, 1024);
+      int bx = (int)std::min<int64_t>(std::min<int64_t>((maxasm + 255) / 256, 1024), per_front);
       HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_front_asm<T><<<dim3(bx, cnt), 256, 0, s>>>(nd, t0, (const AsmEntry*)c->d_asm.p,
                                                    (const double*)c->d_kval.p, arena));
     }
     if (has_children) {
-      int bx = std::min(std::max(1, maxld), 1024);
+      int bx = std::min({std::max(1, maxld), 1024, 2 * per_front});     // 128-thread blocks
       for (int slot = 0; slot < 2; ++slot)
         HF_LAUNCH(c, HF_PROF_ASSEMBLE, k_extend_add<T><<<dim3(bx, cnt), 128, 0, s>>>(nd, st, t0, slot, (const int32_t*)c->d_cbmap.p, arena));
     }
