@@ -1705,7 +1705,7 @@ int run_levels(hf_ctx* c) {
                                                                            (int32_t*)c->d_pos0.p, nbl, c->tau, tau_null, cap));
       if (tc_level) {
         uint4* parts = (uint4*)c->d_tparts.p;
-        HF_LAUNCH(c, HF_PROF_TC_PREP, k_trailing_split<<<dim3((unsigned)std::min(1024, (maxld + 31) / 32), cnt), 256, 0, s>>>(
+        HF_LAUNCH(c, HF_PROF_TC_PREP, k_trailing_split<<<dim3((unsigned)std::min({1024, (maxld + 31) / 32, std::max(1, 4864 / cnt)}), cnt), 256, 0, s>>>(
                                            nd, st, t0, (const float*)arena, parts));
         float* fa = (float*)arena;
         switch (tc_form) {

@@ -437,16 +437,22 @@ k_oz_mma(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtenso
   }
 }
 
-__global__ void k_oz_reduce(int Mi, int Nj, int nch, const double* __restrict__ part, double* __restrict__ G,
-                            double scale, int sym) {
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Mi * Nj) return;
-  int i = e / Nj, j = e % Nj;
+// One warp per entry of G: lane l adds the chunks l, l + 32, ... in order, then the lanes'
+// sums are added by a butterfly (every lane ends with the same value; a fixed order, so the
+// result is the same from run to run)
+__global__ void __launch_bounds__(256) k_oz_reduce(int Mi, int Nj, int nch, const double* __restrict__ part,
+                                                   double* __restrict__ G, double scale, int sym) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= (int64_t)Mi * Nj) return;                       // uniform per warp
+  const int i = (int)(e / Nj), j = (int)(e % Nj);
   // A^T A: only the upper triangle was computed; the lower one mirrors it (exactly symmetric)
   const int a = (sym && i > j) ? j : i, b = (sym && i > j) ? i : j;
   double s = 0.0;
-  for (int c = 0; c < nch; ++c) s += part[((int64_t)c * Mi + a) * Nj + b];
-  G[e] = scale * s;
+  for (int c = lane; c < nch; c += 32) s += part[((int64_t)c * Mi + a) * Nj + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) G[e] = scale * s;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -556,7 +562,7 @@ int hf_oz_gram(hf_ctx* c, int64_t L, int ma, int mb, const double* A, const doub
   a.upper = same ? 1 : 0;
   dim3 grid((mb + OZ_BJ - 1) / OZ_BJ, (ma + OZ_BI - 1) / OZ_BI, (unsigned)nch);
   HF_LAUNCH(c, HF_PROF_GRAM, k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, a));
-  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_reduce<<<(ma * mb + 255) / 256, 256, 0, s>>>(ma, mb, (int)nch, scratch, G, scale,
+  HF_LAUNCH(c, HF_PROF_TC_PREP, k_oz_reduce<<<(unsigned)(((int64_t)ma * mb * 32 + 255) / 256), 256, 0, s>>>(ma, mb, (int)nch, scratch, G, scale,
                                                                                same ? 1 : 0));
   HF_CUDA_TRY(cudaGetLastError());
   return HF_OK;
